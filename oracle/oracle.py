@@ -1,0 +1,246 @@
+"""FP64 CPU oracle -- TEST INFRASTRUCTURE ONLY.
+
+Only tests/, __graft_entry__.smoke() and bench.py's cpu_baseline leg may
+import this module.  It shares no code with the CUDA path (the product
+package never imports it).  Everything runs in float64 on the host.
+
+Contents, each citing the paper passage it follows:
+  cells()         generalized Laguerre cells: volume, free-surface area,
+                  restricted facet areas, centroid (Eq. 1, Sec. 3.2-3.4,
+                  Algorithm 2) -- computed by oracle/lgc_oracle.c.
+  hessian_dense() the Hessian of Eq. 2 as M = -grad^2 K (sign flipped so that
+                  M is symmetric positive definite), dense.
+  newton()        Algorithm 1: damped Newton with KMT steps, dense direct solve.
+  fluid_step()    Gallouet-Merigot explicit step of Sec. 5 (pressure spring,
+                  gravity, symplectic update), no viscosity/surface tension.
+  mlp_*()         FP64 reference of the learned warm-start MLP (not in the
+                  paper): forward, backward, Adam, on BF16-rounded operands.
+
+Parity pins: tests/test_oracle_geometry.py, tests/test_oracle_newton.py,
+tests/test_oracle_mlp.py (closed forms, Monte Carlo, finite differences,
+invariants).  Functions without such a pin say "parity unpinned" below.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lgc_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+STATUS_OK = 0
+STATUS_TOO_MANY_FACETS = 1
+STATUS_COINCIDENT = 2
+
+
+def build(force: bool = False) -> str:
+    """Compile lgc_oracle.c (gcc -O2 -fopenmp, no fast-math) into liboracle.so."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-D_DEFAULT_SOURCE",
+               "-o", _LIB, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        P = ctypes.c_void_p
+        lib.oracle_cells.restype = ctypes.c_int
+        lib.oracle_cells.argtypes = [ctypes.c_int64, P, P, P, P, ctypes.c_int64, P, ctypes.c_int,
+                                     ctypes.c_int] + [P] * 13 + [ctypes.c_int]
+        lib.oracle_max_threads.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def max_threads() -> int:
+    return int(_load().oracle_max_threads())
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def cells(pos, psi, query=None, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), brute=False,
+          max_facets=128, nthreads=0):
+    """Generalized Laguerre cells of the sites `query` (default: all).
+
+    pos (n,3), psi (n,) are widened to float64 exactly.  Returns a dict:
+      vol, karea (free-surface |K_i|), omega_sum, inside, n_planes, cen (q,3),
+      status, wall_area (q,6), nfac, fac_j, fac_area, fac_dist, fac_h (q,max_facets)
+    fac_* list every bisector plane that cuts the ball (area may be 0).
+    """
+    lib = _load()
+    pos = np.ascontiguousarray(np.asarray(pos, dtype=np.float64).reshape(-1, 3))
+    psi = np.ascontiguousarray(np.asarray(psi, dtype=np.float64).reshape(-1))
+    n = pos.shape[0]
+    if query is None:
+        query = np.arange(n, dtype=np.int64)
+    query = np.ascontiguousarray(np.asarray(query, dtype=np.int64))
+    q = query.shape[0]
+    lo = np.ascontiguousarray(np.asarray(lo, np.float64))
+    hi = np.ascontiguousarray(np.asarray(hi, np.float64))
+    out = {
+        "vol": np.zeros(q), "karea": np.zeros(q), "omega_sum": np.zeros(q),
+        "inside": np.zeros(q, np.int32), "n_planes": np.zeros(q, np.int32),
+        "cen": np.zeros((q, 3)), "status": np.zeros(q, np.int32), "wall_area": np.zeros((q, 6)),
+        "nfac": np.zeros(q, np.int32), "fac_j": np.full((q, max_facets), -1, np.int64),
+        "fac_area": np.zeros((q, max_facets)), "fac_dist": np.zeros((q, max_facets)),
+        "fac_h": np.zeros((q, max_facets)),
+    }
+    lib.oracle_cells(n, _p(pos), _p(psi), _p(lo), _p(hi), q, _p(query), int(brute), int(max_facets),
+                     _p(out["vol"]), _p(out["karea"]), _p(out["omega_sum"]), _p(out["inside"]),
+                     _p(out["n_planes"]), _p(out["cen"]), _p(out["status"]), _p(out["wall_area"]),
+                     _p(out["nfac"]), _p(out["fac_j"]), _p(out["fac_area"]), _p(out["fac_dist"]),
+                     _p(out["fac_h"]), int(nthreads))
+    out["query"] = query
+    return out
+
+
+def hessian_entries(res, psi, query=None):
+    """Rows of M = -grad^2 K (Eq. 2 with the sign flipped):
+    M_ij = -|B_ij| / (2 d_ij) for bisector facets with |B_ij| > 0,
+    M_ii = sum_j |B_ij| / (2 d_ij) + |K_i| / (2 sqrt(psi_i)).
+    Returns (diag (q,), list of (cols int64 ascending, vals float64) per row)."""
+    psi = np.asarray(psi, np.float64)
+    q = res["vol"].shape[0]
+    query = res["query"] if query is None else query
+    diag = np.zeros(q)
+    rows = []
+    for k in range(q):
+        nf = int(res["nfac"][k])
+        j = res["fac_j"][k, :nf]
+        a = res["fac_area"][k, :nf]
+        d = res["fac_dist"][k, :nf]
+        keep = a > 0.0
+        j, a, d = j[keep], a[keep], d[keep]
+        off = a / (2.0 * d)
+        ps = psi[query[k]]
+        kterm = res["karea"][k] / (2.0 * math.sqrt(ps)) if ps > 0 else 0.0
+        diag[k] = off.sum() + kterm
+        order = np.argsort(j)
+        rows.append((j[order], -off[order]))
+    return diag, rows
+
+
+def hessian_dense(res, psi):
+    """Dense M (n,n) for a full evaluation (query = all sites)."""
+    n = res["vol"].shape[0]
+    diag, rows = hessian_entries(res, psi)
+    m = np.zeros((n, n))
+    for i in range(n):
+        m[i, i] = diag[i]
+        cols, vals = rows[i]
+        m[i, cols] = vals
+    return m
+
+
+class NewtonResult:
+    def __init__(self, psi, vol, iters, halvings, status, history, res):
+        self.psi = psi
+        self.vol = vol
+        self.iters = iters
+        self.halvings = halvings
+        self.status = status
+        self.history = history
+        self.res = res
+
+
+NEWTON_OK = 0
+NEWTON_NOT_CONVERGED = 1
+NEWTON_LINESEARCH_FAILED = 2
+NEWTON_EMPTY_CELL_AT_START = 3
+
+
+def newton(pos, nu, psi0, tol=1e-4, max_newton=100, max_halvings=30,
+           lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), nthreads=0):
+    """Algorithm 1 (damped Newton with KMT steps), dense direct solve.
+
+    Readings (Algorithm 1 is garbled in the paper):
+      - start from the given psi0 > 0, not psi = 0 (psi = 0 gives empty cells);
+      - Newton system M u = nu - V(psi), M = -grad^2 K (Eq. 2);
+      - stop when max_i |V_i - nu_i| / nu_i <= tol (relative worst-cell error, Sec. 7);
+      - KMT step: alpha = 1, 1/2, ... until min V(psi + alpha u) >= eps0 and
+        ||nu - V(psi + alpha u)||_2 <= (1 - alpha/2) ||nu - V(psi)||_2,
+        eps0 = 1/2 min(min nu, min V(psi0)); at most max_halvings halvings.
+    """
+    pos = np.asarray(pos, np.float64)
+    nu = np.asarray(nu, np.float64)
+    psi = np.asarray(psi0, np.float64).copy()
+    res = cells(pos, psi, lo=lo, hi=hi, nthreads=nthreads)
+    vol = res["vol"]
+    if vol.min() <= 0.0:
+        return NewtonResult(psi, vol, 0, 0, NEWTON_EMPTY_CELL_AT_START, [], res)
+    eps0 = 0.5 * min(nu.min(), vol.min())
+    history = []
+    halv_total = 0
+    for it in range(max_newton + 1):
+        g = nu - vol
+        err = float(np.max(np.abs(g) / nu))
+        history.append(err)
+        if err <= tol:
+            return NewtonResult(psi, vol, it, halv_total, NEWTON_OK, history, res)
+        if it == max_newton:
+            break
+        m = hessian_dense(res, psi)
+        u = np.linalg.solve(m, g)
+        gnorm = float(np.linalg.norm(g))
+        alpha = 1.0
+        accepted = False
+        for _ in range(max_halvings + 1):
+            pt = psi + alpha * u
+            rt = cells(pos, pt, lo=lo, hi=hi, nthreads=nthreads)
+            vt = rt["vol"]
+            if vt.min() >= eps0 and np.linalg.norm(nu - vt) <= (1.0 - 0.5 * alpha) * gnorm:
+                accepted = True
+                break
+            alpha *= 0.5
+            halv_total += 1
+        if not accepted:
+            return NewtonResult(psi, vol, it, halv_total, NEWTON_LINESEARCH_FAILED, history, res)
+        psi, res, vol = pt, rt, vt
+    return NewtonResult(psi, vol, max_newton, halv_total, NEWTON_NOT_CONVERGED, history, res)
+
+
+def advect_and_clamp(pos, vel, dt, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), margin=1e-6):
+    """First half of the fluid step (Sec. 5, numerical integration):
+    x^{k+1} = x^k + dt v^k, then clamp into [lo+margin, hi-margin] and zero the
+    velocity component that pointed through the wall (reading: the paper leaves
+    wall handling unstated)."""
+    x = np.asarray(pos, np.float64) + dt * np.asarray(vel, np.float64)
+    v = np.asarray(vel, np.float64).copy()
+    lo = np.asarray(lo, np.float64) + margin
+    hi = np.asarray(hi, np.float64) - margin
+    below = x < lo
+    above = x > hi
+    x = np.where(below, lo, np.where(above, hi, x))
+    v = np.where(below & (v < 0), 0.0, v)
+    v = np.where(above & (v > 0), 0.0, v)
+    return x, v
+
+
+def velocity_update(x1, v, cen, dt, eps=0.01, g=(0.0, 0.0, -9.81)):
+    """v^{k+1} = v + dt (g + (c_i - x_i)/eps^2): Gallouet-Merigot pressure spring
+    F_p = (c_i - p_i)/eps^2 (Sec. 5, incompressibility) with unit mass."""
+    return np.asarray(v, np.float64) + dt * (np.asarray(g, np.float64)[None, :]
+                                             + (np.asarray(cen, np.float64) - x1) / (eps * eps))
+
+
+def fluid_step(pos, vel, psi, nu, dt, eps=0.01, g=(0.0, 0.0, -9.81), tol=1e-4,
+               max_newton=100, nthreads=0):
+    """One explicit fluid step: advect + clamp, Newton at x^{k+1} warm-started
+    from psi, centroids of the converged cells, velocity update."""
+    x1, v = advect_and_clamp(pos, vel, dt)
+    nr = newton(x1, nu, psi, tol=tol, max_newton=max_newton, nthreads=nthreads)
+    cen = nr.res["cen"]
+    v1 = velocity_update(x1, v, cen, dt, eps=eps, g=g)
+    return x1, v1, nr

@@ -1,0 +1,104 @@
+"""Pins of the oracle's Newton solve (Algorithm 1 with KMT steps) and fluid step.
+
+Closed forms: an isolated site converges to psi* = (3 nu / 4 pi)^(2/3); two
+symmetric sites converge to the root of the spherical-cap volume equation
+(found here by bisection, independently of the oracle).  The weights of the
+partial transport problem are unique (Sec. 2.2, psi_0 = 0 fixed), so two
+different starts must reach the same psi.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2601_05765_b300 import scenes
+
+
+def test_isolated_site_closed_form():
+    nu = np.array([1e-4])
+    r0 = 0.5 * (3 * nu[0] / (4 * math.pi)) ** (1 / 3)
+    nr = O.newton([[0.5, 0.5, 0.5]], nu, [r0 * r0], tol=1e-12)
+    assert nr.status == O.NEWTON_OK
+    assert nr.psi[0] == pytest.approx((3 * nu[0] / (4 * math.pi)) ** (2 / 3), rel=1e-11)
+
+
+def test_two_symmetric_sites_bisection():
+    d = 0.05
+    nu = 1e-4
+
+    def vol(r):  # ball minus the cap beyond the mid-plane
+        if r <= d / 2:
+            return 4 / 3 * math.pi * r ** 3
+        t = r - d / 2
+        return 4 / 3 * math.pi * r ** 3 - math.pi * t * t * (3 * r - t) / 3
+
+    lo, hi = 1e-4, 0.2
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        lo, hi = (mid, hi) if vol(mid) < nu else (lo, mid)
+    r_star = 0.5 * (lo + hi)
+    assert r_star > d / 2  # the two cells touch
+    pos = [[0.5 - d / 2, 0.5, 0.5], [0.5 + d / 2, 0.5, 0.5]]
+    nr = O.newton(pos, [nu, nu], [(0.7 * r_star) ** 2] * 2, tol=1e-12)
+    assert nr.status == O.NEWTON_OK
+    np.testing.assert_allclose(nr.psi, r_star ** 2, rtol=1e-10)
+
+
+def test_block_uniqueness_and_tolerance():
+    sc = scenes.jittered_block(n_side=4, spacing=0.05, seed=0)
+    pos = sc.pos.astype(np.float64)
+    a = O.newton(pos, sc.nu, sc.psi.astype(np.float64), tol=1e-10)
+    b = O.newton(pos, sc.nu, 1.3 * sc.psi.astype(np.float64), tol=1e-10)
+    assert a.status == O.NEWTON_OK and b.status == O.NEWTON_OK
+    np.testing.assert_allclose(a.psi, b.psi, rtol=1e-8)
+    # self-verification: the geometry, recomputed, meets the tolerance
+    v = O.cells(pos, a.psi)["vol"]
+    assert np.max(np.abs(v - sc.nu) / sc.nu) <= 1e-10
+    # the converged cells hold the prescribed total volume
+    assert v.sum() == pytest.approx(sc.nu.sum(), rel=1e-9)
+
+
+def test_kmt_halving_and_failure_codes():
+    sc = scenes.jittered_block(n_side=3, spacing=0.05, seed=4)
+    pos = sc.pos.astype(np.float64)
+    # a far start (tiny balls) needs damped steps
+    far = 0.05 * sc.psi.astype(np.float64)
+    nr = O.newton(pos, sc.nu, far, tol=1e-8)
+    assert nr.status == O.NEWTON_OK
+    assert nr.halvings > 0
+    # the error history is eventually monotone and quadratic near the end
+    h = nr.history
+    assert h[-1] <= 1e-8 and h[-2] > h[-1]
+    # no halving allowed: the KMT test rejects alpha = 1 and the search fails
+    nr0 = O.newton(pos, sc.nu, far, tol=1e-8, max_halvings=0)
+    assert nr0.status == O.NEWTON_LINESEARCH_FAILED
+    # a start with an empty cell is refused (the KMT bound eps0 would be 0)
+    bad = sc.psi.astype(np.float64).copy()
+    bad[0] = 0.0
+    assert O.newton(pos, sc.nu, bad).status == O.NEWTON_EMPTY_CELL_AT_START
+    # the iteration cap is reported
+    assert O.newton(pos, sc.nu, far, tol=1e-12, max_newton=2).status == O.NEWTON_NOT_CONVERGED
+
+
+def test_fluid_step_free_fall_single_site():
+    # an isolated cell's centroid is its site: only gravity acts
+    nu = np.array([1e-4])
+    psi = np.array([(3 * nu[0] / (4 * math.pi)) ** (2 / 3)])
+    x1, v1, nr = O.fluid_step([[0.5, 0.5, 0.5]], [[0.1, 0.0, 0.0]], psi, nu, dt=1e-3, tol=1e-10)
+    np.testing.assert_allclose(x1[0], [0.5001, 0.5, 0.5], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(v1[0], [0.1, 0.0, -9.81e-3], rtol=0, atol=1e-9)
+
+
+def test_fluid_step_wall_clamp_and_spring():
+    # a cell cut by the floor: the centroid is above the site, so the spring
+    # pushes up against gravity; the site is clamped into the box
+    nu = np.array([2e-4])
+    x, v = np.array([[0.5, 0.5, 0.002]]), np.array([[0.0, 0.0, -3.0]])
+    psi = np.array([(3 * nu[0] / (4 * math.pi)) ** (2 / 3)])
+    x1, v1, nr = O.fluid_step(x, v, psi, nu, dt=1e-3, tol=1e-10)
+    assert x1[0, 2] == pytest.approx(1e-6)
+    cen = nr.res["cen"][0]
+    assert cen[2] > x1[0, 2]
+    expect = 0.0 + 1e-3 * (-9.81 + (cen[2] - x1[0, 2]) / 1e-4)
+    assert v1[0, 2] == pytest.approx(expect, rel=1e-12)
