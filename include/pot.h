@@ -1,0 +1,216 @@
+/*
+ * pot.h -- C ABI of libpot.so: generalized Laguerre cells, the partial
+ * optimal transport Newton solve and the explicit fluid step on one B300.
+ *
+ * Paper: "More Power to the Particles: Analytic Geometry for Partial Optimal
+ * Transport-based Fluid Simulation" (arXiv 2601.05765).
+ *
+ * Conventions (every entry point):
+ *  - Array arguments are DEVICE pointers on the context's device, owned by the
+ *    caller, unless stated otherwise.  Positions are AoS (n,3) row-major.
+ *    Indices of sites are 0..n-1 in the caller's order.
+ *  - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *    stream.  Work is enqueued on that stream; a call returns after its own
+ *    small host reads (status words, scalars) have completed, so outputs are
+ *    ready for later work on the same stream.
+ *  - The library owns its workspace inside the opaque context (allocated by
+ *    pot_create); no other call allocates device memory.
+ *  - Every call returns an int status (POT_OK = 0) and never aborts or prints.
+ *    On error the array outputs are undefined; stats structs are filled as
+ *    far as the call got.
+ *  - The domain is an axis-aligned box [lo, hi].
+ *  - Weights psi: the ball of site i has radius sqrt(psi_i); psi_i <= 0 gives
+ *    an empty cell.
+ *  - A context is not thread-safe: one call at a time per context.
+ */
+#ifndef POT_H
+#define POT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define POT_OK 0
+#define POT_ERR_INVALID_ARG 1         /* NULL pointer, n <= 0, n > n_max, bad box, ... */
+#define POT_ERR_CUDA 2                /* a CUDA runtime call failed */
+#define POT_ERR_NEIGHBOUR_OVERFLOW 3  /* a cell has more than k_max cutting bisectors */
+#define POT_ERR_COINCIDENT_SITES 4    /* two sites at distance 0 cut each other's ball */
+#define POT_ERR_EMPTY_CELL_AT_START 5 /* Newton start has a cell of volume 0 */
+#define POT_ERR_NOT_CONVERGED 6       /* Newton iteration cap reached */
+#define POT_ERR_LINESEARCH_FAILED 7   /* KMT step not found within max_halvings */
+#define POT_ERR_POLYGON_OVERFLOW 8    /* a facet polygon exceeded its edge capacity */
+#define POT_ERR_CAPACITY 9            /* CSR capacity too small for the Hessian */
+#define POT_ERR_PCG_BREAKDOWN 10      /* PCG met p.Mp <= 0 (matrix not SPD) */
+
+/* ---- types ------------------------------------------------------------ */
+typedef struct pot_ctx pot_ctx;
+
+/* Axis-aligned box domain [lo, hi] (Sec. 2.2: the cells live in the box). */
+typedef struct {
+  double lo[3];
+  double hi[3];
+} pot_domain;
+
+/* CSR of M = -grad^2 K (the Hessian of Eq. 2 with its sign flipped so that M
+ * is symmetric positive definite):
+ *   M_ij = -|B_ij| / (2 |p_i - p_j|) for every restricted bisector facet B_ij
+ *          with area above 4e-7 psi_i (1e-13 psi_i in FP64),
+ *   M_ii = sum_j |B_ij| / (2 |p_i - p_j|) + |K_i| / (2 sqrt(psi_i)),
+ * |K_i| the free-surface (spherical patch) area.  Every row holds its
+ * diagonal; columns ascend within a row.  The caller allocates row_ptr (n+1),
+ * cols and vals (cap each); the call writes nnz (also when it exceeds cap,
+ * then it returns POT_ERR_CAPACITY and leaves cols/vals undefined). */
+typedef struct {
+  int32_t* row_ptr;
+  int32_t* cols;
+  float* vals;
+  int64_t cap;
+  int64_t nnz;
+} pot_csr;
+
+typedef struct {
+  int32_t* row_ptr;
+  int32_t* cols;
+  double* vals;
+  int64_t cap;
+  int64_t nnz;
+} pot_csr_f64;
+
+/* Per-call statistics of lgc_compute_cells*. */
+typedef struct {
+  int64_t n_empty;    /* cells of volume 0 */
+  int64_t n_planes;   /* total cutting planes (walls + bisectors) */
+  int64_t nnz;        /* Hessian entries incl. the diagonal */
+  int64_t error_site; /* site index behind an error status, else -1 */
+  int32_t max_planes; /* largest cutting-plane count of one cell */
+  float ms_grid;      /* device time: grid build + sort */
+  float ms_cells;     /* device time: candidates + cell geometry */
+  float ms_csr;       /* device time: CSR assembly */
+} pot_cell_stats;
+
+/* Newton / fluid-step parameters (pot_default_params fills the defaults). */
+typedef struct {
+  double tol;           /* stop when max_i |V_i - nu_i| / nu_i <= tol (1e-4) */
+  int32_t max_newton;   /* Newton iteration cap (100, Sec. 7) */
+  int32_t max_halvings; /* KMT step halvings per iteration (30) */
+  int32_t max_pcg;      /* PCG iteration cap per Newton step (2000) */
+  int32_t pcg_chunk;    /* PCG iterations per CUDA-graph launch (16) */
+  double pcg_rtol;      /* PCG relative residual; <= 0 selects the adaptive
+                           forcing term (default) */
+  double dt;            /* fluid step (2e-3) */
+  double eps;           /* spring length of the pressure force (0.01, Sec. 5) */
+  double gravity[3];    /* (0, 0, -9.81) */
+  double wall_margin;   /* sites are clamped to [lo+m, hi-m] (1e-6) */
+  int32_t warm_start;   /* 0: previous psi; 1: learned MLP start */
+  int32_t reserved;
+} pot_params;
+
+/* Statistics of one Newton solve (and of the solve inside a fluid step). */
+typedef struct {
+  int32_t status;
+  int32_t newton_iters;
+  int32_t pcg_iters;   /* total over the solve */
+  int32_t halvings;    /* total KMT halvings */
+  int32_t cell_evals;  /* evaluations of all cells (incl. line search) */
+  int32_t grid_builds;
+  double err_max;      /* final max_i |V_i - nu_i| / nu_i */
+  double err_l2;       /* final ||nu - V||_2 */
+  double err_start;    /* max relative error at the start */
+  double ms_total;     /* host wall time of the call */
+  double ms_cells;     /* device time in cell evaluations */
+  double ms_pcg;       /* device time in PCG */
+  int64_t nnz;         /* Hessian entries of the last assembly */
+  int32_t mlp_used;    /* warm start: 1 if the MLP start was kept */
+  int32_t mlp_fallback;/* warm start: 1 if the MLP start was rejected */
+} pot_solve_stats;
+
+/* ---- context ---------------------------------------------------------- */
+
+/* Create a context on `device` for up to n_max sites and k_max (<= 64)
+ * cutting bisectors per cell, and allocate all its workspace.
+ * precision_mask: bit 0 = FP32 geometry (mixed-precision entry points),
+ * bit 1 = FP64 entry points (*_f64).
+ * Returns POT_ERR_INVALID_ARG / POT_ERR_CUDA on failure (*ctx = NULL). */
+int pot_create(pot_ctx** ctx, int device, int64_t n_max, int32_t k_max, int32_t precision_mask);
+
+/* Free the context and its workspace.  NULL is accepted. */
+int pot_destroy(pot_ctx* ctx);
+
+/* Static string for a status code. */
+const char* pot_status_string(int status);
+
+/* Default parameters (see pot_params). */
+void pot_default_params(pot_params* p);
+
+/* ---- generalized Laguerre cells (Eq. 1, Sec. 3.2-3.4, Algorithm 2) ------ */
+
+/* Build every generalized Laguerre cell
+ *   C_i = box ∩ B(p_i, sqrt(psi_i)) ∩ {x : |x-p_i|^2 - psi_i <= |x-p_j|^2 - psi_j, all j}
+ * and evaluate analytically:
+ *   volumes[i] = |C_i| (pyramid decomposition, Sec. 3.2, Algorithm 2),
+ *   grad[i]    = targets[i] - |C_i|  (dK/dpsi_i, Sec. 3.1; -|C_i| if targets is NULL),
+ *   hess       = M = -grad^2 K in CSR (Eq. 2, see pot_csr), optional (NULL),
+ *   centroids  = (n,3) cell centroids c_i (pressure force, Sec. 5), optional,
+ *   karea      = |K_i| free-surface area (Sec. 3.3), optional.
+ * Inputs: pos (n,3) float, psi (n) float, targets (n) double or NULL.
+ * FP32 geometry; grad in FP64.
+ * Errors: POT_ERR_NEIGHBOUR_OVERFLOW, POT_ERR_COINCIDENT_SITES,
+ *         POT_ERR_POLYGON_OVERFLOW (stats->error_site names a site),
+ *         POT_ERR_CAPACITY (hess->nnz > hess->cap). */
+int lgc_compute_cells(pot_ctx* ctx, void* stream, int64_t n, const float* pos, const float* psi,
+                      const double* targets, const pot_domain* dom, float* volumes, double* grad,
+                      pot_csr* hess, float* centroids, float* karea, pot_cell_stats* stats);
+
+/* Same in FP64 throughout (pos, psi, volumes, centroids, karea, hess values). */
+int lgc_compute_cells_f64(pot_ctx* ctx, void* stream, int64_t n, const double* pos,
+                          const double* psi, const double* targets, const pot_domain* dom,
+                          double* volumes, double* grad, pot_csr_f64* hess, double* centroids,
+                          double* karea, pot_cell_stats* stats);
+
+/* ---- Newton solve (Algorithm 1 with KMT steps) --------------------------- */
+
+/* Find the weights psi with |C_i(psi)| = targets[i] for all i (partial OT,
+ * Sec. 2.2) by damped Newton (Algorithm 1): M u = nu - V(psi) solved by
+ * Jacobi-preconditioned CG (Sec. 7), then the KMT step: alpha = 1, 1/2, ...
+ * until min V(psi + alpha u) >= eps0 and
+ * ||nu - V(psi + alpha u)||_2 <= (1 - alpha/2) ||nu - V(psi)||_2,
+ * eps0 = 1/2 min(min nu, min V(psi_start)).  Stops when
+ * max_i |V_i - nu_i| / nu_i <= params->tol.
+ * psi_inout: start (must give non-empty cells) in, solution out.
+ * Mixed precision: FP32 geometry and matrix, FP64 residuals, PCG dot
+ * products and KMT test.  Errors: POT_ERR_EMPTY_CELL_AT_START,
+ * POT_ERR_NOT_CONVERGED, POT_ERR_LINESEARCH_FAILED, geometry errors.
+ * psi_inout holds the last accepted iterate on NOT_CONVERGED. */
+int pot_newton_solve(pot_ctx* ctx, void* stream, int64_t n, const float* pos, const double* targets,
+                     float* psi_inout, const pot_domain* dom, const pot_params* params,
+                     pot_solve_stats* stats);
+
+/* Same with FP64 geometry, matrix and PCG vectors. */
+int pot_newton_solve_f64(pot_ctx* ctx, void* stream, int64_t n, const double* pos,
+                         const double* targets, double* psi_inout, const pot_domain* dom,
+                         const pot_params* params, pot_solve_stats* stats);
+
+/* ---- fluid step (Sec. 5, Gallouet-Merigot scheme) ------------------------ */
+
+/* One explicit step, all on the device:
+ *   x <- x + dt v, clamped to [lo+m, hi-m] (velocity component through the
+ *        wall set to 0);
+ *   psi <- Newton solve at the new x, warm-started from psi;
+ *   v <- v + dt (g + (c_i - x_i) / eps^2)   (pressure spring F_p, Sec. 5).
+ * pos, vel (n,3) and psi (n) are updated in place. */
+int pot_fluid_step(pot_ctx* ctx, void* stream, int64_t n, float* pos, float* vel, float* psi,
+                   const double* targets, const pot_domain* dom, const pot_params* params,
+                   pot_solve_stats* stats);
+
+int pot_fluid_step_f64(pot_ctx* ctx, void* stream, int64_t n, double* pos, double* vel,
+                       double* psi, const double* targets, const pot_domain* dom,
+                       const pot_params* params, pot_solve_stats* stats);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* POT_H */

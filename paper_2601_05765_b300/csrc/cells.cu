@@ -1,0 +1,861 @@
+// Generalized Laguerre cells on the GPU (Eq. 1, Sec. 3.2-3.4, Algorithm 2).
+//
+// Two kernels per evaluation, both in grid-sorted order:
+//
+// k_candidates (one thread per cell): exact radius query over the grid rows
+//   around p_i.  Site j is kept iff its radical plane cuts the ball of i
+//   (|h_ij| < r_i, which implies |p_i - p_j| < r_i + r_j); a plane with
+//   h <= -r_i empties the cell.  The six box walls are planes too.
+//
+// k_cells (one warp per group of cells, one lane per cutting plane): each
+//   warp packs consecutive cells into its 32 lanes (a cell with m planes
+//   takes m lanes; cells with more than 32 planes take the whole warp in
+//   rounds).  Lane f clips the disk of its plane f by the traces of the other
+//   planes of its cell (2D convex clipping of a line-list polygon: every
+//   vertex is recomputed from its two lines, never interpolated), restricts
+//   the polygon to the disk (Sec. 3.4) and integrates, per fan piece from the
+//   disk centre, the facet area |B_f|, the signed solid angle Omega_f it
+//   subtends at the site (its projection on the sphere, Sec. 3.3) and its
+//   first moment.  Segmented warp reductions then give per cell
+//     |K_i| = psi_i (4 pi [p_i inside all planes] - sum_f Omega_f),
+//     |V_i| = (sum_f h_f |B_f| + r_i |K_i|) / 3          (pyramids, Sec. 3.2),
+//     centroid, and the Hessian row of Eq. 2 (M = -grad^2 K):
+//     M_ij = -|B_ij|/(2 d_ij), M_ii = sum_j |B_ij|/(2 d_ij) + |K_i|/(2 r_i).
+//   The paper's interior point c (Sec. 3.3) is replaced by the site with
+//   signed solid angles, exact whether or not p_i lies in its cell.
+#include <math.h>
+
+#include "pot_internal.cuh"
+
+namespace pot {
+namespace {
+
+template <typename T>
+__device__ __forceinline__ T sqdist(const V4<T>& pi, const V4<T>& pj, T& dx, T& dy, T& dz) {
+  dx = r_sub(pj.x, pi.x);
+  dy = r_sub(pj.y, pi.y);
+  dz = r_sub(pj.z, pi.z);
+  return r_add(r_add(r_mul(dx, dx), r_mul(dy, dy)), r_mul(dz, dz));
+}
+
+// offset of the radical plane: h = (d^2 + psi_i - psi_j) / (2 d)
+template <typename T>
+__device__ __forceinline__ T plane_offset(T d2, T psi_i, T psi_j, T& d) {
+  d = r_sqrt(d2);
+  return r_div(r_add(d2, r_sub(psi_i, psi_j)), r_add(d, d));
+}
+
+template <typename T>
+__device__ __forceinline__ int cell_coord(T x, T lo, T inv_cs, int dim) {
+  T f = (x - lo) * inv_cs;
+  int c = (f < T(0)) ? 0 : (f >= T(dim) ? dim - 1 : (int)f);
+  return c;
+}
+
+__device__ __forceinline__ void set_error(int32_t* err, int code, int64_t site) {
+  atomicMax(&err[kErrCode], code);
+  atomicMin(&err[kErrSite], (int)site);
+}
+
+// ---------------------------------------------------------------------------
+// candidates
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_candidates(int64_t n, const V4<T>* __restrict__ sxp, const int32_t* __restrict__ cell_start,
+                 GridParams<T> g, Box<T> box, const T* __restrict__ psi_max, int kmax,
+                 int32_t* __restrict__ cand, int32_t* __restrict__ meta, int32_t* err) {
+  int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const V4<T> p = sxp[s];
+  const T ps = p.w;
+  if (!(ps > T(0))) {
+    meta[s] = kMetaEmpty;
+    return;
+  }
+  const T r = r_sqrt(ps);
+  int wmask = 0, nw = 0;
+  for (int w = 0; w < 6; w++) {
+    T h = fix_zero(wall_offset(p, w, box.lo, box.hi), r);
+    if (h <= -r) {
+      meta[s] = kMetaEmpty;
+      return;
+    }
+    if (h < r) {
+      wmask |= 1 << w;
+      nw++;
+    }
+  }
+  const T R = r + sqrt(*psi_max);
+  const T R2 = R * R;
+  int c0[3], c1[3];
+  const T pc[3] = {p.x, p.y, p.z};
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    c0[k] = cell_coord(pc[k] - R, g.lo[k], g.inv_cs, g.dim[k]);
+    c1[k] = cell_coord(pc[k] + R, g.lo[k], g.inv_cs, g.dim[k]);
+  }
+  int nc = 0;
+  bool empty = false;
+  int64_t row = s * (int64_t)kmax;
+  for (int cz = c0[2]; cz <= c1[2] && !empty; cz++) {
+    T zlo = g.lo[2] + cz * g.cs;
+    T ez = fmax(T(0), fmax(zlo - p.z, p.z - (zlo + g.cs)));
+    if (cz == 0 && p.z < zlo) ez = T(0);
+    if (cz == g.dim[2] - 1 && p.z > zlo) ez = T(0);
+    for (int cy = c0[1]; cy <= c1[1] && !empty; cy++) {
+      T ylo = g.lo[1] + cy * g.cs;
+      T ey = fmax(T(0), fmax(ylo - p.y, p.y - (ylo + g.cs)));
+      if (cy == 0 && p.y < ylo) ey = T(0);
+      if (cy == g.dim[1] - 1 && p.y > ylo) ey = T(0);
+      T rem2 = R2 - ey * ey - ez * ez;
+      if (rem2 <= T(0)) continue;
+      T rem = sqrt(rem2);
+      int x0 = cell_coord(p.x - rem, g.lo[0], g.inv_cs, g.dim[0]);
+      int x1 = cell_coord(p.x + rem, g.lo[0], g.inv_cs, g.dim[0]);
+      int key0 = (cz * g.dim[1] + cy) * g.dim[0];
+      int a = cell_start[key0 + x0], b = cell_start[key0 + x1 + 1];
+      for (int t = a; t < b; t++) {
+        if (t == s) continue;
+        const V4<T> q = sxp[t];
+        T dx, dy, dz;
+        T d2 = sqdist(p, q, dx, dy, dz);
+        T rj = q.w > T(0) ? sqrt(q.w) : T(0);
+        T sr = r + rj;
+        if (!(d2 < sr * sr)) continue;
+        if (d2 == T(0)) {
+          set_error(err, POT_ERR_COINCIDENT_SITES, s);
+          continue;
+        }
+        T d;
+        T h = fix_zero(plane_offset(d2, ps, q.w, d), r);
+        if (h <= -r) {
+          empty = true;
+          break;
+        }
+        if (h < r) {
+          if (nc < kmax) cand[row + nc] = t;
+          nc++;
+        }
+      }
+    }
+  }
+  if (empty) {
+    meta[s] = kMetaEmpty;
+  } else if (nc > kmax) {
+    set_error(err, POT_ERR_NEIGHBOUR_OVERFLOW, s);
+    meta[s] = kMetaEmpty;
+  } else {
+    meta[s] = (nw + nc) | (wmask << kMetaWallShift);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// facet geometry
+
+template <typename T>
+struct Facet {
+  T area, omega, mx, my, mz;
+  int overflow;
+};
+
+// Orthonormal basis (u, v) of the plane with unit normal n, branch-free:
+// Duff, Burgess, Christensen, Hery, Kensler, Liani, Villemin (2017),
+// "Building an Orthonormal Basis, Revisited", JCGT 6(1).
+template <typename T>
+__device__ __forceinline__ void onb(T nx, T ny, T nz, T& ux, T& uy, T& uz, T& vx, T& vy, T& vz) {
+  T sg = copysign(T(1), nz);
+  T a = T(-1) / (sg + nz);
+  T b = nx * ny * a;
+  ux = T(1) + sg * nx * nx * a;
+  uy = sg * b;
+  uz = -sg * nx;
+  vx = b;
+  vy = sg + ny * ny * a;
+  vz = -ny;
+}
+
+template <typename T>
+__device__ __forceinline__ void isect(T a1, T b1, T c1, T a2, T b2, T c2, T& x, T& y) {
+  T det = a1 * b2 - a2 * b1;
+  if (det == T(0)) det = T(1e-30);
+  T inv = T(1) / det;
+  x = (c1 * b2 - c2 * b1) * inv;
+  y = (a1 * c2 - a2 * c1) * inv;
+}
+
+// Facet fi of a cell whose planes are pl[0..m): (n, h) with y.n <= h.
+// Returns area, signed solid angle at the site and first moment (about the site).
+template <typename T>
+__device__ Facet<T> facet_eval(const V4<T>* __restrict__ pl, int m, int fi, T ps, T r) {
+  Facet<T> out = {T(0), T(0), T(0), T(0), T(0), 0};
+  const V4<T> P = pl[fi];
+  const T h = P.w;
+  const T rho2 = ps - h * h;
+  if (!(rho2 > T(0))) return out;
+  const T rho = sqrt(rho2);
+  T ux, uy, uz, vx, vy, vz;
+  onb(P.x, P.y, P.z, ux, uy, uz, vx, vy, vz);
+  const T B = T(2) * rho;
+
+  // polygon: line ids (plane index, or 252..255 for the square around the
+  // disk) and vertices; vertex k = intersection of lines k-1 and k
+  uint8_t lid[2][kMaxLines];
+  T px[2][kMaxLines], py[2][kMaxLines];
+  int cur = 0, nl = 4;
+  lid[0][0] = 252; lid[0][1] = 253; lid[0][2] = 254; lid[0][3] = 255;
+  px[0][0] = -B; py[0][0] = -B;
+  px[0][1] = B;  py[0][1] = -B;
+  px[0][2] = B;  py[0][2] = B;
+  px[0][3] = -B; py[0][3] = B;
+
+  auto line = [&](int id, T& a, T& b, T& c) {
+    if (id >= 252) {
+      a = (id == 253) ? T(1) : ((id == 255) ? T(-1) : T(0));
+      b = (id == 254) ? T(1) : ((id == 252) ? T(-1) : T(0));
+      c = B;
+    } else {
+      const V4<T> G = pl[id];
+      a = ux * G.x + uy * G.y + uz * G.z;
+      b = vx * G.x + vy * G.y + vz * G.z;
+      c = G.w - h * (P.x * G.x + P.y * G.y + P.z * G.z);
+    }
+  };
+
+  for (int gi = 0; gi < m; gi++) {
+    if (gi == fi) continue;
+    T a, b, c;
+    line(gi, a, b, c);
+    T len2 = a * a + b * b;
+    if (len2 == T(0)) {  // parallel plane: keeps all or nothing
+      if (c < T(0)) return out;
+      continue;
+    }
+    T lr = rho * sqrt(len2);
+    if (c >= lr) continue;            // the disk lies inside this half-plane
+    if (c <= -lr) return out;         // the disk lies outside: no facet
+    unsigned om = 0;
+    for (int k = 0; k < nl; k++)
+      if (a * px[cur][k] + b * py[cur][k] > c) om |= 1u << k;
+    if (om == 0) continue;
+    const unsigned full = (1u << nl) - 1u;
+    if (om == full) return out;
+    unsigned prev = ((om << 1) | (om >> (nl - 1))) & full;  // bit k: vertex k-1 outside
+    int s = __ffs(om & ~prev) - 1;                          // first outside vertex of a run
+    unsigned nxt = ((om >> 1) | (om << (nl - 1))) & full;   // bit k: vertex k+1 outside
+    unsigned em = om & ~nxt;                                // last outside vertex of a run
+    unsigned rot = s == 0 ? em : (((em >> s) | (em << (nl - s))) & full);
+    int e = s + __ffs(rot) - 1;
+    if (e >= nl) e -= nl;
+    int cnt = s - e - 1;
+    if (cnt < 0) cnt += nl;
+    cnt += 1;  // lines e, e+1, ..., s-1 stay
+    if (cnt + 1 > kMaxLines) {
+      out.overflow = 1;
+      return out;
+    }
+    const int nx = cur ^ 1;
+    for (int k = 0; k < cnt; k++) {
+      int idx = e + k;
+      if (idx >= nl) idx -= nl;
+      lid[nx][k] = lid[cur][idx];
+      px[nx][k] = px[cur][idx];
+      py[nx][k] = py[cur][idx];
+    }
+    lid[nx][cnt] = (uint8_t)gi;
+    T a2, b2, c2;
+    line(lid[cur][e], a2, b2, c2);
+    isect(a, b, c, a2, b2, c2, px[nx][0], py[nx][0]);
+    int sm1 = s == 0 ? nl - 1 : s - 1;
+    line(lid[cur][sm1], a2, b2, c2);
+    isect(a2, b2, c2, a, b, c, px[nx][cnt], py[nx][cnt]);
+    nl = cnt + 1;
+    cur = nx;
+  }
+
+  // restrict to the disk and integrate over the fan from the disk centre
+  const T sg = h >= T(0) ? T(1) : T(-1);
+  const T ah = fabs(h), h2 = h * h;
+  const T rho3 = rho2 * rho / T(3);
+  const T sect_om = sg - h / r;
+  T area = T(0), omg = T(0), mx = T(0), my = T(0);
+  auto sector = [&](T ax, T ay, T bx, T by) {
+    T cr = ax * by - ay * bx;
+    T dt = ax * bx + ay * by;
+    T phi = atan2(cr, dt);
+    area += T(0.5) * rho2 * phi;
+    omg += phi * sect_om;
+    T na = sqrt(ax * ax + ay * ay), nb = sqrt(bx * bx + by * by);
+    if (na > T(0) && nb > T(0)) {
+      mx += rho3 * (by / nb - ay / na);
+      my += rho3 * (ax / na - bx / nb);
+    }
+  };
+  auto tri = [&](T ax, T ay, T bx, T by) {
+    T cr = ax * by - ay * bx;
+    T dt = ax * bx + ay * by;
+    T la = sqrt(ax * ax + ay * ay + h2), lb = sqrt(bx * bx + by * by + h2);
+    T den = la * lb + ah * (la + lb) + dt + h2;
+    T ta = T(0.5) * cr;
+    area += ta;
+    omg += sg * T(2) * atan2(cr, den);
+    mx += ta * (ax + bx) * T(1.0 / 3.0);
+    my += ta * (ay + by) * T(1.0 / 3.0);
+  };
+  for (int k = 0; k < nl; k++) {
+    int k2 = k + 1 == nl ? 0 : k + 1;
+    T pxk = px[cur][k], pyk = py[cur][k], qx = px[cur][k2], qy = py[cur][k2];
+    T dx = qx - pxk, dy = qy - pyk;
+    T a2 = dx * dx + dy * dy;
+    if (a2 == T(0)) continue;
+    T b2 = pxk * dx + pyk * dy;
+    T c2 = pxk * pxk + pyk * pyk - rho2;
+    T disc = b2 * b2 - a2 * c2;
+    if (disc <= T(0)) {
+      sector(pxk, pyk, qx, qy);
+      continue;
+    }
+    T sq = sqrt(disc);
+    T t1 = (-b2 - sq) / a2, t2 = (-b2 + sq) / a2;
+    t1 = fmin(fmax(t1, T(0)), T(1));
+    t2 = fmin(fmax(t2, T(0)), T(1));
+    // a clamped crossing is the vertex itself, exactly
+    T x1 = t1 == T(0) ? pxk : (t1 == T(1) ? qx : pxk + t1 * dx);
+    T y1 = t1 == T(0) ? pyk : (t1 == T(1) ? qy : pyk + t1 * dy);
+    T x2 = t2 == T(0) ? pxk : (t2 == T(1) ? qx : pxk + t2 * dx);
+    T y2 = t2 == T(0) ? pyk : (t2 == T(1) ? qy : pyk + t2 * dy);
+    if (t1 > T(0)) sector(pxk, pyk, x1, y1);
+    if (t2 > t1) tri(x1, y1, x2, y2);
+    if (t2 < T(1)) sector(x2, y2, qx, qy);
+  }
+  out.area = area;
+  out.omega = omg;
+  out.mx = h * P.x * area + ux * mx + vx * my;
+  out.my = h * P.y * area + uy * mx + vy * my;
+  out.mz = h * P.z * area + uz * mx + vz * my;
+  return out;
+}
+
+// Plane f of cell `cell` (walls first in order -x,+x,-y,+y,-z,+z, then the
+// candidate bisectors in ascending sorted index).
+template <typename T>
+__device__ __forceinline__ void plane_of(int f, int64_t cell, const V4<T>& p, int mt, T r,
+                                         const V4<T>* __restrict__ sxp,
+                                         const int32_t* __restrict__ cand, int kmax,
+                                         const Box<T>& box, V4<T>& pl, T& pd, int& pj) {
+  int wmask = (mt >> kMetaWallShift) & 63;
+  int nw = __popc(wmask);
+  if (f < nw) {
+    int w = 0, k = f;
+    for (w = 0; w < 6; w++) {
+      if (wmask & (1 << w)) {
+        if (k == 0) break;
+        k--;
+      }
+    }
+    T h = fix_zero(wall_offset(p, w, box.lo, box.hi), r);
+    int ax = w >> 1;
+    T sgn = (w & 1) ? T(1) : T(-1);
+    pl.x = ax == 0 ? sgn : T(0);
+    pl.y = ax == 1 ? sgn : T(0);
+    pl.z = ax == 2 ? sgn : T(0);
+    pl.w = h;
+    pd = T(0);
+    pj = -1;
+  } else {
+    int t = cand[cell * kmax + (f - nw)];
+    const V4<T> q = sxp[t];
+    T dx, dy, dz;
+    T d2 = sqdist(p, q, dx, dy, dz);
+    T d;
+    T h = fix_zero(plane_offset(d2, p.w, q.w, d), r);
+    T inv = T(1) / d;
+    pl.x = dx * inv;
+    pl.y = dy * inv;
+    pl.z = dz * inv;
+    pl.w = h;
+    pd = d;
+    pj = t;
+  }
+}
+
+template <typename T>
+struct CellAcc {
+  T hA, om, nx, ny, nz, hx, hy, hz, dg;
+};
+
+template <typename T>
+__device__ __forceinline__ void acc_facet(CellAcc<T>& a, const V4<T>& pl, T pd, int pj,
+                                          const Facet<T>& fo) {
+  a.hA += pl.w * fo.area;
+  a.om += fo.omega;
+  a.nx += pl.x * fo.area;
+  a.ny += pl.y * fo.area;
+  a.nz += pl.z * fo.area;
+  a.hx += pl.w * fo.mx;
+  a.hy += pl.w * fo.my;
+  a.hz += pl.w * fo.mz;
+  if (pj >= 0) a.dg += fo.area / (T(2) * pd);
+}
+
+// sum over lanes [lane, last] into the first lane of the window (segment head)
+template <typename T>
+__device__ __forceinline__ T seg_sum(T v, int lane, int last) {
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    T t = __shfl_down_sync(kFull, v, off);
+    if (lane + off <= last) v += t;
+  }
+  return v;
+}
+
+template <typename T>
+__device__ __forceinline__ void seg_reduce(CellAcc<T>& a, int lane, int last) {
+  a.hA = seg_sum(a.hA, lane, last);
+  a.om = seg_sum(a.om, lane, last);
+  a.nx = seg_sum(a.nx, lane, last);
+  a.ny = seg_sum(a.ny, lane, last);
+  a.nz = seg_sum(a.nz, lane, last);
+  a.hx = seg_sum(a.hx, lane, last);
+  a.hy = seg_sum(a.hy, lane, last);
+  a.hz = seg_sum(a.hz, lane, last);
+  a.dg = seg_sum(a.dg, lane, last);
+}
+
+struct CellOut {
+  void* vol;
+  void* karea;
+  void* diag;
+  void* cen;
+  int32_t* row_cnt;
+  double* grad;
+  const double* snu;
+};
+
+template <typename T>
+__device__ __forceinline__ void write_cell(int64_t cell, const V4<T>& p, bool empty, bool inside,
+                                           const CellAcc<T>& a, int cnt, const CellOut& o) {
+  const T ps = p.w;
+  T V = T(0), K = T(0), dg = T(0);
+  T cx = p.x, cy = p.y, cz = p.z;
+  if (!empty && ps > T(0)) {
+    const T r = sqrt(ps);
+    K = ps * (T(4.0 * 3.14159265358979323846) * (inside ? T(1) : T(0)) - a.om);
+    K = fmax(K, T(0));
+    V = (a.hA + r * K) * T(1.0 / 3.0);
+    dg = a.dg + K / (T(2) * r);
+    if (V > T(0)) {
+      T iv = T(0.25) / V;
+      cx += (a.hx - ps * a.nx) * iv;
+      cy += (a.hy - ps * a.ny) * iv;
+      cz += (a.hz - ps * a.nz) * iv;
+    }
+  }
+  ((T*)o.vol)[cell] = V;
+  ((T*)o.karea)[cell] = K;
+  ((T*)o.diag)[cell] = dg;
+  T* cen = (T*)o.cen;
+  cen[3 * cell + 0] = cx;
+  cen[3 * cell + 1] = cy;
+  cen[3 * cell + 2] = cz;
+  o.row_cnt[cell] = cnt;
+  if (o.grad) o.grad[cell] = o.snu[cell] - (double)V;
+}
+
+// A cell with more than 32 planes: the whole warp, planes in rounds of 32.
+template <typename T>
+__device__ void big_cell(int64_t cell, int lane, V4<T>* pl, T* pd, int* pj,
+                         const V4<T>* __restrict__ sxp, const int32_t* __restrict__ meta,
+                         int32_t* cand, int kmax, const Box<T>& box, T* stage_vals,
+                         const CellOut& o, int32_t* err) {
+  const int mt = meta[cell];
+  const int m = mt & kMetaPlanes;
+  const V4<T> p = sxp[cell];
+  const T r = sqrt(p.w);
+  for (int f = lane; f < m; f += 32) plane_of(f, cell, p, mt, r, sxp, cand, kmax, box, pl[f], pd[f], pj[f]);
+  __syncwarp();
+  CellAcc<T> a = {};
+  bool neg = false;
+  int emitted = 0;
+  for (int f0 = 0; f0 < m; f0 += 32) {
+    const int f = f0 + lane;
+    const bool has = f < m;
+    Facet<T> fo = {};
+    if (has) {
+      fo = facet_eval(pl, m, f, p.w, r);
+      if (fo.overflow) set_error(err, POT_ERR_POLYGON_OVERFLOW, cell);
+      acc_facet(a, pl[f], pd[f], pj[f], fo);
+      neg |= pl[f].w < T(0);
+    }
+    const bool emit = has && pj[f] >= 0 && fo.area > Real<T>::kEmitArea * p.w;
+    const unsigned em = __ballot_sync(kFull, emit);
+    if (emit) {
+      int rank = emitted + __popc(em & ((1u << lane) - 1u));
+      int64_t at = cell * kmax + rank;
+      cand[at] = pj[f];
+      stage_vals[at] = -fo.area / (T(2) * pd[f]);
+    }
+    emitted += __popc(em);
+  }
+  seg_reduce(a, lane, 31);
+  const bool anyneg = __any_sync(kFull, neg);
+  if (lane == 0) write_cell(cell, p, (mt & kMetaEmpty) != 0, !anyneg, a, emitted, o);
+  __syncwarp();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kCellWarps * 32)
+    k_cells(int64_t n, const V4<T>* __restrict__ sxp, const int32_t* __restrict__ meta,
+            int32_t* cand, int kmax, Box<T> box, T* stage_vals, CellOut o, int32_t* err) {
+  __shared__ V4<T> s_pl[kCellWarps][kPlaneCap];
+  __shared__ T s_d[kCellWarps][kPlaneCap];
+  __shared__ int s_j[kCellWarps][kPlaneCap];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  V4<T>* pl = s_pl[wid];
+  T* pd = s_d[wid];
+  int* pj = s_j[wid];
+  const int64_t c0 = ((int64_t)blockIdx.x * kCellWarps + wid) * kCellsPerWarp;
+  if (c0 >= n) return;
+  const int64_t c1 = c0 + kCellsPerWarp < n ? c0 + kCellsPerWarp : n;
+  int64_t base = c0;
+  while (base < c1) {
+    const int64_t cell = base + lane;
+    const bool valid = cell < c1;
+    const int mt = valid ? meta[cell] : 0;
+    const int m = mt & kMetaPlanes;
+    const int slots = valid ? (m > 1 ? m : 1) : 0;
+    int incl = slots;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      int t = __shfl_up_sync(kFull, incl, off);
+      if (lane >= off) incl += t;
+    }
+    const int excl = incl - slots;
+    const bool fits = valid && incl <= 32;
+    const int ncell = __popc(__ballot_sync(kFull, fits));
+    if (ncell == 0) {
+      big_cell(base, lane, pl, pd, pj, sxp, meta, cand, kmax, box, stage_vals, o, err);
+      base += 1;
+      continue;
+    }
+    const unsigned head = __reduce_or_sync(kFull, fits ? (1u << excl) : 0u);
+    const int used = __shfl_sync(kFull, incl, ncell - 1);
+    const bool active = lane < used;
+    const int seg = active ? __popc(head & (kFull >> (31 - lane))) - 1 : 0;
+    const int sstart = __shfl_sync(kFull, excl, seg);
+    const int cmt = __shfl_sync(kFull, mt, seg);
+    const int cm = cmt & kMetaPlanes;
+    const int64_t ccell = base + seg;
+    const int f = lane - sstart;
+    const bool has = active && f < cm;
+    V4<T> p = {};
+    T r = T(0);
+    if (active) {
+      p = sxp[ccell];
+      r = p.w > T(0) ? sqrt(p.w) : T(0);
+    }
+    if (has) plane_of(f, ccell, p, cmt, r, sxp, cand, kmax, box, pl[lane], pd[lane], pj[lane]);
+    __syncwarp();
+    CellAcc<T> a = {};
+    Facet<T> fo = {};
+    if (has) {
+      fo = facet_eval(pl + sstart, cm, f, p.w, r);
+      if (fo.overflow) set_error(err, POT_ERR_POLYGON_OVERFLOW, ccell);
+      acc_facet(a, pl[lane], pd[lane], pj[lane], fo);
+    }
+    const int last = active ? sstart + (cm > 1 ? cm : 1) - 1 : lane;
+    seg_reduce(a, lane, last);
+    const unsigned negm = __ballot_sync(kFull, has && pl[lane].w < T(0));
+    const bool emit = has && pj[lane] >= 0 && fo.area > Real<T>::kEmitArea * p.w;
+    const unsigned emm = __ballot_sync(kFull, emit);
+    const int len = last - sstart + 1;
+    const unsigned segmask = active ? ((len == 32 ? kFull : ((1u << len) - 1u)) << sstart) : 0u;
+    if (emit) {
+      int rank = __popc(emm & segmask & ((1u << lane) - 1u));
+      int64_t at = ccell * kmax + rank;
+      cand[at] = pj[lane];
+      stage_vals[at] = -fo.area / (T(2) * pd[lane]);
+    }
+    if (active && lane == sstart)
+      write_cell(ccell, p, (cmt & kMetaEmpty) != 0, (negm & segmask) == 0u, a,
+                 __popc(emm & segmask), o);
+    __syncwarp();
+    base += ncell;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// reductions, CSR, scatter
+
+template <typename T>
+__global__ void k_resid(int64_t n, const T* __restrict__ vol, const double* __restrict__ snu,
+                        const int32_t* __restrict__ meta, double* part) {
+  double emax = 0.0, ss = 0.0, vmin = 1e300, nemp = 0.0, npl = 0.0, mpl = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double v = (double)vol[i], nu = snu[i];
+    double g = nu - v;
+    if (nu > 0.0) emax = fmax(emax, fabs(g) / nu);
+    ss += g * g;
+    vmin = fmin(vmin, v);
+    nemp += v <= 0.0 ? 1.0 : 0.0;
+    int m = meta[i] & kMetaPlanes;
+    npl += m;
+    mpl = fmax(mpl, (double)m);
+  }
+  __shared__ double sh[6][8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int off = 16; off > 0; off >>= 1) {
+    emax = fmax(emax, __shfl_down_sync(kFull, emax, off));
+    ss += __shfl_down_sync(kFull, ss, off);
+    vmin = fmin(vmin, __shfl_down_sync(kFull, vmin, off));
+    nemp += __shfl_down_sync(kFull, nemp, off);
+    npl += __shfl_down_sync(kFull, npl, off);
+    mpl = fmax(mpl, __shfl_down_sync(kFull, mpl, off));
+  }
+  if (lane == 0) {
+    sh[0][wid] = emax; sh[1][wid] = ss; sh[2][wid] = vmin;
+    sh[3][wid] = nemp; sh[4][wid] = npl; sh[5][wid] = mpl;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int nw = blockDim.x >> 5;
+    for (int w = 1; w < nw; w++) {
+      sh[0][0] = fmax(sh[0][0], sh[0][w]);
+      sh[1][0] += sh[1][w];
+      sh[2][0] = fmin(sh[2][0], sh[2][w]);
+      sh[3][0] += sh[3][w];
+      sh[4][0] += sh[4][w];
+      sh[5][0] = fmax(sh[5][0], sh[5][w]);
+    }
+    for (int k = 0; k < 6; k++) part[blockIdx.x * 6 + k] = sh[k][0];
+  }
+}
+
+__global__ void k_resid_final(const double* __restrict__ part, int nb, double* out) {
+  if (threadIdx.x != 0) return;
+  double r[6] = {0.0, 0.0, 1e300, 0.0, 0.0, 0.0};
+  for (int b = 0; b < nb; b++) {
+    r[0] = fmax(r[0], part[6 * b + 0]);
+    r[1] += part[6 * b + 1];
+    r[2] = fmin(r[2], part[6 * b + 2]);
+    r[3] += part[6 * b + 3];
+    r[4] += part[6 * b + 4];
+    r[5] = fmax(r[5], part[6 * b + 5]);
+  }
+  for (int k = 0; k < 6; k++) out[k] = r[k];
+}
+
+template <typename T>
+__global__ void k_csr_copy(int64_t n, const int32_t* __restrict__ row_ptr,
+                           const int32_t* __restrict__ cand, const T* __restrict__ stage, int kmax,
+                           int32_t* cols, T* vals) {
+  // 8 threads per row
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t s = t >> 3;
+  int sub = (int)(t & 7);
+  if (s >= n) return;
+  int a = row_ptr[s], cnt = row_ptr[s + 1] - a;
+  for (int k = sub; k < cnt; k += 8) {
+    cols[a + k] = cand[s * kmax + k];
+    vals[a + k] = stage[s * kmax + k];
+  }
+}
+
+__global__ void k_user_count(int64_t n, const int32_t* __restrict__ iperm,
+                             const int32_t* __restrict__ row_cnt, int32_t* ucnt) {
+  int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= n) return;
+  ucnt[o] = row_cnt[iperm[o]] + 1;
+}
+
+template <typename T>
+__global__ void k_user_rows(int64_t n, const int32_t* __restrict__ iperm,
+                            const int32_t* __restrict__ perm, const int32_t* __restrict__ row_ptr,
+                            const int32_t* __restrict__ cand, const T* __restrict__ stage,
+                            const T* __restrict__ diag, int kmax, int32_t* cols, T* vals) {
+  int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= n) return;
+  const int64_t s = iperm[o];
+  const int a = row_ptr[o];
+  const int cnt = row_ptr[o + 1] - a;
+  cols[a] = (int32_t)o;
+  vals[a] = diag[s];
+  for (int k = 1; k < cnt; k++) {
+    int c = perm[cand[s * kmax + (k - 1)]];
+    T v = stage[s * kmax + (k - 1)];
+    int j = a + k - 1;
+    while (j >= a && cols[j] > c) {  // insertion into the sorted prefix
+      cols[j + 1] = cols[j];
+      vals[j + 1] = vals[j];
+      j--;
+    }
+    cols[j + 1] = c;
+    vals[j + 1] = v;
+  }
+}
+
+template <typename T>
+__global__ void k_unsort(int64_t n, const int32_t* __restrict__ perm, const T* __restrict__ vol,
+                         const double* __restrict__ grad, const T* __restrict__ cen,
+                         const T* __restrict__ karea, const V4<T>* __restrict__ sxp, T* o_vol,
+                         double* o_grad, T* o_cen, T* o_karea, T* o_psi) {
+  int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  int64_t o = perm[s];
+  if (o_vol) o_vol[o] = vol[s];
+  if (o_grad) o_grad[o] = grad[s];
+  if (o_karea) o_karea[o] = karea[s];
+  if (o_cen) {
+    o_cen[3 * o + 0] = cen[3 * s + 0];
+    o_cen[3 * o + 1] = cen[3 * s + 1];
+    o_cen[3 * o + 2] = cen[3 * s + 2];
+  }
+  if (o_psi) o_psi[o] = sxp[s].w;
+}
+
+template <typename T>
+__global__ void k_psi_update(int64_t n, const T* __restrict__ base, const T* __restrict__ u,
+                             T alpha, V4<T>* sxp, T* psi_max) {
+  int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  T v = T(0);
+  if (s < n) {
+    v = base[s] + alpha * u[s];
+    sxp[s].w = v;
+  }
+  T m = v > T(0) ? v : T(0);
+  for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_down_sync(kFull, m, off));
+  if ((threadIdx.x & 31) == 0 && m > T(0)) {
+    if (sizeof(T) == 4)
+      atomicMax((int*)psi_max, __float_as_int((float)m));
+    else
+      atomicMax((unsigned long long*)psi_max, (unsigned long long)__double_as_longlong((double)m));
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host side
+
+template <typename T>
+int cells_eval(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* dom, bool want_grad) {
+  Work<T>& w = ctx->work<T>();
+  if (!w.grid_valid) return POT_ERR_INVALID_ARG;
+  Box<T> box;
+  for (int k = 0; k < 3; k++) {
+    box.lo[k] = (T)dom->lo[k];
+    box.hi[k] = (T)dom->hi[k];
+  }
+  k_candidates<T><<<blocks_for(n, 256), 256, 0, st>>>(n, w.sxp, ctx->cell_start, w.grid, box,
+                                                       w.psi_max, ctx->k_max, ctx->cand, ctx->meta,
+                                                       ctx->err);
+  CellOut o;
+  o.vol = w.vol;
+  o.karea = w.karea;
+  o.diag = w.diag;
+  o.cen = w.cen;
+  o.row_cnt = ctx->row_cnt;
+  o.grad = want_grad ? ctx->grad : nullptr;
+  o.snu = ctx->snu;
+  int64_t warps = (n + kCellsPerWarp - 1) / kCellsPerWarp;
+  int blocks = (int)((warps + kCellWarps - 1) / kCellWarps);
+  k_cells<T><<<blocks, kCellWarps * 32, 0, st>>>(n, w.sxp, ctx->meta, ctx->cand, ctx->k_max, box,
+                                                 w.stage_vals, o, ctx->err);
+  POT_CUDA(cudaGetLastError());
+  return POT_OK;
+}
+
+template <typename T>
+int residuals(pot_ctx* ctx, cudaStream_t st, int64_t n, double out[6]) {
+  Work<T>& w = ctx->work<T>();
+  k_resid<T><<<kRedBlocks, 256, 0, st>>>(n, w.vol, ctx->snu, ctx->meta, ctx->red);
+  k_resid_final<<<1, 32, 0, st>>>(ctx->red, kRedBlocks, ctx->red_out);
+  POT_CUDA(cudaMemcpyAsync(ctx->h_pinned, ctx->red_out, 6 * sizeof(double),
+                           cudaMemcpyDeviceToHost, st));
+  POT_CUDA(cudaStreamSynchronize(st));
+  for (int k = 0; k < 6; k++) out[k] = ctx->h_pinned[k];
+  return POT_OK;
+}
+
+int read_status(pot_ctx* ctx, cudaStream_t st, int64_t* site) {
+  int32_t* h = (int32_t*)(ctx->h_pinned + 8);
+  POT_CUDA(cudaMemcpyAsync(h, ctx->err, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  POT_CUDA(cudaStreamSynchronize(st));
+  int code = h[0];
+  int32_t s = h[1];
+  if (site) *site = -1;
+  if (code != 0) {
+    int32_t reset[2] = {0, 0x7fffffff};
+    POT_CUDA(cudaMemcpy(ctx->err, reset, sizeof(reset), cudaMemcpyHostToDevice));
+    if (site && s >= 0 && s < ctx->n_max) {
+      int32_t o = -1;
+      POT_CUDA(cudaMemcpy(&o, ctx->perm + s, sizeof(int32_t), cudaMemcpyDeviceToHost));
+      *site = o;
+    }
+  }
+  return code;
+}
+
+template <typename T>
+int csr_compact(pot_ctx* ctx, cudaStream_t st, int64_t n, int64_t* nnz_off) {
+  Work<T>& w = ctx->work<T>();
+  POT_CHECK(scan_exclusive(ctx, st, ctx->row_cnt, ctx->row_ptr, n));
+  k_csr_copy<T><<<blocks_for(n * 8, 256), 256, 0, st>>>(n, ctx->row_ptr, ctx->cand, w.stage_vals,
+                                                         ctx->k_max, ctx->csr_cols, w.csr_vals);
+  int32_t* h = (int32_t*)(ctx->h_pinned + 8);
+  POT_CUDA(cudaMemcpyAsync(h, ctx->row_ptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  POT_CUDA(cudaStreamSynchronize(st));
+  *nnz_off = h[0];
+  return POT_OK;
+}
+
+template <typename T>
+int csr_user(pot_ctx* ctx, cudaStream_t st, int64_t n, int32_t* row_ptr, int32_t* cols, T* vals,
+             int64_t cap, int64_t* nnz) {
+  Work<T>& w = ctx->work<T>();
+  k_user_count<<<blocks_for(n, 256), 256, 0, st>>>(n, ctx->iperm, ctx->row_cnt, ctx->ucnt);
+  POT_CHECK(scan_exclusive(ctx, st, ctx->ucnt, row_ptr, n));
+  int32_t* h = (int32_t*)(ctx->h_pinned + 8);
+  POT_CUDA(cudaMemcpyAsync(h, row_ptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  POT_CUDA(cudaStreamSynchronize(st));
+  *nnz = h[0];
+  if (*nnz > cap) return POT_ERR_CAPACITY;
+  k_user_rows<T><<<blocks_for(n, 128), 128, 0, st>>>(n, ctx->iperm, ctx->perm, row_ptr, ctx->cand,
+                                                      w.stage_vals, w.diag, ctx->k_max, cols, vals);
+  POT_CUDA(cudaGetLastError());
+  return POT_OK;
+}
+
+template <typename T>
+int unsort_outputs(pot_ctx* ctx, cudaStream_t st, int64_t n, T* vol, double* grad, T* cen,
+                   T* karea, T* psi) {
+  Work<T>& w = ctx->work<T>();
+  k_unsort<T><<<blocks_for(n, 256), 256, 0, st>>>(n, ctx->perm, w.vol, ctx->grad, w.cen, w.karea,
+                                                   w.sxp, vol, grad, cen, karea, psi);
+  POT_CUDA(cudaGetLastError());
+  return POT_OK;
+}
+
+template <typename T>
+int psi_update(pot_ctx* ctx, cudaStream_t st, int64_t n, double alpha) {
+  Work<T>& w = ctx->work<T>();
+  POT_CUDA(cudaMemsetAsync(w.psi_max, 0, sizeof(T), st));
+  k_psi_update<T><<<blocks_for(n, 256), 256, 0, st>>>(n, w.psi_base, w.u, (T)alpha, w.sxp,
+                                                       w.psi_max);
+  POT_CUDA(cudaGetLastError());
+  return POT_OK;
+}
+
+#define POT_INST(T)                                                                              \
+  template int cells_eval<T>(pot_ctx*, cudaStream_t, int64_t, const pot_domain*, bool);          \
+  template int residuals<T>(pot_ctx*, cudaStream_t, int64_t, double*);                          \
+  template int csr_compact<T>(pot_ctx*, cudaStream_t, int64_t, int64_t*);                       \
+  template int csr_user<T>(pot_ctx*, cudaStream_t, int64_t, int32_t*, int32_t*, T*, int64_t,    \
+                           int64_t*);                                                           \
+  template int unsort_outputs<T>(pot_ctx*, cudaStream_t, int64_t, T*, double*, T*, T*, T*);     \
+  template int psi_update<T>(pot_ctx*, cudaStream_t, int64_t, double);
+POT_INST(float)
+POT_INST(double)
+
+}  // namespace pot

@@ -1,0 +1,154 @@
+// Grid build: bucket the sites by a uniform grid over the box, sort them by
+// cell (counting sort; ties in caller order, so the result is deterministic)
+// and gather positions, weights and targets into grid order.
+//
+// The grid replaces the paper's geometry-driven neighbour search (Sec. 4,
+// "Finding Contributing Neighbors") by an exact radius query: site j can
+// clip the cell of i only if |p_i - p_j| < r_i + r_j, so a search of radius
+// r_i + r_max around p_i is complete for any cell size.
+#include <math.h>
+
+#include "pot_internal.cuh"
+
+namespace pot {
+namespace {
+
+template <typename T>
+__device__ __forceinline__ int cell_coord(T x, T lo, T inv_cs, int dim) {
+  T f = (x - lo) * inv_cs;
+  int c = (f < T(0)) ? 0 : (int)f;  // NaN-safe lower clamp
+  return c >= dim ? dim - 1 : c;
+}
+
+template <typename T>
+__global__ void k_psi_max_in(const T* __restrict__ psi, int64_t n, T* out) {
+  T m = T(0);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    m = fmax(m, psi[i]);
+  for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_down_sync(kFull, m, off));
+  if ((threadIdx.x & 31) == 0) {
+    if (sizeof(T) == 4)
+      atomicMax((int*)out, __float_as_int((float)m));
+    else
+      atomicMax((unsigned long long*)out, (unsigned long long)__double_as_longlong((double)m));
+  }
+}
+
+template <typename T>
+__global__ void k_keys(const T* __restrict__ pos, int64_t n, GridParams<T> g, uint32_t* keys,
+                       int32_t* count) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int cx = cell_coord(pos[3 * i + 0], g.lo[0], g.inv_cs, g.dim[0]);
+  int cy = cell_coord(pos[3 * i + 1], g.lo[1], g.inv_cs, g.dim[1]);
+  int cz = cell_coord(pos[3 * i + 2], g.lo[2], g.inv_cs, g.dim[2]);
+  uint32_t key = ((uint32_t)cz * g.dim[1] + cy) * g.dim[0] + cx;
+  keys[i] = key;
+  atomicAdd(&count[key], 1);
+}
+
+__global__ void k_scatter(const uint32_t* __restrict__ keys, int64_t n,
+                          const int32_t* __restrict__ start, int32_t* cursor, int32_t* perm) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t k = keys[i];
+  int slot = start[k] + atomicAdd(&cursor[k], 1);
+  perm[slot] = (int32_t)i;
+}
+
+// order each grid cell's sites by caller index (cells hold a few sites)
+__global__ void k_cell_sort(const int32_t* __restrict__ start, int64_t ncell, int32_t* perm) {
+  int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  int a = start[c], b = start[c + 1];
+  for (int i = a + 1; i < b; i++) {
+    int v = perm[i];
+    int j = i - 1;
+    while (j >= a && perm[j] > v) {
+      perm[j + 1] = perm[j];
+      j--;
+    }
+    perm[j + 1] = v;
+  }
+}
+
+template <typename T>
+__global__ void k_gather(const int32_t* __restrict__ perm, int64_t n, const T* __restrict__ pos,
+                         const T* __restrict__ psi, const double* __restrict__ targets,
+                         V4<T>* sxp, T* psi_base, double* snu, int32_t* iperm) {
+  int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  int i = perm[s];
+  V4<T> v;
+  v.x = pos[3 * (int64_t)i + 0];
+  v.y = pos[3 * (int64_t)i + 1];
+  v.z = pos[3 * (int64_t)i + 2];
+  v.w = psi[i];
+  sxp[s] = v;
+  psi_base[s] = v.w;
+  snu[s] = targets ? targets[i] : 0.0;
+  iperm[i] = (int32_t)s;
+}
+
+}  // namespace
+
+template <typename T>
+int grid_build(pot_ctx* ctx, cudaStream_t st, int64_t n, const T* pos, const T* psi,
+               const double* targets, const pot_domain* dom) {
+  Work<T>& w = ctx->work<T>();
+  // largest weight -> cell size (one host read)
+  POT_CUDA(cudaMemsetAsync(w.psi_max, 0, sizeof(T), st));
+  k_psi_max_in<T><<<kRedBlocks, 256, 0, st>>>(psi, n, w.psi_max);
+  POT_CUDA(cudaMemcpyAsync(ctx->h_pinned, w.psi_max, sizeof(T), cudaMemcpyDeviceToHost, st));
+  POT_CUDA(cudaStreamSynchronize(st));
+  double pmax = sizeof(T) == 4 ? (double)*(float*)ctx->h_pinned : *(double*)ctx->h_pinned;
+  if (!(pmax >= 0.0) || isinf(pmax)) return POT_ERR_INVALID_ARG;
+  double ext[3], emax = 0.0;
+  for (int k = 0; k < 3; k++) {
+    ext[k] = dom->hi[k] - dom->lo[k];
+    emax = fmax(emax, ext[k]);
+  }
+  // cell = diameter of the largest ball: the 27-cell block around a site
+  // holds every candidate; never more cells than the grid capacity
+  double cs = 2.0 * sqrt(pmax);
+  cs = fmax(cs, emax / 1024.0);
+  int dim[3];
+  for (;;) {
+    int64_t tot = 1;
+    for (int k = 0; k < 3; k++) {
+      dim[k] = (int)fmax(1.0, ceil(ext[k] / cs));
+      tot *= dim[k];
+    }
+    if (tot <= ctx->grid_cap) break;
+    cs *= 1.25;
+  }
+  GridParams<T> g;
+  for (int k = 0; k < 3; k++) {
+    g.lo[k] = (T)dom->lo[k];
+    g.dim[k] = dim[k];
+  }
+  g.cs = (T)cs;
+  g.inv_cs = (T)(1.0 / cs);
+  int64_t ncell = (int64_t)dim[0] * dim[1] * dim[2];
+  POT_CUDA(cudaMemsetAsync(ctx->cell_count, 0, sizeof(int32_t) * (ncell + 1), st));
+  k_keys<T><<<blocks_for(n, 256), 256, 0, st>>>(pos, n, g, ctx->keys, ctx->cell_count);
+  POT_CHECK(scan_exclusive(ctx, st, ctx->cell_count, ctx->cell_start, ncell));
+  POT_CUDA(cudaMemsetAsync(ctx->cell_count, 0, sizeof(int32_t) * (ncell + 1), st));
+  k_scatter<<<blocks_for(n, 256), 256, 0, st>>>(ctx->keys, n, ctx->cell_start, ctx->cell_count,
+                                                  ctx->perm);
+  k_cell_sort<<<blocks_for(ncell, 256), 256, 0, st>>>(ctx->cell_start, ncell, ctx->perm);
+  k_gather<T><<<blocks_for(n, 256), 256, 0, st>>>(ctx->perm, n, pos, psi, targets, w.sxp,
+                                                  w.psi_base, ctx->snu, ctx->iperm);
+  POT_CUDA(cudaGetLastError());
+  w.grid = g;
+  w.grid_valid = true;
+  return POT_OK;
+}
+
+template int grid_build<float>(pot_ctx*, cudaStream_t, int64_t, const float*, const float*,
+                               const double*, const pot_domain*);
+template int grid_build<double>(pot_ctx*, cudaStream_t, int64_t, const double*, const double*,
+                                const double*, const pot_domain*);
+
+}  // namespace pot

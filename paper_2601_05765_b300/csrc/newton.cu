@@ -1,0 +1,245 @@
+// Damped Newton with KMT steps (Algorithm 1) and the explicit fluid step
+// (Sec. 5), driven from the host; every per-site step runs in the kernels of
+// cells.cu / pcg.cu.  The only device-to-host traffic per Newton iteration is
+// the FP64 residual summary (max relative error, squared l2 norm, min volume)
+// read after each cell evaluation, and the PCG done flag once per chunk.
+//
+// Readings of Algorithm 1 (its printed form is garbled):
+//   - the Newton system is M u = nu - V(psi), M = -grad^2 K (Eq. 2);
+//   - the KMT step halves alpha from 1 until min V(psi + alpha u) >= eps0 and
+//     ||nu - V(psi + alpha u)||_2 <= (1 - alpha/2) ||nu - V(psi)||_2, with
+//     eps0 = 1/2 min(min nu, min V(psi_start));
+//   - the start is the given psi (psi = 0 would give empty cells);
+//   - convergence: max_i |V_i - nu_i| / nu_i <= tol (relative, Sec. 7).
+#include <chrono>
+#include <math.h>
+
+#include "pot_internal.cuh"
+
+namespace pot {
+namespace {
+
+template <typename T>
+__global__ void k_accept(int64_t n, const V4<T>* __restrict__ sxp, T* base) {
+  int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < n) base[s] = sxp[s].w;
+}
+
+__global__ void k_nu_min(int64_t n, const double* __restrict__ snu, double* part) {
+  double m = 1e300;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    m = fmin(m, snu[i]);
+  for (int off = 16; off > 0; off >>= 1) m = fmin(m, __shfl_down_sync(kFull, m, off));
+  __shared__ double sh[8];
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); w++) m = fmin(m, sh[w]);
+    part[blockIdx.x] = m;
+  }
+}
+
+__global__ void k_min_final(const double* __restrict__ part, int nb, double* out) {
+  if (threadIdx.x) return;
+  double m = 1e300;
+  for (int b = 0; b < nb; b++) m = fmin(m, part[b]);
+  *out = m;
+}
+
+// x <- x + dt v, clamped into [lo+m, hi-m]; velocity through a wall -> 0
+template <typename T>
+__global__ void k_advect(int64_t n, T* pos, T* vel, T dt, Box<T> box, T margin) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    T x = pos[3 * i + k] + dt * vel[3 * i + k];
+    T v = vel[3 * i + k];
+    T lo = box.lo[k] + margin, hi = box.hi[k] - margin;
+    if (x < lo) {
+      x = lo;
+      if (v < T(0)) v = T(0);
+    } else if (x > hi) {
+      x = hi;
+      if (v > T(0)) v = T(0);
+    }
+    pos[3 * i + k] = x;
+    vel[3 * i + k] = v;
+  }
+}
+
+// v <- v + dt (g + (c_i - x_i) / eps^2)  (pressure spring, Sec. 5); psi out
+template <typename T>
+__global__ void k_velocity(int64_t n, const int32_t* __restrict__ perm,
+                           const V4<T>* __restrict__ sxp, const T* __restrict__ cen,
+                           const T* __restrict__ psi_base, T* vel, T* psi, T dt, T inv_eps2,
+                           T gx, T gy, T gz) {
+  int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  int64_t o = perm[s];
+  const V4<T> p = sxp[s];
+  vel[3 * o + 0] += dt * (gx + (cen[3 * s + 0] - p.x) * inv_eps2);
+  vel[3 * o + 1] += dt * (gy + (cen[3 * s + 1] - p.y) * inv_eps2);
+  vel[3 * o + 2] += dt * (gz + (cen[3 * s + 2] - p.z) * inv_eps2);
+  psi[o] = psi_base[s];
+}
+
+template <typename T>
+__global__ void k_unsort_psi(int64_t n, const int32_t* __restrict__ perm, const T* __restrict__ base,
+                             T* psi) {
+  int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < n) psi[perm[s]] = base[s];
+}
+
+double now_ms() {
+  return std::chrono::duration<double, std::milli>(
+             std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+struct EvTimer {
+  cudaEvent_t a, b;
+  cudaStream_t st;
+  EvTimer(pot_ctx* ctx, int k, cudaStream_t s) : a(ctx->ev[2 * k]), b(ctx->ev[2 * k + 1]), st(s) {
+    cudaEventRecord(a, st);
+  }
+  double stop() {
+    cudaEventRecord(b, st);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    return ms;
+  }
+};
+
+// one full evaluation + status + residual summary
+template <typename T>
+int eval_and_reduce(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* dom,
+                    double res[6], pot_solve_stats* S) {
+  EvTimer tm(ctx, 0, st);
+  POT_CHECK(cells_eval<T>(ctx, st, n, dom, true));
+  POT_CHECK(residuals<T>(ctx, st, n, res));
+  S->ms_cells += tm.stop();
+  S->cell_evals++;
+  int64_t site;
+  int code = read_status(ctx, st, &site);
+  if (code) return code;
+  return POT_OK;
+}
+
+}  // namespace
+
+// Newton solve in sorted space.  Requires grid_build (sxp.w = psi_base = start).
+template <typename T>
+int newton_sorted(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* dom,
+                  const pot_params* P, pot_solve_stats* S) {
+  Work<T>& w = ctx->work<T>();
+  double res[6];
+  POT_CHECK(eval_and_reduce<T>(ctx, st, n, dom, res, S));
+  S->err_start = res[0];
+  S->err_max = res[0];
+  S->err_l2 = sqrt(res[1]);
+  if (!(res[2] > 0.0)) return POT_ERR_EMPTY_CELL_AT_START;
+  k_nu_min<<<kRedBlocks, 256, 0, st>>>(n, ctx->snu, ctx->red);
+  k_min_final<<<1, 32, 0, st>>>(ctx->red, kRedBlocks, ctx->red_out);
+  POT_CUDA(cudaMemcpyAsync(ctx->h_pinned, ctx->red_out, sizeof(double), cudaMemcpyDeviceToHost, st));
+  POT_CUDA(cudaStreamSynchronize(st));
+  const double eps0 = 0.5 * fmin(ctx->h_pinned[0], res[2]);
+  double err = res[0], gnorm = sqrt(res[1]);
+  for (int it = 0;; it++) {
+    S->newton_iters = it;
+    S->err_max = err;
+    S->err_l2 = gnorm;
+    if (err <= P->tol) return POT_OK;
+    if (it >= P->max_newton) return POT_ERR_NOT_CONVERGED;
+    int64_t nnz_off = 0;
+    POT_CHECK(csr_compact<T>(ctx, st, n, &nnz_off));
+    S->nnz = nnz_off + n;
+    // inexact Newton: the linear residual only needs to be small against
+    // the distance still to go to the tolerance
+    double rtol = P->pcg_rtol;
+    if (!(rtol > 0.0)) rtol = fmin(0.1, fmax(1e-7, 0.1 * P->tol / err));
+    int iters = 0;
+    {
+      EvTimer tm(ctx, 1, st);
+      int ps = pcg_solve<T>(ctx, st, n, nnz_off, rtol, P->max_pcg, P->pcg_chunk, &iters, nullptr);
+      S->ms_pcg += tm.stop();
+      S->pcg_iters += iters;
+      if (ps != POT_OK) return ps;
+    }
+    double alpha = 1.0;
+    bool accepted = false;
+    for (int hv = 0; hv <= P->max_halvings; hv++) {
+      POT_CHECK(psi_update<T>(ctx, st, n, alpha));
+      POT_CHECK(eval_and_reduce<T>(ctx, st, n, dom, res, S));
+      if (res[2] >= eps0 && sqrt(res[1]) <= (1.0 - 0.5 * alpha) * gnorm) {
+        accepted = true;
+        break;
+      }
+      alpha *= 0.5;
+      S->halvings++;
+    }
+    if (!accepted) {
+      // back to the last accepted weights, with their cells
+      POT_CHECK(psi_update<T>(ctx, st, n, 0.0));
+      POT_CHECK(eval_and_reduce<T>(ctx, st, n, dom, res, S));
+      return POT_ERR_LINESEARCH_FAILED;
+    }
+    k_accept<T><<<blocks_for(n, 256), 256, 0, st>>>(n, w.sxp, w.psi_base);
+    err = res[0];
+    gnorm = sqrt(res[1]);
+  }
+}
+
+template <typename T>
+int newton_solve(pot_ctx* ctx, cudaStream_t st, int64_t n, const T* pos, const double* targets,
+                 T* psi_inout, const pot_domain* dom, const pot_params* P, pot_solve_stats* S) {
+  double t0 = now_ms();
+  POT_CHECK(grid_build<T>(ctx, st, n, pos, psi_inout, targets, dom));
+  S->grid_builds++;
+  int status = newton_sorted<T>(ctx, st, n, dom, P, S);
+  Work<T>& w = ctx->work<T>();
+  if (status == POT_OK || status == POT_ERR_NOT_CONVERGED || status == POT_ERR_LINESEARCH_FAILED)
+    k_unsort_psi<T><<<blocks_for(n, 256), 256, 0, st>>>(n, ctx->perm, w.psi_base, psi_inout);
+  POT_CUDA(cudaStreamSynchronize(st));
+  S->status = status;
+  S->ms_total = now_ms() - t0;
+  return status;
+}
+
+template <typename T>
+int fluid_step(pot_ctx* ctx, cudaStream_t st, int64_t n, T* pos, T* vel, T* psi,
+               const double* targets, const pot_domain* dom, const pot_params* P,
+               pot_solve_stats* S) {
+  double t0 = now_ms();
+  Box<T> box;
+  for (int k = 0; k < 3; k++) {
+    box.lo[k] = (T)dom->lo[k];
+    box.hi[k] = (T)dom->hi[k];
+  }
+  k_advect<T><<<blocks_for(n, 256), 256, 0, st>>>(n, pos, vel, (T)P->dt, box, (T)P->wall_margin);
+  POT_CHECK(grid_build<T>(ctx, st, n, pos, psi, targets, dom));
+  S->grid_builds++;
+  int status = newton_sorted<T>(ctx, st, n, dom, P, S);
+  if (status == POT_OK || status == POT_ERR_NOT_CONVERGED || status == POT_ERR_LINESEARCH_FAILED) {
+    Work<T>& w = ctx->work<T>();
+    k_velocity<T><<<blocks_for(n, 256), 256, 0, st>>>(
+        n, ctx->perm, w.sxp, w.cen, w.psi_base, vel, psi, (T)P->dt, (T)(1.0 / (P->eps * P->eps)),
+        (T)P->gravity[0], (T)P->gravity[1], (T)P->gravity[2]);
+  }
+  POT_CUDA(cudaStreamSynchronize(st));
+  S->status = status;
+  S->ms_total = now_ms() - t0;
+  return status;
+}
+
+#define POT_NINST(T)                                                                             \
+  template int newton_solve<T>(pot_ctx*, cudaStream_t, int64_t, const T*, const double*, T*,    \
+                               const pot_domain*, const pot_params*, pot_solve_stats*);         \
+  template int fluid_step<T>(pot_ctx*, cudaStream_t, int64_t, T*, T*, T*, const double*,        \
+                             const pot_domain*, const pot_params*, pot_solve_stats*);
+POT_NINST(float)
+POT_NINST(double)
+
+}  // namespace pot

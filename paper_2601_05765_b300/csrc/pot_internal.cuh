@@ -1,0 +1,248 @@
+// Internal declarations of libpot.so (not part of the C ABI).
+//
+// Data layout in HBM.  Inside the library every per-site array is in
+// grid-sorted order ("sorted space"); the C ABI maps to and from the
+// caller's order.
+//   sxp[s]      V4<T> (x, y, z, psi) of the s-th site in grid order
+//   perm[s]     caller index of sorted site s; iperm is its inverse
+//   cell_start  first sorted site of each grid cell (exclusive scan of counts)
+//   cand        per cell up to k_max sorted indices of the bisectors that cut
+//               its ball (row s at s*k_max, ascending); the cell kernel
+//               rewrites each row in place into its Hessian column list
+//   meta[s]     cutting-plane count | wall mask << 8 | flags
+//   stage_vals  per cell the off-diagonal Hessian values of its row (row s at s*k_max)
+//   vol, karea, diag, cen  per-cell outputs of the cell kernel
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/pot.h"
+
+namespace pot {
+
+constexpr int kWarp = 32;
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kMaxK = 64;          // cutting bisectors per cell (k_max <= 64)
+constexpr int kPlaneCap = kMaxK + 6;
+constexpr int kMaxLines = 24;      // edges of one facet polygon
+constexpr int kCellWarps = 4;      // warps per block of the cell kernel
+constexpr int kCellsPerWarp = 32;  // cells per warp task
+
+// meta word written by the candidate kernel
+constexpr int kMetaPlanes = 0xff;
+constexpr int kMetaWallShift = 8;
+constexpr int kMetaEmpty = 1 << 14;
+
+// device status words: [0] error code (max over sites), [1] smallest site with that error
+enum { kErrCode = 0, kErrSite = 1 };
+
+template <typename T>
+struct alignas(4 * sizeof(T)) V4 {
+  T x, y, z, w;
+};
+
+template <typename T>
+struct Real;
+template <>
+struct Real<float> {
+  // relative area (of psi_i) below which a bisector facet is not emitted
+  static constexpr float kEmitArea = 4e-7f;
+  // a plane exactly through the site moves outward by this fraction of r
+  static constexpr float kZeroShift = 9.313225746154785e-10f;  // 2^-30
+};
+template <>
+struct Real<double> {
+  static constexpr double kEmitArea = 1e-13;
+  static constexpr double kZeroShift = 9.094947017729282e-13;  // 2^-40
+};
+
+// Explicitly rounded arithmetic: the candidate kernel and the cell kernel
+// must take the same decisions on the same inputs, so the steps that decide
+// (squared distance, plane offset) are pinned against FMA contraction.
+__device__ __forceinline__ float r_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double r_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float r_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double r_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float r_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double r_sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float r_div(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ double r_div(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ float r_sqrt(float a) { return __fsqrt_rn(a); }
+__device__ __forceinline__ double r_sqrt(double a) { return __dsqrt_rn(a); }
+
+// Bisector (radical) plane of sites i and j seen from i (Eq. 1):
+// points y - p_i with y.n <= h, n = (p_j - p_i)/d,
+// h = (d^2 + psi_i - psi_j) / (2 d).  Returns d2 (0 for coincident sites).
+template <typename T>
+__device__ __forceinline__ T bisector(const V4<T>& pi, const V4<T>& pj, T& dx, T& dy, T& dz, T& d,
+                                      T& h) {
+  dx = r_sub(pj.x, pi.x);
+  dy = r_sub(pj.y, pi.y);
+  dz = r_sub(pj.z, pi.z);
+  T d2 = r_add(r_add(r_mul(dx, dx), r_mul(dy, dy)), r_mul(dz, dz));
+  d = r_sqrt(d2);
+  h = r_div(r_add(d2, r_sub(pi.w, pj.w)), r_add(d, d));
+  return d2;
+}
+
+// A plane exactly through the site is moved outward by r * kZeroShift: the
+// limit of the site moving into its own cell (stays right when several
+// planes meet at the site, e.g. a site on a box corner).
+template <typename T>
+__device__ __forceinline__ T fix_zero(T h, T r) {
+  return h == T(0) ? r * Real<T>::kZeroShift : h;
+}
+
+// Signed distance from the site to wall w (0..5 = -x,+x,-y,+y,-z,+z), positive inside.
+template <typename T>
+__device__ __forceinline__ T wall_offset(const V4<T>& p, int w, const T* lo, const T* hi) {
+  int ax = w >> 1;
+  T pk = ax == 0 ? p.x : (ax == 1 ? p.y : p.z);
+  return (w & 1) ? r_sub(hi[ax], pk) : r_sub(pk, lo[ax]);
+}
+
+template <typename T>
+struct Box {
+  T lo[3];
+  T hi[3];
+};
+
+// Grid over the domain box: cell (cx,cy,cz) has key (cz*dim1 + cy)*dim0 + cx.
+template <typename T>
+struct GridParams {
+  T lo[3];
+  T cs;
+  T inv_cs;
+  int dim[3];
+};
+
+// Per-precision workspace.
+template <typename T>
+struct Work {
+  V4<T>* sxp = nullptr;     // sorted (x,y,z,psi)
+  T* psi_base = nullptr;    // accepted psi (sorted)
+  T* vol = nullptr;
+  T* karea = nullptr;
+  T* diag = nullptr;
+  T* cen = nullptr;         // 3 per site
+  T* stage_vals = nullptr;  // n_max * k_max
+  T* csr_vals = nullptr;    // n_max * k_max (off-diagonal, compacted)
+  T* u = nullptr;           // Newton direction
+  T* x = nullptr;           // PCG vectors
+  T* r = nullptr;
+  T* z = nullptr;
+  T* p0 = nullptr;
+  T* p1 = nullptr;
+  T* q = nullptr;
+  T* vel_s = nullptr;       // sorted velocities, 3 per site
+  T* psi_max = nullptr;     // device scalar: max psi of the current evaluation
+  GridParams<T> grid{};
+  bool grid_valid = false;
+};
+
+}  // namespace pot
+
+struct pot_ctx {
+  int device = 0;
+  int64_t n_max = 0;
+  int32_t k_max = 0;
+  int32_t mask = 0;
+  int64_t grid_cap = 0;
+  int sm_count = 148;
+  uint32_t* keys = nullptr;
+  int32_t* perm = nullptr;
+  int32_t* iperm = nullptr;
+  int32_t* cell_count = nullptr;  // grid_cap + 1
+  int32_t* cell_start = nullptr;  // grid_cap + 1
+  int32_t* cand = nullptr;        // n_max * k_max
+  int32_t* meta = nullptr;
+  int32_t* row_cnt = nullptr;     // n_max + 1
+  int32_t* row_ptr = nullptr;     // n_max + 1
+  int32_t* ucnt = nullptr;        // n_max + 1 (caller-order row counts)
+  int32_t* csr_cols = nullptr;    // n_max * k_max
+  int32_t* scan_tmp = nullptr;
+  int64_t scan_tmp_len = 0;
+  double* snu = nullptr;          // sorted targets
+  double* grad = nullptr;         // sorted gradient nu - V
+  double* red = nullptr;          // reduction partials
+  double* red_out = nullptr;      // reduction results (device)
+  double* pcg_red = nullptr;      // PCG reduction partials
+  int32_t* pcg_ctl = nullptr;     // PCG control words
+  int32_t* err = nullptr;         // device status words
+  double* h_pinned = nullptr;     // pinned host scalars
+  cudaEvent_t ev[8] = {};
+  pot::Work<float> wf;
+  pot::Work<double> wd;
+  template <typename T>
+  pot::Work<T>& work();
+};
+
+template <>
+inline pot::Work<float>& pot_ctx::work<float>() { return wf; }
+template <>
+inline pot::Work<double>& pot_ctx::work<double>() { return wd; }
+
+namespace pot {
+
+#define POT_CUDA(call)                          \
+  do {                                          \
+    cudaError_t e_ = (call);                    \
+    if (e_ != cudaSuccess) return POT_ERR_CUDA; \
+  } while (0)
+
+#define POT_CHECK(call)          \
+  do {                           \
+    int s_ = (call);             \
+    if (s_ != POT_OK) return s_; \
+  } while (0)
+
+inline int blocks_for(int64_t n, int threads) { return (int)((n + threads - 1) / threads); }
+
+constexpr int kRedBlocks = 296;  // partial count of the deterministic reductions
+
+// exclusive scan of n int32 values: out[k] = sum_{i<k} in[i]; out[n] = total.
+// in may alias out.  Enqueued on the stream; no host sync.
+int scan_exclusive(pot_ctx* ctx, cudaStream_t st, const int32_t* in, int32_t* out, int64_t n);
+
+// Grid build, sort and gather into sorted space (grid.cu).  One host sync.
+template <typename T>
+int grid_build(pot_ctx* ctx, cudaStream_t st, int64_t n, const T* pos, const T* psi,
+               const double* targets, const pot_domain* dom);
+
+// Cell evaluation in sorted space (cells.cu): candidates + geometry.
+template <typename T>
+int cells_eval(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* dom, bool want_grad);
+
+// FP64 reductions over sorted cells:
+// out = {max |V-nu|/nu, sum (nu-V)^2, min V, #empty, #planes, max planes}.  Host sync.
+template <typename T>
+int residuals(pot_ctx* ctx, cudaStream_t st, int64_t n, double out[6]);
+
+// read and clear the device status word; returns a POT status
+int read_status(pot_ctx* ctx, cudaStream_t st, int64_t* site);
+
+// internal CSR (off-diagonal, sorted space) from the staged rows; nnz on host
+template <typename T>
+int csr_compact(pot_ctx* ctx, cudaStream_t st, int64_t n, int64_t* nnz_off);
+
+// caller-order CSR with the diagonal
+template <typename T>
+int csr_user(pot_ctx* ctx, cudaStream_t st, int64_t n, int32_t* row_ptr, int32_t* cols, T* vals,
+             int64_t cap, int64_t* nnz);
+
+// scatter sorted per-site outputs back to caller order (NULL outputs skipped)
+template <typename T>
+int unsort_outputs(pot_ctx* ctx, cudaStream_t st, int64_t n, T* vol, double* grad, T* cen,
+                   T* karea, T* psi);
+
+// psi_trial = psi_base + alpha * u written into sxp.w; updates psi_max
+template <typename T>
+int psi_update(pot_ctx* ctx, cudaStream_t st, int64_t n, double alpha);
+
+// PCG (pcg.cu): solve M u = grad (sorted space) into work.u
+template <typename T>
+int pcg_solve(pot_ctx* ctx, cudaStream_t st, int64_t n, int64_t nnz_off, double rtol, int max_iter,
+              int chunk, int* iters, double* rel_res);
+
+}  // namespace pot
