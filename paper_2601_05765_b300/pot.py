@@ -1,0 +1,275 @@
+"""Thin ctypes binding of libpot.so (C ABI in include/pot.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of libpot.so.  Tensors are torch CUDA tensors (PyTorch provides
+device memory and streams); float32 inputs select the mixed-precision entry
+points, float64 inputs the *_f64 ones.  Nothing here falls back to the CPU:
+if libpot.so is missing or a call fails, an exception is raised.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpot.so")
+
+POT_OK = 0
+STATUS = {
+    0: "POT_OK", 1: "POT_ERR_INVALID_ARG", 2: "POT_ERR_CUDA", 3: "POT_ERR_NEIGHBOUR_OVERFLOW",
+    4: "POT_ERR_COINCIDENT_SITES", 5: "POT_ERR_EMPTY_CELL_AT_START", 6: "POT_ERR_NOT_CONVERGED",
+    7: "POT_ERR_LINESEARCH_FAILED", 8: "POT_ERR_POLYGON_OVERFLOW", 9: "POT_ERR_CAPACITY",
+    10: "POT_ERR_PCG_BREAKDOWN",
+}
+UNIT_BOX = ((0.0, 0.0, 0.0), (1.0, 1.0, 1.0))
+
+
+class PotError(RuntimeError):
+    def __init__(self, code, where, stats=None):
+        self.code = code
+        self.stats = stats
+        super().__init__(f"{where}: {STATUS.get(code, code)}")
+
+
+class Domain(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3)]
+
+
+class Csr(ctypes.Structure):
+    _fields_ = [("row_ptr", ctypes.c_void_p), ("cols", ctypes.c_void_p), ("vals", ctypes.c_void_p),
+                ("cap", ctypes.c_int64), ("nnz", ctypes.c_int64)]
+
+
+class CellStats(ctypes.Structure):
+    _fields_ = [("n_empty", ctypes.c_int64), ("n_planes", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("error_site", ctypes.c_int64), ("max_planes", ctypes.c_int32),
+                ("ms_grid", ctypes.c_float), ("ms_cells", ctypes.c_float), ("ms_csr", ctypes.c_float)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_newton", ctypes.c_int32),
+                ("max_halvings", ctypes.c_int32), ("max_pcg", ctypes.c_int32),
+                ("pcg_chunk", ctypes.c_int32), ("pcg_rtol", ctypes.c_double),
+                ("dt", ctypes.c_double), ("eps", ctypes.c_double), ("gravity", ctypes.c_double * 3),
+                ("wall_margin", ctypes.c_double), ("warm_start", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class SolveStats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("newton_iters", ctypes.c_int32),
+                ("pcg_iters", ctypes.c_int32), ("halvings", ctypes.c_int32),
+                ("cell_evals", ctypes.c_int32), ("grid_builds", ctypes.c_int32),
+                ("err_max", ctypes.c_double), ("err_l2", ctypes.c_double),
+                ("err_start", ctypes.c_double), ("ms_total", ctypes.c_double),
+                ("ms_cells", ctypes.c_double), ("ms_pcg", ctypes.c_double),
+                ("nnz", ctypes.c_int64), ("mlp_used", ctypes.c_int32),
+                ("mlp_fallback", ctypes.c_int32)]
+
+
+def _as_dict(st):
+    return {name: getattr(st, name) for name, _ in st._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """Load libpot.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libpot.so not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I64, I32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+        L.pot_create.argtypes = [ctypes.POINTER(P), ctypes.c_int, I64, I32, I32]
+        L.pot_destroy.argtypes = [P]
+        L.pot_status_string.restype = ctypes.c_char_p
+        L.pot_status_string.argtypes = [ctypes.c_int]
+        L.pot_default_params.argtypes = [ctypes.POINTER(Params)]
+        L.pot_default_params.restype = None
+        for name in ("lgc_compute_cells", "lgc_compute_cells_f64"):
+            f = getattr(L, name)
+            f.argtypes = [P, P, I64, P, P, P, ctypes.POINTER(Domain), P, P, ctypes.POINTER(Csr), P, P,
+                          ctypes.POINTER(CellStats)]
+        for name in ("pot_newton_solve", "pot_newton_solve_f64"):
+            f = getattr(L, name)
+            f.argtypes = [P, P, I64, P, P, P, ctypes.POINTER(Domain), ctypes.POINTER(Params),
+                          ctypes.POINTER(SolveStats)]
+        for name in ("pot_fluid_step", "pot_fluid_step_f64"):
+            f = getattr(L, name)
+            f.argtypes = [P, P, I64, P, P, P, P, ctypes.POINTER(Domain), ctypes.POINTER(Params),
+                          ctypes.POINTER(SolveStats)]
+        for f in (L.pot_create, L.pot_destroy, L.lgc_compute_cells, L.lgc_compute_cells_f64,
+                  L.pot_newton_solve, L.pot_newton_solve_f64, L.pot_fluid_step, L.pot_fluid_step_f64):
+            f.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    lib().pot_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        if k == "gravity":
+            for i in range(3):
+                p.gravity[i] = v[i]
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def _domain(dom) -> Domain:
+    d = Domain()
+    for k in range(3):
+        d.lo[k] = float(dom[0][k])
+        d.hi[k] = float(dom[1][k])
+    return d
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev(t, dtype, shape, name, device):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if t.device != device:
+        raise ValueError(f"{name} is on {t.device}, context on {device}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return t.contiguous()
+
+
+class Context:
+    """A libpot context (workspace for up to n_max sites) on one device."""
+
+    def __init__(self, n_max: int, k_max: int = 64, device: int = 0, fp32: bool = True,
+                 fp64: bool = True):
+        self._h = ctypes.c_void_p()
+        self.device = torch.device("cuda", device)
+        self.n_max = int(n_max)
+        self.k_max = int(k_max)
+        mask = (1 if fp32 else 0) | (2 if fp64 else 0)
+        with torch.cuda.device(device):
+            code = lib().pot_create(ctypes.byref(self._h), device, self.n_max, self.k_max, mask)
+        if code != POT_OK:
+            raise PotError(code, "pot_create")
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            lib().pot_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def lgc_compute_cells(ctx: Context, pos, psi, targets=None, domain=UNIT_BOX, hessian=True,
+                      centroids=True, karea=True, csr_cap=None, stream=None, check=True):
+    """Generalized Laguerre cells (Eq. 1): volumes, gradient nu - V, CSR of
+    M = -grad^2 K (Eq. 2), centroids, free-surface areas.  Returns a dict of
+    CUDA tensors plus 'stats' and 'status'."""
+    dt = pos.dtype
+    if dt not in (torch.float32, torch.float64):
+        raise TypeError("pos must be float32 or float64")
+    n = int(pos.shape[0])
+    dev = ctx.device
+    pos = _dev(pos, dt, (n, 3), "pos", dev)
+    psi = _dev(psi, dt, (n,), "psi", dev)
+    if targets is not None:
+        targets = _dev(targets, torch.float64, (n,), "targets", dev)
+    out = {"volumes": torch.empty(n, dtype=dt, device=dev),
+           "grad": torch.empty(n, dtype=torch.float64, device=dev)}
+    out["centroids"] = torch.empty((n, 3), dtype=dt, device=dev) if centroids else None
+    out["karea"] = torch.empty(n, dtype=dt, device=dev) if karea else None
+    csr = None
+    if hessian:
+        cap = int(csr_cap) if csr_cap is not None else n * (ctx.k_max + 1)
+        out["row_ptr"] = torch.empty(n + 1, dtype=torch.int32, device=dev)
+        out["cols"] = torch.empty(cap, dtype=torch.int32, device=dev)
+        out["vals"] = torch.empty(cap, dtype=dt, device=dev)
+        csr = Csr(out["row_ptr"].data_ptr(), out["cols"].data_ptr(), out["vals"].data_ptr(), cap, 0)
+    st = CellStats()
+    f = lib().lgc_compute_cells if dt == torch.float32 else lib().lgc_compute_cells_f64
+    dom = _domain(domain)
+    code = f(ctx.handle, _stream(stream), n, _ptr(pos), _ptr(psi), _ptr(targets), ctypes.byref(dom),
+             _ptr(out["volumes"]), _ptr(out["grad"]), ctypes.byref(csr) if csr else None,
+             _ptr(out["centroids"]), _ptr(out["karea"]), ctypes.byref(st))
+    out["stats"] = _as_dict(st)
+    out["status"] = code
+    if hessian:
+        out["nnz"] = int(csr.nnz)
+        if code == POT_OK:
+            out["cols"] = out["cols"][: csr.nnz]
+            out["vals"] = out["vals"][: csr.nnz]
+    if check and code != POT_OK:
+        raise PotError(code, "lgc_compute_cells", out["stats"])
+    return out
+
+
+def pot_newton_solve(ctx: Context, pos, targets, psi, domain=UNIT_BOX, params=None, stream=None,
+                     check=True):
+    """Damped Newton with KMT steps (Algorithm 1); psi is updated in place.
+    Returns the stats dict (status included)."""
+    dt = pos.dtype
+    n = int(pos.shape[0])
+    dev = ctx.device
+    pos = _dev(pos, dt, (n, 3), "pos", dev)
+    targets = _dev(targets, torch.float64, (n,), "targets", dev)
+    if not (psi.is_cuda and psi.is_contiguous() and psi.dtype == dt and psi.shape == (n,)):
+        raise ValueError("psi must be a contiguous CUDA tensor of shape (n,) and pos's dtype")
+    p = params if params is not None else default_params()
+    st = SolveStats()
+    f = lib().pot_newton_solve if dt == torch.float32 else lib().pot_newton_solve_f64
+    dom = _domain(domain)
+    code = f(ctx.handle, _stream(stream), n, _ptr(pos), _ptr(targets), _ptr(psi), ctypes.byref(dom),
+             ctypes.byref(p), ctypes.byref(st))
+    s = _as_dict(st)
+    s["status"] = code
+    if check and code != POT_OK:
+        raise PotError(code, "pot_newton_solve", s)
+    return s
+
+
+def pot_fluid_step(ctx: Context, pos, vel, psi, targets, domain=UNIT_BOX, params=None, stream=None,
+                   check=True):
+    """One fluid step (Sec. 5); pos, vel, psi updated in place.  Returns stats."""
+    dt = pos.dtype
+    n = int(pos.shape[0])
+    for name, t, shape in (("pos", pos, (n, 3)), ("vel", vel, (n, 3)), ("psi", psi, (n,))):
+        if not (t.is_cuda and t.is_contiguous() and t.dtype == dt and tuple(t.shape) == shape):
+            raise ValueError(f"{name} must be a contiguous CUDA tensor {shape} of pos's dtype")
+    targets = _dev(targets, torch.float64, (n,), "targets", ctx.device)
+    p = params if params is not None else default_params()
+    st = SolveStats()
+    f = lib().pot_fluid_step if dt == torch.float32 else lib().pot_fluid_step_f64
+    dom = _domain(domain)
+    code = f(ctx.handle, _stream(stream), n, _ptr(pos), _ptr(vel), _ptr(psi), _ptr(targets),
+             ctypes.byref(dom), ctypes.byref(p), ctypes.byref(st))
+    s = _as_dict(st)
+    s["status"] = code
+    if check and code != POT_OK:
+        raise PotError(code, "pot_fluid_step", s)
+    return s

@@ -1,0 +1,98 @@
+"""Element-by-element comparison of GPU cell outputs with the FP64 oracle.
+
+Tolerance bases:
+  volumes    |V_gpu - V_ref| <= tol_v * max(V_ref, 1e-3 * 4/3 pi r^3)
+  gradient   |g_gpu - (nu - V_ref)| <= tol_v * max(nu, 1e-3 * 4/3 pi r^3)
+  |K|        |K_gpu - K_ref| <= tol_v * 4 pi psi
+  centroid   |c_gpu - c_ref| <= tol_c * r   (cells with V_ref > 1e-3 ball)
+  Hessian    |M_gpu - M_ref| <= tol_h * |M_ii,ref| for every entry of row i
+Topology: a bisector facet with oracle area > 1e-6 psi_i must be in the GPU
+row; a GPU entry must be a facet with oracle area > 0; facets in between are
+ambiguous (counted, not compared).
+"""
+import math
+
+import numpy as np
+
+from oracle import oracle as O
+
+
+def to_np(t):
+    return None if t is None else t.detach().cpu().numpy()
+
+
+def compare_cells(out, ref, psi, nu, tol_v, tol_h, tol_c=None, check_hessian=True):
+    q = ref["query"]
+    psi = np.asarray(psi, np.float64)
+    ps = psi[q]
+    r = np.sqrt(np.maximum(ps, 0))
+    ball = 4.0 / 3.0 * math.pi * r ** 3
+    v_gpu = to_np(out["volumes"]).astype(np.float64)[q]
+    base = np.maximum(ref["vol"], 1e-3 * ball)
+    base = np.where(base > 0, base, 1.0)
+    ev = np.abs(v_gpu - ref["vol"]) / base
+    worst = int(np.argmax(ev))
+    assert ev.max() <= tol_v, f"volume rel err {ev.max():.3e} at site {q[worst]}"
+    report = {"vol_max_rel": float(ev.max())}
+    if nu is not None:
+        g = to_np(out["grad"])[q]
+        nb = np.maximum(np.asarray(nu)[q], 1e-3 * ball)
+        eg = np.abs(g - (np.asarray(nu)[q] - ref["vol"])) / nb
+        assert eg.max() <= tol_v, f"grad rel err {eg.max():.3e}"
+        report["grad_max_rel"] = float(eg.max())
+    if out.get("karea") is not None:
+        k = to_np(out["karea"]).astype(np.float64)[q]
+        kb = np.where(ps > 0, 4 * math.pi * ps, 1.0)
+        ek = np.abs(k - ref["karea"]) / kb
+        assert ek.max() <= tol_v, f"karea rel err {ek.max():.3e}"
+        report["karea_max_rel"] = float(ek.max())
+    if tol_c is not None and out.get("centroids") is not None:
+        c = to_np(out["centroids"]).astype(np.float64)[q]
+        ok = ref["vol"] > 1e-3 * ball
+        ec = np.linalg.norm(c - ref["cen"], axis=1)[ok] / r[ok]
+        if ec.size:
+            assert ec.max() <= tol_c, f"centroid err {ec.max():.3e} r"
+            report["cen_max_rel"] = float(ec.max())
+    if check_hessian:
+        report.update(compare_hessian(out, ref, psi, tol_h))
+    return report
+
+
+def compare_hessian(out, ref, psi, tol_h):
+    q = ref["query"]
+    rp = to_np(out["row_ptr"]).astype(np.int64)
+    cols = to_np(out["cols"]).astype(np.int64)
+    vals = to_np(out["vals"]).astype(np.float64)
+    diag_ref, rows_ref = O.hessian_entries(ref, psi)
+    amb = 0
+    worst = 0.0
+    for k, i in enumerate(q):
+        gc = cols[rp[i]:rp[i + 1]]
+        gv = vals[rp[i]:rp[i + 1]]
+        assert np.all(np.diff(gc) > 0), f"row {i} columns not ascending"
+        assert i in gc, f"row {i} has no diagonal"
+        d_gpu = gv[gc == i][0]
+        scale = abs(diag_ref[k])
+        off = gc != i
+        gcols = set(gc[off].tolist())
+        nf = int(ref["nfac"][k])
+        fj = ref["fac_j"][k, :nf]
+        fa = ref["fac_area"][k, :nf]
+        strong = set(fj[fa > 1e-6 * psi[i]].tolist())
+        positive = set(fj[fa > 0].tolist())
+        missing = strong - gcols
+        assert not missing, f"row {i}: facets {sorted(missing)} missing on the GPU"
+        extra = gcols - positive
+        assert not extra, f"row {i}: GPU facets {sorted(extra)} have zero oracle area"
+        amb += len(positive - strong)
+        if scale == 0:
+            assert abs(d_gpu) <= 1e-30 and not gcols
+            continue
+        e = abs(d_gpu - diag_ref[k]) / scale
+        rc, rv = rows_ref[k]
+        rmap = dict(zip(rc.tolist(), rv.tolist()))
+        for c, v in zip(gc[off].tolist(), gv[off].tolist()):
+            e = max(e, abs(v - rmap[c]) / scale)
+        worst = max(worst, e)
+        assert e <= tol_h, f"row {i}: Hessian rel err {e:.3e}"
+    return {"hess_max_rel": worst, "ambiguous_facets": amb}

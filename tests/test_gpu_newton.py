@@ -1,0 +1,116 @@
+"""GPU Newton solve (Algorithm 1, KMT steps, Jacobi-PCG) and fluid step
+(Sec. 5) against the FP64 oracle.
+
+The partial-transport weights are unique (psi_0 = 0 fixed, Sec. 2.2), so the
+converged psi of GPU and oracle must agree: with both solved far below the
+tolerance in FP64 they agree to ~1e-8; the mixed-precision solve at 1e-4 is
+checked by recomputing its volumes with the oracle."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2601_05765_b300 import pot, scenes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = pot.Context(200000, 64, 0)
+    yield c
+    c.close()
+
+
+def tens(a, dtype, dev):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device=dev)
+
+
+def test_block_fp64_matches_oracle(ctx):
+    sc = scenes.jittered_block()
+    pos = sc.pos.astype(np.float64)
+    ref = O.newton(pos, sc.nu, sc.psi.astype(np.float64), tol=1e-11)
+    assert ref.status == O.NEWTON_OK
+    dev = ctx.device
+    psi = tens(sc.psi, torch.float64, dev)
+    st = pot.pot_newton_solve(ctx, tens(pos, torch.float64, dev), tens(sc.nu, torch.float64, dev), psi,
+                              params=pot.default_params(tol=1e-11))
+    assert st["status"] == 0 and st["err_max"] <= 1e-11
+    got = psi.cpu().numpy()
+    np.testing.assert_allclose(got, ref.psi, rtol=1e-8)
+    # the iteration count follows the oracle's (same algorithm, different rounding)
+    assert abs(st["newton_iters"] - ref.iters) <= 1
+
+
+def test_block_mixed_precision(ctx):
+    sc = scenes.jittered_block()
+    dev = ctx.device
+    psi = tens(sc.psi, torch.float32, dev)
+    st = pot.pot_newton_solve(ctx, tens(sc.pos, torch.float32, dev), tens(sc.nu, torch.float64, dev), psi)
+    assert st["status"] == 0 and st["err_max"] <= 1e-4
+    got = psi.cpu().numpy().astype(np.float64)
+    v = O.cells(sc.pos.astype(np.float64), got)["vol"]
+    err = np.max(np.abs(v - sc.nu) / sc.nu)
+    assert err <= 1.5e-4, err  # FP32 geometry error on top of the 1e-4 tolerance
+    ref = O.newton(sc.pos.astype(np.float64), sc.nu, sc.psi.astype(np.float64), tol=1e-10)
+    np.testing.assert_allclose(got, ref.psi, rtol=2e-3)
+
+
+def test_far_start_needs_kmt_halving(ctx):
+    sc = scenes.jittered_block(n_side=6, seed=4)
+    dev = ctx.device
+    far = (0.05 * sc.psi.astype(np.float64))
+    psi = tens(far, torch.float64, dev)
+    st = pot.pot_newton_solve(ctx, tens(sc.pos.astype(np.float64), torch.float64, dev),
+                              tens(sc.nu, torch.float64, dev), psi, params=pot.default_params(tol=1e-8))
+    ref = O.newton(sc.pos.astype(np.float64), sc.nu, far, tol=1e-8)
+    assert st["status"] == 0 and ref.status == O.NEWTON_OK
+    assert st["halvings"] > 0
+    np.testing.assert_allclose(psi.cpu().numpy(), ref.psi, rtol=1e-5)
+
+
+def test_failure_statuses(ctx):
+    sc = scenes.jittered_block(n_side=3, seed=4)
+    dev = ctx.device
+    pos = tens(sc.pos, torch.float32, dev)
+    nu = tens(sc.nu, torch.float64, dev)
+    bad = sc.psi.copy()
+    bad[0] = 0.0
+    st = pot.pot_newton_solve(ctx, pos, nu, tens(bad, torch.float32, dev), check=False)
+    assert st["status"] == 5  # empty cell at the start
+    far = tens(0.05 * sc.psi, torch.float32, dev)
+    st = pot.pot_newton_solve(ctx, pos, nu, far, params=pot.default_params(max_halvings=0), check=False)
+    assert st["status"] == 7  # KMT step not found
+    st = pot.pot_newton_solve(ctx, pos, nu, tens(0.05 * sc.psi, torch.float32, dev),
+                              params=pot.default_params(max_newton=1), check=False)
+    assert st["status"] == 6  # iteration cap
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_fluid_step_matches_oracle(ctx, dtype):
+    sc = scenes.dam_break(nx=10, ny=10, nz=20, width=0.16, seed=2)
+    dev = ctx.device
+    npdt = np.float64 if dtype == torch.float64 else np.float32
+    # converge the start first so that one step is a warm-started solve
+    r0 = O.newton(sc.pos.astype(npdt).astype(np.float64), sc.nu, sc.psi.astype(np.float64), tol=1e-10)
+    psi0 = r0.psi.astype(npdt)
+    vel0 = np.zeros_like(sc.pos, dtype=npdt)
+    vel0[:, 0] = 0.5
+    pos = tens(sc.pos.astype(npdt), dtype, dev)
+    vel = tens(vel0, dtype, dev)
+    psi = tens(psi0, dtype, dev)
+    tol = 1e-10 if dtype == torch.float64 else 1e-4
+    prm = pot.default_params(tol=tol, dt=2e-3)
+    st = pot.pot_fluid_step(ctx, pos, vel, psi, tens(sc.nu, torch.float64, dev), params=prm)
+    assert st["status"] == 0
+    x1, v1, nr = O.fluid_step(sc.pos.astype(npdt).astype(np.float64), vel0.astype(np.float64),
+                              psi0.astype(np.float64), sc.nu, dt=2e-3, tol=1e-11)
+    gx = pos.cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(gx, x1, rtol=0, atol=1e-15 if dtype == torch.float64 else 1e-7)
+    gv = vel.cpu().numpy().astype(np.float64)
+    # velocity = dt/eps^2 * centroid offset: centroid error of ~1e-4 r (FP32) or ~1e-9 r (FP64)
+    r = math.sqrt(float(psi0.max()))
+    atol = 2e-3 / 1e-4 * r * (1e-9 if dtype == torch.float64 else 2e-3)
+    np.testing.assert_allclose(gv, v1, rtol=0, atol=atol)
