@@ -145,6 +145,10 @@ const char* pot_status_string(int status);
 /* Default parameters (see pot_params). */
 void pot_default_params(pot_params* p);
 
+/* Number of CUDA kernel launches this library has issued in this process
+ * (all contexts and devices), for launch accounting by callers. */
+int64_t pot_kernel_launches(void);
+
 /* ---- generalized Laguerre cells (Eq. 1, Sec. 3.2-3.4, Algorithm 2) ------ */
 
 /* Build every generalized Laguerre cell

@@ -17,6 +17,10 @@ int fluid_step(pot_ctx*, cudaStream_t, int64_t, T*, T*, T*, const double*, const
                const pot_params*, pot_solve_stats*);
 }  // namespace pot
 
+namespace pot {
+std::atomic<long long> g_launches{0};
+}  // namespace pot
+
 using namespace pot;
 
 namespace {
@@ -130,6 +134,8 @@ int compute_cells(pot_ctx* ctx, void* stream, int64_t n, const T* pos, const T* 
 }  // namespace
 
 extern "C" {
+
+int64_t pot_kernel_launches(void) { return g_launches.load(); }
 
 void pot_default_params(pot_params* p) {
   if (!p) return;

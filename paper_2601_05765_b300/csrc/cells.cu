@@ -747,6 +747,7 @@ int cells_eval(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* dom, 
     box.lo[k] = (T)dom->lo[k];
     box.hi[k] = (T)dom->hi[k];
   }
+  note_launch();
   k_candidates<T><<<blocks_for(n, 256), 256, 0, st>>>(n, w.sxp, ctx->cell_start, w.grid, box,
                                                        w.psi_max, ctx->k_max, ctx->cand, ctx->meta,
                                                        ctx->err);
@@ -760,6 +761,7 @@ int cells_eval(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* dom, 
   o.snu = ctx->snu;
   int64_t warps = (n + kCellsPerWarp - 1) / kCellsPerWarp;
   int blocks = (int)((warps + kCellWarps - 1) / kCellWarps);
+  note_launch();
   k_cells<T><<<blocks, kCellWarps * 32, 0, st>>>(n, w.sxp, ctx->meta, ctx->cand, ctx->k_max, box,
                                                  w.stage_vals, o, ctx->err);
   POT_CUDA(cudaGetLastError());
@@ -769,7 +771,9 @@ int cells_eval(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* dom, 
 template <typename T>
 int residuals(pot_ctx* ctx, cudaStream_t st, int64_t n, double out[6]) {
   Work<T>& w = ctx->work<T>();
+  note_launch();
   k_resid<T><<<kRedBlocks, 256, 0, st>>>(n, w.vol, ctx->snu, ctx->meta, ctx->red);
+  note_launch();
   k_resid_final<<<1, 32, 0, st>>>(ctx->red, kRedBlocks, ctx->red_out);
   POT_CUDA(cudaMemcpyAsync(ctx->h_pinned, ctx->red_out, 6 * sizeof(double),
                            cudaMemcpyDeviceToHost, st));
@@ -801,6 +805,7 @@ template <typename T>
 int csr_compact(pot_ctx* ctx, cudaStream_t st, int64_t n, int64_t* nnz_off) {
   Work<T>& w = ctx->work<T>();
   POT_CHECK(scan_exclusive(ctx, st, ctx->row_cnt, ctx->row_ptr, n));
+  note_launch();
   k_csr_copy<T><<<blocks_for(n * 8, 256), 256, 0, st>>>(n, ctx->row_ptr, ctx->cand, w.stage_vals,
                                                          ctx->k_max, ctx->csr_cols, w.csr_vals);
   int32_t* h = (int32_t*)(ctx->h_pinned + 8);
@@ -814,6 +819,7 @@ template <typename T>
 int csr_user(pot_ctx* ctx, cudaStream_t st, int64_t n, int32_t* row_ptr, int32_t* cols, T* vals,
              int64_t cap, int64_t* nnz) {
   Work<T>& w = ctx->work<T>();
+  note_launch();
   k_user_count<<<blocks_for(n, 256), 256, 0, st>>>(n, ctx->iperm, ctx->row_cnt, ctx->ucnt);
   POT_CHECK(scan_exclusive(ctx, st, ctx->ucnt, row_ptr, n));
   int32_t* h = (int32_t*)(ctx->h_pinned + 8);
@@ -821,6 +827,7 @@ int csr_user(pot_ctx* ctx, cudaStream_t st, int64_t n, int32_t* row_ptr, int32_t
   POT_CUDA(cudaStreamSynchronize(st));
   *nnz = h[0];
   if (*nnz > cap) return POT_ERR_CAPACITY;
+  note_launch();
   k_user_rows<T><<<blocks_for(n, 128), 128, 0, st>>>(n, ctx->iperm, ctx->perm, row_ptr, ctx->cand,
                                                       w.stage_vals, w.diag, ctx->k_max, cols, vals);
   POT_CUDA(cudaGetLastError());
@@ -831,6 +838,7 @@ template <typename T>
 int unsort_outputs(pot_ctx* ctx, cudaStream_t st, int64_t n, T* vol, double* grad, T* cen,
                    T* karea, T* psi) {
   Work<T>& w = ctx->work<T>();
+  note_launch();
   k_unsort<T><<<blocks_for(n, 256), 256, 0, st>>>(n, ctx->perm, w.vol, ctx->grad, w.cen, w.karea,
                                                    w.sxp, vol, grad, cen, karea, psi);
   POT_CUDA(cudaGetLastError());
@@ -841,6 +849,7 @@ template <typename T>
 int psi_update(pot_ctx* ctx, cudaStream_t st, int64_t n, double alpha) {
   Work<T>& w = ctx->work<T>();
   POT_CUDA(cudaMemsetAsync(w.psi_max, 0, sizeof(T), st));
+  note_launch();
   k_psi_update<T><<<blocks_for(n, 256), 256, 0, st>>>(n, w.psi_base, w.u, (T)alpha, w.sxp,
                                                        w.psi_max);
   POT_CUDA(cudaGetLastError());

@@ -99,6 +99,7 @@ int grid_build(pot_ctx* ctx, cudaStream_t st, int64_t n, const T* pos, const T* 
   Work<T>& w = ctx->work<T>();
   // largest weight -> cell size (one host read)
   POT_CUDA(cudaMemsetAsync(w.psi_max, 0, sizeof(T), st));
+  note_launch();
   k_psi_max_in<T><<<kRedBlocks, 256, 0, st>>>(psi, n, w.psi_max);
   POT_CUDA(cudaMemcpyAsync(ctx->h_pinned, w.psi_max, sizeof(T), cudaMemcpyDeviceToHost, st));
   POT_CUDA(cudaStreamSynchronize(st));
@@ -132,12 +133,16 @@ int grid_build(pot_ctx* ctx, cudaStream_t st, int64_t n, const T* pos, const T* 
   g.inv_cs = (T)(1.0 / cs);
   int64_t ncell = (int64_t)dim[0] * dim[1] * dim[2];
   POT_CUDA(cudaMemsetAsync(ctx->cell_count, 0, sizeof(int32_t) * (ncell + 1), st));
+  note_launch();
   k_keys<T><<<blocks_for(n, 256), 256, 0, st>>>(pos, n, g, ctx->keys, ctx->cell_count);
   POT_CHECK(scan_exclusive(ctx, st, ctx->cell_count, ctx->cell_start, ncell));
   POT_CUDA(cudaMemsetAsync(ctx->cell_count, 0, sizeof(int32_t) * (ncell + 1), st));
+  note_launch();
   k_scatter<<<blocks_for(n, 256), 256, 0, st>>>(ctx->keys, n, ctx->cell_start, ctx->cell_count,
                                                   ctx->perm);
+  note_launch();
   k_cell_sort<<<blocks_for(ncell, 256), 256, 0, st>>>(ctx->cell_start, ncell, ctx->perm);
+  note_launch();
   k_gather<T><<<blocks_for(n, 256), 256, 0, st>>>(ctx->perm, n, pos, psi, targets, w.sxp,
                                                   w.psi_base, ctx->snu, ctx->iperm);
   POT_CUDA(cudaGetLastError());

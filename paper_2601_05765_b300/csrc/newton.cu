@@ -141,7 +141,9 @@ int newton_sorted(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* do
   S->err_max = res[0];
   S->err_l2 = sqrt(res[1]);
   if (!(res[2] > 0.0)) return POT_ERR_EMPTY_CELL_AT_START;
+  note_launch();
   k_nu_min<<<kRedBlocks, 256, 0, st>>>(n, ctx->snu, ctx->red);
+  note_launch();
   k_min_final<<<1, 32, 0, st>>>(ctx->red, kRedBlocks, ctx->red_out);
   POT_CUDA(cudaMemcpyAsync(ctx->h_pinned, ctx->red_out, sizeof(double), cudaMemcpyDeviceToHost, st));
   POT_CUDA(cudaStreamSynchronize(st));
@@ -186,6 +188,7 @@ int newton_sorted(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* do
       POT_CHECK(eval_and_reduce<T>(ctx, st, n, dom, res, S));
       return POT_ERR_LINESEARCH_FAILED;
     }
+    note_launch();
     k_accept<T><<<blocks_for(n, 256), 256, 0, st>>>(n, w.sxp, w.psi_base);
     err = res[0];
     gnorm = sqrt(res[1]);
@@ -200,8 +203,10 @@ int newton_solve(pot_ctx* ctx, cudaStream_t st, int64_t n, const T* pos, const d
   S->grid_builds++;
   int status = newton_sorted<T>(ctx, st, n, dom, P, S);
   Work<T>& w = ctx->work<T>();
-  if (status == POT_OK || status == POT_ERR_NOT_CONVERGED || status == POT_ERR_LINESEARCH_FAILED)
+  if (status == POT_OK || status == POT_ERR_NOT_CONVERGED || status == POT_ERR_LINESEARCH_FAILED) {
+    note_launch();
     k_unsort_psi<T><<<blocks_for(n, 256), 256, 0, st>>>(n, ctx->perm, w.psi_base, psi_inout);
+  }
   POT_CUDA(cudaStreamSynchronize(st));
   S->status = status;
   S->ms_total = now_ms() - t0;
@@ -218,12 +223,14 @@ int fluid_step(pot_ctx* ctx, cudaStream_t st, int64_t n, T* pos, T* vel, T* psi,
     box.lo[k] = (T)dom->lo[k];
     box.hi[k] = (T)dom->hi[k];
   }
+  note_launch();
   k_advect<T><<<blocks_for(n, 256), 256, 0, st>>>(n, pos, vel, (T)P->dt, box, (T)P->wall_margin);
   POT_CHECK(grid_build<T>(ctx, st, n, pos, psi, targets, dom));
   S->grid_builds++;
   int status = newton_sorted<T>(ctx, st, n, dom, P, S);
   if (status == POT_OK || status == POT_ERR_NOT_CONVERGED || status == POT_ERR_LINESEARCH_FAILED) {
     Work<T>& w = ctx->work<T>();
+    note_launch();
     k_velocity<T><<<blocks_for(n, 256), 256, 0, st>>>(
         n, ctx->perm, w.sxp, w.cen, w.psi_base, vel, psi, (T)P->dt, (T)(1.0 / (P->eps * P->eps)),
         (T)P->gravity[0], (T)P->gravity[1], (T)P->gravity[2]);

@@ -177,6 +177,7 @@ int pcg_solve(pot_ctx* ctx, cudaStream_t st, int64_t n, int64_t nnz_off, double 
   const int nb = ctx->sm_count * 2;
   double* part = ctx->pcg_red;
   if (chunk < 1) chunk = 1;
+  note_launch();
   k_pcg_init<T><<<nb, kPcgThreads, 0, st>>>(n, ctx->grad, w.diag, w.u, w.r, w.z, w.p0, part, nb,
                                             ctx->pcg_ctl);
   const double rtol2 = rtol * rtol;
@@ -184,9 +185,11 @@ int pcg_solve(pot_ctx* ctx, cudaStream_t st, int64_t n, int64_t nnz_off, double 
   int32_t* hctl = (int32_t*)(ctx->h_pinned + 16);
   for (;;) {
     for (int k = 0; k < chunk; k++) {
+      note_launch();
       k_spmv<T><<<nb, kPcgThreads, 0, st>>>(n, ctx->row_ptr, ctx->csr_cols, w.csr_vals, w.diag,
                                             w.z, w.p0, w.p1, w.q, part, nb, ctx->pcg_ctl, rtol2,
                                             max_iter);
+      note_launch();
       k_update<T><<<nb, kPcgThreads, 0, st>>>(n, w.diag, w.u, w.r, w.z, w.p0, w.p1, w.q, part, nb,
                                               ctx->pcg_ctl);
     }

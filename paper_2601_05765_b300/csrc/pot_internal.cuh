@@ -17,6 +17,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "../../include/pot.h"
 
 namespace pot {
@@ -196,6 +198,10 @@ namespace pot {
     int s_ = (call);             \
     if (s_ != POT_OK) return s_; \
   } while (0)
+
+// kernel launches issued by this library in this process (pot_kernel_launches)
+extern std::atomic<long long> g_launches;
+inline void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 inline int blocks_for(int64_t n, int threads) { return (int)((n + threads - 1) / threads); }
 

@@ -100,8 +100,11 @@ int scan_exclusive(pot_ctx* ctx, cudaStream_t st, const int32_t* in, int32_t* ou
   }
   int64_t nb = (n + kScanTile - 1) / kScanTile;
   if (nb + 1 > ctx->scan_tmp_len) return POT_ERR_INVALID_ARG;
+  note_launch();
   k_tile_sums<<<(unsigned)nb, kScanThreads, 0, st>>>(in, n, ctx->scan_tmp);
+  note_launch();
   k_scan_sums<<<1, kScanThreads, 0, st>>>(ctx->scan_tmp, nb, out + n);
+  note_launch();
   k_tile_scan<<<(unsigned)nb, kScanThreads, 0, st>>>(in, out, n, ctx->scan_tmp);
   POT_CUDA(cudaGetLastError());
   return POT_OK;

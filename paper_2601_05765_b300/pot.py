@@ -89,6 +89,8 @@ def lib():
         L.pot_status_string.argtypes = [ctypes.c_int]
         L.pot_default_params.argtypes = [ctypes.POINTER(Params)]
         L.pot_default_params.restype = None
+        L.pot_kernel_launches.argtypes = []
+        L.pot_kernel_launches.restype = I64
         for name in ("lgc_compute_cells", "lgc_compute_cells_f64"):
             f = getattr(L, name)
             f.argtypes = [P, P, I64, P, P, P, ctypes.POINTER(Domain), P, P, ctypes.POINTER(Csr), P, P,
@@ -106,6 +108,11 @@ def lib():
             f.restype = ctypes.c_int
         _lib = L
     return _lib
+
+
+def kernel_launches() -> int:
+    """Kernel launches issued by libpot.so so far in this process."""
+    return int(lib().pot_kernel_launches())
 
 
 def default_params(**kw) -> Params:
