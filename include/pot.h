@@ -44,6 +44,7 @@ extern "C" {
 #define POT_ERR_POLYGON_OVERFLOW 8    /* a facet polygon exceeded its edge capacity */
 #define POT_ERR_CAPACITY 9            /* CSR capacity too small for the Hessian */
 #define POT_ERR_PCG_BREAKDOWN 10      /* PCG met p.Mp <= 0 (matrix not SPD) */
+#define POT_ERR_TOO_LARGE 11          /* n above the no-alloc entry point's maximum */
 
 /* ---- types ------------------------------------------------------------ */
 typedef struct pot_ctx pot_ctx;
@@ -173,6 +174,35 @@ int lgc_compute_cells_f64(pot_ctx* ctx, void* stream, int64_t n, const double* p
                           const double* psi, const double* targets, const pot_domain* dom,
                           double* volumes, double* grad, pot_csr_f64* hess, double* centroids,
                           double* karea, pot_cell_stats* stats);
+
+/* ---- cell evaluation without allocation ----------------------------------- */
+
+/* The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory: plugins whose host application owns
+ * every device allocation (a fixed arena with no room for, or no permission
+ * to make, cudaMalloc calls of its own), and real-time loops where a
+ * cudaMalloc/cudaFree pair would stall the device at the wrong moment.
+ *
+ * Computes what lgc_compute_cells computes, except the Hessian (volumes,
+ * grad, centroids, karea; same meaning, layout and FP32/FP64 split), with
+ * no context and no allocation: all scratch memory is one file-scope device
+ * array inside libpot.so sized for n <= 8192 sites and 64 cutting bisectors
+ * per cell (about 4.8 MB, held by every GPU that loads the library until the
+ * process exits).  The caller passes device inputs and outputs as usual;
+ * centroids, karea and grad may be NULL.
+ *  - n > 8192 returns POT_ERR_TOO_LARGE before any device work.
+ *  - The first call on each device looks up the array's device address with
+ *    that device current (the calling thread's current device is used);
+ *    make that first call before any stream capture.
+ *  - Every call shares the array and overwrites the previous call's
+ *    contents; calls whose work overlaps on the GPU race on it (a host mutex
+ *    serialises calls from several threads, and each call waits for its own
+ *    stream before returning).
+ * Errors: as lgc_compute_cells (no POT_ERR_CAPACITY), plus POT_ERR_TOO_LARGE.
+ * Timing fields of stats stay 0. */
+int lgc_compute_cells_noalloc(void* stream, int64_t n, const float* pos, const float* psi,
+                              const double* targets, const pot_domain* dom, float* volumes,
+                              double* grad, float* centroids, float* karea, pot_cell_stats* stats);
 
 /* ---- Newton solve (Algorithm 1 with KMT steps) --------------------------- */
 

@@ -168,6 +168,7 @@ const char* pot_status_string(int status) {
     case POT_ERR_POLYGON_OVERFLOW: return "facet polygon exceeded its edge capacity";
     case POT_ERR_CAPACITY: return "CSR capacity too small";
     case POT_ERR_PCG_BREAKDOWN: return "PCG breakdown (matrix not positive definite)";
+    case POT_ERR_TOO_LARGE: return "more sites than the no-alloc entry point holds (8192)";
     default: return "unknown status";
   }
 }

@@ -21,7 +21,7 @@ STATUS = {
     0: "POT_OK", 1: "POT_ERR_INVALID_ARG", 2: "POT_ERR_CUDA", 3: "POT_ERR_NEIGHBOUR_OVERFLOW",
     4: "POT_ERR_COINCIDENT_SITES", 5: "POT_ERR_EMPTY_CELL_AT_START", 6: "POT_ERR_NOT_CONVERGED",
     7: "POT_ERR_LINESEARCH_FAILED", 8: "POT_ERR_POLYGON_OVERFLOW", 9: "POT_ERR_CAPACITY",
-    10: "POT_ERR_PCG_BREAKDOWN",
+    10: "POT_ERR_PCG_BREAKDOWN", 11: "POT_ERR_TOO_LARGE",
 }
 UNIT_BOX = ((0.0, 0.0, 0.0), (1.0, 1.0, 1.0))
 
