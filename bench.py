@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", default="step", choices=["step", "cells"],
+                    help="step: fluid steps on the splash; cells: lgc_compute_cells alone on the "
+                         "2^20-site random cloud")
     ap.add_argument("--spacing", type=float, default=3.224e-3, help="splash lattice spacing")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -324,10 +327,46 @@ def run_ours(args):
     ctx.close()
 
 
+def run_cells(args):
+    """lgc_compute_cells (grid, candidates, cell geometry, CSR) on the 2^20-site
+    random cloud: generalized Laguerre cells per second of the cell path."""
+    import torch
+
+    from paper_2601_05765_b300 import pot, scenes
+    dev = torch.device("cuda", 0)
+    sc = scenes.uniform_cloud(n=1 << 20, seed=1)
+    n = sc.n
+    ctx = pot.Context(n, 64, 0, fp32=True, fp64=False)
+    pos = torch.from_numpy(sc.pos).to(dev)
+    psi = torch.from_numpy(sc.psi).to(dev)
+    nu = torch.from_numpy(sc.nu).to(dev)
+    for _ in range(args.warmup):
+        pot.lgc_compute_cells(ctx, pos, psi, nu)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    st = []
+    l0 = pot.kernel_launches()
+    e0.record(stream)
+    for _ in range(args.steps):
+        st.append(pot.lgc_compute_cells(ctx, pos, psi, nu)["stats"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / args.steps
+    ms = {k: statistics.mean(s[k] for s in st) for k in ("ms_grid", "ms_cells", "ms_csr")}
+    print(json.dumps({"metric": "generalized Laguerre cells/s (lgc_compute_cells, 2^20-site random cloud)",
+                      "value": n / t, "unit": "cells/s", "ms_per_call": 1e3 * t, **ms,
+                      "nnz": st[-1]["nnz"], "gpu_launches": pot.kernel_launches() - l0,
+                      "geometry_cells_per_s": n / (ms["ms_cells"] / 1e3)}))
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.mode == "cells":
+        run_cells(args)
     else:
         run_ours(args)
 
