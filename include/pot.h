@@ -243,6 +243,64 @@ int pot_fluid_step_f64(pot_ctx* ctx, void* stream, int64_t n, double* pos, doubl
                        double* psi, const double* targets, const pot_domain* dom,
                        const pot_params* params, pot_solve_stats* stats);
 
+/* ---- learned warm start (not in the paper; task statement) --------------- */
+
+/* A small MLP predicts each site's new weight from its neighbourhood:
+ * inputs (80 BF16 values per site, row-major): offsets to the up to 24
+ * nearest other sites closer than 2 sqrt(max psi), by increasing distance,
+ * divided by h = nu^(1/3) (zero-padded); psi_prev / h^2; v dt / h; 4 zeros.
+ * Network: 80 -> 128 -> 128 -> 128 (ReLU) -> 1, BF16 weights and activations,
+ * FP32 accumulation on the tcgen05 tensor cores.  Prediction:
+ * psi_start = psi_prev + h^2 * output.  Parameters are one FP32 vector of
+ * pot_mlp_num_params() values: W1 (80 x 128, row = input), b1 (128),
+ * W2 (128 x 128), b2, W3 (128 x 128), b3, w4 (128), b4 (1). */
+typedef struct pot_mlp pot_mlp;
+
+/* Model with workspace for inference on up to max_rows rows (training batches
+ * up to 16384 rows, multiples of 8).  Parameters start at zero. */
+int pot_mlp_create(pot_mlp** mlp, int device, int64_t max_rows);
+int pot_mlp_destroy(pot_mlp* mlp);
+int pot_mlp_num_params(void);
+
+/* Copy parameters in/out (device FP32 vectors); set also resets Adam. */
+int pot_mlp_set_params(pot_mlp* mlp, void* stream, const float* params);
+int pot_mlp_get_params(pot_mlp* mlp, void* stream, float* params);
+
+/* out[r] = MLP(x[r]) for rows x (rows x 80 BF16, device). */
+int pot_mlp_forward(pot_mlp* mlp, void* stream, int64_t rows, const uint16_t* x, float* out);
+
+/* Rows idx[0..batch) of the dataset (x_all: n_all x 80 BF16, y_all: n_all
+ * FP32 targets) form one batch; loss = mean (out - y)^2.
+ * pot_mlp_gradients writes d loss / d params (FP32, pot_mlp_num_params
+ * values) and the loss (device scalar), without updating;
+ * pot_mlp_train_step takes one Adam step (beta 0.9 / 0.999, eps 1e-8) with
+ * learning rate lr and writes the batch loss before the step.
+ * batch <= 16384 and a multiple of 8. */
+int pot_mlp_gradients(pot_mlp* mlp, void* stream, int64_t n_all, const uint16_t* x_all,
+                      const float* y_all, const int32_t* idx, int64_t batch, float* grads,
+                      float* loss);
+int pot_mlp_train_step(pot_mlp* mlp, void* stream, int64_t n_all, const uint16_t* x_all,
+                       const float* y_all, const int32_t* idx, int64_t batch, float lr,
+                       float* loss);
+
+/* Status of the model's kernels since the last check (a bounded tensor-core
+ * wait that ran out reports POT_ERR_CUDA); clears it. */
+int pot_mlp_check(pot_mlp* mlp, void* stream);
+
+/* Features (n x 80 BF16, caller order) at the positions and velocities the
+ * next pot_fluid_step will solve at (x + dt v clamped into the box, same rule),
+ * with psi as the previous weights.  Uses ctx's grid workspace. */
+int pot_mlp_features(pot_ctx* ctx, pot_mlp* mlp, void* stream, int64_t n, const float* pos,
+                     const float* vel, const float* psi, const double* targets,
+                     const pot_domain* dom, const pot_params* params, uint16_t* feat);
+
+/* Attach a model to a context (NULL detaches; the context does not own it).
+ * pot_fluid_step then starts Newton from the MLP's prediction when
+ * params->warm_start is 1, and falls back to the previous weights when the
+ * prediction gives an empty cell, a geometry error or a worst relative
+ * volume error above 0.5 (stats: mlp_used / mlp_fallback).  FP32 path only. */
+int pot_set_warm_start(pot_ctx* ctx, pot_mlp* mlp);
+
 #ifdef __cplusplus
 }
 #endif

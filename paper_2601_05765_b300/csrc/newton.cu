@@ -85,6 +85,27 @@ __global__ void k_velocity(int64_t n, const int32_t* __restrict__ perm,
   psi[o] = psi_base[s];
 }
 
+// psi <- src (sorted), the current weights for evaluation and the base;
+// psi_max follows (reset by the caller)
+template <typename T>
+__global__ void k_set_psi(int64_t n, const T* __restrict__ src, V4<T>* sxp, T* base, T* psi_max) {
+  int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  T v = T(0);
+  if (s < n) {
+    v = src[s];
+    sxp[s].w = v;
+    base[s] = v;
+  }
+  T m = v > T(0) ? v : T(0);
+  for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_down_sync(kFull, m, off));
+  if ((threadIdx.x & 31) == 0 && m > T(0)) {
+    if (sizeof(T) == 4)
+      atomicMax((int*)psi_max, __float_as_int((float)m));
+    else
+      atomicMax((unsigned long long*)psi_max, (unsigned long long)__double_as_longlong((double)m));
+  }
+}
+
 template <typename T>
 __global__ void k_unsort_psi(int64_t n, const int32_t* __restrict__ perm, const T* __restrict__ base,
                              T* psi) {
@@ -131,12 +152,29 @@ int eval_and_reduce(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* 
 }  // namespace
 
 // Newton solve in sorted space.  Requires grid_build (sxp.w = psi_base = start).
+// psi_fallback (sorted, optional): weights to restart from when the given
+// start is rejected -- an empty cell (the KMT bound needs min V > 0), a
+// geometry error, or a worst relative error above 0.5.
 template <typename T>
 int newton_sorted(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* dom,
-                  const pot_params* P, pot_solve_stats* S) {
+                  const pot_params* P, pot_solve_stats* S, const T* psi_fallback = nullptr) {
   Work<T>& w = ctx->work<T>();
   double res[6];
-  POT_CHECK(eval_and_reduce<T>(ctx, st, n, dom, res, S));
+  if (psi_fallback) {
+    int code = eval_and_reduce<T>(ctx, st, n, dom, res, S);
+    const bool bad = code != POT_OK || !(res[2] > 0.0) || !(res[0] <= 0.5);
+    if (bad) {
+      S->mlp_fallback = 1;
+      POT_CUDA(cudaMemsetAsync(w.psi_max, 0, sizeof(T), st));
+      note_launch();
+      k_set_psi<T><<<blocks_for(n, 256), 256, 0, st>>>(n, psi_fallback, w.sxp, w.psi_base, w.psi_max);
+      POT_CHECK(eval_and_reduce<T>(ctx, st, n, dom, res, S));
+    } else {
+      S->mlp_used = 1;
+    }
+  } else {
+    POT_CHECK(eval_and_reduce<T>(ctx, st, n, dom, res, S));
+  }
   S->err_start = res[0];
   S->err_max = res[0];
   S->err_l2 = sqrt(res[1]);
@@ -227,7 +265,13 @@ int fluid_step(pot_ctx* ctx, cudaStream_t st, int64_t n, T* pos, T* vel, T* psi,
   k_advect<T><<<blocks_for(n, 256), 256, 0, st>>>(n, pos, vel, (T)P->dt, box, (T)P->wall_margin);
   POT_CHECK(grid_build<T>(ctx, st, n, pos, psi, targets, dom));
   S->grid_builds++;
-  int status = newton_sorted<T>(ctx, st, n, dom, P, S);
+  const T* fallback = nullptr;
+  if (sizeof(T) == 4 && P->warm_start && ctx->mlp) {
+    float* prev = nullptr;
+    POT_CHECK(mlp_warm_start(ctx, ctx->mlp, st, n, (const float*)vel, (float)P->dt, &prev));
+    fallback = (const T*)prev;
+  }
+  int status = newton_sorted<T>(ctx, st, n, dom, P, S, fallback);
   if (status == POT_OK || status == POT_ERR_NOT_CONVERGED || status == POT_ERR_LINESEARCH_FAILED) {
     Work<T>& w = ctx->work<T>();
     note_launch();

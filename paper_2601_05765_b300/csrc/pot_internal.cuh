@@ -145,7 +145,10 @@ struct Work {
 
 }  // namespace pot
 
+struct pot_mlp;
+
 struct pot_ctx {
+  pot_mlp* mlp = nullptr;  // learned warm-start model (pot_set_warm_start), not owned
   int device = 0;
   int64_t n_max = 0;
   int32_t k_max = 0;
@@ -245,6 +248,12 @@ int unsort_outputs(pot_ctx* ctx, cudaStream_t st, int64_t n, T* vol, double* gra
 // psi_trial = psi_base + alpha * u written into sxp.w; updates psi_max
 template <typename T>
 int psi_update(pot_ctx* ctx, cudaStream_t st, int64_t n, double alpha);
+
+// learned warm start (mlp.cu): features of the sorted sites, the MLP, and
+// psi_pred = psi_prev + h^2 out into sxp.w / psi_base; *psi_prev points to the
+// kept previous weights (sorted)
+int mlp_warm_start(pot_ctx* ctx, pot_mlp* mm, cudaStream_t st, int64_t n, const float* vel, float dt,
+                   float** psi_prev);
 
 // PCG (pcg.cu): solve M u = grad (sorted space) into work.u
 template <typename T>

@@ -103,6 +103,22 @@ def lib():
             f = getattr(L, name)
             f.argtypes = [P, P, I64, P, P, P, P, ctypes.POINTER(Domain), ctypes.POINTER(Params),
                           ctypes.POINTER(SolveStats)]
+        L.pot_mlp_create.argtypes = [ctypes.POINTER(P), ctypes.c_int, I64]
+        L.pot_mlp_destroy.argtypes = [P]
+        L.pot_mlp_num_params.argtypes = []
+        L.pot_mlp_set_params.argtypes = [P, P, P]
+        L.pot_mlp_get_params.argtypes = [P, P, P]
+        L.pot_mlp_forward.argtypes = [P, P, I64, P, P]
+        L.pot_mlp_gradients.argtypes = [P, P, I64, P, P, P, I64, P, P]
+        L.pot_mlp_train_step.argtypes = [P, P, I64, P, P, P, I64, ctypes.c_float, P]
+        L.pot_mlp_check.argtypes = [P, P]
+        L.pot_mlp_features.argtypes = [P, P, P, I64, P, P, P, P, ctypes.POINTER(Domain),
+                                       ctypes.POINTER(Params), P]
+        L.pot_set_warm_start.argtypes = [P, P]
+        for f in (L.pot_mlp_create, L.pot_mlp_destroy, L.pot_mlp_num_params, L.pot_mlp_set_params,
+                  L.pot_mlp_get_params, L.pot_mlp_forward, L.pot_mlp_gradients, L.pot_mlp_train_step,
+                  L.pot_mlp_check, L.pot_mlp_features, L.pot_set_warm_start):
+            f.restype = ctypes.c_int
         for f in (L.pot_create, L.pot_destroy, L.lgc_compute_cells, L.lgc_compute_cells_f64,
                   L.pot_newton_solve, L.pot_newton_solve_f64, L.pot_fluid_step, L.pot_fluid_step_f64):
             f.restype = ctypes.c_int
@@ -280,3 +296,110 @@ def pot_fluid_step(ctx: Context, pos, vel, psi, targets, domain=UNIT_BOX, params
     if check and code != POT_OK:
         raise PotError(code, "pot_fluid_step", s)
     return s
+
+
+# ---------------------------------------------------------------------------
+# learned warm start
+
+
+class Mlp:
+    """The warm-start MLP (80 -> 128 -> 128 -> 128 -> 1, BF16 on tensor cores)."""
+
+    N_IN = 80
+
+    def __init__(self, max_rows: int, device: int = 0):
+        self._h = ctypes.c_void_p()
+        self.device = torch.device("cuda", device)
+        self.max_rows = int(max_rows)
+        with torch.cuda.device(device):
+            code = lib().pot_mlp_create(ctypes.byref(self._h), device, self.max_rows)
+        if code != POT_OK:
+            raise PotError(code, "pot_mlp_create")
+
+    @staticmethod
+    def num_params() -> int:
+        return int(lib().pot_mlp_num_params())
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            lib().pot_mlp_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, code, where):
+        if code != POT_OK:
+            raise PotError(code, where)
+
+    def set_params(self, params, stream=None):
+        p = _dev(params, torch.float32, (self.num_params(),), "params", self.device)
+        self._check(lib().pot_mlp_set_params(self._h, _stream(stream), _ptr(p)), "pot_mlp_set_params")
+
+    def get_params(self, stream=None):
+        p = torch.empty(self.num_params(), dtype=torch.float32, device=self.device)
+        self._check(lib().pot_mlp_get_params(self._h, _stream(stream), _ptr(p)), "pot_mlp_get_params")
+        return p
+
+    def forward(self, x, stream=None):
+        rows = int(x.shape[0])
+        x = _dev(x, torch.bfloat16, (rows, self.N_IN), "x", self.device)
+        out = torch.empty(rows, dtype=torch.float32, device=self.device)
+        self._check(lib().pot_mlp_forward(self._h, _stream(stream), rows, _ptr(x), _ptr(out)),
+                    "pot_mlp_forward")
+        return out
+
+    def gradients(self, x_all, y_all, idx, stream=None):
+        n_all, batch = int(x_all.shape[0]), int(idx.shape[0])
+        x_all = _dev(x_all, torch.bfloat16, (n_all, self.N_IN), "x_all", self.device)
+        y_all = _dev(y_all, torch.float32, (n_all,), "y_all", self.device)
+        idx = _dev(idx, torch.int32, (batch,), "idx", self.device)
+        g = torch.empty(self.num_params(), dtype=torch.float32, device=self.device)
+        loss = torch.empty(1, dtype=torch.float32, device=self.device)
+        self._check(lib().pot_mlp_gradients(self._h, _stream(stream), n_all, _ptr(x_all), _ptr(y_all),
+                                            _ptr(idx), batch, _ptr(g), _ptr(loss)), "pot_mlp_gradients")
+        return g, loss
+
+    def train_step(self, x_all, y_all, idx, lr=1e-3, loss=None, stream=None):
+        """One Adam step on rows idx; the batch loss lands in `loss` (device)."""
+        n_all, batch = int(x_all.shape[0]), int(idx.shape[0])
+        self._check(lib().pot_mlp_train_step(self._h, _stream(stream), n_all, _ptr(x_all), _ptr(y_all),
+                                             _ptr(idx), batch, ctypes.c_float(lr), _ptr(loss)),
+                    "pot_mlp_train_step")
+
+    def check(self, stream=None):
+        self._check(lib().pot_mlp_check(self._h, _stream(stream)), "pot_mlp_check")
+
+
+def pot_mlp_features(ctx: Context, mlp: Mlp, pos, vel, psi, targets, domain=UNIT_BOX, params=None,
+                     stream=None):
+    """Warm-start features (n x 80 BF16, caller order) at the state the next
+    fluid step solves at."""
+    n = int(pos.shape[0])
+    dev = ctx.device
+    pos = _dev(pos, torch.float32, (n, 3), "pos", dev)
+    vel = _dev(vel, torch.float32, (n, 3), "vel", dev)
+    psi = _dev(psi, torch.float32, (n,), "psi", dev)
+    targets = _dev(targets, torch.float64, (n,), "targets", dev)
+    p = params if params is not None else default_params()
+    feat = torch.empty((n, Mlp.N_IN), dtype=torch.bfloat16, device=dev)
+    dom = _domain(domain)
+    code = lib().pot_mlp_features(ctx.handle, mlp.handle, _stream(stream), n, _ptr(pos), _ptr(vel),
+                                  _ptr(psi), _ptr(targets), ctypes.byref(dom), ctypes.byref(p),
+                                  _ptr(feat))
+    if code != POT_OK:
+        raise PotError(code, "pot_mlp_features")
+    return feat
+
+
+def set_warm_start(ctx: Context, mlp):
+    code = lib().pot_set_warm_start(ctx.handle, mlp.handle if mlp is not None else None)
+    if code != POT_OK:
+        raise PotError(code, "pot_set_warm_start")
