@@ -216,7 +216,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     sc = scenes.splash(spacing=args.spacing, seed=3 + rank)
     n = sc.n
-    ctx = pot.Context(n, 64, local, fp32=True, fp64=False)
+    ctx = pot.Context(n, 128, local, fp32=True, fp64=False)
     pos = torch.from_numpy(sc.pos).to(dev)
     vel = torch.from_numpy(sc.vel).to(dev)
     psi = torch.from_numpy(sc.psi).to(dev)
@@ -336,7 +336,7 @@ def run_cells(args):
     dev = torch.device("cuda", 0)
     sc = scenes.uniform_cloud(n=1 << 20, seed=1)
     n = sc.n
-    ctx = pot.Context(n, 64, 0, fp32=True, fp64=False)
+    ctx = pot.Context(n, 128, 0, fp32=True, fp64=False)
     pos = torch.from_numpy(sc.pos).to(dev)
     psi = torch.from_numpy(sc.psi).to(dev)
     nu = torch.from_numpy(sc.nu).to(dev)

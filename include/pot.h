@@ -130,8 +130,11 @@ typedef struct {
 
 /* ---- context ---------------------------------------------------------- */
 
-/* Create a context on `device` for up to n_max sites and k_max (<= 64)
- * cutting bisectors per cell, and allocate all its workspace.
+/* Create a context on `device` for up to n_max sites and k_max (<= 128)
+ * cutting bisectors per cell (bisectors whose plane cuts the site's ball;
+ * most of them have facets of zero area in packed fluid, and their number
+ * grows like (2r/spacing)^3 -- 128 covers r up to about 1.7 spacings), and
+ * allocate all its workspace.
  * precision_mask: bit 0 = FP32 geometry (mixed-precision entry points),
  * bit 1 = FP64 entry points (*_f64).
  * Returns POT_ERR_INVALID_ARG / POT_ERR_CUDA on failure (*ctx = NULL). */
@@ -187,7 +190,7 @@ int lgc_compute_cells_f64(pot_ctx* ctx, void* stream, int64_t n, const double* p
  * grad, centroids, karea; same meaning, layout and FP32/FP64 split), with
  * no context and no allocation: all scratch memory is one file-scope device
  * array inside libpot.so sized for n <= 8192 sites and 64 cutting bisectors
- * per cell (about 4.8 MB, held by every GPU that loads the library until the
+ * per cell (about 4.9 MB, held by every GPU that loads the library until the
  * process exits).  The caller passes device inputs and outputs as usual;
  * centroids, karea and grad may be NULL.
  *  - n > 8192 returns POT_ERR_TOO_LARGE before any device work.

@@ -33,7 +33,7 @@ int alloc(P** p, size_t count) {
 }
 
 template <typename T>
-int alloc_work(Work<T>& w, int64_t n, int64_t k) {
+int alloc_work(Work<T>& w, int64_t n, int64_t k, int64_t gcap) {
   POT_CHECK(alloc(&w.sxp, n));
   POT_CHECK(alloc(&w.psi_base, n));
   POT_CHECK(alloc(&w.vol, n));
@@ -51,6 +51,10 @@ int alloc_work(Work<T>& w, int64_t n, int64_t k) {
   POT_CHECK(alloc(&w.q, n));
   POT_CHECK(alloc(&w.vel_s, 3 * n));
   POT_CHECK(alloc(&w.psi_max, 1));
+  POT_CHECK(alloc(&w.nu_max, 1));
+  POT_CHECK(alloc(&w.srad, n));
+  POT_CHECK(alloc(&w.rcell, n));
+  POT_CHECK(alloc(&w.gmax, gcap + 1));
   return POT_OK;
 }
 
@@ -58,7 +62,7 @@ template <typename T>
 void free_work(Work<T>& w) {
   void* ptrs[] = {w.sxp, w.psi_base, w.vol,  w.karea, w.diag, w.cen, w.stage_vals, w.csr_vals,
                   w.u,   w.x,        w.r,    w.z,     w.p0,   w.p1,  w.q,          w.vel_s,
-                  w.psi_max};
+                  w.psi_max, w.nu_max, w.srad, w.rcell, w.gmax};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   w = Work<T>();
@@ -179,7 +183,7 @@ int pot_destroy(pot_ctx* ctx) {
   void* ptrs[] = {ctx->keys,     ctx->perm,    ctx->iperm,    ctx->cell_count, ctx->cell_start,
                   ctx->cand,     ctx->meta,    ctx->row_cnt,  ctx->row_ptr,    ctx->ucnt,
                   ctx->csr_cols, ctx->scan_tmp, ctx->snu,     ctx->grad,       ctx->red,
-                  ctx->red_out,  ctx->pcg_red, ctx->pcg_ctl,  ctx->err};
+                  ctx->red_out,  ctx->pcg_red, ctx->pcg_ctl,  ctx->err, ctx->need, ctx->need_count};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   free_work(ctx->wf);
@@ -233,9 +237,11 @@ int pot_create(pot_ctx** out, int device, int64_t n_max, int32_t k_max, int32_t 
   A(ctx->pcg_red, 5 * 2 * ctx->sm_count);
   A(ctx->pcg_ctl, 8);
   A(ctx->err, 2);
+  A(ctx->need, n);
+  A(ctx->need_count, 2);
 #undef A
-  if (s == POT_OK && (ctx->mask & 1)) s = alloc_work(ctx->wf, n, k);
-  if (s == POT_OK && (ctx->mask & 2)) s = alloc_work(ctx->wd, n, k);
+  if (s == POT_OK && (ctx->mask & 1)) s = alloc_work(ctx->wf, n, k, ctx->grid_cap);
+  if (s == POT_OK && (ctx->mask & 2)) s = alloc_work(ctx->wd, n, k, ctx->grid_cap);
   if (s == POT_OK && cudaMallocHost((void**)&ctx->h_pinned, 64 * sizeof(double)) != cudaSuccess)
     s = POT_ERR_CUDA;
   for (auto& e : ctx->ev)

@@ -2,10 +2,11 @@
 //
 // Two kernels per evaluation, both in grid-sorted order:
 //
-// k_candidates (one thread per cell): exact radius query over the grid rows
-//   around p_i.  Site j is kept iff its radical plane cuts the ball of i
-//   (|h_ij| < r_i, which implies |p_i - p_j| < r_i + r_j); a plane with
-//   h <= -r_i empties the cell.  The six box walls are planes too.
+// k_candidates (one thread per cell): exact query over the grid around p_i.
+//   Site j is kept iff its radical plane cuts the ball of i (|h_ij| < r_i,
+//   which implies |p_i - p_j| < r_i + r_j) and lies within the cell's
+//   security radius (h_ij < R_i, see below); a plane with h <= -r_i empties
+//   the cell.  The six box walls are planes too.
 //
 // k_cells (one warp per group of cells, one lane per cutting plane): each
 //   warp packs consecutive cells into its 32 lanes (a cell with m planes
@@ -60,13 +61,26 @@ __device__ __forceinline__ void set_error(int32_t* err, int code, int64_t site) 
 // ---------------------------------------------------------------------------
 // candidates
 
+// Security radius (the paper's contributing-neighbour problem, Sec. 4): a
+// cell is built from the bisectors with h_ij < R_i only, R_i <= r_i.  If the
+// cell so built lies strictly inside the ball of radius R_i around p_i, no
+// plane with h >= R_i can touch it and the cell is exact; otherwise R_i is
+// doubled and the cell rebuilt (pass loop in cells_eval).  Inside deep fluid
+// the weights grow like a pressure and the balls get many spacings wide,
+// while the cells stay small: R_i keeps the candidate lists short.
+//
+// Grid cells are skipped with a lower bound of h over their sites: for
+// |p_i - p_j| >= delta and psi_j <= gmax,  h_ij >= delta/2 - (gmax - psi_i)/(2 delta)
+// (increasing in the distance when gmax >= psi_i), and h_ij >= delta/2 otherwise.
 template <typename T>
 __global__ void __launch_bounds__(256)
     k_candidates(int64_t n, const V4<T>* __restrict__ sxp, const int32_t* __restrict__ cell_start,
-                 GridParams<T> g, Box<T> box, const T* __restrict__ psi_max, int kmax,
-                 int32_t* __restrict__ cand, int32_t* __restrict__ meta, int32_t* err) {
+                 GridParams<T> g, Box<T> box, const T* __restrict__ psi_max,
+                 const T* __restrict__ gmax, const T* __restrict__ srad,
+                 const uint8_t* __restrict__ need, int kmax, int32_t* __restrict__ cand,
+                 int32_t* __restrict__ meta, int32_t* err) {
   int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= n) return;
+  if (s >= n || !need[s]) return;
   const V4<T> p = sxp[s];
   const T ps = p.w;
   if (!(ps > T(0))) {
@@ -86,56 +100,71 @@ __global__ void __launch_bounds__(256)
       nw++;
     }
   }
-  const T R = r + sqrt(*psi_max);
-  const T R2 = R * R;
+  const T R = srad[s];
+  const T pmx = *psi_max;
+  // a site j with h_ij < R lies within R + sqrt(R^2 - psi_i + psi_j) of p_i,
+  // and one that cuts the ball within r + r_j
+  const T D = fmin(R + sqrt(fmax(R * R - ps + pmx, T(0))), r + sqrt(pmx));
+  const T D2 = D * D;
   int c0[3], c1[3];
   const T pc[3] = {p.x, p.y, p.z};
 #pragma unroll
   for (int k = 0; k < 3; k++) {
-    c0[k] = cell_coord(pc[k] - R, g.lo[k], g.inv_cs, g.dim[k]);
-    c1[k] = cell_coord(pc[k] + R, g.lo[k], g.inv_cs, g.dim[k]);
+    c0[k] = cell_coord(pc[k] - D, g.lo[k], g.inv_cs, g.dim[k]);
+    c1[k] = cell_coord(pc[k] + D, g.lo[k], g.inv_cs, g.dim[k]);
   }
   int nc = 0;
   bool empty = false;
-  int64_t row = s * (int64_t)kmax;
+  const int64_t row = s * (int64_t)kmax;
   for (int cz = c0[2]; cz <= c1[2] && !empty; cz++) {
-    T zlo = g.lo[2] + cz * g.cs;
+    const T zlo = g.lo[2] + cz * g.cs;
     T ez = fmax(T(0), fmax(zlo - p.z, p.z - (zlo + g.cs)));
     if (cz == 0 && p.z < zlo) ez = T(0);
     if (cz == g.dim[2] - 1 && p.z > zlo) ez = T(0);
     for (int cy = c0[1]; cy <= c1[1] && !empty; cy++) {
-      T ylo = g.lo[1] + cy * g.cs;
+      const T ylo = g.lo[1] + cy * g.cs;
       T ey = fmax(T(0), fmax(ylo - p.y, p.y - (ylo + g.cs)));
       if (cy == 0 && p.y < ylo) ey = T(0);
       if (cy == g.dim[1] - 1 && p.y > ylo) ey = T(0);
-      T rem2 = R2 - ey * ey - ez * ez;
-      if (rem2 <= T(0)) continue;
-      T rem = sqrt(rem2);
-      int x0 = cell_coord(p.x - rem, g.lo[0], g.inv_cs, g.dim[0]);
-      int x1 = cell_coord(p.x + rem, g.lo[0], g.inv_cs, g.dim[0]);
-      int key0 = (cz * g.dim[1] + cy) * g.dim[0];
-      int a = cell_start[key0 + x0], b = cell_start[key0 + x1 + 1];
-      for (int t = a; t < b; t++) {
-        if (t == s) continue;
-        const V4<T> q = sxp[t];
-        T dx, dy, dz;
-        T d2 = sqdist(p, q, dx, dy, dz);
-        T rj = q.w > T(0) ? sqrt(q.w) : T(0);
-        T sr = r + rj;
-        if (!(d2 < sr * sr)) continue;
-        if (d2 == T(0)) {
-          set_error(err, POT_ERR_COINCIDENT_SITES, s);
-          continue;
+      const T eyz = ey * ey + ez * ez;
+      if (eyz >= D2) continue;
+      for (int cx = c0[0]; cx <= c1[0] && !empty; cx++) {
+        const T xlo = g.lo[0] + cx * g.cs;
+        T ex = fmax(T(0), fmax(xlo - p.x, p.x - (xlo + g.cs)));
+        if (cx == 0 && p.x < xlo) ex = T(0);
+        if (cx == g.dim[0] - 1 && p.x > xlo) ex = T(0);
+        const T dl2 = ex * ex + eyz;
+        if (dl2 >= D2) continue;
+        const int key = (cz * g.dim[1] + cy) * g.dim[0] + cx;
+        if (dl2 > T(0)) {
+          const T dl = sqrt(dl2);
+          const T c = gmax[key] - ps;
+          const T hmin = c >= T(0) ? T(0.5) * dl - c / (T(2) * dl) : T(0.5) * dl;
+          if (hmin >= R) continue;
         }
-        T d;
-        T h = fix_zero(plane_offset(d2, ps, q.w, d), r);
-        if (h <= -r) {
-          empty = true;
-          break;
-        }
-        if (h < r) {
-          if (nc < kmax) cand[row + nc] = t;
-          nc++;
+        const int a = cell_start[key], b = cell_start[key + 1];
+        for (int t = a; t < b; t++) {
+          if (t == s) continue;
+          const V4<T> q = sxp[t];
+          T dx, dy, dz;
+          const T d2 = sqdist(p, q, dx, dy, dz);
+          const T rj = q.w > T(0) ? sqrt(q.w) : T(0);
+          const T sr = r + rj;
+          if (!(d2 < sr * sr)) continue;
+          if (d2 == T(0)) {
+            set_error(err, POT_ERR_COINCIDENT_SITES, s);
+            continue;
+          }
+          T d;
+          const T h = fix_zero(plane_offset(d2, ps, q.w, d), r);
+          if (h <= -r) {
+            empty = true;
+            break;
+          }
+          if (h < r && h < R) {
+            if (nc < kmax) cand[row + nc] = t;
+            nc++;
+          }
         }
       }
     }
@@ -156,6 +185,7 @@ __global__ void __launch_bounds__(256)
 template <typename T>
 struct Facet {
   T area, omega, mx, my, mz;
+  T rm2;  // squared distance from the site of the facet's farthest point
   int overflow;
 };
 
@@ -188,7 +218,7 @@ __device__ __forceinline__ void isect(T a1, T b1, T c1, T a2, T b2, T c2, T& x, 
 // Returns area, signed solid angle at the site and first moment (about the site).
 template <typename T>
 __device__ Facet<T> facet_eval(const V4<T>* __restrict__ pl, int m, int fi, T ps, T r) {
-  Facet<T> out = {T(0), T(0), T(0), T(0), T(0), 0};
+  Facet<T> out = {T(0), T(0), T(0), T(0), T(0), T(0), 0};
   const V4<T> P = pl[fi];
   const T h = P.w;
   const T rho2 = ps - h * h;
@@ -302,9 +332,13 @@ __device__ Facet<T> facet_eval(const V4<T>* __restrict__ pl, int m, int fi, T ps
     mx += ta * (ax + bx) * T(1.0 / 3.0);
     my += ta * (ay + by) * T(1.0 / 3.0);
   };
+  T rm2 = T(0);
+  bool arc = false;
   for (int k = 0; k < nl; k++) {
     int k2 = k + 1 == nl ? 0 : k + 1;
     T pxk = px[cur][k], pyk = py[cur][k], qx = px[cur][k2], qy = py[cur][k2];
+    const T pk2 = pxk * pxk + pyk * pyk;
+    if (pk2 <= rho2) rm2 = fmax(rm2, pk2 + h2);  // a polygon vertex inside the disk
     T dx = qx - pxk, dy = qy - pyk;
     T a2 = dx * dx + dy * dy;
     if (a2 == T(0)) continue;
@@ -313,6 +347,7 @@ __device__ Facet<T> facet_eval(const V4<T>* __restrict__ pl, int m, int fi, T ps
     T disc = b2 * b2 - a2 * c2;
     if (disc <= T(0)) {
       sector(pxk, pyk, qx, qy);
+      arc = true;
       continue;
     }
     T sq = sqrt(disc);
@@ -324,10 +359,17 @@ __device__ Facet<T> facet_eval(const V4<T>* __restrict__ pl, int m, int fi, T ps
     T y1 = t1 == T(0) ? pyk : (t1 == T(1) ? qy : pyk + t1 * dy);
     T x2 = t2 == T(0) ? pxk : (t2 == T(1) ? qx : pxk + t2 * dx);
     T y2 = t2 == T(0) ? pyk : (t2 == T(1) ? qy : pyk + t2 * dy);
-    if (t1 > T(0)) sector(pxk, pyk, x1, y1);
+    if (t1 > T(0)) {
+      sector(pxk, pyk, x1, y1);
+      arc = true;
+    }
     if (t2 > t1) tri(x1, y1, x2, y2);
-    if (t2 < T(1)) sector(x2, y2, qx, qy);
+    if (t2 < T(1)) {
+      sector(x2, y2, qx, qy);
+      arc = true;
+    }
   }
+  out.rm2 = arc ? ps : rm2;  // the facet reaches the sphere when it has an arc
   out.area = area;
   out.omega = omg;
   out.mx = h * P.x * area + ux * mx + vx * my;
@@ -381,7 +423,7 @@ __device__ __forceinline__ void plane_of(int f, int64_t cell, const V4<T>& p, in
 
 template <typename T>
 struct CellAcc {
-  T hA, om, nx, ny, nz, hx, hy, hz, dg;
+  T hA, om, nx, ny, nz, hx, hy, hz, dg, rm2;
 };
 
 template <typename T>
@@ -396,6 +438,7 @@ __device__ __forceinline__ void acc_facet(CellAcc<T>& a, const V4<T>& pl, T pd, 
   a.hy += pl.w * fo.my;
   a.hz += pl.w * fo.mz;
   if (pj >= 0) a.dg += fo.area / (T(2) * pd);
+  a.rm2 = fmax(a.rm2, fo.rm2);
 }
 
 // sum over lanes [lane, last] into the first lane of the window (segment head)
@@ -420,9 +463,16 @@ __device__ __forceinline__ void seg_reduce(CellAcc<T>& a, int lane, int last) {
   a.hy = seg_sum(a.hy, lane, last);
   a.hz = seg_sum(a.hz, lane, last);
   a.dg = seg_sum(a.dg, lane, last);
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    T t = __shfl_down_sync(kFull, a.rm2, off);
+    if (lane + off <= last) a.rm2 = fmax(a.rm2, t);
+  }
 }
 
 struct CellOut {
+  void* rcell;
+  const uint8_t* need;
   void* vol;
   void* karea;
   void* diag;
@@ -451,6 +501,13 @@ __device__ __forceinline__ void write_cell(int64_t cell, const V4<T>& p, bool em
       cz += (a.hz - ps * a.nz) * iv;
     }
   }
+  // farthest point of the cell from its site, decided geometrically (|K|
+  // carries rounding noise of a few ulp of 4 pi psi): the sphere if a facet
+  // leaves its disk (rm2 = psi then) or if there is no facet at all (a full
+  // ball), else the farthest facet vertex
+  T rc = T(0);
+  if (!empty && ps > T(0)) rc = a.rm2 > T(0) ? sqrt(a.rm2) : (V > T(0) ? sqrt(ps) : T(0));
+  ((T*)o.rcell)[cell] = rc;
   ((T*)o.vol)[cell] = V;
   ((T*)o.karea)[cell] = K;
   ((T*)o.diag)[cell] = dg;
@@ -521,9 +578,10 @@ __global__ void __launch_bounds__(kCellWarps * 32)
   while (base < c1) {
     const int64_t cell = base + lane;
     const bool valid = cell < c1;
-    const int mt = valid ? meta[cell] : 0;
+    const bool todo = valid && o.need[cell];  // cells finished in an earlier pass take no lane
+    const int mt = todo ? meta[cell] : 0;
     const int m = mt & kMetaPlanes;
-    const int slots = valid ? (m > 1 ? m : 1) : 0;
+    const int slots = todo ? (m > 1 ? m : 1) : 0;
     int incl = slots;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
@@ -531,21 +589,23 @@ __global__ void __launch_bounds__(kCellWarps * 32)
       if (lane >= off) incl += t;
     }
     const int excl = incl - slots;
-    const bool fits = valid && incl <= 32;
-    const int ncell = __popc(__ballot_sync(kFull, fits));
+    const bool take = valid && incl <= 32;  // a prefix of the cells
+    const int ncell = __popc(__ballot_sync(kFull, take));
     if (ncell == 0) {
       big_cell(base, lane, pl, pd, pj, sxp, meta, cand, kmax, box, stage_vals, o, err);
       base += 1;
       continue;
     }
-    const unsigned head = __reduce_or_sync(kFull, fits ? (1u << excl) : 0u);
+    const unsigned owners = __ballot_sync(kFull, take && slots > 0);
+    const unsigned head = __reduce_or_sync(kFull, (take && slots > 0) ? (1u << excl) : 0u);
     const int used = __shfl_sync(kFull, incl, ncell - 1);
     const bool active = lane < used;
     const int seg = active ? __popc(head & (kFull >> (31 - lane))) - 1 : 0;
-    const int sstart = __shfl_sync(kFull, excl, seg);
-    const int cmt = __shfl_sync(kFull, mt, seg);
+    const int owner = active ? (int)__fns(owners, 0, seg + 1) : 0;  // lane of the seg-th cell
+    const int sstart = __shfl_sync(kFull, excl, owner);
+    const int cmt = __shfl_sync(kFull, mt, owner);
     const int cm = cmt & kMetaPlanes;
-    const int64_t ccell = base + seg;
+    const int64_t ccell = base + owner;
     const int f = lane - sstart;
     const bool has = active && f < cm;
     V4<T> p = {};
@@ -581,6 +641,57 @@ __global__ void __launch_bounds__(kCellWarps * 32)
                  __popc(emm & segmask), o);
     __syncwarp();
     base += ncell;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// security-radius passes
+
+// largest weight of the sites of each grid cell (very negative when empty)
+template <typename T>
+__global__ void k_gmax(int64_t ncell, const int32_t* __restrict__ cell_start,
+                       const V4<T>* __restrict__ sxp, T* gmax) {
+  int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  T m = T(-1e30);
+  for (int t = cell_start[c]; t < cell_start[c + 1]; t++) m = fmax(m, sxp[t].w);
+  gmax[c] = m;
+}
+
+// first security radius: 1.25 x the cell's extent in the previous evaluation
+// (Newton changes cells little), else 1.5 nu^(1/3), never beyond the ball
+template <typename T>
+__global__ void k_srad_init(int64_t n, const V4<T>* __restrict__ sxp, const double* __restrict__ snu,
+                            const T* __restrict__ rcell, int have_prev, T* srad, uint8_t* need) {
+  int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const T ps = sxp[s].w;
+  const T r = ps > T(0) ? sqrt(ps) : T(0);
+  T R = r;
+  if (have_prev && rcell[s] > T(0))
+    R = T(1.25) * rcell[s];
+  else if (snu[s] > 0.0)
+    R = T(1.5) * (T)cbrt(snu[s]);
+  srad[s] = fmin(R, r);
+  need[s] = 1;
+}
+
+// a cell built inside radius R is exact if it stays strictly inside R (or R
+// reached the ball); otherwise double R and rebuild it
+template <typename T>
+__global__ void k_need_update(int64_t n, const V4<T>* __restrict__ sxp, const T* __restrict__ rcell,
+                              T* srad, uint8_t* need, int32_t* count) {
+  int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n || !need[s]) return;
+  const T ps = sxp[s].w;
+  const T r = ps > T(0) ? sqrt(ps) : T(0);
+  const T R = srad[s];
+  const bool done = !(ps > T(0)) || R >= r || rcell[s] < R * T(1.0 - 1e-5);
+  if (done) {
+    need[s] = 0;
+  } else {
+    srad[s] = fmin(r, T(2) * R);
+    atomicAdd(count, 1);
   }
 }
 
@@ -747,11 +858,15 @@ int cells_eval(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* dom, 
     box.lo[k] = (T)dom->lo[k];
     box.hi[k] = (T)dom->hi[k];
   }
+  const int64_t ncell = (int64_t)w.grid.dim[0] * w.grid.dim[1] * w.grid.dim[2];
   note_launch();
-  k_candidates<T><<<blocks_for(n, 256), 256, 0, st>>>(n, w.sxp, ctx->cell_start, w.grid, box,
-                                                       w.psi_max, ctx->k_max, ctx->cand, ctx->meta,
-                                                       ctx->err);
+  k_gmax<T><<<blocks_for(ncell, 256), 256, 0, st>>>(ncell, ctx->cell_start, w.sxp, w.gmax);
+  note_launch();
+  k_srad_init<T><<<blocks_for(n, 256), 256, 0, st>>>(n, w.sxp, ctx->snu, w.rcell,
+                                                      w.have_rcell ? 1 : 0, w.srad, ctx->need);
   CellOut o;
+  o.rcell = w.rcell;
+  o.need = ctx->need;
   o.vol = w.vol;
   o.karea = w.karea;
   o.diag = w.diag;
@@ -759,12 +874,27 @@ int cells_eval(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* dom, 
   o.row_cnt = ctx->row_cnt;
   o.grad = want_grad ? ctx->grad : nullptr;
   o.snu = ctx->snu;
-  int64_t warps = (n + kCellsPerWarp - 1) / kCellsPerWarp;
-  int blocks = (int)((warps + kCellWarps - 1) / kCellWarps);
-  note_launch();
-  k_cells<T><<<blocks, kCellWarps * 32, 0, st>>>(n, w.sxp, ctx->meta, ctx->cand, ctx->k_max, box,
-                                                 w.stage_vals, o, ctx->err);
+  const int64_t warps = (n + kCellsPerWarp - 1) / kCellsPerWarp;
+  const int blocks = (int)((warps + kCellWarps - 1) / kCellWarps);
+  int32_t* hcount = (int32_t*)(ctx->h_pinned + 24);
+  for (int pass = 0; pass < 24; pass++) {
+    note_launch();
+    k_candidates<T><<<blocks_for(n, 256), 256, 0, st>>>(n, w.sxp, ctx->cell_start, w.grid, box,
+                                                         w.psi_max, w.gmax, w.srad, ctx->need,
+                                                         ctx->k_max, ctx->cand, ctx->meta, ctx->err);
+    note_launch();
+    k_cells<T><<<blocks, kCellWarps * 32, 0, st>>>(n, w.sxp, ctx->meta, ctx->cand, ctx->k_max, box,
+                                                   w.stage_vals, o, ctx->err);
+    POT_CUDA(cudaMemsetAsync(ctx->need_count, 0, sizeof(int32_t), st));
+    note_launch();
+    k_need_update<T><<<blocks_for(n, 256), 256, 0, st>>>(n, w.sxp, w.rcell, w.srad, ctx->need,
+                                                          ctx->need_count);
+    POT_CUDA(cudaMemcpyAsync(hcount, ctx->need_count, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    POT_CUDA(cudaStreamSynchronize(st));
+    if (*hcount == 0) break;
+  }
   POT_CUDA(cudaGetLastError());
+  w.have_rcell = true;
   return POT_OK;
 }
 

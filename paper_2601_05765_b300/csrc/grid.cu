@@ -35,6 +35,16 @@ __global__ void k_psi_max_in(const T* __restrict__ psi, int64_t n, T* out) {
   }
 }
 
+__global__ void k_nu_max_in(const double* __restrict__ nu, int64_t n, double* out) {
+  double m = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    m = fmax(m, nu[i]);
+  for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_down_sync(kFull, m, off));
+  if ((threadIdx.x & 31) == 0)
+    atomicMax((unsigned long long*)out, (unsigned long long)__double_as_longlong(m));
+}
+
 template <typename T>
 __global__ void k_keys(const T* __restrict__ pos, int64_t n, GridParams<T> g, uint32_t* keys,
                        int32_t* count) {
@@ -101,18 +111,30 @@ int grid_build(pot_ctx* ctx, cudaStream_t st, int64_t n, const T* pos, const T* 
   POT_CUDA(cudaMemsetAsync(w.psi_max, 0, sizeof(T), st));
   note_launch();
   k_psi_max_in<T><<<kRedBlocks, 256, 0, st>>>(psi, n, w.psi_max);
+  POT_CUDA(cudaMemsetAsync(ctx->red_out + 7, 0, sizeof(double), st));
+  if (targets) {
+    note_launch();
+    k_nu_max_in<<<kRedBlocks, 256, 0, st>>>(targets, n, ctx->red_out + 7);
+  }
   POT_CUDA(cudaMemcpyAsync(ctx->h_pinned, w.psi_max, sizeof(T), cudaMemcpyDeviceToHost, st));
+  POT_CUDA(cudaMemcpyAsync(ctx->h_pinned + 1, ctx->red_out + 7, sizeof(double),
+                           cudaMemcpyDeviceToHost, st));
   POT_CUDA(cudaStreamSynchronize(st));
   double pmax = sizeof(T) == 4 ? (double)*(float*)ctx->h_pinned : *(double*)ctx->h_pinned;
+  const double numax = ctx->h_pinned[1];
   if (!(pmax >= 0.0) || isinf(pmax)) return POT_ERR_INVALID_ARG;
   double ext[3], emax = 0.0;
   for (int k = 0; k < 3; k++) {
     ext[k] = dom->hi[k] - dom->lo[k];
     emax = fmax(emax, ext[k]);
   }
-  // cell = diameter of the largest ball: the 27-cell block around a site
-  // holds every candidate; never more cells than the grid capacity
+  // cell ~ a few site spacings: the diameter of the largest ball, but no more
+  // than 3 nu_max^(1/3) (weights grow like a pressure inside deep fluid, so
+  // the largest ball says little about the spacing); the search of a cell
+  // covers as many grid cells as its radius needs.  Never more cells than
+  // the grid capacity.
   double cs = 2.0 * sqrt(pmax);
+  if (numax > 0.0) cs = fmin(cs, 3.0 * cbrt(numax));
   cs = fmax(cs, emax / 1024.0);
   int dim[3];
   for (;;) {
@@ -148,6 +170,7 @@ int grid_build(pot_ctx* ctx, cudaStream_t st, int64_t n, const T* pos, const T* 
   POT_CUDA(cudaGetLastError());
   w.grid = g;
   w.grid_valid = true;
+  w.have_rcell = false;
   return POT_OK;
 }
 

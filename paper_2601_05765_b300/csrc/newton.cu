@@ -212,8 +212,12 @@ int newton_sorted(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* do
     bool accepted = false;
     for (int hv = 0; hv <= P->max_halvings; hv++) {
       POT_CHECK(psi_update<T>(ctx, st, n, alpha));
-      POT_CHECK(eval_and_reduce<T>(ctx, st, n, dom, res, S));
-      if (res[2] >= eps0 && sqrt(res[1]) <= (1.0 - 0.5 * alpha) * gnorm) {
+      // a trial whose balls grew past the cell kernel's capacities is a
+      // rejected step (halve), not a failure of the solve
+      const int code = eval_and_reduce<T>(ctx, st, n, dom, res, S);
+      if (code != POT_OK && code != POT_ERR_NEIGHBOUR_OVERFLOW && code != POT_ERR_POLYGON_OVERFLOW)
+        return code;
+      if (code == POT_OK && res[2] >= eps0 && sqrt(res[1]) <= (1.0 - 0.5 * alpha) * gnorm) {
         accepted = true;
         break;
       }

@@ -2,7 +2,8 @@
 // allocate device memory.
 //
 // Every scratch buffer of the evaluation (sorted sites, grid, candidate
-// lists, per-cell results, reduction partials, status words) lives in one
+// lists, per-cell results, security radii, reduction partials, status
+// words) lives in one
 // file-scope device array of fixed size, so a call allocates nothing: no
 // cudaMalloc, cudaFree, pinned host memory or event.  The array is sized for
 // kNoAllocMaxSites sites and k_max = 64 and is held by every GPU that loads
@@ -54,7 +55,13 @@ constexpr size_t oDiag = oKarea + al(4 * N);
 constexpr size_t oCen = oDiag + al(4 * N);
 constexpr size_t oStage = oCen + al(12 * N);
 constexpr size_t oPsiMax = oStage + al(4 * N * kNoAllocK);
-constexpr size_t kScratchBytes = oPsiMax + al(8);
+constexpr size_t oNuMax = oPsiMax + al(8);
+constexpr size_t oSrad = oNuMax + al(8);
+constexpr size_t oRcell = oSrad + al(4 * N);
+constexpr size_t oGmax = oRcell + al(4 * N);
+constexpr size_t oNeed = oGmax + al(4 * (kNoAllocGridCap + 1));
+constexpr size_t oNeedCount = oNeed + al(N);
+constexpr size_t kScratchBytes = oNeedCount + al(8);
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -134,6 +141,12 @@ extern "C" int lgc_compute_cells_noalloc(void* stream, int64_t n, const float* p
   w.cen = (float*)(b + oCen);
   w.stage_vals = (float*)(b + oStage);
   w.psi_max = (float*)(b + oPsiMax);
+  w.nu_max = (float*)(b + oNuMax);
+  w.srad = (float*)(b + oSrad);
+  w.rcell = (float*)(b + oRcell);
+  w.gmax = (float*)(b + oGmax);
+  c.need = (uint8_t*)(b + oNeed);
+  c.need_count = (int32_t*)(b + oNeedCount);
 
   // the previous call's status words are stale: clear them
   POT_CUDA(cudaMemcpyAsync(c.err, kErrInit, sizeof(kErrInit), cudaMemcpyHostToDevice, st));

@@ -25,7 +25,7 @@ namespace pot {
 
 constexpr int kWarp = 32;
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kMaxK = 64;          // cutting bisectors per cell (k_max <= 64)
+constexpr int kMaxK = 128;         // cutting bisectors per cell (k_max <= 128)
 constexpr int kPlaneCap = kMaxK + 6;
 constexpr int kMaxLines = 24;      // edges of one facet polygon
 constexpr int kCellWarps = 4;      // warps per block of the cell kernel
@@ -139,8 +139,13 @@ struct Work {
   T* q = nullptr;
   T* vel_s = nullptr;       // sorted velocities, 3 per site
   T* psi_max = nullptr;     // device scalar: max psi of the current evaluation
+  T* nu_max = nullptr;      // device scalar: max target volume (grid build)
+  T* srad = nullptr;        // per cell: security radius of the current pass
+  T* rcell = nullptr;       // per cell: farthest point of the cell from its site
+  T* gmax = nullptr;        // per grid cell: largest psi of its sites
   GridParams<T> grid{};
   bool grid_valid = false;
+  bool have_rcell = false;  // rcell belongs to the current grid order
 };
 
 }  // namespace pot
@@ -175,6 +180,8 @@ struct pot_ctx {
   double* pcg_red = nullptr;      // PCG reduction partials
   int32_t* pcg_ctl = nullptr;     // PCG control words
   int32_t* err = nullptr;         // device status words
+  uint8_t* need = nullptr;        // per cell: still to be (re)built in this evaluation
+  int32_t* need_count = nullptr;  // device counter of cells to rebuild
   double* h_pinned = nullptr;     // pinned host scalars
   cudaEvent_t ev[8] = {};
   pot::Work<float> wf;

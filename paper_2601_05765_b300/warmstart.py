@@ -1,0 +1,111 @@
+"""Training and evaluation of the learned warm start.
+
+Data: plain-Newton fluid steps on dam-break columns (seeded); every `every`
+steps, the features at the state the step solves at (positions advanced by
+dt v and clamped, previous weights psi^k, velocities) and the converged
+weights psi^{k+1} of `per_sample` random sites give samples
+(x, y = (psi^{k+1} - psi^k) / h^2), h = nu^(1/3).
+
+Training: Adam on the mean squared error, shuffled batches, all kernels in
+libpot.so (tensor-core forward and back-propagation).  Evaluation: the same
+fluid steps started from the MLP prediction and from the previous weights.
+
+Dataset assembly (row sampling, the target difference) uses torch indexing as
+plumbing; features, training and solves run in the library.
+"""
+from __future__ import annotations
+
+import math
+import time
+
+import numpy as np
+import torch
+
+from . import pot, scenes
+
+
+def _state(sc, dev):
+    return (torch.from_numpy(sc.pos).to(dev), torch.from_numpy(sc.vel).to(dev),
+            torch.from_numpy(sc.psi).to(dev), torch.from_numpy(sc.nu).to(dev))
+
+
+def settle(ctx, pos, vel, psi, nu, prm):
+    """Converge the initial weights (not a sample): a Newton solve in place."""
+    st = pot.pot_newton_solve(ctx, pos, nu, psi, params=prm, check=False)
+    return st
+
+
+def collect(ctx, mlp, scene, steps, every, per_sample, seed, dt, tol=1e-4):
+    """Samples from `steps` plain-Newton fluid steps of `scene`."""
+    dev = ctx.device
+    pos, vel, psi, nu = _state(scene, dev)
+    prm = pot.default_params(dt=dt, tol=tol)
+    settle(ctx, pos, vel, psi, nu, prm)
+    h2 = torch.pow(nu, 2.0 / 3.0).float()
+    gen = torch.Generator(device="cpu").manual_seed(seed)
+    xs, ys = [], []
+    for k in range(steps):
+        take = k % every == 0
+        if take:
+            feat = pot.pot_mlp_features(ctx, mlp, pos, vel, psi, nu, params=prm)
+            psi_prev = psi.clone()
+        st = pot.pot_fluid_step(ctx, pos, vel, psi, nu, params=prm, check=False)
+        if st["status"] != 0:
+            raise RuntimeError(f"fluid step {k} failed: {st}")
+        if take:
+            idx = torch.randperm(scene.n, generator=gen)[:per_sample].to(dev)
+            xs.append(feat[idx])
+            ys.append(((psi - psi_prev) / h2)[idx])
+    return torch.cat(xs), torch.cat(ys)
+
+
+def train(mlp, x, y, epochs, batch=8192, lr=1e-3, seed=0):
+    """Adam epochs over (x, y); returns the mean loss of each epoch."""
+    n = int(x.shape[0])
+    batch = min(batch, (n // 8) * 8)
+    gen = torch.Generator(device="cpu").manual_seed(seed)
+    loss = torch.zeros(1, dtype=torch.float32, device=x.device)
+    hist = []
+    for _ in range(epochs):
+        perm = torch.randperm(n, generator=gen).to(torch.int32).to(x.device)
+        acc, nb = 0.0, 0
+        for b0 in range(0, n - batch + 1, batch):
+            mlp.train_step(x, y, perm[b0:b0 + batch], lr=lr, loss=loss)
+            acc += float(loss.item()) if nb % 64 == 0 else 0.0
+            nb += 1
+        mlp.check()
+        hist.append(acc / max(1, (nb + 63) // 64))
+    return hist
+
+
+def compare(ctx, mlp, scene, steps, dt, warm_steps=0, tol=1e-4):
+    """Run the same fluid steps from the same state with the plain start and
+    with the MLP start; returns per-step stats for both."""
+    dev = ctx.device
+    pos, vel, psi, nu = _state(scene, dev)
+    prm = pot.default_params(dt=dt, tol=tol)
+    settle(ctx, pos, vel, psi, nu, prm)
+    for _ in range(warm_steps):
+        pot.pot_fluid_step(ctx, pos, vel, psi, nu, params=prm)
+    state = (pos.clone(), vel.clone(), psi.clone())
+    out = {}
+    for mode in (0, 1):
+        pos, vel, psi = (t.clone() for t in state)
+        p = pot.default_params(dt=dt, tol=tol, warm_start=mode)
+        pot.set_warm_start(ctx, mlp if mode else None)
+        stats = []
+        for _ in range(steps):
+            stats.append(pot.pot_fluid_step(ctx, pos, vel, psi, nu, params=p, check=False))
+        out["mlp" if mode else "plain"] = stats
+    pot.set_warm_start(ctx, None)
+    return out
+
+
+def summarize(stats):
+    keys = ("err_start", "newton_iters", "pcg_iters", "halvings", "cell_evals", "ms_total")
+    s = {k: float(np.mean([st[k] for st in stats])) for k in keys}
+    s["fallback_rate"] = float(np.mean([st["mlp_fallback"] for st in stats]))
+    s["used_rate"] = float(np.mean([st["mlp_used"] for st in stats]))
+    s["all_converged"] = all(st["status"] == 0 for st in stats)
+    s["max_err"] = float(max(st["err_max"] for st in stats))
+    return s
