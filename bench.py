@@ -216,7 +216,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     sc = scenes.splash(spacing=args.spacing, seed=3 + rank)
     n = sc.n
-    ctx = pot.Context(n, 128, local, fp32=True, fp64=False)
+    ctx = pot.Context(n, 256, local, fp32=True, fp64=False)
     pos = torch.from_numpy(sc.pos).to(dev)
     vel = torch.from_numpy(sc.vel).to(dev)
     psi = torch.from_numpy(sc.psi).to(dev)

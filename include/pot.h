@@ -126,15 +126,21 @@ typedef struct {
   int64_t nnz;         /* Hessian entries of the last assembly */
   int32_t mlp_used;    /* warm start: 1 if the MLP start was kept */
   int32_t mlp_fallback;/* warm start: 1 if the MLP start was rejected */
+  int32_t repairs;     /* empty cells at the start whose weight was raised */
+  int32_t passes;      /* security-radius passes over all cell evaluations */
 } pot_solve_stats;
 
 /* ---- context ---------------------------------------------------------- */
 
-/* Create a context on `device` for up to n_max sites and k_max (<= 128)
- * cutting bisectors per cell (bisectors whose plane cuts the site's ball;
- * most of them have facets of zero area in packed fluid, and their number
- * grows like (2r/spacing)^3 -- 128 covers r up to about 1.7 spacings), and
- * allocate all its workspace.
+/* Create a context on `device` for up to n_max sites and k_max (<= 256)
+ * candidate bisectors per cell, and allocate all its workspace.  A cell is
+ * built from the bisectors whose plane cuts its ball within the cell's
+ * security radius (the distance from the site that the cell is verified not
+ * to exceed, Sec. 4); in packed fluid that is about 15-40 planes, in
+ * strongly compressed fluid (sites much closer than nu^(1/3)) cells reach
+ * past several neighbours and need more.  A cell that needs more than k_max
+ * gives POT_ERR_NEIGHBOUR_OVERFLOW.  Workspace: about 16 k_max + 250 bytes
+ * per site and precision.
  * precision_mask: bit 0 = FP32 geometry (mixed-precision entry points),
  * bit 1 = FP64 entry points (*_f64).
  * Returns POT_ERR_INVALID_ARG / POT_ERR_CUDA on failure (*ctx = NULL). */
@@ -152,6 +158,15 @@ void pot_default_params(pot_params* p);
 /* Number of CUDA kernel launches this library has issued in this process
  * (all contexts and devices), for launch accounting by callers. */
 int64_t pot_kernel_launches(void);
+
+/* Device time of the cell kernel (clipping, restriction and analytic
+ * quantities, Sec. 3.2-3.4) accumulated over this context's evaluations since
+ * the last reset, measured with CUDA events on the caller's stream around each
+ * launch: the number of launches (one per security-radius pass), the cells
+ * they processed and the milliseconds.  Any output pointer may be NULL;
+ * reset != 0 clears the counters after reading them.
+ * Errors: POT_ERR_INVALID_ARG for a NULL context. */
+int pot_cell_kernel_time(pot_ctx* ctx, int reset, int64_t* launches, int64_t* cells, double* ms);
 
 /* ---- generalized Laguerre cells (Eq. 1, Sec. 3.2-3.4, Algorithm 2) ------ */
 
@@ -210,7 +225,10 @@ int lgc_compute_cells_noalloc(void* stream, int64_t n, const float* pos, const f
 /* ---- Newton solve (Algorithm 1 with KMT steps) --------------------------- */
 
 /* Find the weights psi with |C_i(psi)| = targets[i] for all i (partial OT,
- * Sec. 2.2) by damped Newton (Algorithm 1): M u = nu - V(psi) solved by
+ * Sec. 2.2) by damped Newton (Algorithm 1).  A start with empty cells is
+ * repaired first: each empty cell's weight is raised to
+ * max_j (psi_j - d_ij^2) + 0.1 d*^2, which puts its site inside its own cell
+ * (stats->repairs counts them).  Then M u = nu - V(psi) is solved by
  * Jacobi-preconditioned CG (Sec. 7), then the KMT step: alpha = 1, 1/2, ...
  * until min V(psi + alpha u) >= eps0 and
  * ||nu - V(psi + alpha u)||_2 <= (1 - alpha/2) ||nu - V(psi)||_2,
@@ -218,7 +236,8 @@ int lgc_compute_cells_noalloc(void* stream, int64_t n, const float* pos, const f
  * max_i |V_i - nu_i| / nu_i <= params->tol.
  * psi_inout: start (must give non-empty cells) in, solution out.
  * Mixed precision: FP32 geometry and matrix, FP64 residuals, PCG dot
- * products and KMT test.  Errors: POT_ERR_EMPTY_CELL_AT_START,
+ * products and KMT test.  Errors: POT_ERR_EMPTY_CELL_AT_START (if the repair
+ * fails),
  * POT_ERR_NOT_CONVERGED, POT_ERR_LINESEARCH_FAILED, geometry errors.
  * psi_inout holds the last accepted iterate on NOT_CONVERGED. */
 int pot_newton_solve(pot_ctx* ctx, void* stream, int64_t n, const float* pos, const double* targets,
@@ -246,15 +265,17 @@ int pot_fluid_step_f64(pot_ctx* ctx, void* stream, int64_t n, double* pos, doubl
                        double* psi, const double* targets, const pot_domain* dom,
                        const pot_params* params, pot_solve_stats* stats);
 
-/* ---- learned warm start (not in the paper; task statement) --------------- */
+/* ---- learned warm start (not in the paper) ------------------------------- */
 
 /* A small MLP predicts each site's new weight from its neighbourhood:
  * inputs (80 BF16 values per site, row-major): offsets to the up to 24
  * nearest other sites closer than 2 sqrt(max psi), by increasing distance,
- * divided by h = nu^(1/3) (zero-padded); psi_prev / h^2; v dt / h; 4 zeros.
+ * divided by h = nu^(1/3) (zero-padded); psi_prev / h^2; v dt / h; the
+ * previous weight change (psi_prev - psi_old) / h^2 (0 without history);
+ * 3 zeros.
  * Network: 80 -> 128 -> 128 -> 128 (ReLU) -> 1, BF16 weights and activations,
  * FP32 accumulation on the tcgen05 tensor cores.  Prediction:
- * psi_start = psi_prev + h^2 * output.  Parameters are one FP32 vector of
+ * psi_start = psi_prev + h^2 * clamp(output, -1, 1).  Parameters are one FP32 vector of
  * pot_mlp_num_params() values: W1 (80 x 128, row = input), b1 (128),
  * W2 (128 x 128), b2, W3 (128 x 128), b3, w4 (128), b4 (1). */
 typedef struct pot_mlp pot_mlp;
@@ -292,16 +313,27 @@ int pot_mlp_check(pot_mlp* mlp, void* stream);
 
 /* Features (n x 80 BF16, caller order) at the positions and velocities the
  * next pot_fluid_step will solve at (x + dt v clamped into the box, same rule),
- * with psi as the previous weights.  Uses ctx's grid workspace. */
+ * with psi as the previous weights and psi_old as the weights one step before
+ * them (NULL: no history, the change feature is 0).  Uses ctx's grid
+ * workspace. */
 int pot_mlp_features(pot_ctx* ctx, pot_mlp* mlp, void* stream, int64_t n, const float* pos,
-                     const float* vel, const float* psi, const double* targets,
-                     const pot_domain* dom, const pot_params* params, uint16_t* feat);
+                     const float* vel, const float* psi, const float* psi_old,
+                     const double* targets, const pot_domain* dom, const pot_params* params,
+                     uint16_t* feat);
+
+/* Weight history of the warm start.  Each warm-started pot_fluid_step keeps
+ * its starting weights (caller order) as the next step's psi_old, valid while
+ * the site count stays n.  This call seeds the history with psi_old (device,
+ * n values, caller order), or clears it (psi_old NULL).  Errors:
+ * POT_ERR_INVALID_ARG when n exceeds the model's max_rows. */
+int pot_mlp_set_history(pot_mlp* mlp, void* stream, int64_t n, const float* psi_old);
 
 /* Attach a model to a context (NULL detaches; the context does not own it).
- * pot_fluid_step then starts Newton from the MLP's prediction when
- * params->warm_start is 1, and falls back to the previous weights when the
- * prediction gives an empty cell, a geometry error or a worst relative
- * volume error above 0.5 (stats: mlp_used / mlp_fallback).  FP32 path only. */
+ * pot_fluid_step then starts Newton from the MLP's prediction (its change
+ * clamped to |dpsi| <= h^2) when params->warm_start is 1, and falls back to
+ * plain Newton from the previous weights when the prediction fails the KMT
+ * precondition (an empty cell, or a geometry error) or when Newton from it
+ * does not converge (stats: mlp_used / mlp_fallback).  FP32 path only. */
 int pot_set_warm_start(pot_ctx* ctx, pot_mlp* mlp);
 
 #ifdef __cplusplus

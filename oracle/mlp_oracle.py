@@ -2,9 +2,10 @@
 
 Only tests/ may import this module.  The warm start is not in the paper; it
 follows the benchmark spec: an MLP over each site's 24 nearest-neighbour
-offsets, previous weight and velocity (76 inputs, padded to 80), three hidden
-layers of width 128 with ReLU, one output, BF16 weights and activations with
-FP32 accumulation, trained with Adam on the mean squared error.
+offsets, previous weight, velocity and previous weight change (77 inputs,
+padded to 80), three hidden layers of width 128 with ReLU, one output, BF16
+weights and activations with FP32 accumulation, trained with Adam on the mean
+squared error.
 
 The GPU rounds the weights, the inputs and every hidden activation to BF16
 (round to nearest even) and accumulates in FP32; `forward` reproduces those
@@ -21,7 +22,7 @@ from __future__ import annotations
 
 import numpy as np
 
-N_IN, N_FEAT, N_HID, N_KNN = 80, 76, 128, 24
+N_IN, N_FEAT, N_HID, N_KNN = 80, 77, 128, 24
 
 
 def bf16(x):
@@ -118,11 +119,12 @@ def init_params(seed=0):
     return flatten(p)
 
 
-def knn_features(pos, psi_prev, vel, nu, dt, radius=None):
+def knn_features(pos, psi_prev, vel, nu, dt, radius=None, psi_old=None):
     """Features of every site, brute force: offsets to the (up to) 24 nearest
     other sites closer than `radius` (default 2 sqrt(max psi_prev)), by
     increasing distance, over h = nu^(1/3), zero-padded; psi_prev / h^2;
-    vel * dt / h; 4 zeros.  (n, 80) float64."""
+    vel * dt / h; (psi_prev - psi_old) / h^2 (0 when psi_old is None);
+    3 zeros.  (n, 80) float64."""
     pos = np.asarray(pos, np.float64)
     n = pos.shape[0]
     h = np.cbrt(np.asarray(nu, np.float64))
@@ -140,4 +142,6 @@ def knn_features(pos, psi_prev, vel, nu, dt, radius=None):
         F[i, : 3 * len(order)] = off.ravel()
         F[i, 72] = psi_prev[i] / h[i] ** 2
         F[i, 73:76] = np.asarray(vel[i], np.float64) * dt / h[i]
+        if psi_old is not None:
+            F[i, 76] = (psi_prev[i] - psi_old[i]) / h[i] ** 2
     return F

@@ -161,8 +161,30 @@ NEWTON_LINESEARCH_FAILED = 2
 NEWTON_EMPTY_CELL_AT_START = 3
 
 
+def repair_empty(pos, psi, vol, nu):
+    """Raise the weight of every empty cell i to
+    max(max_j (psi_j - d_ij^2) + 0.1 d*^2, (nu_i^(1/3) / 2)^2), d* the distance
+    to the maximising site: then every bisector of i has h_ij > 0, so p_i is
+    inside its own (non-empty) cell, and each neighbour j keeps h_ji > 0
+    (reading: Algorithm 1 needs a start without empty cells; the paper does
+    not say how to get one after a fast step).  Brute force over all sites."""
+    pos = np.asarray(pos, np.float64)
+    psi = np.asarray(psi, np.float64).copy()
+    new = psi.copy()
+    for i in np.nonzero(np.asarray(vol) <= 0.0)[0]:
+        d2 = np.sum((pos - pos[i]) ** 2, 1)
+        v = psi - d2
+        v[i] = -np.inf
+        j = int(np.argmax(v))
+        cand = psi[i]
+        if d2[j] > 0 and np.isfinite(v[j]):
+            cand = max(cand, v[j] + 0.1 * d2[j])
+        new[i] = max(cand, 0.25 * np.cbrt(nu[i]) ** 2)
+    return new
+
+
 def newton(pos, nu, psi0, tol=1e-4, max_newton=100, max_halvings=30,
-           lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), nthreads=0):
+           lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), nthreads=0, repair=False):
     """Algorithm 1 (damped Newton with KMT steps), dense direct solve.
 
     Readings (Algorithm 1 is garbled in the paper):
@@ -178,6 +200,12 @@ def newton(pos, nu, psi0, tol=1e-4, max_newton=100, max_halvings=30,
     psi = np.asarray(psi0, np.float64).copy()
     res = cells(pos, psi, lo=lo, hi=hi, nthreads=nthreads)
     vol = res["vol"]
+    for _ in range(8 if repair else 0):
+        if vol.min() > 0.0:
+            break
+        psi = repair_empty(pos, psi, vol, nu)
+        res = cells(pos, psi, lo=lo, hi=hi, nthreads=nthreads)
+        vol = res["vol"]
     if vol.min() <= 0.0:
         return NewtonResult(psi, vol, 0, 0, NEWTON_EMPTY_CELL_AT_START, [], res)
     eps0 = 0.5 * min(nu.min(), vol.min())

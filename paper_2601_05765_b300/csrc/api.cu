@@ -53,6 +53,8 @@ int alloc_work(Work<T>& w, int64_t n, int64_t k, int64_t gcap) {
   POT_CHECK(alloc(&w.psi_max, 1));
   POT_CHECK(alloc(&w.nu_max, 1));
   POT_CHECK(alloc(&w.srad, n));
+  POT_CHECK(alloc(&w.srad_lo, n));
+  POT_CHECK(alloc(&w.rcell_acc, n));
   POT_CHECK(alloc(&w.rcell, n));
   POT_CHECK(alloc(&w.gmax, gcap + 1));
   return POT_OK;
@@ -62,7 +64,7 @@ template <typename T>
 void free_work(Work<T>& w) {
   void* ptrs[] = {w.sxp, w.psi_base, w.vol,  w.karea, w.diag, w.cen, w.stage_vals, w.csr_vals,
                   w.u,   w.x,        w.r,    w.z,     w.p0,   w.p1,  w.q,          w.vel_s,
-                  w.psi_max, w.nu_max, w.srad, w.rcell, w.gmax};
+                  w.psi_max, w.nu_max, w.srad, w.srad_lo, w.rcell_acc, w.rcell, w.gmax};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   w = Work<T>();
@@ -103,10 +105,11 @@ int compute_cells(pot_ctx* ctx, void* stream, int64_t n, const T* pos, const T* 
   cudaEventRecord(ev[0], st);
   POT_CHECK(grid_build<T>(ctx, st, n, pos, psi, targets, dom));
   cudaEventRecord(ev[1], st);
-  POT_CHECK(cells_eval<T>(ctx, st, n, dom, grad != nullptr));
+  const int ce = cells_eval<T>(ctx, st, n, dom, grad != nullptr);
   cudaEventRecord(ev[2], st);
   int64_t site = -1;
-  int code = read_status(ctx, st, &site);
+  int code = read_status(ctx, st, &site);  // also clears the device status
+  if (code == POT_OK) code = ce;
   if (code) {
     if (stats) stats->error_site = site;
     return code;
@@ -140,6 +143,19 @@ int compute_cells(pot_ctx* ctx, void* stream, int64_t n, const T* pos, const T* 
 extern "C" {
 
 int64_t pot_kernel_launches(void) { return g_launches.load(); }
+
+int pot_cell_kernel_time(pot_ctx* ctx, int reset, int64_t* launches, int64_t* cells, double* ms) {
+  if (!ctx) return POT_ERR_INVALID_ARG;
+  if (launches) *launches = ctx->kc_launches;
+  if (cells) *cells = ctx->kc_cells;
+  if (ms) *ms = ctx->kc_ms;
+  if (reset) {
+    ctx->kc_launches = 0;
+    ctx->kc_cells = 0;
+    ctx->kc_ms = 0.0;
+  }
+  return POT_OK;
+}
 
 void pot_default_params(pot_params* p) {
   if (!p) return;

@@ -64,10 +64,18 @@ __device__ __forceinline__ void set_error(int32_t* err, int code, int64_t site) 
 // Security radius (the paper's contributing-neighbour problem, Sec. 4): a
 // cell is built from the bisectors with h_ij < R_i only, R_i <= r_i.  If the
 // cell so built lies strictly inside the ball of radius R_i around p_i, no
-// plane with h >= R_i can touch it and the cell is exact; otherwise R_i is
-// doubled and the cell rebuilt (pass loop in cells_eval).  Inside deep fluid
+// plane with h >= R_i can touch it and the cell is exact; otherwise R_i grows
+// and the cell is rebuilt (pass loop in cells_eval).  Inside deep fluid
 // the weights grow like a pressure and the balls get many spacings wide,
 // while the cells stay small: R_i keeps the candidate lists short.
+//
+// The first R_i of an evaluation is a guess from the previous evaluation's
+// cells, and a growth step can overshoot, so a list that overflows k_max
+// does not yet mean the cell needs more than k_max planes.  Each cell keeps
+// a bracket: R_lo, the largest radius at which its cell was built and found
+// too small, and the current R_i.  An overflow at R_i retries at the
+// midpoint of (R_lo, R_i) (R_i / 2 while R_lo = 0); only when the bracket has
+// narrowed to 3 % of R_i is the overflow a real capacity error.
 //
 // Grid cells are skipped with a lower bound of h over their sites: for
 // |p_i - p_j| >= delta and psi_j <= gmax,  h_ij >= delta/2 - (gmax - psi_i)/(2 delta)
@@ -76,7 +84,7 @@ template <typename T>
 __global__ void __launch_bounds__(256)
     k_candidates(int64_t n, const V4<T>* __restrict__ sxp, const int32_t* __restrict__ cell_start,
                  GridParams<T> g, Box<T> box, const T* __restrict__ psi_max,
-                 const T* __restrict__ gmax, const T* __restrict__ srad,
+                 const T* __restrict__ gmax, T* __restrict__ srad, const T* __restrict__ srad_lo,
                  const uint8_t* __restrict__ need, int kmax, int32_t* __restrict__ cand,
                  int32_t* __restrict__ meta, int32_t* err) {
   int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -172,8 +180,14 @@ __global__ void __launch_bounds__(256)
   if (empty) {
     meta[s] = kMetaEmpty;
   } else if (nc > kmax) {
-    set_error(err, POT_ERR_NEIGHBOUR_OVERFLOW, s);
-    meta[s] = kMetaEmpty;
+    const T lo = srad_lo[s];
+    if (R - lo <= T(0.03) * R) {
+      set_error(err, POT_ERR_NEIGHBOUR_OVERFLOW, s);
+      meta[s] = kMetaEmpty;
+    } else {
+      srad[s] = lo > T(0) ? T(0.5) * (lo + R) : T(0.5) * R;
+      meta[s] = kMetaEmpty | kMetaRetry;
+    }
   } else {
     meta[s] = (nw + nc) | (wmask << kMetaWallShift);
   }
@@ -659,39 +673,122 @@ __global__ void k_gmax(int64_t ncell, const int32_t* __restrict__ cell_start,
 }
 
 // first security radius: 1.25 x the cell's extent in the previous evaluation
-// (Newton changes cells little), else 1.5 nu^(1/3), never beyond the ball
+// (Newton changes cells little) or at the last accepted Newton iterate,
+// whichever is smaller (a rejected line-search trial can have far larger
+// cells), else 1.5 nu^(1/3); never beyond the ball
 template <typename T>
 __global__ void k_srad_init(int64_t n, const V4<T>* __restrict__ sxp, const double* __restrict__ snu,
-                            const T* __restrict__ rcell, int have_prev, T* srad, uint8_t* need) {
+                            const T* __restrict__ rcell, int have_prev,
+                            const T* __restrict__ rcell_acc, int have_acc, T* srad, T* srad_lo,
+                            uint8_t* need) {
   int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   const T ps = sxp[s].w;
   const T r = ps > T(0) ? sqrt(ps) : T(0);
   T R = r;
-  if (have_prev && rcell[s] > T(0))
-    R = T(1.25) * rcell[s];
+  T prev = have_prev ? rcell[s] : T(0);
+  if (have_acc && rcell_acc[s] > T(0)) prev = prev > T(0) ? fmin(prev, rcell_acc[s]) : rcell_acc[s];
+  if (prev > T(0))
+    R = T(1.25) * prev;
   else if (snu[s] > 0.0)
     R = T(1.5) * (T)cbrt(snu[s]);
   srad[s] = fmin(R, r);
+  srad_lo[s] = T(0);
   need[s] = 1;
 }
 
-// a cell built inside radius R is exact if it stays strictly inside R (or R
-// reached the ball); otherwise double R and rebuild it
+// After a pass: a cell inside its security ball is final.  Otherwise R is
+// too small (it becomes R_lo), and the cell just built (from a subset of the
+// planes) contains the true cell, so its farthest point rcell bounds the
+// radius that suffices: R grows to 1.05 rcell (the margin covers the rounding
+// of rcell), by a factor between 1.25 and 2, and the next pass normally
+// builds a cell inside that ball.
 template <typename T>
 __global__ void k_need_update(int64_t n, const V4<T>* __restrict__ sxp, const T* __restrict__ rcell,
-                              T* srad, uint8_t* need, int32_t* count) {
+                              const int32_t* __restrict__ meta, T* srad, T* srad_lo, uint8_t* need,
+                              int32_t* count) {
   int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n || !need[s]) return;
+  if (meta[s] & kMetaRetry) {  // radius already reduced by the candidate pass
+    atomicAdd(count, 1);
+    return;
+  }
   const T ps = sxp[s].w;
   const T r = ps > T(0) ? sqrt(ps) : T(0);
   const T R = srad[s];
-  const bool done = !(ps > T(0)) || R >= r || rcell[s] < R * T(1.0 - 1e-5);
+  const T rc = rcell[s];
+  const bool done = !(ps > T(0)) || R >= r || rc < R * T(1.0 - 1e-5);
   if (done) {
     need[s] = 0;
   } else {
-    srad[s] = fmin(r, T(2) * R);
+    srad_lo[s] = R;
+    srad[s] = fmin(r, fmin(T(2) * R, fmax(T(1.25) * R, T(1.05) * rc)));
     atomicAdd(count, 1);
+  }
+}
+
+// A start with empty cells cannot enter Algorithm 1 (its KMT bound needs
+// min V > 0).  For an empty cell i, psi_i <- max_j (psi_j - d_ij^2) + 0.1 d*^2
+// (d* the distance to the maximising site): then h_ij > 0 for every j, so p_i
+// lies strictly inside its own cell, which is no longer empty, while each
+// neighbour keeps h_ji = (2 d^2 - 0.1 d*^2)/(2d) > 0 with respect to i.  Sites
+// with psi_j - d^2 > psi_i lie within sqrt(psi_max - psi_i); grid cells are
+// skipped when gmax - delta^2 <= psi_i.
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_repair(int64_t n, V4<T>* sxp, T* psi_base, const T* __restrict__ vol,
+             const int32_t* __restrict__ cell_start, GridParams<T> g, const T* __restrict__ gmax,
+             const double* __restrict__ snu, T* psi_max, int32_t* count) {
+  int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n || vol[s] > T(0)) return;
+  const V4<T> p = sxp[s];
+  const T ps = p.w;
+  const T D = sqrt(fmax(*psi_max - ps, T(0)));
+  T best = T(-1e30), bd2 = T(0);
+  if (D > T(0)) {
+    int c0[3], c1[3];
+    const T pc[3] = {p.x, p.y, p.z};
+    for (int k = 0; k < 3; k++) {
+      c0[k] = cell_coord(pc[k] - D, g.lo[k], g.inv_cs, g.dim[k]);
+      c1[k] = cell_coord(pc[k] + D, g.lo[k], g.inv_cs, g.dim[k]);
+    }
+    for (int cz = c0[2]; cz <= c1[2]; cz++)
+      for (int cy = c0[1]; cy <= c1[1]; cy++)
+        for (int cx = c0[0]; cx <= c1[0]; cx++) {
+          const T lo3[3] = {g.lo[0] + cx * g.cs, g.lo[1] + cy * g.cs, g.lo[2] + cz * g.cs};
+          T dl2 = T(0);
+          for (int k = 0; k < 3; k++) {
+            const T e = fmax(T(0), fmax(lo3[k] - pc[k], pc[k] - (lo3[k] + g.cs)));
+            dl2 += e * e;
+          }
+          const int key = (cz * g.dim[1] + cy) * g.dim[0] + cx;
+          if (gmax[key] - dl2 <= ps) continue;
+          for (int t = cell_start[key]; t < cell_start[key + 1]; t++) {
+            if (t == s) continue;
+            const V4<T> q = sxp[t];
+            const T dx = q.x - p.x, dy = q.y - p.y, dz = q.z - p.z;
+            const T d2 = dx * dx + dy * dy + dz * dz;
+            const T v = q.w - d2;
+            if (v > best) {
+              best = v;
+              bd2 = d2;
+            }
+          }
+        }
+  }
+  T nv = ps;
+  if (best > T(-1e29) && bd2 > T(0)) nv = fmax(nv, best + T(0.1) * bd2);
+  // a non-positive weight is an empty ball: give it half the radius of its target
+  const T floor = snu[s] > 0.0 ? T(0.25) * (T)cbrt(snu[s] * snu[s]) : T(0);
+  nv = fmax(nv, floor);
+  if (nv > ps) {
+    sxp[s].w = nv;
+    psi_base[s] = nv;
+    atomicAdd(count, 1);
+    if (sizeof(T) == 4)
+      atomicMax((int*)psi_max, __float_as_int((float)nv));
+    else
+      atomicMax((unsigned long long*)psi_max, (unsigned long long)__double_as_longlong((double)nv));
   }
 }
 
@@ -863,7 +960,9 @@ int cells_eval(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* dom, 
   k_gmax<T><<<blocks_for(ncell, 256), 256, 0, st>>>(ncell, ctx->cell_start, w.sxp, w.gmax);
   note_launch();
   k_srad_init<T><<<blocks_for(n, 256), 256, 0, st>>>(n, w.sxp, ctx->snu, w.rcell,
-                                                      w.have_rcell ? 1 : 0, w.srad, ctx->need);
+                                                      w.have_rcell ? 1 : 0, w.rcell_acc,
+                                                      w.have_acc ? 1 : 0, w.srad, w.srad_lo,
+                                                      ctx->need);
   CellOut o;
   o.rcell = w.rcell;
   o.need = ctx->need;
@@ -877,24 +976,53 @@ int cells_eval(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* dom, 
   const int64_t warps = (n + kCellsPerWarp - 1) / kCellsPerWarp;
   const int blocks = (int)((warps + kCellWarps - 1) / kCellWarps);
   int32_t* hcount = (int32_t*)(ctx->h_pinned + 24);
-  for (int pass = 0; pass < 24; pass++) {
+  ctx->last_passes = 0;
+  int64_t todo = n;  // cells rebuilt in this pass
+  for (int pass = 0; pass < kMaxPasses; pass++) {
+    ctx->last_passes = pass + 1;
     note_launch();
     k_candidates<T><<<blocks_for(n, 256), 256, 0, st>>>(n, w.sxp, ctx->cell_start, w.grid, box,
-                                                         w.psi_max, w.gmax, w.srad, ctx->need,
+                                                         w.psi_max, w.gmax, w.srad, w.srad_lo,
+                                                         ctx->need,
                                                          ctx->k_max, ctx->cand, ctx->meta, ctx->err);
     note_launch();
+    cudaEventRecord(ctx->ev[6], st);
     k_cells<T><<<blocks, kCellWarps * 32, 0, st>>>(n, w.sxp, ctx->meta, ctx->cand, ctx->k_max, box,
                                                    w.stage_vals, o, ctx->err);
+    cudaEventRecord(ctx->ev[7], st);
     POT_CUDA(cudaMemsetAsync(ctx->need_count, 0, sizeof(int32_t), st));
     note_launch();
-    k_need_update<T><<<blocks_for(n, 256), 256, 0, st>>>(n, w.sxp, w.rcell, w.srad, ctx->need,
-                                                          ctx->need_count);
+    k_need_update<T><<<blocks_for(n, 256), 256, 0, st>>>(n, w.sxp, w.rcell, ctx->meta, w.srad,
+                                                          w.srad_lo, ctx->need, ctx->need_count);
     POT_CUDA(cudaMemcpyAsync(hcount, ctx->need_count, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     POT_CUDA(cudaStreamSynchronize(st));
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ctx->ev[6], ctx->ev[7]) == cudaSuccess) {
+      ctx->kc_launches++;
+      ctx->kc_cells += todo;
+      ctx->kc_ms += ms;
+    }
+    todo = *hcount;
     if (*hcount == 0) break;
   }
   POT_CUDA(cudaGetLastError());
   w.have_rcell = true;
+  // cells still unresolved after the last pass are not exact
+  if (*hcount != 0) return POT_ERR_NEIGHBOUR_OVERFLOW;
+  return POT_OK;
+}
+
+template <typename T>
+int repair_empty(pot_ctx* ctx, cudaStream_t st, int64_t n, int* repaired) {
+  Work<T>& w = ctx->work<T>();
+  POT_CUDA(cudaMemsetAsync(ctx->need_count, 0, sizeof(int32_t), st));
+  note_launch();
+  k_repair<T><<<blocks_for(n, 256), 256, 0, st>>>(n, w.sxp, w.psi_base, w.vol, ctx->cell_start, w.grid,
+                                                   w.gmax, ctx->snu, w.psi_max, ctx->need_count);
+  int32_t* h = (int32_t*)(ctx->h_pinned + 24);
+  POT_CUDA(cudaMemcpyAsync(h, ctx->need_count, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  POT_CUDA(cudaStreamSynchronize(st));
+  *repaired = h[0];
   return POT_OK;
 }
 
@@ -989,6 +1117,7 @@ int psi_update(pot_ctx* ctx, cudaStream_t st, int64_t n, double alpha) {
 #define POT_INST(T)                                                                              \
   template int cells_eval<T>(pot_ctx*, cudaStream_t, int64_t, const pot_domain*, bool);          \
   template int residuals<T>(pot_ctx*, cudaStream_t, int64_t, double*);                          \
+  template int repair_empty<T>(pot_ctx*, cudaStream_t, int64_t, int*);                          \
   template int csr_compact<T>(pot_ctx*, cudaStream_t, int64_t, int64_t*);                       \
   template int csr_user<T>(pot_ctx*, cudaStream_t, int64_t, int32_t*, int32_t*, T*, int64_t,    \
                            int64_t*);                                                           \

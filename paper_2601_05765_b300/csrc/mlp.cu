@@ -1,8 +1,8 @@
 // Learned warm start for the Newton solve (not in the paper): features from
-// each site's 24 nearest neighbours, previous weight and velocity, and a
-// BF16 MLP 80 -> 128 -> 128 -> 128 -> 1 (ReLU) whose output is the change of
-// the weight in units of h^2 (h = nu^(1/3)).  Plain Newton from the previous
-// weights stays the fallback.
+// each site's 24 nearest neighbours, previous weight, velocity and previous
+// weight change, and a BF16 MLP 80 -> 128 -> 128 -> 128 -> 1 (ReLU) whose
+// output is the change of the weight in units of h^2 (h = nu^(1/3)).  Plain
+// Newton from the previous weights stays the fallback.
 //
 // Every GEMM (forward layers, back-propagation, weight gradients) runs on the
 // 5th-generation tensor cores: one CTA computes a 128 x 128 FP32 tile in
@@ -28,7 +28,7 @@ typedef __nv_bfloat16 bf16;
 namespace pot {
 namespace {
 
-constexpr int kIn = 80, kFeat = 76, kHid = 128, kKnn = 24;
+constexpr int kIn = 80, kFeat = 77, kHid = 128, kKnn = 24;
 constexpr int kTM = 128;  // rows of a tile (and N of every GEMM)
 constexpr int kKC = 64;   // K staged per chunk
 constexpr int kGemmThreads = 128;
@@ -253,12 +253,14 @@ __device__ __forceinline__ int fcell(float x, float lo, float inv, int dim) {
 
 // one thread per site (sorted order): the (up to) 24 nearest other sites with
 // |d| < 2 sqrt(psi_max), offsets / h by increasing distance; psi / h^2;
-// v dt / h; zero padding to 80.  feat row = out_perm ? out_perm[s] : s.
+// v dt / h; the previous weight change / h^2 (0 without history); zero
+// padding to 80.  feat row = out_perm ? out_perm[s] : s.
 __global__ void __launch_bounds__(128)
     k_features(int64_t n, const V4<float>* __restrict__ sxp, const int32_t* __restrict__ cell_start,
                GridParams<float> g, const float* __restrict__ psi_max,
-               const float* __restrict__ vel_s, const double* __restrict__ snu, float dt,
-               const int32_t* __restrict__ out_perm, bf16* feat) {
+               const float* __restrict__ vel_s, const float* __restrict__ dpsi_s,
+               const double* __restrict__ snu, float dt, const int32_t* __restrict__ out_perm,
+               bf16* feat) {
   int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   const V4<float> p = sxp[s];
@@ -317,6 +319,7 @@ __global__ void __launch_bounds__(128)
   f[73] = __float2bfloat16_rn(vel_s[3 * s + 0] * dt * ih);
   f[74] = __float2bfloat16_rn(vel_s[3 * s + 1] * dt * ih);
   f[75] = __float2bfloat16_rn(vel_s[3 * s + 2] * dt * ih);
+  f[76] = __float2bfloat16_rn(dpsi_s ? dpsi_s[s] * ih * ih : 0.f);
   for (int k = kFeat; k < kIn; k++) f[k] = __float2bfloat16_rn(0.f);
 }
 
@@ -341,14 +344,18 @@ __global__ void k_advect_copy(int64_t n, const float* __restrict__ pos, const fl
   }
 }
 
+// sorted velocities, and the sorted previous weight change psi - psi_old
+// (caller order inputs; psi_old may be NULL)
 __global__ void k_gather_vel(int64_t n, const int32_t* __restrict__ perm, const float* __restrict__ vel,
-                             float* vel_s) {
+                             const float* __restrict__ psi, const float* __restrict__ psi_old,
+                             float* vel_s, float* dpsi_s) {
   int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   const int64_t i = perm[s];
   vel_s[3 * s + 0] = vel[3 * i + 0];
   vel_s[3 * s + 1] = vel[3 * i + 1];
   vel_s[3 * s + 2] = vel[3 * i + 2];
+  if (psi_old) dpsi_s[s] = psi[i] - psi_old[i];
 }
 
 // psi_pred = psi_prev + h^2 out, written as the Newton start; psi_prev kept
@@ -359,7 +366,8 @@ __global__ void k_apply_warm(int64_t n, const float* __restrict__ out, const dou
   if (s < n) {
     const float prev = sxp[s].w;
     const float h = (float)cbrt(snu[s]);
-    v = prev + h * h * out[s];
+    // a loose guard against extrapolation: at most h^2 of change per step
+    v = prev + h * h * fminf(fmaxf(out[s], -1.f), 1.f);
     if (!(v == v)) v = prev;  // a NaN prediction keeps the previous weight
     psi_prev[s] = prev;
     sxp[s].w = v;
@@ -508,6 +516,9 @@ struct pot_mlp {
   float* pos_tmp = nullptr;  // features: advected positions (3 x max_rows)
   float* vel_adv = nullptr;  // features: advected velocities (3 x max_rows)
   float* psi_prev = nullptr;  // warm start: previous weights (sorted)
+  float* dpsi_s = nullptr;    // features: previous weight change (sorted)
+  float* psi_hist = nullptr;  // warm start: weights of the previous step (caller order)
+  int64_t hist_n = -1;        // sites of psi_hist (-1: no history)
 };
 
 namespace pot {
@@ -639,23 +650,31 @@ int alloc(P** p, size_t count) {
 // features of sorted sites into feat (rows in sorted order, or caller order
 // through out_perm); requires grid_build<float> (sxp.w = previous psi)
 int mlp_features_sorted(pot_ctx* ctx, pot_mlp* mm, cudaStream_t st, int64_t n, const float* vel,
-                        float dt, const int32_t* out_perm, void* feat) {
+                        const float* psi, const float* psi_old, float dt, const int32_t* out_perm,
+                        void* feat) {
   Work<float>& w = ctx->wf;
   note_launch();
-  k_gather_vel<<<blocks_for(n, 256), 256, 0, st>>>(n, ctx->perm, vel, mm->vel_tmp);
+  k_gather_vel<<<blocks_for(n, 256), 256, 0, st>>>(n, ctx->perm, vel, psi, psi_old, mm->vel_tmp,
+                                                    mm->dpsi_s);
   note_launch();
   k_features<<<blocks_for(n, 128), 128, 0, st>>>(n, w.sxp, ctx->cell_start, w.grid, w.psi_max,
-                                                  mm->vel_tmp, ctx->snu, dt, out_perm, (bf16*)feat);
+                                                  mm->vel_tmp, psi_old ? mm->dpsi_s : nullptr,
+                                                  ctx->snu, dt, out_perm, (bf16*)feat);
   POT_CUDA(cudaGetLastError());
   return POT_OK;
 }
 
 // warm start inside the fluid step: features, MLP, psi_pred into sxp.w /
 // psi_base; the previous psi is kept in mm->psi_prev (returned)
-int mlp_warm_start(pot_ctx* ctx, pot_mlp* mm, cudaStream_t st, int64_t n, const float* vel, float dt,
-                   float** psi_prev) {
+int mlp_warm_start(pot_ctx* ctx, pot_mlp* mm, cudaStream_t st, int64_t n, const float* vel,
+                   const float* psi, float dt, float** psi_prev) {
   if (!mm || n > mm->max_rows) return POT_ERR_INVALID_ARG;
-  POT_CHECK(mlp_features_sorted(ctx, mm, st, n, vel, dt, nullptr, mm->x));
+  const bool hist = mm->hist_n == n;
+  POT_CHECK(mlp_features_sorted(ctx, mm, st, n, vel, psi, hist ? mm->psi_hist : nullptr, dt, nullptr,
+                                mm->x));
+  // this step's weights are the next step's history
+  POT_CUDA(cudaMemcpyAsync(mm->psi_hist, psi, n * sizeof(float), cudaMemcpyDeviceToDevice, st));
+  mm->hist_n = n;
   POT_CHECK(forward(mm, st, n, mm->x, mm->out, false));
   Work<float>& w = ctx->wf;
   note_launch();
@@ -683,7 +702,7 @@ int pot_mlp_destroy(pot_mlp* mm) {
                   mm->xbT,    mm->t1,    mm->t2,  mm->h1T,  mm->h2T,   mm->h3,   mm->h3T,
                   mm->dz3,    mm->dz3T,  mm->dz2, mm->dz2T, mm->dz1T,  mm->yb,   mm->tout,
                   mm->dout,   mm->sqerr, mm->part, mm->loss, mm->err,  mm->vel_tmp,
-                  mm->pos_tmp, mm->vel_adv, mm->psi_prev};
+                  mm->pos_tmp, mm->vel_adv, mm->psi_prev, mm->dpsi_s, mm->psi_hist};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete mm;
@@ -714,7 +733,8 @@ int pot_mlp_create(pot_mlp** out, int device, int64_t max_rows) {
   A(dz2, T * kHid); A(dz2T, T * kHid); A(dz1T, T * kHid);
   A(yb, T); A(tout, T); A(dout, T); A(sqerr, T);
   A(part, (T / kSplitK) * kHid * kHid); A(loss, 1); A(err, 2);
-  A(vel_tmp, 3 * R); A(pos_tmp, 3 * R); A(vel_adv, 3 * R); A(psi_prev, R);
+  A(vel_tmp, 3 * R); A(pos_tmp, 3 * R); A(vel_adv, 3 * R); A(psi_prev, R); A(dpsi_s, R);
+  A(psi_hist, R);
 #undef A
   if (s == POT_OK && cudaMemset(mm->err, 0, 2 * sizeof(int32_t)) != cudaSuccess) s = POT_ERR_CUDA;
   if (s == POT_OK && cudaMemset(mm->params, 0, kParams * sizeof(float)) != cudaSuccess)
@@ -809,8 +829,9 @@ int pot_mlp_check(pot_mlp* mm, void* stream) {
 }
 
 int pot_mlp_features(pot_ctx* ctx, pot_mlp* mm, void* stream, int64_t n, const float* pos,
-                     const float* vel, const float* psi, const double* targets,
-                     const pot_domain* dom, const pot_params* prm, uint16_t* feat) {
+                     const float* vel, const float* psi, const float* psi_old,
+                     const double* targets, const pot_domain* dom, const pot_params* prm,
+                     uint16_t* feat) {
   if (!ctx || !mm || !pos || !vel || !psi || !targets || !dom || !prm || !feat || n <= 0 ||
       n > ctx->n_max || n > mm->max_rows || !(ctx->mask & 1) || mm->device != ctx->device)
     return POT_ERR_INVALID_ARG;
@@ -827,8 +848,23 @@ int pot_mlp_features(pot_ctx* ctx, pot_mlp* mm, void* stream, int64_t n, const f
                                                      (float)prm->dt, box, (float)prm->wall_margin);
   POT_CUDA(cudaGetLastError());
   POT_CHECK(grid_build<float>(ctx, st, n, mm->pos_tmp, psi, targets, dom));
-  POT_CHECK(mlp_features_sorted(ctx, mm, st, n, mm->vel_adv, (float)prm->dt, ctx->perm, feat));
+  POT_CHECK(mlp_features_sorted(ctx, mm, st, n, mm->vel_adv, psi, psi_old, (float)prm->dt, ctx->perm,
+                                feat));
   POT_CUDA(cudaStreamSynchronize(st));
+  return POT_OK;
+}
+
+int pot_mlp_set_history(pot_mlp* mm, void* stream, int64_t n, const float* psi_old) {
+  if (!mm || n > mm->max_rows) return POT_ERR_INVALID_ARG;
+  if (cudaSetDevice(mm->device) != cudaSuccess) return POT_ERR_CUDA;
+  if (!psi_old || n <= 0) {
+    mm->hist_n = -1;
+    return POT_OK;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  POT_CUDA(cudaMemcpyAsync(mm->psi_hist, psi_old, n * sizeof(float), cudaMemcpyDeviceToDevice, st));
+  POT_CUDA(cudaStreamSynchronize(st));
+  mm->hist_n = n;
   return POT_OK;
 }
 

@@ -139,22 +139,22 @@ template <typename T>
 int eval_and_reduce(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* dom,
                     double res[6], pot_solve_stats* S) {
   EvTimer tm(ctx, 0, st);
-  POT_CHECK(cells_eval<T>(ctx, st, n, dom, true));
-  POT_CHECK(residuals<T>(ctx, st, n, res));
+  const int ce = cells_eval<T>(ctx, st, n, dom, true);
+  if (ce == POT_OK) POT_CHECK(residuals<T>(ctx, st, n, res));
   S->ms_cells += tm.stop();
   S->cell_evals++;
+  S->passes += ctx->last_passes;
   int64_t site;
-  int code = read_status(ctx, st, &site);
-  if (code) return code;
-  return POT_OK;
+  const int code = read_status(ctx, st, &site);  // also clears the device status
+  return code != POT_OK ? code : ce;
 }
 
 }  // namespace
 
 // Newton solve in sorted space.  Requires grid_build (sxp.w = psi_base = start).
 // psi_fallback (sorted, optional): weights to restart from when the given
-// start is rejected -- an empty cell (the KMT bound needs min V > 0), a
-// geometry error, or a worst relative error above 0.5.
+// start fails the KMT precondition -- an empty cell (the bound eps0 needs
+// min V > 0) or a geometry error.
 template <typename T>
 int newton_sorted(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* dom,
                   const pot_params* P, pot_solve_stats* S, const T* psi_fallback = nullptr) {
@@ -162,7 +162,7 @@ int newton_sorted(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* do
   double res[6];
   if (psi_fallback) {
     int code = eval_and_reduce<T>(ctx, st, n, dom, res, S);
-    const bool bad = code != POT_OK || !(res[2] > 0.0) || !(res[0] <= 0.5);
+    const bool bad = code != POT_OK || !(res[2] > 0.0);
     if (bad) {
       S->mlp_fallback = 1;
       POT_CUDA(cudaMemsetAsync(w.psi_max, 0, sizeof(T), st));
@@ -176,9 +176,22 @@ int newton_sorted(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* do
     POT_CHECK(eval_and_reduce<T>(ctx, st, n, dom, res, S));
   }
   S->err_start = res[0];
+  // empty cells at the start (sites pushed deep into a heavier neighbour's
+  // cell by a fast step): raise their weights until every site is inside its
+  // own cell, then start Algorithm 1 from the repaired weights
+  for (int rep = 0; rep < 8 && !(res[2] > 0.0); rep++) {
+    int repaired = 0;
+    POT_CHECK(repair_empty<T>(ctx, st, n, &repaired));
+    if (repaired == 0) break;
+    S->repairs += repaired;
+    POT_CHECK(eval_and_reduce<T>(ctx, st, n, dom, res, S));
+  }
   S->err_max = res[0];
   S->err_l2 = sqrt(res[1]);
   if (!(res[2] > 0.0)) return POT_ERR_EMPTY_CELL_AT_START;
+  // cell extents of the accepted iterate seed the security radii of the trials
+  POT_CUDA(cudaMemcpyAsync(w.rcell_acc, w.rcell, n * sizeof(T), cudaMemcpyDeviceToDevice, st));
+  w.have_acc = true;
   note_launch();
   k_nu_min<<<kRedBlocks, 256, 0, st>>>(n, ctx->snu, ctx->red);
   note_launch();
@@ -232,6 +245,7 @@ int newton_sorted(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* do
     }
     note_launch();
     k_accept<T><<<blocks_for(n, 256), 256, 0, st>>>(n, w.sxp, w.psi_base);
+    POT_CUDA(cudaMemcpyAsync(w.rcell_acc, w.rcell, n * sizeof(T), cudaMemcpyDeviceToDevice, st));
     err = res[0];
     gnorm = sqrt(res[1]);
   }
@@ -272,10 +286,23 @@ int fluid_step(pot_ctx* ctx, cudaStream_t st, int64_t n, T* pos, T* vel, T* psi,
   const T* fallback = nullptr;
   if (sizeof(T) == 4 && P->warm_start && ctx->mlp) {
     float* prev = nullptr;
-    POT_CHECK(mlp_warm_start(ctx, ctx->mlp, st, n, (const float*)vel, (float)P->dt, &prev));
+    POT_CHECK(mlp_warm_start(ctx, ctx->mlp, st, n, (const float*)vel, (const float*)psi,
+                             (float)P->dt, &prev));
     fallback = (const T*)prev;
   }
   int status = newton_sorted<T>(ctx, st, n, dom, P, S, fallback);
+  if (fallback && S->mlp_used &&
+      (status == POT_ERR_NOT_CONVERGED || status == POT_ERR_LINESEARCH_FAILED)) {
+    // Newton from the learned start failed: plain Newton from the previous
+    // weights judges the step
+    S->mlp_used = 0;
+    S->mlp_fallback = 1;
+    Work<T>& w = ctx->work<T>();
+    POT_CUDA(cudaMemsetAsync(w.psi_max, 0, sizeof(T), st));
+    note_launch();
+    k_set_psi<T><<<blocks_for(n, 256), 256, 0, st>>>(n, fallback, w.sxp, w.psi_base, w.psi_max);
+    status = newton_sorted<T>(ctx, st, n, dom, P, S, nullptr);
+  }
   if (status == POT_OK || status == POT_ERR_NOT_CONVERGED || status == POT_ERR_LINESEARCH_FAILED) {
     Work<T>& w = ctx->work<T>();
     note_launch();

@@ -57,7 +57,8 @@ constexpr size_t oStage = oCen + al(12 * N);
 constexpr size_t oPsiMax = oStage + al(4 * N * kNoAllocK);
 constexpr size_t oNuMax = oPsiMax + al(8);
 constexpr size_t oSrad = oNuMax + al(8);
-constexpr size_t oRcell = oSrad + al(4 * N);
+constexpr size_t oSradLo = oSrad + al(4 * N);
+constexpr size_t oRcell = oSradLo + al(4 * N);
 constexpr size_t oGmax = oRcell + al(4 * N);
 constexpr size_t oNeed = oGmax + al(4 * (kNoAllocGridCap + 1));
 constexpr size_t oNeedCount = oNeed + al(N);
@@ -143,6 +144,7 @@ extern "C" int lgc_compute_cells_noalloc(void* stream, int64_t n, const float* p
   w.psi_max = (float*)(b + oPsiMax);
   w.nu_max = (float*)(b + oNuMax);
   w.srad = (float*)(b + oSrad);
+  w.srad_lo = (float*)(b + oSradLo);
   w.rcell = (float*)(b + oRcell);
   w.gmax = (float*)(b + oGmax);
   c.need = (uint8_t*)(b + oNeed);
@@ -151,9 +153,10 @@ extern "C" int lgc_compute_cells_noalloc(void* stream, int64_t n, const float* p
   // the previous call's status words are stale: clear them
   POT_CUDA(cudaMemcpyAsync(c.err, kErrInit, sizeof(kErrInit), cudaMemcpyHostToDevice, st));
   POT_CHECK(grid_build<float>(&c, st, n, pos, psi, targets, dom));
-  POT_CHECK(cells_eval<float>(&c, st, n, dom, grad != nullptr));
+  const int ce = cells_eval<float>(&c, st, n, dom, grad != nullptr);
   int64_t site = -1;
   int code = read_status(&c, st, &site);
+  if (code == POT_OK) code = ce;
   if (code) {
     if (stats) stats->error_site = site;
     return code;

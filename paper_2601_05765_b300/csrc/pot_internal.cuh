@@ -25,16 +25,18 @@ namespace pot {
 
 constexpr int kWarp = 32;
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kMaxK = 128;         // cutting bisectors per cell (k_max <= 128)
+constexpr int kMaxK = 256;         // candidate bisectors per cell (k_max <= 256)
 constexpr int kPlaneCap = kMaxK + 6;
 constexpr int kMaxLines = 24;      // edges of one facet polygon
 constexpr int kCellWarps = 4;      // warps per block of the cell kernel
 constexpr int kCellsPerWarp = 32;  // cells per warp task
 
 // meta word written by the candidate kernel
-constexpr int kMetaPlanes = 0xff;
-constexpr int kMetaWallShift = 8;
-constexpr int kMetaEmpty = 1 << 14;
+constexpr int kMetaPlanes = 0x1ff;  // planes (walls + candidates) <= kMaxK + 6
+constexpr int kMetaWallShift = 9;   // 6 wall bits
+constexpr int kMetaEmpty = 1 << 15;
+constexpr int kMetaRetry = 1 << 16;  // candidate list overflowed: redo at a smaller radius
+constexpr int kMaxPasses = 48;       // security-radius passes of one cell evaluation
 
 // device status words: [0] error code (max over sites), [1] smallest site with that error
 enum { kErrCode = 0, kErrSite = 1 };
@@ -141,11 +143,14 @@ struct Work {
   T* psi_max = nullptr;     // device scalar: max psi of the current evaluation
   T* nu_max = nullptr;      // device scalar: max target volume (grid build)
   T* srad = nullptr;        // per cell: security radius of the current pass
+  T* srad_lo = nullptr;     // per cell: largest radius found too small in this evaluation
+  T* rcell_acc = nullptr;   // per cell: rcell at the last accepted Newton iterate
   T* rcell = nullptr;       // per cell: farthest point of the cell from its site
   T* gmax = nullptr;        // per grid cell: largest psi of its sites
   GridParams<T> grid{};
   bool grid_valid = false;
   bool have_rcell = false;  // rcell belongs to the current grid order
+  bool have_acc = false;    // rcell_acc belongs to the current grid order
 };
 
 }  // namespace pot
@@ -182,6 +187,10 @@ struct pot_ctx {
   int32_t* err = nullptr;         // device status words
   uint8_t* need = nullptr;        // per cell: still to be (re)built in this evaluation
   int32_t* need_count = nullptr;  // device counter of cells to rebuild
+  int last_passes = 0;            // security-radius passes of the last cell evaluation
+  int64_t kc_launches = 0;        // cell-kernel timer: launches, cells processed, device ms
+  int64_t kc_cells = 0;
+  double kc_ms = 0.0;
   double* h_pinned = nullptr;     // pinned host scalars
   cudaEvent_t ev[8] = {};
   pot::Work<float> wf;
@@ -235,6 +244,12 @@ int cells_eval(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* dom, 
 template <typename T>
 int residuals(pot_ctx* ctx, cudaStream_t st, int64_t n, double out[6]);
 
+// raise the weights of empty cells so that each site lies inside its own
+// cell (cells.cu); *repaired = number of cells changed.  Needs a preceding
+// cells_eval (volumes, grid maxima).
+template <typename T>
+int repair_empty(pot_ctx* ctx, cudaStream_t st, int64_t n, int* repaired);
+
 // read and clear the device status word; returns a POT status
 int read_status(pot_ctx* ctx, cudaStream_t st, int64_t* site);
 
@@ -259,8 +274,8 @@ int psi_update(pot_ctx* ctx, cudaStream_t st, int64_t n, double alpha);
 // learned warm start (mlp.cu): features of the sorted sites, the MLP, and
 // psi_pred = psi_prev + h^2 out into sxp.w / psi_base; *psi_prev points to the
 // kept previous weights (sorted)
-int mlp_warm_start(pot_ctx* ctx, pot_mlp* mm, cudaStream_t st, int64_t n, const float* vel, float dt,
-                   float** psi_prev);
+int mlp_warm_start(pot_ctx* ctx, pot_mlp* mm, cudaStream_t st, int64_t n, const float* vel,
+                   const float* psi, float dt, float** psi_prev);
 
 // PCG (pcg.cu): solve M u = grad (sorted space) into work.u
 template <typename T>

@@ -65,7 +65,8 @@ class SolveStats(ctypes.Structure):
                 ("err_start", ctypes.c_double), ("ms_total", ctypes.c_double),
                 ("ms_cells", ctypes.c_double), ("ms_pcg", ctypes.c_double),
                 ("nnz", ctypes.c_int64), ("mlp_used", ctypes.c_int32),
-                ("mlp_fallback", ctypes.c_int32)]
+                ("mlp_fallback", ctypes.c_int32), ("repairs", ctypes.c_int32),
+                ("passes", ctypes.c_int32)]
 
 
 def _as_dict(st):
@@ -112,12 +113,17 @@ def lib():
         L.pot_mlp_gradients.argtypes = [P, P, I64, P, P, P, I64, P, P]
         L.pot_mlp_train_step.argtypes = [P, P, I64, P, P, P, I64, ctypes.c_float, P]
         L.pot_mlp_check.argtypes = [P, P]
-        L.pot_mlp_features.argtypes = [P, P, P, I64, P, P, P, P, ctypes.POINTER(Domain),
+        L.pot_mlp_features.argtypes = [P, P, P, I64, P, P, P, P, P, ctypes.POINTER(Domain),
                                        ctypes.POINTER(Params), P]
+        L.pot_mlp_set_history.argtypes = [P, P, I64, P]
         L.pot_set_warm_start.argtypes = [P, P]
+        L.pot_cell_kernel_time.argtypes = [P, ctypes.c_int, ctypes.POINTER(I64), ctypes.POINTER(I64),
+                                           ctypes.POINTER(ctypes.c_double)]
+        L.pot_cell_kernel_time.restype = ctypes.c_int
         for f in (L.pot_mlp_create, L.pot_mlp_destroy, L.pot_mlp_num_params, L.pot_mlp_set_params,
                   L.pot_mlp_get_params, L.pot_mlp_forward, L.pot_mlp_gradients, L.pot_mlp_train_step,
-                  L.pot_mlp_check, L.pot_mlp_features, L.pot_set_warm_start):
+                  L.pot_mlp_check, L.pot_mlp_features, L.pot_mlp_set_history,
+                  L.pot_set_warm_start):
             f.restype = ctypes.c_int
         for f in (L.pot_create, L.pot_destroy, L.lgc_compute_cells, L.lgc_compute_cells_f64,
                   L.pot_newton_solve, L.pot_newton_solve_f64, L.pot_fluid_step, L.pot_fluid_step_f64):
@@ -129,6 +135,17 @@ def lib():
 def kernel_launches() -> int:
     """Kernel launches issued by libpot.so so far in this process."""
     return int(lib().pot_kernel_launches())
+
+
+def cell_kernel_time(ctx: "Context", reset: bool = False) -> dict:
+    """Cell-kernel launches, cells processed and device ms accumulated in
+    `ctx` (CUDA events around each launch); reset clears them after reading."""
+    la, ce, ms = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_double(0.0)
+    code = lib().pot_cell_kernel_time(ctx.handle, int(reset), ctypes.byref(la), ctypes.byref(ce),
+                                      ctypes.byref(ms))
+    if code != POT_OK:
+        raise PotError(code, "pot_cell_kernel_time")
+    return {"launches": int(la.value), "cells": int(ce.value), "ms": float(ms.value)}
 
 
 def default_params(**kw) -> Params:
@@ -175,7 +192,7 @@ def _dev(t, dtype, shape, name, device):
 class Context:
     """A libpot context (workspace for up to n_max sites) on one device."""
 
-    def __init__(self, n_max: int, k_max: int = 128, device: int = 0, fp32: bool = True,
+    def __init__(self, n_max: int, k_max: int = 256, device: int = 0, fp32: bool = True,
                  fp64: bool = True):
         self._h = ctypes.c_void_p()
         self.device = torch.device("cuda", device)
@@ -377,23 +394,38 @@ class Mlp:
     def check(self, stream=None):
         self._check(lib().pot_mlp_check(self._h, _stream(stream)), "pot_mlp_check")
 
+    def set_history(self, psi_old, stream=None):
+        """Seed (psi_old: n weights, caller order) or clear (None) the weight
+        history the next warm-started fluid step reads."""
+        if psi_old is None:
+            self._check(lib().pot_mlp_set_history(self._h, _stream(stream), 0, None),
+                        "pot_mlp_set_history")
+            return
+        n = int(psi_old.shape[0])
+        psi_old = _dev(psi_old, torch.float32, (n,), "psi_old", self.device)
+        self._check(lib().pot_mlp_set_history(self._h, _stream(stream), n, _ptr(psi_old)),
+                    "pot_mlp_set_history")
+
 
 def pot_mlp_features(ctx: Context, mlp: Mlp, pos, vel, psi, targets, domain=UNIT_BOX, params=None,
-                     stream=None):
+                     stream=None, psi_old=None):
     """Warm-start features (n x 80 BF16, caller order) at the state the next
-    fluid step solves at."""
+    fluid step solves at; psi_old: the weights one step before psi (None: no
+    history)."""
     n = int(pos.shape[0])
     dev = ctx.device
     pos = _dev(pos, torch.float32, (n, 3), "pos", dev)
     vel = _dev(vel, torch.float32, (n, 3), "vel", dev)
     psi = _dev(psi, torch.float32, (n,), "psi", dev)
+    if psi_old is not None:
+        psi_old = _dev(psi_old, torch.float32, (n,), "psi_old", dev)
     targets = _dev(targets, torch.float64, (n,), "targets", dev)
     p = params if params is not None else default_params()
     feat = torch.empty((n, Mlp.N_IN), dtype=torch.bfloat16, device=dev)
     dom = _domain(domain)
     code = lib().pot_mlp_features(ctx.handle, mlp.handle, _stream(stream), n, _ptr(pos), _ptr(vel),
-                                  _ptr(psi), _ptr(targets), ctypes.byref(dom), ctypes.byref(p),
-                                  _ptr(feat))
+                                  _ptr(psi), _ptr(psi_old) if psi_old is not None else None,
+                                  _ptr(targets), ctypes.byref(dom), ctypes.byref(p), _ptr(feat))
     if code != POT_OK:
         raise PotError(code, "pot_mlp_features")
     return feat

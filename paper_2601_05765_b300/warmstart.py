@@ -2,9 +2,9 @@
 
 Data: plain-Newton fluid steps on dam-break columns (seeded); every `every`
 steps, the features at the state the step solves at (positions advanced by
-dt v and clamped, previous weights psi^k, velocities) and the converged
-weights psi^{k+1} of `per_sample` random sites give samples
-(x, y = (psi^{k+1} - psi^k) / h^2), h = nu^(1/3).
+dt v and clamped, previous weights psi^k, velocities, the change
+psi^k - psi^{k-1}) and the converged weights psi^{k+1} of `per_sample` random
+sites give samples (x, y = (psi^{k+1} - psi^k) / h^2), h = nu^(1/3).
 
 Training: Adam on the mean squared error, shuffled batches, all kernels in
 libpot.so (tensor-core forward and back-propagation).  Evaluation: the same
@@ -44,11 +44,13 @@ def collect(ctx, mlp, scene, steps, every, per_sample, seed, dt, tol=1e-4):
     h2 = torch.pow(nu, 2.0 / 3.0).float()
     gen = torch.Generator(device="cpu").manual_seed(seed)
     xs, ys = [], []
+    psi_old = None
     for k in range(steps):
         take = k % every == 0
+        psi_prev = psi.clone()
         if take:
-            feat = pot.pot_mlp_features(ctx, mlp, pos, vel, psi, nu, params=prm)
-            psi_prev = psi.clone()
+            feat = pot.pot_mlp_features(ctx, mlp, pos, vel, psi, nu, params=prm, psi_old=psi_old)
+        psi_old = psi_prev
         st = pot.pot_fluid_step(ctx, pos, vel, psi, nu, params=prm, check=False)
         if st["status"] != 0:
             raise RuntimeError(f"fluid step {k} failed: {st}")
@@ -85,7 +87,9 @@ def compare(ctx, mlp, scene, steps, dt, warm_steps=0, tol=1e-4):
     pos, vel, psi, nu = _state(scene, dev)
     prm = pot.default_params(dt=dt, tol=tol)
     settle(ctx, pos, vel, psi, nu, prm)
+    psi_old = None
     for _ in range(warm_steps):
+        psi_old = psi.clone()
         pot.pot_fluid_step(ctx, pos, vel, psi, nu, params=prm)
     state = (pos.clone(), vel.clone(), psi.clone())
     out = {}
@@ -93,6 +97,8 @@ def compare(ctx, mlp, scene, steps, dt, warm_steps=0, tol=1e-4):
         pos, vel, psi = (t.clone() for t in state)
         p = pot.default_params(dt=dt, tol=tol, warm_start=mode)
         pot.set_warm_start(ctx, mlp if mode else None)
+        if mode:
+            mlp.set_history(psi_old)
         stats = []
         for _ in range(steps):
             stats.append(pot.pot_fluid_step(ctx, pos, vel, psi, nu, params=p, check=False))

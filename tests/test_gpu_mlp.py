@@ -99,21 +99,28 @@ def test_adam_step(mlp):
     mlp.check()
 
 
-def test_features_match_oracle(mlp):
+@pytest.mark.parametrize("history", [False, True])
+def test_features_match_oracle(mlp, history):
     sc = scenes.jittered_block(n_side=10, seed=0)
     n = sc.n
     rng = np.random.default_rng(10)
     vel = (rng.normal(size=(n, 3)) * 0.2).astype(np.float32)
+    h2 = np.cbrt(sc.nu) ** 2
+    old = (sc.psi - rng.uniform(-0.2, 0.2, size=n) * h2).astype(np.float32) if history else None
     ctx = pot.Context(n, 64, 0, fp64=False)
     prm = pot.default_params(dt=1e-3)
     feat = pot.pot_mlp_features(ctx, mlp, to_dev(sc.pos, torch.float32), to_dev(vel, torch.float32),
-                                to_dev(sc.psi, torch.float32), to_dev(sc.nu, torch.float64), params=prm)
+                                to_dev(sc.psi, torch.float32), to_dev(sc.nu, torch.float64), params=prm,
+                                psi_old=to_dev(old, torch.float32) if history else None)
     got = feat.float().cpu().numpy().astype(np.float64)
     x1 = np.clip(sc.pos.astype(np.float32) + np.float32(1e-3) * vel, 1e-6, 1 - 1e-6).astype(np.float64)
     ref = M.bf16(M.knn_features(x1, sc.psi.astype(np.float64), vel.astype(np.float64), sc.nu, 1e-3,
-                                radius=2 * np.sqrt(float(sc.psi.astype(np.float32).max()))))
+                                radius=2 * np.sqrt(float(sc.psi.astype(np.float32).max())),
+                                psi_old=old.astype(np.float64) if history else None))
     diff = np.abs(got - ref)
     # one BF16 ulp of the offsets (values ~1) or of the scaled psi
     assert np.mean(diff <= 1e-2 * np.abs(ref) + 1e-6) > 0.999
-    assert np.all(got[:, 76:] == 0)
+    # the weight change: an FP32 difference, then one BF16 rounding
+    np.testing.assert_allclose(got[:, 76], ref[:, 76], rtol=1e-2, atol=1e-5)
+    assert np.all(got[:, 77:] == 0)
     ctx.close()

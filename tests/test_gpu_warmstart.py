@@ -1,0 +1,68 @@
+"""Learned warm start end to end on the GPU: features, training and the
+MLP-started fluid step against the plain start (previous weights).
+
+The warm start only changes where Newton starts, so correctness is the
+converged result (checked in test_gpu_newton.py); what is checked here is
+that (a) a model whose output is 0 reproduces the plain start exactly, and
+(b) a model trained on a few dam-break steps needs fewer Newton and PCG
+iterations than the start from the previous weights on unseen steps of
+another seed, with no fallback and every step converged.  (The worst-cell
+start error is not the measure: the prediction moves most cells much closer
+and a few outliers further.)"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import mlp_oracle as M
+from paper_2601_05765_b300 import pot, scenes
+from paper_2601_05765_b300 import warmstart as W
+
+pytestmark = pytest.mark.gpu
+
+DT = 2e-3
+
+
+def column(seed, nx=12):
+    return scenes.dam_break(nx=nx, ny=nx, nz=2 * nx, width=0.15, seed=seed)
+
+
+@pytest.fixture(scope="module")
+def setup():
+    sc = column(19)
+    ctx = pot.Context(sc.n, 128, 0, fp64=False)
+    mlp = pot.Mlp(65536, 0)
+    yield ctx, mlp
+    pot.set_warm_start(ctx, None)
+    mlp.close()
+    ctx.close()
+
+
+def test_zero_model_is_the_plain_start(setup):
+    ctx, mlp = setup
+    mlp.set_params(torch.zeros(pot.Mlp.num_params(), dtype=torch.float32, device=ctx.device))
+    res = W.compare(ctx, mlp, column(19), steps=3, dt=DT, warm_steps=2)
+    for a, b in zip(res["plain"], res["mlp"]):
+        assert a["status"] == 0 and b["status"] == 0
+        assert b["mlp_used"] == 1 and b["mlp_fallback"] == 0
+        assert b["err_start"] == pytest.approx(a["err_start"], rel=1e-6)
+        assert b["newton_iters"] == a["newton_iters"]
+
+
+def test_trained_model_starts_closer(setup):
+    ctx, mlp = setup
+    dev = ctx.device
+    mlp.set_params(torch.as_tensor(M.init_params(0), dtype=torch.float32, device=dev))
+    xs, ys = [], []
+    for seed in (10, 11, 12):
+        x, y = W.collect(ctx, mlp, column(seed), steps=30, every=2, per_sample=2048, seed=seed, dt=DT)
+        xs.append(x)
+        ys.append(y)
+    x, y = torch.cat(xs), torch.cat(ys)
+    hist = W.train(mlp, x, y, epochs=120, batch=4096, lr=1e-3)
+    assert hist[-1] < 0.1 * hist[0]
+    res = W.compare(ctx, mlp, column(19), steps=8, dt=DT, warm_steps=12)
+    plain, learned = W.summarize(res["plain"]), W.summarize(res["mlp"])
+    assert plain["all_converged"] and learned["all_converged"]
+    assert learned["fallback_rate"] == 0.0 and learned["used_rate"] == 1.0
+    assert learned["newton_iters"] <= plain["newton_iters"] - 0.5, (learned, plain)
+    assert learned["pcg_iters"] < plain["pcg_iters"], (learned, plain)

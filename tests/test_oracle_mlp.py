@@ -75,3 +75,11 @@ def test_knn_features_against_kdtree():
         assert F[i, 72] == pytest.approx(psi[i] / h[i] ** 2)
         np.testing.assert_allclose(F[i, 73:76], vel[i] * 1e-3 / h[i])
         assert np.all(F[i, 76:] == 0)
+    # history: an unchanged weight gives the no-history features; a change of
+    # c h^2 per site gives c in input 76 and nothing else moves
+    np.testing.assert_array_equal(M.knn_features(pos, psi, vel, nu, dt=1e-3, psi_old=psi), F)
+    c = rng.uniform(-0.3, 0.3, size=n)
+    G = M.knn_features(pos, psi, vel, nu, dt=1e-3, psi_old=psi - c * h ** 2)
+    np.testing.assert_allclose(G[:, 76], c, rtol=1e-9, atol=1e-12)
+    G[:, 76] = 0.0
+    np.testing.assert_array_equal(G, F)

@@ -102,3 +102,30 @@ def test_fluid_step_wall_clamp_and_spring():
     assert cen[2] > x1[0, 2]
     expect = 0.0 + 1e-3 * (-9.81 + (cen[2] - x1[0, 2]) / 1e-4)
     assert v1[0, 2] == pytest.approx(expect, rel=1e-12)
+
+
+def test_empty_cell_repair_puts_sites_inside_their_cells():
+    sc = scenes.jittered_block(n_side=4, seed=0)
+    pos = sc.pos.astype(np.float64)
+    psi = sc.psi.astype(np.float64).copy()
+    # two empty cells: a zero weight, and a ball swallowed by a heavy neighbour
+    psi[5] = 0.0
+    psi[6] = psi[6] * 0.01
+    psi[7] = psi[7] * 6.0
+    res = O.cells(pos, psi)
+    assert np.sum(res["vol"] <= 0) >= 1
+    fixed = O.repair_empty(pos, psi, res["vol"], sc.nu)
+    after = O.cells(pos, fixed)
+    for i in np.nonzero(res["vol"] <= 0)[0]:
+        d = np.linalg.norm(pos - pos[i], axis=1)
+        d[i] = np.inf
+        h = (d * d + fixed[i] - fixed) / (2 * d)
+        assert np.all(h[np.isfinite(d)] > 0)  # the site lies inside its own cell
+        assert after["vol"][i] > 0
+    # non-empty cells keep their weights; Newton from the repaired start converges
+    keep = res["vol"] > 0
+    np.testing.assert_array_equal(fixed[keep], psi[keep])
+    nr = O.newton(pos, sc.nu, psi, tol=1e-10, repair=True)
+    ref = O.newton(pos, sc.nu, sc.psi.astype(np.float64), tol=1e-10)
+    assert nr.status == O.NEWTON_OK
+    np.testing.assert_allclose(nr.psi, ref.psi, rtol=1e-8)
