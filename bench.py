@@ -12,8 +12,16 @@ value  = cells/s: sites whose generalized Laguerre cell is solved to 1e-4 per
          second (N x steps / device time), summed over ranks.
 extras = Newton solve ms (median, p90), geometry throughput (cell
          evaluations per second of the cell kernels), iteration counts.
-e2e    = the same metric through the public API with host buffers: every step
-         copies the state from pinned host memory and reads it back.
+e2e    = the same metric through the public API with host buffers: the same
+         steps are run again from a pinned-host snapshot of the state the
+         timed region started from; every step copies the state in from
+         pinned host memory and the new state back out.
+roofline = the dominant kernel, k_cells (clipping, restriction, analytic
+         quantities), against the FP32 ALU peak: FLOP per processed cell
+         from ncu x cells per launch / the launch's event-timed duration
+         (the library times every k_cells launch with CUDA events).
+         roofline_pcg: the PCG iteration against the measured HBM copy
+         bandwidth.
 --gpus N runs N independent replicas (one process per GPU, different seeds);
 the path has no exchange step of its own.
 
@@ -38,6 +46,12 @@ sys.path.insert(0, ROOT)
 
 SPLASH_DT = 5e-4
 SMALL_SPACING = 0.032  # ~2000 sites with the splash recipe
+# FP32 FLOP executed (fadd + fmul + 2 ffma) and DRAM bytes per cell processed
+# by k_cells, from ncu captures of the 536k-site splash (converged weights, and
+# three launches inside fluid steps: 14.59k FLOP and 305 B per cell in both);
+# profiles/k_cells_splash_converged.md
+K_CELLS_FLOP_PER_CELL = 14590.0
+K_CELLS_DRAM_BYTES_PER_CELL = 305.0
 
 
 def parse():
@@ -46,9 +60,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="step", choices=["step", "cells"],
-                    help="step: fluid steps on the splash; cells: lgc_compute_cells alone on the "
-                         "2^20-site random cloud")
+    ap.add_argument("--mode", default="step", choices=["step", "cells", "warmstart"],
+                    help="step: fluid steps on the splash; cells: lgc_compute_cells alone; "
+                         "warmstart: train the warm-start MLP on dam-break columns, then run the "
+                         "same splash steps from the plain and the learned start")
+    ap.add_argument("--scene", default="cloud", choices=["cloud", "splash"],
+                    help="cells mode: the 2^20-site random cloud, or the splash at converged weights")
     ap.add_argument("--spacing", type=float, default=3.224e-3, help="splash lattice spacing")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -204,8 +221,33 @@ def measured_peaks():
     return 6400.0, "fallback"
 
 
+def k_cells_roofline(kc, clocks, sm_count):
+    """ALU roofline of the cell kernel from its live event timings.
+
+    Work per cell = FP32 FLOP executed per processed cell (fadd + fmul +
+    2 ffma) counted by ncu on the splash at converged weights; peak = SMs x
+    128 FP32 lanes x 2 FLOP x the median SM clock sampled during the timed
+    region.  Traffic per launch = DRAM bytes per processed cell from the same
+    capture x cells per launch."""
+    if not kc["launches"] or kc["ms"] <= 0:
+        return None
+    mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2032.0
+    peak = sm_count * 128 * 2 * mhz * 1e6 / 1e12
+    cells_per_launch = kc["cells"] / kc["launches"]
+    launch_ms = kc["ms"] / kc["launches"]
+    out = {"kernel": "k_cells", "bound": "alu", "unit": "TFLOP/s", "peak": peak,
+           "peak_kind": f"derived: {sm_count} SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz (median under load)",
+           "cells_per_launch": cells_per_launch, "launch_ms": launch_ms, "launches": kc["launches"],
+           "flop_per_cell": K_CELLS_FLOP_PER_CELL, "achieved": None, "frac": None, "traffic": None}
+    if K_CELLS_FLOP_PER_CELL:
+        out["achieved"] = K_CELLS_FLOP_PER_CELL * cells_per_launch / (launch_ms / 1e3) / 1e12
+        out["frac"] = out["achieved"] / peak
+    if K_CELLS_DRAM_BYTES_PER_CELL:
+        out["traffic"] = K_CELLS_DRAM_BYTES_PER_CELL * cells_per_launch
+    return out
+
+
 def run_ours(args):
-    import numpy as np
     import torch
 
     from paper_2601_05765_b300 import pot, scenes
@@ -226,6 +268,9 @@ def run_ours(args):
 
     for _ in range(args.warmup):
         pot.pot_fluid_step(ctx, pos, vel, psi, nu, params=prm)
+    # the state the timed steps start from, kept in pinned host memory: the
+    # end-to-end run below repeats the same steps from it
+    h0 = [t.cpu().pin_memory() for t in (pos, vel, psi)]
 
     # ---- device-timed region
     gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local]) \
@@ -234,6 +279,7 @@ def run_ours(args):
     barrier(world)
     torch.cuda.synchronize()
     sampler.start()
+    pot.cell_kernel_time(ctx, reset=True)
     l0 = pot.kernel_launches()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     stats = []
@@ -243,16 +289,17 @@ def run_ours(args):
     e1.record(stream)
     torch.cuda.synchronize()
     launches = pot.kernel_launches() - l0
+    kc = pot.cell_kernel_time(ctx, reset=True)
     barrier(world)
     clocks = sampler.stop()
     t_dev = e0.elapsed_time(e1) / 1e3
     T, units = reduce_timing(t_dev, n * args.steps, world, dev)
     value = units / T
 
-    # ---- end to end through the public API with host buffers
-    h_pos = pos.cpu().pin_memory()
-    h_vel = vel.cpu().pin_memory()
-    h_psi = psi.cpu().pin_memory()
+    # ---- end to end through the public API with host buffers: the same
+    # steps, each one copying the state in from pinned host memory and the
+    # new state back out
+    h_pos, h_vel, h_psi = (t.clone().pin_memory() for t in h0)
     h_nu = nu.cpu().pin_memory()
     barrier(world)
     torch.cuda.synchronize()
@@ -289,13 +336,16 @@ def run_ours(args):
     bytes_per_iter = 8.0 * nnz_off + 4.0 * (6 + 8) * n
     peak, peak_kind = measured_peaks()
     achieved = bytes_per_iter * pcg_iters / (ms_pcg / 1e3) / 1e9 if ms_pcg > 0 else None
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     line = {
         "metric": "generalized Laguerre cells/s (cells solved to 1e-4 per second)",
         "value": value, "unit": "cells/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * T / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 geometry, f64 reductions", "data": "synthetic",
-        "config": {"workload": f"two-ball splash (configs[3] recipe), {n} sites per GPU, 1e-4 Newton per step",
-                   "sites_per_gpu": n, "dt": SPLASH_DT, "tol": 1e-4, "parallelism": f"replicas x{world}",
+        "config": {"workload": f"two-ball splash (radius 0.2, \u00b13 m/s), {n} sites per GPU, "
+                               f"1e-4 Newton per step",
+                   "sites_per_gpu": n, "dt": SPLASH_DT, "eps": prm.eps, "tol": 1e-4,
+                   "first_timed_step": args.warmup, "parallelism": f"replicas x{world}",
                    "l2": "working set > 126 MB L2, no flush"},
         "newton_solve_ms": {"median": solve_ms[len(solve_ms) // 2],
                             "p90": solve_ms[min(len(solve_ms) - 1, int(0.9 * len(solve_ms)))]},
@@ -303,19 +353,21 @@ def run_ours(args):
         "newton_iters_per_step": statistics.mean(s["newton_iters"] for s in stats),
         "pcg_iters_per_step": pcg_iters / args.steps,
         "cell_evals_per_step": evals / args.steps,
+        "passes_per_step": sum(s["passes"] for s in stats) / args.steps,
         "ms_cells_per_step": ms_cells / args.steps,
         "ms_pcg_per_step": ms_pcg / args.steps,
         "nnz": nnz,
         "max_err": max(s["err_max"] for s in stats),
         "status": sorted({s["status"] for s in stats}),
-        "roofline": {"kernel": "PCG iteration (k_spmv + k_update)", "bound": "hbm",
-                     "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak if achieved else None, "traffic": None,
-                     "peak_kind": peak_kind, "bytes_per_iter": bytes_per_iter},
+        "roofline": k_cells_roofline(kc, clocks, sm_count),
+        "roofline_pcg": {"kernel": "PCG iteration (k_spmv + k_update)", "bound": "hbm",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak if achieved else None, "traffic": None,
+                         "peak_kind": peak_kind, "bytes_per_iter": bytes_per_iter},
         "clocks": clocks,
         "gpu_launches": launches,
         "e2e": {"value": units_e2e / T_e2e, "unit": "cells/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
+                "d2h_bytes_per_step": d2h, "steps": "the same steps as the device-timed region"},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         val, steps, nsm, cores, dt = oracle_steps(args.cpu_seconds, 1000)
@@ -328,21 +380,31 @@ def run_ours(args):
 
 
 def run_cells(args):
-    """lgc_compute_cells (grid, candidates, cell geometry, CSR) on the 2^20-site
-    random cloud: generalized Laguerre cells per second of the cell path."""
+    """lgc_compute_cells (grid, candidates, cell geometry, CSR) alone:
+    generalized Laguerre cells per second of the cell path, on the 2^20-site
+    random cloud or on the splash at converged weights (one untimed Newton
+    solve first)."""
     import torch
 
     from paper_2601_05765_b300 import pot, scenes
     dev = torch.device("cuda", 0)
-    sc = scenes.uniform_cloud(n=1 << 20, seed=1)
+    if args.scene == "splash":
+        sc = scenes.splash(spacing=args.spacing, seed=3)
+        label = f"two-ball splash at converged weights, {sc.n} sites"
+    else:
+        sc = scenes.uniform_cloud(n=1 << 20, seed=1)
+        label = "2^20-site random cloud"
     n = sc.n
-    ctx = pot.Context(n, 128, 0, fp32=True, fp64=False)
+    ctx = pot.Context(n, 256 if args.scene == "splash" else 128, 0, fp32=True, fp64=False)
     pos = torch.from_numpy(sc.pos).to(dev)
     psi = torch.from_numpy(sc.psi).to(dev)
     nu = torch.from_numpy(sc.nu).to(dev)
+    if args.scene == "splash":
+        pot.pot_newton_solve(ctx, pos, nu, psi)
     for _ in range(args.warmup):
         pot.lgc_compute_cells(ctx, pos, psi, nu)
     torch.cuda.synchronize()
+    before = pot.cell_kernel_time(ctx, reset=True)
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     st = []
@@ -352,13 +414,89 @@ def run_cells(args):
         st.append(pot.lgc_compute_cells(ctx, pos, psi, nu)["stats"])
     e1.record(stream)
     torch.cuda.synchronize()
+    kc = pot.cell_kernel_time(ctx, reset=True)
     t = e0.elapsed_time(e1) / 1e3 / args.steps
     ms = {k: statistics.mean(s[k] for s in st) for k in ("ms_grid", "ms_cells", "ms_csr")}
-    print(json.dumps({"metric": "generalized Laguerre cells/s (lgc_compute_cells, 2^20-site random cloud)",
+    print(json.dumps({"metric": f"generalized Laguerre cells/s (lgc_compute_cells, {label})",
                       "value": n / t, "unit": "cells/s", "ms_per_call": 1e3 * t, **ms,
-                      "nnz": st[-1]["nnz"], "gpu_launches": pot.kernel_launches() - l0,
-                      "geometry_cells_per_s": n / (ms["ms_cells"] / 1e3)}))
+                      "nnz": st[-1]["nnz"], "max_planes": st[-1]["max_planes"],
+                      "gpu_launches": pot.kernel_launches() - l0,
+                      "geometry_cells_per_s": n / (ms["ms_cells"] / 1e3),
+                      "k_cells": kc, "k_cells_launches_before_timed": before["launches"]}))
     ctx.close()
+
+
+def run_warmstart(args):
+    """Learned warm start against the plain start on the splash.
+
+    Training: plain-Newton fluid steps on dam-break columns (the dam-break
+    recipe at spacing 0.4/24, 24 x 24 x 48 sites, seeds 10-19, 40 steps of
+    dt 2e-3 each, every 2nd step 4096 sampled sites), Adam on the library's
+    tensor-core kernels.  Evaluation: after `warmup` plain steps, the same
+    `steps` splash steps from the same state with the plain start (previous
+    weights) and with the MLP start (its history seeded with the weights one
+    step earlier), both FP32 geometry with FP64 reductions at tol 1e-4; the
+    same comparison on a dam-break column of an unseen seed (in the training
+    distribution) is reported beside it."""
+    import torch
+
+    from paper_2601_05765_b300 import pot, scenes
+    from paper_2601_05765_b300 import warmstart as W
+    dev = torch.device("cuda", 0)
+    t0 = time.perf_counter()
+    cols = [scenes.dam_break(nx=24, ny=24, nz=48, width=0.4, seed=s) for s in range(10, 20)]
+    sc = scenes.splash(spacing=args.spacing, seed=3)
+    ctx_t = pot.Context(cols[0].n, 256, 0, fp32=True, fp64=False)
+    mlp = pot.Mlp(max(sc.n, 65536), 0)
+    mlp.set_params(W.init_params(0, device=dev))
+    xs, ys = [], []
+    for k, col in enumerate(cols):
+        x, y = W.collect(ctx_t, mlp, col, steps=40, every=2, per_sample=4096, seed=10 + k, dt=2e-3)
+        xs.append(x)
+        ys.append(y)
+    x, y = torch.cat(xs), torch.cat(ys)
+    t1 = time.perf_counter()
+    hist = W.train(mlp, x, y, epochs=60, batch=8192, lr=1e-3)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    ctx_t.close()
+
+    def both(ctx, scene, dt, warm):
+        res = W.compare(ctx, mlp, scene, steps=args.steps, dt=dt, warm_steps=warm)
+        out = {}
+        for k in ("plain", "mlp"):
+            out[k] = W.summarize(res[k])
+            ms = sorted(st["ms_total"] for st in res[k])
+            out[k]["ms_total_median"] = ms[len(ms) // 2]
+        return out
+
+    # in distribution: a dam-break column of an unseen seed, 3x the sites
+    dam = scenes.dam_break(nx=36, ny=36, nz=72, width=0.4, seed=20)
+    ctx_d = pot.Context(dam.n, 256, 0, fp32=True, fp64=False)
+    held = both(ctx_d, dam, 2e-3, 12)
+    pot.set_warm_start(ctx_d, None)
+    ctx_d.close()
+    ctx = pot.Context(sc.n, 256, 0, fp32=True, fp64=False)
+    spl = both(ctx, sc, SPLASH_DT, args.warmup)
+    plain, learned = spl["plain"], spl["mlp"]
+    print(json.dumps({
+        "metric": "Newton iterations and ms per fluid-step solve, learned vs plain start",
+        "workload": f"two-ball splash, {sc.n} sites, steps {args.warmup}..{args.warmup + args.steps - 1}, "
+                    f"dt {SPLASH_DT}, tol 1e-4, FP32 geometry with FP64 reductions",
+        "training": {"samples": int(x.shape[0]), "epochs": len(hist), "loss_first": hist[0],
+                     "loss_last": hist[-1], "collect_s": t1 - t0, "train_s": t2 - t1,
+                     "scenes": "dam-break columns 24x24x48, seeds 10-19, 40 steps of dt 2e-3"},
+        "plain": plain, "mlp": learned,
+        "newton_iters_saved": plain["newton_iters"] - learned["newton_iters"],
+        "ms_saved_per_solve": plain["ms_total"] - learned["ms_total"],
+        "holdout_dam_break": {"workload": f"dam-break column 36x36x72 ({dam.n} sites), seed 20, "
+                                          f"steps 12..{12 + args.steps - 1}, dt 2e-3",
+                              "plain": held["plain"], "mlp": held["mlp"],
+                              "newton_iters_saved": held["plain"]["newton_iters"] - held["mlp"]["newton_iters"],
+                              "ms_saved_per_solve": held["plain"]["ms_total"] - held["mlp"]["ms_total"]}}))
+    pot.set_warm_start(ctx, None)
+    ctx.close()
+    mlp.close()
 
 
 def main():
@@ -367,6 +505,8 @@ def main():
         run_reference(args)
     elif args.mode == "cells":
         run_cells(args)
+    elif args.mode == "warmstart":
+        run_warmstart(args)
     else:
         run_ours(args)
 

@@ -11,6 +11,9 @@ Contents, each citing the paper passage it follows:
   hessian_dense() the Hessian of Eq. 2 as M = -grad^2 K (sign flipped so that
                   M is symmetric positive definite), dense.
   newton()        Algorithm 1: damped Newton with KMT steps, dense direct solve.
+  repair_empty()  raise the weights of empty cells until each site is inside
+                  its own cell, before Algorithm 1 (not in the paper: its
+                  precondition, no empty cell at the start, made to hold).
   fluid_step()    Gallouet-Merigot explicit step of Sec. 5 (pressure spring,
                   gravity, symplectic update), no viscosity/surface tension.
   mlp_*()         FP64 reference of the learned warm-start MLP (not in the

@@ -533,66 +533,54 @@ __device__ __forceinline__ void write_cell(int64_t cell, const V4<T>& p, bool em
   if (o.grad) o.grad[cell] = o.snu[cell] - (double)V;
 }
 
-// A cell with more than 32 planes: the whole warp, planes in rounds of 32.
+// Warps per block of the cell kernel: the plane window of every warp lives in
+// static shared memory (kPlaneCap planes of 16 or 32 bytes plus distance and
+// index), so the FP64 kernel runs half as many warps per block.
 template <typename T>
-__device__ void big_cell(int64_t cell, int lane, V4<T>* pl, T* pd, int* pj,
-                         const V4<T>* __restrict__ sxp, const int32_t* __restrict__ meta,
-                         int32_t* cand, int kmax, const Box<T>& box, T* stage_vals,
-                         const CellOut& o, int32_t* err) {
-  const int mt = meta[cell];
-  const int m = mt & kMetaPlanes;
-  const V4<T> p = sxp[cell];
-  const T r = sqrt(p.w);
-  for (int f = lane; f < m; f += 32) plane_of(f, cell, p, mt, r, sxp, cand, kmax, box, pl[f], pd[f], pj[f]);
-  __syncwarp();
-  CellAcc<T> a = {};
-  bool neg = false;
-  int emitted = 0;
-  for (int f0 = 0; f0 < m; f0 += 32) {
-    const int f = f0 + lane;
-    const bool has = f < m;
-    Facet<T> fo = {};
-    if (has) {
-      fo = facet_eval(pl, m, f, p.w, r);
-      if (fo.overflow) set_error(err, POT_ERR_POLYGON_OVERFLOW, cell);
-      acc_facet(a, pl[f], pd[f], pj[f], fo);
-      neg |= pl[f].w < T(0);
-    }
-    const bool emit = has && pj[f] >= 0 && fo.area > Real<T>::kEmitArea * p.w;
-    const unsigned em = __ballot_sync(kFull, emit);
-    if (emit) {
-      int rank = emitted + __popc(em & ((1u << lane) - 1u));
-      int64_t at = cell * kmax + rank;
-      cand[at] = pj[f];
-      stage_vals[at] = -fo.area / (T(2) * pd[f]);
-    }
-    emitted += __popc(em);
-  }
-  seg_reduce(a, lane, 31);
-  const bool anyneg = __any_sync(kFull, neg);
-  if (lane == 0) write_cell(cell, p, (mt & kMetaEmpty) != 0, !anyneg, a, emitted, o);
-  __syncwarp();
-}
+struct CellCfg {
+  static constexpr int warps = sizeof(T) == 4 ? kCellWarps : kCellWarps / 2;
+};
 
+// Per-cell accumulators of a window, in shared memory.
 template <typename T>
-__global__ void __launch_bounds__(kCellWarps * 32)
+struct CellSlot {
+  CellAcc<T> a;
+  int neg;      // some plane has h < 0 (the site is outside the polytope)
+  int emitted;  // Hessian entries written so far
+};
+
+// One warp per task of up to 32 consecutive cells (grid order).  The task is
+// processed in windows: as many of its cells as have all their planes fit in
+// the warp's kPlaneCap-slot buffer (a cell with no plane takes one slot).
+// The window's planes are built first, then the flat list of its
+// (cell, plane) slots is evaluated 32 at a time, one lane per slot; a cell's
+// slots may span several rounds.  After each round a segmented warp sum per
+// cell is added, in round order, to the cell's accumulator in shared memory
+// (deterministic), and the facets with positive area are written to the
+// cell's Hessian row in plane order.  Finally one lane per cell writes it.
+template <typename T>
+__global__ void __launch_bounds__(CellCfg<T>::warps * 32, 5)
     k_cells(int64_t n, const V4<T>* __restrict__ sxp, const int32_t* __restrict__ meta,
             int32_t* cand, int kmax, Box<T> box, T* stage_vals, CellOut o, int32_t* err) {
-  __shared__ V4<T> s_pl[kCellWarps][kPlaneCap];
-  __shared__ T s_d[kCellWarps][kPlaneCap];
-  __shared__ int s_j[kCellWarps][kPlaneCap];
+  constexpr int W = CellCfg<T>::warps;
+  __shared__ V4<T> s_pl[W][kPlaneCap];
+  __shared__ T s_d[W][kPlaneCap];
+  __shared__ int s_j[W][kPlaneCap];
+  __shared__ CellSlot<T> s_cell[W][32];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   V4<T>* pl = s_pl[wid];
   T* pd = s_d[wid];
   int* pj = s_j[wid];
-  const int64_t c0 = ((int64_t)blockIdx.x * kCellWarps + wid) * kCellsPerWarp;
+  CellSlot<T>* sc = s_cell[wid];
+  const int64_t c0 = ((int64_t)blockIdx.x * W + wid) * kCellsPerWarp;
   if (c0 >= n) return;
   const int64_t c1 = c0 + kCellsPerWarp < n ? c0 + kCellsPerWarp : n;
   int64_t base = c0;
   while (base < c1) {
+    // window: lane w stands for cell base + w
     const int64_t cell = base + lane;
     const bool valid = cell < c1;
-    const bool todo = valid && o.need[cell];  // cells finished in an earlier pass take no lane
+    const bool todo = valid && o.need[cell];  // cells finished in an earlier pass take no slot
     const int mt = todo ? meta[cell] : 0;
     const int m = mt & kMetaPlanes;
     const int slots = todo ? (m > 1 ? m : 1) : 0;
@@ -603,56 +591,98 @@ __global__ void __launch_bounds__(kCellWarps * 32)
       if (lane >= off) incl += t;
     }
     const int excl = incl - slots;
-    const bool take = valid && incl <= 32;  // a prefix of the cells
+    // a prefix of the cells (m <= kPlaneCap, so the first always fits)
+    const bool take = valid && incl <= kPlaneCap;
     const int ncell = __popc(__ballot_sync(kFull, take));
-    if (ncell == 0) {
-      big_cell(base, lane, pl, pd, pj, sxp, meta, cand, kmax, box, stage_vals, o, err);
-      base += 1;
-      continue;
-    }
+    const int total = __shfl_sync(kFull, incl, ncell - 1);
     const unsigned owners = __ballot_sync(kFull, take && slots > 0);
-    const unsigned head = __reduce_or_sync(kFull, (take && slots > 0) ? (1u << excl) : 0u);
-    const int used = __shfl_sync(kFull, incl, ncell - 1);
-    const bool active = lane < used;
-    const int seg = active ? __popc(head & (kFull >> (31 - lane))) - 1 : 0;
-    const int owner = active ? (int)__fns(owners, 0, seg + 1) : 0;  // lane of the seg-th cell
-    const int sstart = __shfl_sync(kFull, excl, owner);
-    const int cmt = __shfl_sync(kFull, mt, owner);
-    const int cm = cmt & kMetaPlanes;
-    const int64_t ccell = base + owner;
-    const int f = lane - sstart;
-    const bool has = active && f < cm;
-    V4<T> p = {};
-    T r = T(0);
-    if (active) {
-      p = sxp[ccell];
-      r = p.w > T(0) ? sqrt(p.w) : T(0);
+    V4<T> pw = {};
+    T rw = T(0);
+    if (take && slots > 0) {
+      pw = sxp[cell];
+      rw = pw.w > T(0) ? sqrt(pw.w) : T(0);
+      sc[lane].a = CellAcc<T>{};
+      sc[lane].neg = 0;
+      sc[lane].emitted = 0;
     }
-    if (has) plane_of(f, ccell, p, cmt, r, sxp, cand, kmax, box, pl[lane], pd[lane], pj[lane]);
+    // build the window's planes, one slot per lane
+    for (int t0 = 0; t0 < total; t0 += 32) {
+      const int t = t0 + lane;
+      const unsigned before = __ballot_sync(kFull, take && slots > 0 && excl <= t0);
+      const unsigned heads = __reduce_or_sync(
+          kFull, (take && slots > 0 && excl > t0 && excl < t0 + 32) ? (1u << (excl - t0)) : 0u);
+      const int idx = __popc(before) + __popc(heads & (0xffffffffu >> (31 - lane))) - 1;
+      const int ow = t < total ? (int)__fns(owners, 0, idx + 1) : 0;
+      const int omt = __shfl_sync(kFull, mt, ow);
+      const int oex = __shfl_sync(kFull, excl, ow);
+      const V4<T> op = {__shfl_sync(kFull, pw.x, ow), __shfl_sync(kFull, pw.y, ow),
+                        __shfl_sync(kFull, pw.z, ow), __shfl_sync(kFull, pw.w, ow)};
+      const T orr = __shfl_sync(kFull, rw, ow);
+      const int f = t - oex;
+      if (t < total && f < (omt & kMetaPlanes))
+        plane_of(f, base + ow, op, omt, orr, sxp, cand, kmax, box, pl[t], pd[t], pj[t]);
+    }
     __syncwarp();
-    CellAcc<T> a = {};
-    Facet<T> fo = {};
-    if (has) {
-      fo = facet_eval(pl + sstart, cm, f, p.w, r);
-      if (fo.overflow) set_error(err, POT_ERR_POLYGON_OVERFLOW, ccell);
-      acc_facet(a, pl[lane], pd[lane], pj[lane], fo);
+    // evaluate the slots, 32 per round
+    for (int t0 = 0; t0 < total; t0 += 32) {
+      const int t = t0 + lane;
+      const bool inr = t < total;
+      const unsigned before = __ballot_sync(kFull, take && slots > 0 && excl <= t0);
+      const unsigned heads = __reduce_or_sync(
+          kFull, (take && slots > 0 && excl > t0 && excl < t0 + 32) ? (1u << (excl - t0)) : 0u);
+      const int idx = __popc(before) + __popc(heads & (0xffffffffu >> (31 - lane))) - 1;
+      const int ow = inr ? (int)__fns(owners, 0, idx + 1) : 0;
+      const int omt = __shfl_sync(kFull, mt, ow);
+      const int oex = __shfl_sync(kFull, excl, ow);
+      const int osl = __shfl_sync(kFull, slots, ow);
+      const V4<T> op = {__shfl_sync(kFull, pw.x, ow), __shfl_sync(kFull, pw.y, ow),
+                        __shfl_sync(kFull, pw.z, ow), __shfl_sync(kFull, pw.w, ow)};
+      const T orr = __shfl_sync(kFull, rw, ow);
+      const int cm = omt & kMetaPlanes;
+      const int f = t - oex;
+      const bool has = inr && f < cm;
+      CellAcc<T> a = {};
+      Facet<T> fo = {};
+      if (has) {
+        fo = facet_eval(pl + oex, cm, f, op.w, orr);
+        if (fo.overflow) set_error(err, POT_ERR_POLYGON_OVERFLOW, base + ow);
+        acc_facet(a, pl[t], pd[t], pj[t], fo);
+      }
+      // this round's part of the owner's slots: lanes [lo, hi]
+      const int lo = inr ? max(oex - t0, 0) : lane;
+      const int hi = inr ? min(oex + osl - 1 - t0, 31) : lane;
+      seg_reduce(a, lane, hi);
+      const unsigned segmask = inr ? ((0xffffffffu >> (31 - hi)) & ~((1u << lo) - 1u)) : 0u;
+      const unsigned negm = __ballot_sync(kFull, has && pl[t].w < T(0));
+      const bool emit = has && pj[t] >= 0 && fo.area > Real<T>::kEmitArea * op.w;
+      const unsigned emm = __ballot_sync(kFull, emit);
+      const int done = inr ? sc[ow].emitted : 0;
+      if (emit) {
+        const int rank = done + __popc(emm & segmask & ((1u << lane) - 1u));
+        const int64_t at = (base + ow) * kmax + rank;
+        cand[at] = pj[t];
+        stage_vals[at] = -fo.area / (T(2) * pd[t]);
+      }
+      __syncwarp();
+      if (inr && lane == lo) {
+        CellAcc<T>& s = sc[ow].a;
+        s.hA += a.hA;
+        s.om += a.om;
+        s.nx += a.nx;
+        s.ny += a.ny;
+        s.nz += a.nz;
+        s.hx += a.hx;
+        s.hy += a.hy;
+        s.hz += a.hz;
+        s.dg += a.dg;
+        s.rm2 = fmax(s.rm2, a.rm2);
+        sc[ow].neg |= (negm & segmask) != 0u;
+        sc[ow].emitted = done + __popc(emm & segmask);
+      }
+      __syncwarp();
     }
-    const int last = active ? sstart + (cm > 1 ? cm : 1) - 1 : lane;
-    seg_reduce(a, lane, last);
-    const unsigned negm = __ballot_sync(kFull, has && pl[lane].w < T(0));
-    const bool emit = has && pj[lane] >= 0 && fo.area > Real<T>::kEmitArea * p.w;
-    const unsigned emm = __ballot_sync(kFull, emit);
-    const int len = last - sstart + 1;
-    const unsigned segmask = active ? ((len == 32 ? kFull : ((1u << len) - 1u)) << sstart) : 0u;
-    if (emit) {
-      int rank = __popc(emm & segmask & ((1u << lane) - 1u));
-      int64_t at = ccell * kmax + rank;
-      cand[at] = pj[lane];
-      stage_vals[at] = -fo.area / (T(2) * pd[lane]);
-    }
-    if (active && lane == sstart)
-      write_cell(ccell, p, (cmt & kMetaEmpty) != 0, (negm & segmask) == 0u, a,
-                 __popc(emm & segmask), o);
+    if (take && slots > 0)
+      write_cell(cell, pw, (mt & kMetaEmpty) != 0, sc[lane].neg == 0, sc[lane].a, sc[lane].emitted, o);
     __syncwarp();
     base += ncell;
   }
@@ -974,7 +1004,7 @@ int cells_eval(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* dom, 
   o.grad = want_grad ? ctx->grad : nullptr;
   o.snu = ctx->snu;
   const int64_t warps = (n + kCellsPerWarp - 1) / kCellsPerWarp;
-  const int blocks = (int)((warps + kCellWarps - 1) / kCellWarps);
+  const int blocks = (int)((warps + CellCfg<T>::warps - 1) / CellCfg<T>::warps);
   int32_t* hcount = (int32_t*)(ctx->h_pinned + 24);
   ctx->last_passes = 0;
   int64_t todo = n;  // cells rebuilt in this pass
@@ -986,10 +1016,12 @@ int cells_eval(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* dom, 
                                                          ctx->need,
                                                          ctx->k_max, ctx->cand, ctx->meta, ctx->err);
     note_launch();
-    cudaEventRecord(ctx->ev[6], st);
-    k_cells<T><<<blocks, kCellWarps * 32, 0, st>>>(n, w.sxp, ctx->meta, ctx->cand, ctx->k_max, box,
+    // the no-alloc entry point's context has no events: no timing there
+    const bool timed = ctx->ev[6] && ctx->ev[7];
+    if (timed) POT_CUDA(cudaEventRecord(ctx->ev[6], st));
+    k_cells<T><<<blocks, CellCfg<T>::warps * 32, 0, st>>>(n, w.sxp, ctx->meta, ctx->cand, ctx->k_max, box,
                                                    w.stage_vals, o, ctx->err);
-    cudaEventRecord(ctx->ev[7], st);
+    if (timed) POT_CUDA(cudaEventRecord(ctx->ev[7], st));
     POT_CUDA(cudaMemsetAsync(ctx->need_count, 0, sizeof(int32_t), st));
     note_launch();
     k_need_update<T><<<blocks_for(n, 256), 256, 0, st>>>(n, w.sxp, w.rcell, ctx->meta, w.srad,
@@ -997,7 +1029,7 @@ int cells_eval(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* dom, 
     POT_CUDA(cudaMemcpyAsync(hcount, ctx->need_count, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     POT_CUDA(cudaStreamSynchronize(st));
     float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, ctx->ev[6], ctx->ev[7]) == cudaSuccess) {
+    if (timed && cudaEventElapsedTime(&ms, ctx->ev[6], ctx->ev[7]) == cudaSuccess) {
       ctx->kc_launches++;
       ctx->kc_cells += todo;
       ctx->kc_ms += ms;

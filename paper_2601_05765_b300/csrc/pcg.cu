@@ -3,16 +3,16 @@
 // off-diagonal CSR in sorted space.
 //
 // Two kernels per iteration, no host round trip:
-//   k_spmv:   beta from the device partials; p_new = z + beta p_old fused into
-//             the gather of the SpMV (p double-buffered); q = M p_new;
-//             partial sums of p_new . q
+//   k_spmv:   beta = rz / rz_prev; p_new = z + beta p_old fused into the
+//             gather of the SpMV (p double-buffered); q = M p_new; p_new . q
 //   k_update: alpha = rz / pq; x += alpha p; r -= alpha q; z = r / diag;
-//             partial sums of r . z and r . r
-// Dot products accumulate in FP64 (per-thread, then fixed-order block and
-// grid reductions, so the result is deterministic).  Every block re-reduces
-// the previous kernel's partials and takes the same decision (converged,
-// breakdown), so no grid-wide barrier is needed.  The host checks the done
-// flag once per chunk of iterations.
+//             r . z and r . r; convergence test
+// Dot products accumulate in FP64: per thread, then per block (fixed tree),
+// then over blocks by the last block to finish (an arrival counter after a
+// memory fence), which adds the block partials in index order and publishes
+// the scalars and the decisions (converged, breakdown) for the next kernel.
+// The result is deterministic and no block re-reads all partials.  The
+// host checks the done flag once per chunk of iterations.
 #include "pot_internal.cuh"
 
 namespace pot {
@@ -21,41 +21,58 @@ namespace {
 constexpr int kPcgThreads = 256;
 constexpr int kTpr = 8;  // threads per CSR row
 
-enum { kRZ0 = 0, kRZ1 = 1, kPQ = 2, kRR = 3, kRR0 = 4, kSlots = 5 };
-enum { kDone = 0, kItA = 1, kItB = 2, kBreak = 3, kIters = 4 };
+// partial-sum arrays (nb doubles each) and scalars at the end of pcg_red
+enum { kPartA = 0, kPartB = 1, kPartC = 2, kParts = 3 };
+enum { kRZ = 0, kRZP = 1, kPQ = 2, kRR = 3, kRR0 = 4, kScalars = 8 };
+// control words
+enum { kDone = 0, kIt = 1, kBreak = 2, kIters = 3, kArrive = 4 };
 
-// Sum of nb partials, same order in every block; result broadcast.
-__device__ __forceinline__ double sum_partials(const double* __restrict__ part, int nb) {
-  __shared__ double sh;
-  if (threadIdx.x < 32) {
-    double s = 0.0;
-    for (int b = threadIdx.x; b < nb; b += 32) s += part[b];
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(kFull, s, off);
-    if (threadIdx.x == 0) sh = s;
-  }
-  __syncthreads();
-  double v = sh;
-  __syncthreads();
-  return v;
-}
-
-__device__ __forceinline__ void block_partial(double v, double* out) {
+// Block sum of v (fixed shape) into thread 0's return value.
+__device__ __forceinline__ double block_sum(double v) {
   __shared__ double sh[kPcgThreads / 32];
   for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(kFull, v, off);
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0;
+  double s = 0.0;
+  if (threadIdx.x == 0)
     for (int w = 0; w < kPcgThreads / 32; w++) s += sh[w];
-    out[blockIdx.x] = s;
+  __syncthreads();
+  return s;
+}
+
+// Publish up to three block partials; returns true in every thread of the
+// block that arrived last (which then sees every block's partials).
+__device__ __forceinline__ bool arrive(double* part, int nb, int count, double a, double b,
+                                       double c, int32_t* ctl) {
+  __shared__ bool last;
+  a = block_sum(a);
+  if (count > 1) b = block_sum(b);
+  if (count > 2) c = block_sum(c);
+  if (threadIdx.x == 0) {
+    part[kPartA * nb + blockIdx.x] = a;
+    if (count > 1) part[kPartB * nb + blockIdx.x] = b;
+    if (count > 2) part[kPartC * nb + blockIdx.x] = c;
+    __threadfence();
+    last = atomicAdd(&ctl[kArrive], 1) == nb - 1;
   }
   __syncthreads();
+  if (last) __threadfence();
+  return last;
+}
+
+// Sum of nb partials in index order (strided per thread, fixed tree), in
+// thread 0; called by the last block only.
+__device__ __forceinline__ double sum_parts(const double* part, int nb) {
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nb; b += kPcgThreads) s += __ldcg(part + b);
+  return block_sum(s);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kPcgThreads)
     k_pcg_init(int64_t n, const double* __restrict__ b, const T* __restrict__ diag, T* x, T* r,
-               T* z, T* p0, double* part, int nb, int32_t* ctl) {
+               T* z, T* p0, double* part, double* scal, int nb, int32_t* ctl, double rtol2,
+               int max_iter) {
   double rz = 0.0, rr = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -68,37 +85,32 @@ __global__ void __launch_bounds__(kPcgThreads)
     rz += (double)ri * (double)zi;
     rr += (double)ri * (double)ri;
   }
-  block_partial(rz, part + kRZ0 * nb);
-  block_partial(rr, part + kRR * nb);
-  block_partial(rr, part + kRR0 * nb);
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    ctl[kDone] = 0;
-    ctl[kItA] = 0;
-    ctl[kItB] = 0;
-    ctl[kBreak] = 0;
-    ctl[kIters] = 0;
+  if (arrive(part, nb, 2, rz, rr, 0.0, ctl)) {
+    const double trz = sum_parts(part + kPartA * nb, nb);
+    const double trr = sum_parts(part + kPartB * nb, nb);
+    if (threadIdx.x == 0) {
+      scal[kRZ] = trz;
+      scal[kRZP] = 1.0;
+      scal[kRR] = trr;
+      scal[kRR0] = trr;
+      ctl[kIt] = 0;
+      ctl[kBreak] = 0;
+      ctl[kIters] = 0;
+      ctl[kDone] = (trr <= 0.0 || max_iter <= 0) ? 1 : 0;
+      ctl[kArrive] = 0;
+    }
   }
+  (void)rtol2;
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kPcgThreads)
     k_spmv(int64_t n, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ cols,
            const T* __restrict__ vals, const T* __restrict__ diag, const T* __restrict__ z,
-           T* pa, T* pb, T* q, double* part, int nb, int32_t* ctl, double rtol2, int max_iter) {
+           T* pa, T* pb, T* q, double* part, double* scal, int nb, int32_t* ctl) {
   if (ctl[kDone]) return;
-  const int it = ctl[kItA];
-  const double rr = sum_partials(part + kRR * nb, nb);
-  const double rr0 = sum_partials(part + kRR0 * nb, nb);
-  if (rr <= rtol2 * rr0 || it >= max_iter) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      ctl[kDone] = 1;
-      ctl[kIters] = it;
-    }
-    return;
-  }
-  const double rz = sum_partials(part + ((it & 1) ? kRZ1 : kRZ0) * nb, nb);
-  const double rzp = sum_partials(part + ((it & 1) ? kRZ0 : kRZ1) * nb, nb);
-  const T beta = it == 0 ? T(0) : (T)(rz / rzp);
+  const int it = ctl[kIt];
+  const T beta = it == 0 ? T(0) : (T)(scal[kRZ] / scal[kRZP]);
   const T* __restrict__ pold = (it & 1) ? pb : pa;
   T* pnew = (it & 1) ? pa : pb;
   const int sub = threadIdx.x & (kTpr - 1);
@@ -128,28 +140,28 @@ __global__ void __launch_bounds__(kPcgThreads)
       pq += (double)pi * (double)qi;
     }
   }
-  block_partial(pq, part + kPQ * nb);
-  if (blockIdx.x == 0 && threadIdx.x == 0) ctl[kItB] = it;
+  if (arrive(part, nb, 1, pq, 0.0, 0.0, ctl)) {
+    const double tpq = sum_parts(part + kPartA * nb, nb);
+    if (threadIdx.x == 0) {
+      scal[kPQ] = tpq;
+      if (!(tpq > 0.0)) {  // M not positive definite along p: breakdown
+        ctl[kBreak] = 1;
+        ctl[kIters] = it;
+        ctl[kDone] = 1;
+      }
+      ctl[kArrive] = 0;
+    }
+  }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kPcgThreads)
     k_update(int64_t n, const T* __restrict__ diag, T* x, T* r, T* z, const T* __restrict__ pa,
-             const T* __restrict__ pb, const T* __restrict__ q, double* part, int nb,
-             int32_t* ctl) {
+             const T* __restrict__ pb, const T* __restrict__ q, double* part, double* scal,
+             int nb, int32_t* ctl, double rtol2, int max_iter) {
   if (ctl[kDone]) return;
-  const int it = ctl[kItB];
-  const double rz = sum_partials(part + ((it & 1) ? kRZ1 : kRZ0) * nb, nb);
-  const double pq = sum_partials(part + kPQ * nb, nb);
-  if (!(pq > 0.0)) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      ctl[kBreak] = 1;
-      ctl[kDone] = 1;
-      ctl[kIters] = it;
-    }
-    return;
-  }
-  const T alpha = (T)(rz / pq);
+  const int it = ctl[kIt];
+  const T alpha = (T)(scal[kRZ] / scal[kPQ]);
   const T* __restrict__ p = (it & 1) ? pa : pb;
   double rzn = 0.0, rr = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -162,44 +174,68 @@ __global__ void __launch_bounds__(kPcgThreads)
     rzn += (double)ri * (double)zi;
     rr += (double)ri * (double)ri;
   }
-  block_partial(rzn, part + ((it & 1) ? kRZ0 : kRZ1) * nb);
-  block_partial(rr, part + kRR * nb);
-  if (blockIdx.x == 0 && threadIdx.x == 0) ctl[kItA] = it + 1;
+  if (arrive(part, nb, 2, rzn, rr, 0.0, ctl)) {
+    const double trz = sum_parts(part + kPartA * nb, nb);
+    const double trr = sum_parts(part + kPartB * nb, nb);
+    if (threadIdx.x == 0) {
+      scal[kRZP] = scal[kRZ];
+      scal[kRZ] = trz;
+      scal[kRR] = trr;
+      ctl[kIt] = it + 1;
+      if (trr <= rtol2 * scal[kRR0] || it + 1 >= max_iter) {
+        ctl[kIters] = it + 1;
+        ctl[kDone] = 1;
+      }
+      ctl[kArrive] = 0;
+    }
+  }
 }
 
 }  // namespace
+
+int pcg_blocks(int sm_count) { return sm_count * kPcgMaxBlocksPerSm; }
+size_t pcg_red_len(int sm_count) { return (size_t)kParts * pcg_blocks(sm_count) + kScalars; }
 
 template <typename T>
 int pcg_solve(pot_ctx* ctx, cudaStream_t st, int64_t n, int64_t nnz_off, double rtol, int max_iter,
               int chunk, int* iters, double* rel_res) {
   (void)nnz_off;
   Work<T>& w = ctx->work<T>();
-  const int nb = ctx->sm_count * 2;
+  // one full wave of the SpMV kernel: as many blocks as fit on the SMs
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmv<T>, kPcgThreads, 0) !=
+          cudaSuccess ||
+      per_sm < 1)
+    per_sm = 2;
+  if (per_sm > kPcgMaxBlocksPerSm) per_sm = kPcgMaxBlocksPerSm;
+  const int nb = ctx->sm_count * per_sm;
   double* part = ctx->pcg_red;
+  double* scal = ctx->pcg_red + (size_t)kParts * pcg_blocks(ctx->sm_count);
   if (chunk < 1) chunk = 1;
-  note_launch();
-  k_pcg_init<T><<<nb, kPcgThreads, 0, st>>>(n, ctx->grad, w.diag, w.u, w.r, w.z, w.p0, part, nb,
-                                            ctx->pcg_ctl);
   const double rtol2 = rtol * rtol;
+  // the arrival counter must start at zero
+  POT_CUDA(cudaMemsetAsync(ctx->pcg_ctl + kArrive, 0, sizeof(int32_t), st));
+  note_launch();
+  k_pcg_init<T><<<nb, kPcgThreads, 0, st>>>(n, ctx->grad, w.diag, w.u, w.r, w.z, w.p0, part, scal,
+                                            nb, ctx->pcg_ctl, rtol2, max_iter);
   int launched = 0;
   int32_t* hctl = (int32_t*)(ctx->h_pinned + 16);
   for (;;) {
     for (int k = 0; k < chunk; k++) {
       note_launch();
       k_spmv<T><<<nb, kPcgThreads, 0, st>>>(n, ctx->row_ptr, ctx->csr_cols, w.csr_vals, w.diag,
-                                            w.z, w.p0, w.p1, w.q, part, nb, ctx->pcg_ctl, rtol2,
-                                            max_iter);
+                                            w.z, w.p0, w.p1, w.q, part, scal, nb, ctx->pcg_ctl);
       note_launch();
-      k_update<T><<<nb, kPcgThreads, 0, st>>>(n, w.diag, w.u, w.r, w.z, w.p0, w.p1, w.q, part, nb,
-                                              ctx->pcg_ctl);
+      k_update<T><<<nb, kPcgThreads, 0, st>>>(n, w.diag, w.u, w.r, w.z, w.p0, w.p1, w.q, part,
+                                              scal, nb, ctx->pcg_ctl, rtol2, max_iter);
     }
     launched += chunk;
     POT_CUDA(cudaGetLastError());
-    POT_CUDA(cudaMemcpyAsync(hctl, ctx->pcg_ctl, 5 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    POT_CUDA(cudaMemcpyAsync(hctl, ctx->pcg_ctl, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     POT_CUDA(cudaStreamSynchronize(st));
     if (hctl[kDone] || launched > max_iter + chunk) break;
   }
-  *iters = hctl[kIters];
+  *iters = hctl[kDone] ? hctl[kIters] : hctl[kIt];
   if (rel_res) *rel_res = -1.0;
   if (hctl[kBreak]) return POT_ERR_PCG_BREAKDOWN;
   return POT_OK;

@@ -278,6 +278,9 @@ int mlp_warm_start(pot_ctx* ctx, pot_mlp* mm, cudaStream_t st, int64_t n, const 
                    const float* psi, float dt, float** psi_prev);
 
 // PCG (pcg.cu): solve M u = grad (sorted space) into work.u
+constexpr int kPcgMaxBlocksPerSm = 8;
+int pcg_blocks(int sm_count);       // largest grid of the PCG kernels
+size_t pcg_red_len(int sm_count);   // doubles of ctx->pcg_red
 template <typename T>
 int pcg_solve(pot_ctx* ctx, cudaStream_t st, int64_t n, int64_t nnz_off, double rtol, int max_iter,
               int chunk, int* iters, double* rel_res);

@@ -131,13 +131,6 @@ def splash(spacing: float = 3.224e-3, radius: float = 0.2, speed: float = 3.0,
     is jittered by U(-jitter, jitter)^3*spacing (one draw, default_rng(seed)).
     Ball 0 moves with (+speed,0,0), ball 1 with (-speed,0,0).  nu = fill*s^3,
     psi0 as jittered_block.  The defaults give about 2.0M sites.
-
-    extra["eps"] is the spring strength of the pressure force (Sec. 5) for
-    this impact: with a site held at most about one spacing from its centroid
-    the spring decelerates it by at most s/eps^2, so stopping `speed` within
-    one spacing needs eps = sqrt(2) s / speed (1.5e-3 at the default spacing);
-    a softer spring lets the balls pass through each other, piling sites up
-    until cells reach past dozens of neighbours.
     """
     rng = np.random.default_rng(seed)
     parts, vels = [], []
@@ -161,8 +154,7 @@ def splash(spacing: float = 3.224e-3, radius: float = 0.2, speed: float = 3.0,
     nu = np.full(n, fill * spacing ** 3, dtype=np.float64)
     r = r_factor * _ball_radius_for_volume(nu)
     return Scene(pos=pos.astype(np.float32), psi=(r * r).astype(np.float32), nu=nu,
-                 vel=vel.astype(np.float32), name=f"splash_{n}",
-                 extra={"spacing": spacing, "eps": math.sqrt(2.0) * spacing / speed})
+                 vel=vel.astype(np.float32), name=f"splash_{n}", extra={"spacing": spacing})
 
 
 def random_subset(n: int, k: int, seed: int) -> np.ndarray:

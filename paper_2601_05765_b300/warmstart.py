@@ -24,6 +24,34 @@ import torch
 from . import pot, scenes
 
 
+# parameter layout of the model (pot.h: W1 80x128 (row = input), b1, W2
+# 128x128, b2, W3 128x128, b3, w4 128, b4 1); inputs 77..79 are padding
+_SHAPES = ((80, 128), (128,), (128, 128), (128,), (128, 128), (128,), (128,), (1,))
+_N_FEAT = 77
+
+
+def init_params(seed: int = 0, device="cuda") -> torch.Tensor:
+    """Fresh parameters: He-uniform weights (limit sqrt(6 / fan_in)), zero
+    biases, the head scaled by 0.1 so that the first predictions are small,
+    zero weights for the padding inputs.  FP32 vector on `device`."""
+    gen = torch.Generator(device="cpu").manual_seed(seed)
+    parts = []
+    for k, shp in enumerate(_SHAPES):
+        if len(shp) == 2 or k == 6:
+            lim = math.sqrt(6.0 / shp[0])
+            w = (torch.rand(shp, generator=gen, dtype=torch.float64) * 2.0 - 1.0) * lim
+            if k == 0:
+                w[_N_FEAT:, :] = 0.0
+            if k == 6:
+                w *= 0.1
+        else:
+            w = torch.zeros(shp, dtype=torch.float64)
+        parts.append(w.reshape(-1))
+    flat = torch.cat(parts).to(torch.float32)
+    assert flat.numel() == pot.Mlp.num_params()
+    return flat.to(device)
+
+
 def _state(sc, dev):
     return (torch.from_numpy(sc.pos).to(dev), torch.from_numpy(sc.vel).to(dev),
             torch.from_numpy(sc.psi).to(dev), torch.from_numpy(sc.nu).to(dev))
