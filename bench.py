@@ -47,11 +47,11 @@ sys.path.insert(0, ROOT)
 SPLASH_DT = 5e-4
 SMALL_SPACING = 0.032  # ~2000 sites with the splash recipe
 # FP32 FLOP executed (fadd + fmul + 2 ffma) and DRAM bytes per cell processed
-# by k_cells, from ncu captures of the 536k-site splash (converged weights, and
-# three launches inside fluid steps: 14.59k FLOP and 305 B per cell in both);
+# by k_cells, from an ncu capture of the 536k-site splash at converged weights
+# (the count inside fluid steps agreed to 0.3 %);
 # profiles/k_cells_splash_converged.md
-K_CELLS_FLOP_PER_CELL = 14590.0
-K_CELLS_DRAM_BYTES_PER_CELL = 305.0
+K_CELLS_FLOP_PER_CELL = 14549.0
+K_CELLS_DRAM_BYTES_PER_CELL = 312.0
 
 
 def parse():
@@ -60,10 +60,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="step", choices=["step", "cells", "warmstart"],
+    ap.add_argument("--mode", default="step", choices=["step", "cells", "warmstart", "dam", "solve"],
                     help="step: fluid steps on the splash; cells: lgc_compute_cells alone; "
                          "warmstart: train the warm-start MLP on dam-break columns, then run the "
-                         "same splash steps from the plain and the learned start")
+                         "same splash steps from the plain and the learned start; dam: the 500k "
+                         "dam break in mixed precision and in FP64; solve: the 1000-site single "
+                         "Newton solve")
     ap.add_argument("--scene", default="cloud", choices=["cloud", "splash"],
                     help="cells mode: the 2^20-site random cloud, or the splash at converged weights")
     ap.add_argument("--spacing", type=float, default=3.224e-3, help="splash lattice spacing")
@@ -499,6 +501,103 @@ def run_warmstart(args):
     mlp.close()
 
 
+def _pcts(v):
+    v = sorted(v)
+    return {"median": v[len(v) // 2], "p90": v[min(len(v) - 1, int(0.9 * len(v)))], "max": v[-1]}
+
+
+def run_dam(args):
+    """The 500,094-site dam break (dt 2e-3, eps 0.01), stepped `steps` times
+    from the same converged start in mixed precision (FP32 geometry, FP64
+    reductions) and in FP64: per-step Newton iterations, solve ms and worst
+    volume error, and the distance between the two trajectories."""
+    import numpy as np
+    import torch
+
+    from paper_2601_05765_b300 import pot, scenes
+    dev = torch.device("cuda", 0)
+    sc = scenes.dam_break()
+    n = sc.n
+    marks = sorted({k for k in (args.steps // 4, args.steps // 2, 3 * args.steps // 4, args.steps) if k > 0})
+    out, snaps = {}, {}
+    for prec, dt in (("mixed", torch.float32), ("fp64", torch.float64)):
+        ctx = pot.Context(n, 256, 0, fp32=dt == torch.float32, fp64=dt == torch.float64)
+        pos = torch.as_tensor(sc.pos, dtype=dt, device=dev)
+        vel = torch.as_tensor(sc.vel, dtype=dt, device=dev)
+        psi = torch.as_tensor(sc.psi, dtype=dt, device=dev)
+        nu = torch.as_tensor(sc.nu, dtype=torch.float64, device=dev)
+        prm = pot.default_params(dt=2e-3)
+        pot.pot_newton_solve(ctx, pos, nu, psi, params=prm)
+        stats, snaps[prec] = [], {}
+        for k in range(1, args.steps + 1):
+            stats.append(pot.pot_fluid_step(ctx, pos, vel, psi, nu, params=prm, check=False))
+            if stats[-1]["status"] != 0:
+                break
+            if k in marks:
+                snaps[prec][k] = pos.double().cpu().numpy()
+        out[prec] = {"steps_done": len(stats), "all_converged": all(st["status"] == 0 for st in stats),
+                     "newton_iters_mean": float(np.mean([st["newton_iters"] for st in stats])),
+                     "pcg_iters_mean": float(np.mean([st["pcg_iters"] for st in stats])),
+                     "solve_ms": _pcts([st["ms_total"] for st in stats]),
+                     "err_max_per_step": _pcts([st["err_max"] for st in stats]),
+                     "newton_iters_per_step": [st["newton_iters"] for st in stats]}
+        ctx.close()
+    s = 0.4 / 63
+    drift = {str(k): float(np.max(np.linalg.norm(snaps["mixed"][k] - snaps["fp64"][k], axis=1)) / s)
+             for k in marks if k in snaps["mixed"] and k in snaps["fp64"]}
+    print(json.dumps({"metric": "dam break, mixed precision against FP64 on the GPU",
+                      "workload": f"dam-break column 63x63x126 ({n} sites), dt 2e-3, eps 0.01, "
+                                  f"{args.steps} steps, tol 1e-4",
+                      "mixed": out["mixed"], "fp64": out["fp64"],
+                      "speedup_mixed_over_fp64": out["fp64"]["solve_ms"]["median"] / out["mixed"]["solve_ms"]["median"],
+                      "trajectory_max_distance_in_spacings": drift}))
+
+
+def run_solve(args):
+    """The 1000-site jittered block solved to 1e-4 from psi0 (single Newton
+    solve), FP64 and mixed precision on the GPU; the FP64 oracle's Newton
+    (dense direct solve) timed on the host beside it."""
+    import torch
+
+    from paper_2601_05765_b300 import pot, scenes
+    dev = torch.device("cuda", 0)
+    sc = scenes.jittered_block()
+    res = {}
+    for prec, dt in (("fp64", torch.float64), ("mixed", torch.float32)):
+        ctx = pot.Context(sc.n, 256, 0, fp32=dt == torch.float32, fp64=dt == torch.float64)
+        pos = torch.as_tensor(sc.pos, dtype=dt, device=dev)
+        nu = torch.as_tensor(sc.nu, dtype=torch.float64, device=dev)
+        times, st = [], None
+        for k in range(args.warmup + args.steps):
+            psi = torch.as_tensor(sc.psi, dtype=dt, device=dev)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st = pot.pot_newton_solve(ctx, pos, nu, psi)
+            torch.cuda.synchronize()
+            if k >= args.warmup:
+                times.append(1e3 * (time.perf_counter() - t0))
+        res[prec] = {"ms_per_solve": _pcts(times), "newton_iters": st["newton_iters"],
+                     "halvings": st["halvings"], "pcg_iters": st["pcg_iters"], "err_max": st["err_max"]}
+        ctx.close()
+    line = {"metric": "Newton solve ms to 1e-4, 1000-site jittered block",
+            "workload": "jittered 10x10x10 block, spacing 0.05, psi0 = (0.8 r_nu)^2, tol 1e-4",
+            "fp64": res["fp64"], "mixed": res["mixed"]}
+    if not args.no_cpu_baseline:
+        import numpy as np
+
+        from oracle import oracle as O
+        x = sc.pos.astype(np.float64)
+        t0 = time.perf_counter()
+        reps = 0
+        while reps < 3 or time.perf_counter() - t0 < 2.0:
+            r = O.newton(x, sc.nu, sc.psi.astype(np.float64), tol=1e-4)
+            reps += 1
+        line["cpu_baseline"] = {"value": 1e3 * (time.perf_counter() - t0) / reps, "unit": "ms per solve",
+                                "cores": O.max_threads(), "kind": "oracle",
+                                "sample": f"{reps} oracle Newton solves (dense LU, KMT), {r.iters} iterations"}
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -507,6 +606,10 @@ def main():
         run_cells(args)
     elif args.mode == "warmstart":
         run_warmstart(args)
+    elif args.mode == "dam":
+        run_dam(args)
+    elif args.mode == "solve":
+        run_solve(args)
     else:
         run_ours(args)
 
