@@ -260,7 +260,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     sc = scenes.splash(spacing=args.spacing, seed=3 + rank)
     n = sc.n
-    ctx = pot.Context(n, 256, local, fp32=True, fp64=False)
+    ctx = pot.Context(n, 246, local, fp32=True, fp64=False)
     pos = torch.from_numpy(sc.pos).to(dev)
     vel = torch.from_numpy(sc.vel).to(dev)
     psi = torch.from_numpy(sc.psi).to(dev)
@@ -397,7 +397,7 @@ def run_cells(args):
         sc = scenes.uniform_cloud(n=1 << 20, seed=1)
         label = "2^20-site random cloud"
     n = sc.n
-    ctx = pot.Context(n, 256 if args.scene == "splash" else 128, 0, fp32=True, fp64=False)
+    ctx = pot.Context(n, 246 if args.scene == "splash" else 128, 0, fp32=True, fp64=False)
     pos = torch.from_numpy(sc.pos).to(dev)
     psi = torch.from_numpy(sc.psi).to(dev)
     nu = torch.from_numpy(sc.nu).to(dev)
@@ -448,7 +448,7 @@ def run_warmstart(args):
     t0 = time.perf_counter()
     cols = [scenes.dam_break(nx=24, ny=24, nz=48, width=0.4, seed=s) for s in range(10, 20)]
     sc = scenes.splash(spacing=args.spacing, seed=3)
-    ctx_t = pot.Context(cols[0].n, 256, 0, fp32=True, fp64=False)
+    ctx_t = pot.Context(cols[0].n, 246, 0, fp32=True, fp64=False)
     mlp = pot.Mlp(max(sc.n, 65536), 0)
     mlp.set_params(W.init_params(0, device=dev))
     xs, ys = [], []
@@ -474,11 +474,11 @@ def run_warmstart(args):
 
     # in distribution: a dam-break column of an unseen seed, 3x the sites
     dam = scenes.dam_break(nx=36, ny=36, nz=72, width=0.4, seed=20)
-    ctx_d = pot.Context(dam.n, 256, 0, fp32=True, fp64=False)
+    ctx_d = pot.Context(dam.n, 246, 0, fp32=True, fp64=False)
     held = both(ctx_d, dam, 2e-3, 12)
     pot.set_warm_start(ctx_d, None)
     ctx_d.close()
-    ctx = pot.Context(sc.n, 256, 0, fp32=True, fp64=False)
+    ctx = pot.Context(sc.n, 246, 0, fp32=True, fp64=False)
     spl = both(ctx, sc, SPLASH_DT, args.warmup)
     plain, learned = spl["plain"], spl["mlp"]
     print(json.dumps({
@@ -521,7 +521,7 @@ def run_dam(args):
     marks = sorted({k for k in (args.steps // 4, args.steps // 2, 3 * args.steps // 4, args.steps) if k > 0})
     out, snaps = {}, {}
     for prec, dt in (("mixed", torch.float32), ("fp64", torch.float64)):
-        ctx = pot.Context(n, 256, 0, fp32=dt == torch.float32, fp64=dt == torch.float64)
+        ctx = pot.Context(n, 246, 0, fp32=dt == torch.float32, fp64=dt == torch.float64)
         pos = torch.as_tensor(sc.pos, dtype=dt, device=dev)
         vel = torch.as_tensor(sc.vel, dtype=dt, device=dev)
         psi = torch.as_tensor(sc.psi, dtype=dt, device=dev)
@@ -564,7 +564,7 @@ def run_solve(args):
     sc = scenes.jittered_block()
     res = {}
     for prec, dt in (("fp64", torch.float64), ("mixed", torch.float32)):
-        ctx = pot.Context(sc.n, 256, 0, fp32=dt == torch.float32, fp64=dt == torch.float64)
+        ctx = pot.Context(sc.n, 246, 0, fp32=dt == torch.float32, fp64=dt == torch.float64)
         pos = torch.as_tensor(sc.pos, dtype=dt, device=dev)
         nu = torch.as_tensor(sc.nu, dtype=torch.float64, device=dev)
         times, st = [], None

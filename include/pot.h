@@ -132,7 +132,7 @@ typedef struct {
 
 /* ---- context ---------------------------------------------------------- */
 
-/* Create a context on `device` for up to n_max sites and k_max (<= 256)
+/* Create a context on `device` for up to n_max sites and k_max (<= 246)
  * candidate bisectors per cell, and allocate all its workspace.  A cell is
  * built from the bisectors whose plane cuts its ball within the cell's
  * security radius (the distance from the site that the cell is verified not

@@ -8,17 +8,18 @@
 //   security radius (h_ij < R_i, see below); a plane with h <= -r_i empties
 //   the cell.  The six box walls are planes too.
 //
-// k_cells (one warp per group of cells, one lane per cutting plane): each
-//   warp packs consecutive cells into its 32 lanes (a cell with m planes
-//   takes m lanes; cells with more than 32 planes take the whole warp in
-//   rounds).  Lane f clips the disk of its plane f by the traces of the other
-//   planes of its cell (2D convex clipping of a line-list polygon: every
-//   vertex is recomputed from its two lines, never interpolated), restricts
-//   the polygon to the disk (Sec. 3.4) and integrates, per fan piece from the
-//   disk centre, the facet area |B_f|, the signed solid angle Omega_f it
-//   subtends at the site (its projection on the sphere, Sec. 3.3) and its
-//   first moment.  Segmented warp reductions then give per cell
-//     |K_i| = psi_i (4 pi [p_i inside all planes] - sum_f Omega_f),
+// k_cells (one warp per group of 32 cells, one lane per (cell, plane) slot):
+//   the planes of consecutive cells fill a shared buffer, and their slots are
+//   evaluated 32 per round.  Lane f clips the disk of its plane f by the
+//   traces of the other planes of its cell, nearest first (2D convex
+//   clipping of a line-list polygon: every vertex is recomputed from its two
+//   lines, never interpolated), restricts the polygon to the disk (Sec. 3.4)
+//   and integrates, per fan piece from the disk centre, the facet area
+//   |B_f|, the signed solid angle Omega_f it subtends at the site (its
+//   projection on the sphere, Sec. 3.3) and its first moment.  Segmented
+//   warp reductions then give per cell
+//     |K_i| = psi_i (4 pi [p_i inside all planes] - sum_f Omega_f)
+//             (0 when no facet reaches the sphere),
 //     |V_i| = (sum_f h_f |B_f| + r_i |K_i|) / 3          (pyramids, Sec. 3.2),
 //     centroid, and the Hessian row of Eq. 2 (M = -grad^2 K):
 //     M_ij = -|B_ij|/(2 d_ij), M_ii = sum_j |B_ij|/(2 d_ij) + |K_i|/(2 r_i).
@@ -201,6 +202,7 @@ struct Facet {
   T area, omega, mx, my, mz;
   T rm2;  // squared distance from the site of the facet's farthest point
   int overflow;
+  int arc;  // the restricted facet has a circular edge (it reaches the sphere)
 };
 
 // Orthonormal basis (u, v) of the plane with unit normal n, branch-free:
@@ -229,10 +231,13 @@ __device__ __forceinline__ void isect(T a1, T b1, T c1, T a2, T b2, T c2, T& x, 
 }
 
 // Facet fi of a cell whose planes are pl[0..m): (n, h) with y.n <= h.
+// ord[0..m) lists the planes by increasing h: the facet is clipped by the
+// nearest planes first, so its polygon shrinks early.
 // Returns area, signed solid angle at the site and first moment (about the site).
 template <typename T>
-__device__ Facet<T> facet_eval(const V4<T>* __restrict__ pl, int m, int fi, T ps, T r) {
-  Facet<T> out = {T(0), T(0), T(0), T(0), T(0), T(0), 0};
+__device__ Facet<T> facet_eval(const V4<T>* __restrict__ pl, const uint16_t* __restrict__ ord, int m,
+                               int fi, T ps, T r) {
+  Facet<T> out = {T(0), T(0), T(0), T(0), T(0), T(0), 0, 0};
   const V4<T> P = pl[fi];
   const T h = P.w;
   const T rho2 = ps - h * h;
@@ -242,21 +247,23 @@ __device__ Facet<T> facet_eval(const V4<T>* __restrict__ pl, int m, int fi, T ps
   onb(P.x, P.y, P.z, ux, uy, uz, vx, vy, vz);
   const T B = T(2) * rho;
 
-  // polygon: line ids (plane index, or 252..255 for the square around the
-  // disk) and vertices; vertex k = intersection of lines k-1 and k
+  // polygon: line ids (plane index, or kSq + 0..3 for the square around
+  // the disk) and vertices; vertex k = intersection of lines k-1 and k
+  constexpr int kSq = 0xfc;
+  static_assert(kPlaneCap <= kSq, "plane indices must stay below the square's line ids");
   uint8_t lid[2][kMaxLines];
   T px[2][kMaxLines], py[2][kMaxLines];
   int cur = 0, nl = 4;
-  lid[0][0] = 252; lid[0][1] = 253; lid[0][2] = 254; lid[0][3] = 255;
+  lid[0][0] = kSq; lid[0][1] = kSq + 1; lid[0][2] = kSq + 2; lid[0][3] = kSq + 3;
   px[0][0] = -B; py[0][0] = -B;
   px[0][1] = B;  py[0][1] = -B;
   px[0][2] = B;  py[0][2] = B;
   px[0][3] = -B; py[0][3] = B;
 
   auto line = [&](int id, T& a, T& b, T& c) {
-    if (id >= 252) {
-      a = (id == 253) ? T(1) : ((id == 255) ? T(-1) : T(0));
-      b = (id == 254) ? T(1) : ((id == 252) ? T(-1) : T(0));
+    if (id >= kSq) {
+      a = (id == kSq + 1) ? T(1) : ((id == kSq + 3) ? T(-1) : T(0));
+      b = (id == kSq + 2) ? T(1) : ((id == kSq) ? T(-1) : T(0));
       c = B;
     } else {
       const V4<T> G = pl[id];
@@ -266,7 +273,8 @@ __device__ Facet<T> facet_eval(const V4<T>* __restrict__ pl, int m, int fi, T ps
     }
   };
 
-  for (int gi = 0; gi < m; gi++) {
+  for (int oi = 0; oi < m; oi++) {
+    const int gi = ord[oi];
     if (gi == fi) continue;
     T a, b, c;
     line(gi, a, b, c);
@@ -384,6 +392,7 @@ __device__ Facet<T> facet_eval(const V4<T>* __restrict__ pl, int m, int fi, T ps
     }
   }
   out.rm2 = arc ? ps : rm2;  // the facet reaches the sphere when it has an arc
+  out.arc = arc && area > T(0);
   out.area = area;
   out.omega = omg;
   out.mx = h * P.x * area + ux * mx + vx * my;
@@ -438,6 +447,8 @@ __device__ __forceinline__ void plane_of(int f, int64_t cell, const V4<T>& p, in
 template <typename T>
 struct CellAcc {
   T hA, om, nx, ny, nz, hx, hy, hz, dg, rm2;
+  int nfac;  // facets of positive area
+  int arc;   // facets with a circular edge
 };
 
 template <typename T>
@@ -453,6 +464,8 @@ __device__ __forceinline__ void acc_facet(CellAcc<T>& a, const V4<T>& pl, T pd, 
   a.hz += pl.w * fo.mz;
   if (pj >= 0) a.dg += fo.area / (T(2) * pd);
   a.rm2 = fmax(a.rm2, fo.rm2);
+  a.nfac += fo.area > T(0) ? 1 : 0;
+  a.arc += fo.arc;
 }
 
 // sum over lanes [lane, last] into the first lane of the window (segment head)
@@ -482,6 +495,8 @@ __device__ __forceinline__ void seg_reduce(CellAcc<T>& a, int lane, int last) {
     T t = __shfl_down_sync(kFull, a.rm2, off);
     if (lane + off <= last) a.rm2 = fmax(a.rm2, t);
   }
+  a.nfac = seg_sum(a.nfac, lane, last);
+  a.arc = seg_sum(a.arc, lane, last);
 }
 
 struct CellOut {
@@ -504,8 +519,17 @@ __device__ __forceinline__ void write_cell(int64_t cell, const V4<T>& p, bool em
   T cx = p.x, cy = p.y, cz = p.z;
   if (!empty && ps > T(0)) {
     const T r = sqrt(ps);
-    K = ps * (T(4.0 * 3.14159265358979323846) * (inside ? T(1) : T(0)) - a.om);
-    K = fmax(K, T(0));
+    // A spherical part of the boundary is bounded by circular facet edges:
+    // a cell with facets none of which has an arc is a polytope inside its
+    // ball (or its ball misses the polytope), |K| = 0 exactly.  The formula
+    // would leave a few ulp of 4 pi psi there, a volume error that grows
+    // like psi^(3/2) in deep fluid.
+    if (a.nfac > 0 && a.arc == 0) {
+      K = T(0);
+    } else {
+      K = ps * (T(4.0 * 3.14159265358979323846) * (inside ? T(1) : T(0)) - a.om);
+      K = fmax(K, T(0));
+    }
     V = (a.hA + r * K) * T(1.0 / 3.0);
     dg = a.dg + K / (T(2) * r);
     if (V > T(0)) {
@@ -567,10 +591,12 @@ __global__ void __launch_bounds__(CellCfg<T>::warps * 32, 5)
   __shared__ T s_d[W][kPlaneCap];
   __shared__ int s_j[W][kPlaneCap];
   __shared__ CellSlot<T> s_cell[W][32];
+  __shared__ uint16_t s_ord[W][kPlaneCap];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   V4<T>* pl = s_pl[wid];
   T* pd = s_d[wid];
   int* pj = s_j[wid];
+  uint16_t* po = s_ord[wid];
   CellSlot<T>* sc = s_cell[wid];
   const int64_t c0 = ((int64_t)blockIdx.x * W + wid) * kCellsPerWarp;
   if (c0 >= n) return;
@@ -623,6 +649,28 @@ __global__ void __launch_bounds__(CellCfg<T>::warps * 32, 5)
         plane_of(f, base + ow, op, omt, orr, sxp, cand, kmax, box, pl[t], pd[t], pj[t]);
     }
     __syncwarp();
+    // each cell's planes by increasing h (ties by index): the clipping order
+    for (int t0 = 0; t0 < total; t0 += 32) {
+      const int t = t0 + lane;
+      const unsigned before = __ballot_sync(kFull, take && slots > 0 && excl <= t0);
+      const unsigned heads = __reduce_or_sync(
+          kFull, (take && slots > 0 && excl > t0 && excl < t0 + 32) ? (1u << (excl - t0)) : 0u);
+      const int idx = __popc(before) + __popc(heads & (0xffffffffu >> (31 - lane))) - 1;
+      const int ow = t < total ? (int)__fns(owners, 0, idx + 1) : 0;
+      const int cm = __shfl_sync(kFull, mt, ow) & kMetaPlanes;
+      const int oex = __shfl_sync(kFull, excl, ow);
+      const int f = t - oex;
+      if (t < total && f < cm) {
+        const T hf = pl[t].w;
+        int rank = 0;
+        for (int g = 0; g < cm; g++) {
+          const T hg = pl[oex + g].w;
+          rank += (hg < hf || (hg == hf && g < f)) ? 1 : 0;
+        }
+        po[oex + rank] = (uint16_t)f;
+      }
+    }
+    __syncwarp();
     // evaluate the slots, 32 per round
     for (int t0 = 0; t0 < total; t0 += 32) {
       const int t = t0 + lane;
@@ -644,7 +692,7 @@ __global__ void __launch_bounds__(CellCfg<T>::warps * 32, 5)
       CellAcc<T> a = {};
       Facet<T> fo = {};
       if (has) {
-        fo = facet_eval(pl + oex, cm, f, op.w, orr);
+        fo = facet_eval(pl + oex, po + oex, cm, f, op.w, orr);
         if (fo.overflow) set_error(err, POT_ERR_POLYGON_OVERFLOW, base + ow);
         acc_facet(a, pl[t], pd[t], pj[t], fo);
       }
@@ -676,6 +724,8 @@ __global__ void __launch_bounds__(CellCfg<T>::warps * 32, 5)
         s.hz += a.hz;
         s.dg += a.dg;
         s.rm2 = fmax(s.rm2, a.rm2);
+        s.nfac += a.nfac;
+        s.arc += a.arc;
         sc[ow].neg |= (negm & segmask) != 0u;
         sc[ow].emitted = done + __popc(emm & segmask);
       }

@@ -25,7 +25,7 @@ namespace pot {
 
 constexpr int kWarp = 32;
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kMaxK = 256;         // candidate bisectors per cell (k_max <= 256)
+constexpr int kMaxK = 246;         // candidate bisectors per cell (k_max <= 246)
 constexpr int kPlaneCap = kMaxK + 6;
 constexpr int kMaxLines = 24;      // edges of one facet polygon
 constexpr int kCellWarps = 4;      // warps per block of the cell kernel

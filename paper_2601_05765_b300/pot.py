@@ -192,7 +192,7 @@ def _dev(t, dtype, shape, name, device):
 class Context:
     """A libpot context (workspace for up to n_max sites) on one device."""
 
-    def __init__(self, n_max: int, k_max: int = 256, device: int = 0, fp32: bool = True,
+    def __init__(self, n_max: int, k_max: int = 246, device: int = 0, fp32: bool = True,
                  fp64: bool = True):
         self._h = ctypes.c_void_p()
         self.device = torch.device("cuda", device)
