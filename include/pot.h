@@ -127,20 +127,22 @@ typedef struct {
   int32_t mlp_used;    /* warm start: 1 if the MLP start was kept */
   int32_t mlp_fallback;/* warm start: 1 if the MLP start was rejected */
   int32_t repairs;     /* empty cells at the start whose weight was raised */
-  int32_t passes;      /* security-radius passes over all cell evaluations */
+  int32_t passes;      /* security-ball passes over all cell evaluations */
+  int64_t error_site;  /* caller index of a site behind the last cell error, else -1 */
 } pot_solve_stats;
 
 /* ---- context ---------------------------------------------------------- */
 
 /* Create a context on `device` for up to n_max sites and k_max (<= 246)
  * candidate bisectors per cell, and allocate all its workspace.  A cell is
- * built from the bisectors whose plane cuts its ball within the cell's
- * security radius (the distance from the site that the cell is verified not
- * to exceed, Sec. 4); in packed fluid that is about 15-40 planes, in
- * strongly compressed fluid (sites much closer than nu^(1/3)) cells reach
- * past several neighbours and need more.  A cell that needs more than k_max
- * gives POT_ERR_NEIGHBOUR_OVERFLOW.  Workspace: about 16 k_max + 250 bytes
- * per site and precision.
+ * built from the bisectors whose plane cuts its ball and meets the cell's
+ * security ball (a ball around the cell's previous centroid that the cell
+ * is verified not to leave, Sec. 4); in packed fluid that is about 15-40
+ * planes, in strongly compressed fluid (sites much closer than nu^(1/3))
+ * cells reach past several neighbours and need more.  A cell that needs
+ * more than k_max gives POT_ERR_NEIGHBOUR_OVERFLOW.  Workspace: about
+ * 16 k_max + 280 bytes per site and precision.  Newton solves and fluid
+ * steps on the same sites reuse the previous solve's cell centres.
  * precision_mask: bit 0 = FP32 geometry (mixed-precision entry points),
  * bit 1 = FP64 entry points (*_f64).
  * Returns POT_ERR_INVALID_ARG / POT_ERR_CUDA on failure (*ctx = NULL). */
@@ -162,7 +164,7 @@ int64_t pot_kernel_launches(void);
 /* Device time of the cell kernel (clipping, restriction and analytic
  * quantities, Sec. 3.2-3.4) accumulated over this context's evaluations since
  * the last reset, measured with CUDA events on the caller's stream around each
- * launch: the number of launches (one per security-radius pass), the cells
+ * launch: the number of launches (one per security-ball pass), the cells
  * they processed and the milliseconds.  Any output pointer may be NULL;
  * reset != 0 clears the counters after reading them.
  * Errors: POT_ERR_INVALID_ARG for a NULL context. */

@@ -54,6 +54,8 @@ int alloc_work(Work<T>& w, int64_t n, int64_t k, int64_t gcap) {
   POT_CHECK(alloc(&w.nu_max, 1));
   POT_CHECK(alloc(&w.srad, n));
   POT_CHECK(alloc(&w.srad_lo, n));
+  POT_CHECK(alloc(&w.soff, 3 * n));
+  POT_CHECK(alloc(&w.hint, 4 * n));
   POT_CHECK(alloc(&w.rcell_acc, n));
   POT_CHECK(alloc(&w.rcell, n));
   POT_CHECK(alloc(&w.gmax, gcap + 1));
@@ -64,7 +66,7 @@ template <typename T>
 void free_work(Work<T>& w) {
   void* ptrs[] = {w.sxp, w.psi_base, w.vol,  w.karea, w.diag, w.cen, w.stage_vals, w.csr_vals,
                   w.u,   w.x,        w.r,    w.z,     w.p0,   w.p1,  w.q,          w.vel_s,
-                  w.psi_max, w.nu_max, w.srad, w.srad_lo, w.rcell_acc, w.rcell, w.gmax};
+                  w.psi_max, w.nu_max, w.srad, w.srad_lo, w.soff, w.hint, w.rcell_acc, w.rcell, w.gmax};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   w = Work<T>();
@@ -296,6 +298,7 @@ int pot_newton_solve(pot_ctx* ctx, void* stream, int64_t n, const float* pos, co
   pot_solve_stats local;
   pot_solve_stats* S = stats ? stats : &local;
   memset(S, 0, sizeof(*S));
+  S->error_site = -1;
   POT_CHECK(check_ctx(ctx, n, 1));
   if (!pos || !targets || !psi_inout || !finite_box(dom) || !check_params(params))
     return POT_ERR_INVALID_ARG;
@@ -308,6 +311,7 @@ int pot_newton_solve_f64(pot_ctx* ctx, void* stream, int64_t n, const double* po
   pot_solve_stats local;
   pot_solve_stats* S = stats ? stats : &local;
   memset(S, 0, sizeof(*S));
+  S->error_site = -1;
   POT_CHECK(check_ctx(ctx, n, 2));
   if (!pos || !targets || !psi_inout || !finite_box(dom) || !check_params(params))
     return POT_ERR_INVALID_ARG;
@@ -320,6 +324,7 @@ int pot_fluid_step(pot_ctx* ctx, void* stream, int64_t n, float* pos, float* vel
   pot_solve_stats local;
   pot_solve_stats* S = stats ? stats : &local;
   memset(S, 0, sizeof(*S));
+  S->error_site = -1;
   POT_CHECK(check_ctx(ctx, n, 1));
   if (!pos || !vel || !targets || !psi || !finite_box(dom) || !check_params(params))
     return POT_ERR_INVALID_ARG;
@@ -332,6 +337,7 @@ int pot_fluid_step_f64(pot_ctx* ctx, void* stream, int64_t n, double* pos, doubl
   pot_solve_stats local;
   pot_solve_stats* S = stats ? stats : &local;
   memset(S, 0, sizeof(*S));
+  S->error_site = -1;
   POT_CHECK(check_ctx(ctx, n, 2));
   if (!pos || !vel || !targets || !psi || !finite_box(dom) || !check_params(params))
     return POT_ERR_INVALID_ARG;

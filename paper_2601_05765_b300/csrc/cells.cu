@@ -11,9 +11,9 @@
 // k_cells (one warp per group of 32 cells, one lane per (cell, plane) slot):
 //   the planes of consecutive cells fill a shared buffer, and their slots are
 //   evaluated 32 per round.  Lane f clips the disk of its plane f by the
-//   traces of the other planes of its cell, nearest first (2D convex
-//   clipping of a line-list polygon: every vertex is recomputed from its two
-//   lines, never interpolated), restricts the polygon to the disk (Sec. 3.4)
+//   traces of the other planes of its cell (2D convex clipping of a
+//   line-list polygon: every vertex is recomputed from its two lines, never
+//   interpolated), restricts the polygon to the disk (Sec. 3.4)
 //   and integrates, per fan piece from the disk centre, the facet area
 //   |B_f|, the signed solid angle Omega_f it subtends at the site (its
 //   projection on the sphere, Sec. 3.3) and its first moment.  Segmented
@@ -62,13 +62,17 @@ __device__ __forceinline__ void set_error(int32_t* err, int code, int64_t site) 
 // ---------------------------------------------------------------------------
 // candidates
 
-// Security radius (the paper's contributing-neighbour problem, Sec. 4): a
-// cell is built from the bisectors with h_ij < R_i only, R_i <= r_i.  If the
-// cell so built lies strictly inside the ball of radius R_i around p_i, no
-// plane with h >= R_i can touch it and the cell is exact; otherwise R_i grows
-// and the cell is rebuilt (pass loop in cells_eval).  Inside deep fluid
-// the weights grow like a pressure and the balls get many spacings wide,
-// while the cells stay small: R_i keeps the candidate lists short.
+// Security ball (the paper's contributing-neighbour problem, Sec. 4): a cell
+// is built from the bisectors that meet the ball of radius R_i around
+// p_i + o_i only (signed distance of the plane from that centre,
+// h_ij - n_ij . o_i, below R_i).  If the cell so built lies strictly inside
+// that ball, no other plane can touch it and the cell is exact; otherwise
+// R_i grows and the cell is rebuilt (pass loop in cells_eval).  Inside deep
+// fluid the weights grow like a pressure and the balls get many spacings
+// wide, while the cells stay small, and off their sites: centred on the
+// cell (o_i = the previous centroid - p_i), the ball keeps the candidate
+// lists short.  R_i >= r_i + |o_i| contains the site's ball: every plane
+// that cuts it is then a candidate.
 //
 // The first R_i of an evaluation is a guess from the previous evaluation's
 // cells, and a growth step can overshoot, so a list that overflows k_max
@@ -86,8 +90,8 @@ __global__ void __launch_bounds__(256)
     k_candidates(int64_t n, const V4<T>* __restrict__ sxp, const int32_t* __restrict__ cell_start,
                  GridParams<T> g, Box<T> box, const T* __restrict__ psi_max,
                  const T* __restrict__ gmax, T* __restrict__ srad, const T* __restrict__ srad_lo,
-                 const uint8_t* __restrict__ need, int kmax, int32_t* __restrict__ cand,
-                 int32_t* __restrict__ meta, int32_t* err) {
+                 const T* __restrict__ soff, const uint8_t* __restrict__ need, int kmax,
+                 int32_t* __restrict__ cand, int32_t* __restrict__ meta, int32_t* err) {
   int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n || !need[s]) return;
   const V4<T> p = sxp[s];
@@ -110,10 +114,13 @@ __global__ void __launch_bounds__(256)
     }
   }
   const T R = srad[s];
+  const T ox = soff[3 * s + 0], oy = soff[3 * s + 1], oz = soff[3 * s + 2];
+  // a candidate has h_ij < R + |o| =: Re, so it lies within
+  // Re + sqrt(Re^2 - psi_i + psi_j) of p_i, and one that cuts the ball
+  // within r + r_j
+  const T Re = R + sqrt(ox * ox + oy * oy + oz * oz);
   const T pmx = *psi_max;
-  // a site j with h_ij < R lies within R + sqrt(R^2 - psi_i + psi_j) of p_i,
-  // and one that cuts the ball within r + r_j
-  const T D = fmin(R + sqrt(fmax(R * R - ps + pmx, T(0))), r + sqrt(pmx));
+  const T D = fmin(Re + sqrt(fmax(Re * Re - ps + pmx, T(0))), r + sqrt(pmx));
   const T D2 = D * D;
   int c0[3], c1[3];
   const T pc[3] = {p.x, p.y, p.z};
@@ -149,7 +156,7 @@ __global__ void __launch_bounds__(256)
           const T dl = sqrt(dl2);
           const T c = gmax[key] - ps;
           const T hmin = c >= T(0) ? T(0.5) * dl - c / (T(2) * dl) : T(0.5) * dl;
-          if (hmin >= R) continue;
+          if (hmin >= Re) continue;
         }
         const int a = cell_start[key], b = cell_start[key + 1];
         for (int t = a; t < b; t++) {
@@ -170,7 +177,7 @@ __global__ void __launch_bounds__(256)
             empty = true;
             break;
           }
-          if (h < r && h < R) {
+          if (h < r && h - (dx * ox + dy * oy + dz * oz) / d < R) {
             if (nc < kmax) cand[row + nc] = t;
             nc++;
           }
@@ -231,12 +238,15 @@ __device__ __forceinline__ void isect(T a1, T b1, T c1, T a2, T b2, T c2, T& x, 
 }
 
 // Facet fi of a cell whose planes are pl[0..m): (n, h) with y.n <= h.
-// ord[0..m) lists the planes by increasing h: the facet is clipped by the
-// nearest planes first, so its polygon shrinks early.
+// A plane whose line passes clearly outside the polygon's bounding circle
+// (radius^2 rp2 around the disk centre) is dismissed without visiting the
+// vertices (nor clipping by a line that only grazes a vertex within
+// rounding).
 // Returns area, signed solid angle at the site and first moment (about the site).
+// rm2 is measured from the security-ball centre p + o (oa = |o|).
 template <typename T>
-__device__ Facet<T> facet_eval(const V4<T>* __restrict__ pl, const uint16_t* __restrict__ ord, int m,
-                               int fi, T ps, T r) {
+__device__ Facet<T> facet_eval(const V4<T>* __restrict__ pl, int m, int fi, T ps, T r, T ox, T oy,
+                               T oz, T oa) {
   Facet<T> out = {T(0), T(0), T(0), T(0), T(0), T(0), 0, 0};
   const V4<T> P = pl[fi];
   const T h = P.w;
@@ -273,8 +283,8 @@ __device__ Facet<T> facet_eval(const V4<T>* __restrict__ pl, const uint16_t* __r
     }
   };
 
-  for (int oi = 0; oi < m; oi++) {
-    const int gi = ord[oi];
+  T rp2 = T(2) * B * B;  // squared radius of a circle around the polygon
+  for (int gi = 0; gi < m; gi++) {
     if (gi == fi) continue;
     T a, b, c;
     line(gi, a, b, c);
@@ -286,6 +296,8 @@ __device__ Facet<T> facet_eval(const V4<T>* __restrict__ pl, const uint16_t* __r
     T lr = rho * sqrt(len2);
     if (c >= lr) continue;            // the disk lies inside this half-plane
     if (c <= -lr) return out;         // the disk lies outside: no facet
+    // every vertex v has a.v <= |(a,b)| |v| < c: the polygon is inside
+    if (c > T(0) && c * c >= len2 * rp2 * T(1.0001)) continue;
     unsigned om = 0;
     for (int k = 0; k < nl; k++)
       if (a * px[cur][k] + b * py[cur][k] > c) om |= 1u << k;
@@ -307,12 +319,15 @@ __device__ Facet<T> facet_eval(const V4<T>* __restrict__ pl, const uint16_t* __r
       return out;
     }
     const int nx = cur ^ 1;
+    T mr2 = T(0);
     for (int k = 0; k < cnt; k++) {
       int idx = e + k;
       if (idx >= nl) idx -= nl;
       lid[nx][k] = lid[cur][idx];
-      px[nx][k] = px[cur][idx];
-      py[nx][k] = py[cur][idx];
+      const T vx = px[cur][idx], vy = py[cur][idx];
+      px[nx][k] = vx;
+      py[nx][k] = vy;
+      if (k > 0) mr2 = fmax(mr2, vx * vx + vy * vy);
     }
     lid[nx][cnt] = (uint8_t)gi;
     T a2, b2, c2;
@@ -321,6 +336,8 @@ __device__ Facet<T> facet_eval(const V4<T>* __restrict__ pl, const uint16_t* __r
     int sm1 = s == 0 ? nl - 1 : s - 1;
     line(lid[cur][sm1], a2, b2, c2);
     isect(a2, b2, c2, a, b, c, px[nx][cnt], py[nx][cnt]);
+    mr2 = fmax(mr2, px[nx][0] * px[nx][0] + py[nx][0] * py[nx][0]);
+    rp2 = fmax(mr2, px[nx][cnt] * px[nx][cnt] + py[nx][cnt] * py[nx][cnt]);
     nl = cnt + 1;
     cur = nx;
   }
@@ -354,13 +371,20 @@ __device__ Facet<T> facet_eval(const V4<T>* __restrict__ pl, const uint16_t* __r
     mx += ta * (ax + bx) * T(1.0 / 3.0);
     my += ta * (ay + by) * T(1.0 / 3.0);
   };
+  // the security-ball centre in the facet's frame (disk centre at h n)
+  const T ou = ux * ox + uy * oy + uz * oz, ov = vx * ox + vy * oy + vz * oz;
+  const T on = h - (P.x * ox + P.y * oy + P.z * oz);
+  const T on2 = on * on;
   T rm2 = T(0);
   bool arc = false;
   for (int k = 0; k < nl; k++) {
     int k2 = k + 1 == nl ? 0 : k + 1;
     T pxk = px[cur][k], pyk = py[cur][k], qx = px[cur][k2], qy = py[cur][k2];
     const T pk2 = pxk * pxk + pyk * pyk;
-    if (pk2 <= rho2) rm2 = fmax(rm2, pk2 + h2);  // a polygon vertex inside the disk
+    if (pk2 <= rho2) {  // a polygon vertex inside the disk
+      const T ex = pxk - ou, ey = pyk - ov;
+      rm2 = fmax(rm2, ex * ex + ey * ey + on2);
+    }
     T dx = qx - pxk, dy = qy - pyk;
     T a2 = dx * dx + dy * dy;
     if (a2 == T(0)) continue;
@@ -391,7 +415,8 @@ __device__ Facet<T> facet_eval(const V4<T>* __restrict__ pl, const uint16_t* __r
       arc = true;
     }
   }
-  out.rm2 = arc ? ps : rm2;  // the facet reaches the sphere when it has an arc
+  // a facet with an arc reaches the sphere: bound its points by r + |o|
+  out.rm2 = arc ? (r + oa) * (r + oa) : rm2;
   out.arc = arc && area > T(0);
   out.area = area;
   out.omega = omg;
@@ -513,7 +538,7 @@ struct CellOut {
 
 template <typename T>
 __device__ __forceinline__ void write_cell(int64_t cell, const V4<T>& p, bool empty, bool inside,
-                                           const CellAcc<T>& a, int cnt, const CellOut& o) {
+                                           const CellAcc<T>& a, int cnt, T oa, const CellOut& o) {
   const T ps = p.w;
   T V = T(0), K = T(0), dg = T(0);
   T cx = p.x, cy = p.y, cz = p.z;
@@ -539,12 +564,12 @@ __device__ __forceinline__ void write_cell(int64_t cell, const V4<T>& p, bool em
       cz += (a.hz - ps * a.nz) * iv;
     }
   }
-  // farthest point of the cell from its site, decided geometrically (|K|
-  // carries rounding noise of a few ulp of 4 pi psi): the sphere if a facet
-  // leaves its disk (rm2 = psi then) or if there is no facet at all (a full
-  // ball), else the farthest facet vertex
+  // farthest point of the cell from its security-ball centre, decided
+  // geometrically (|K| carries rounding noise of a few ulp of 4 pi psi):
+  // r + |o| if a facet leaves its disk or if there is no facet at all (a
+  // full ball), else the farthest facet vertex
   T rc = T(0);
-  if (!empty && ps > T(0)) rc = a.rm2 > T(0) ? sqrt(a.rm2) : (V > T(0) ? sqrt(ps) : T(0));
+  if (!empty && ps > T(0)) rc = a.rm2 > T(0) ? sqrt(a.rm2) : (V > T(0) ? sqrt(ps) + oa : T(0));
   ((T*)o.rcell)[cell] = rc;
   ((T*)o.vol)[cell] = V;
   ((T*)o.karea)[cell] = K;
@@ -585,18 +610,17 @@ struct CellSlot {
 template <typename T>
 __global__ void __launch_bounds__(CellCfg<T>::warps * 32, 5)
     k_cells(int64_t n, const V4<T>* __restrict__ sxp, const int32_t* __restrict__ meta,
-            int32_t* cand, int kmax, Box<T> box, T* stage_vals, CellOut o, int32_t* err) {
+            int32_t* cand, int kmax, Box<T> box, T* stage_vals, const T* __restrict__ soff,
+            CellOut o, int32_t* err) {
   constexpr int W = CellCfg<T>::warps;
   __shared__ V4<T> s_pl[W][kPlaneCap];
   __shared__ T s_d[W][kPlaneCap];
   __shared__ int s_j[W][kPlaneCap];
   __shared__ CellSlot<T> s_cell[W][32];
-  __shared__ uint16_t s_ord[W][kPlaneCap];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   V4<T>* pl = s_pl[wid];
   T* pd = s_d[wid];
   int* pj = s_j[wid];
-  uint16_t* po = s_ord[wid];
   CellSlot<T>* sc = s_cell[wid];
   const int64_t c0 = ((int64_t)blockIdx.x * W + wid) * kCellsPerWarp;
   if (c0 >= n) return;
@@ -623,10 +647,13 @@ __global__ void __launch_bounds__(CellCfg<T>::warps * 32, 5)
     const int total = __shfl_sync(kFull, incl, ncell - 1);
     const unsigned owners = __ballot_sync(kFull, take && slots > 0);
     V4<T> pw = {};
-    T rw = T(0);
+    T rw = T(0), oxw = T(0), oyw = T(0), ozw = T(0);
     if (take && slots > 0) {
       pw = sxp[cell];
       rw = pw.w > T(0) ? sqrt(pw.w) : T(0);
+      oxw = soff[3 * cell + 0];
+      oyw = soff[3 * cell + 1];
+      ozw = soff[3 * cell + 2];
       sc[lane].a = CellAcc<T>{};
       sc[lane].neg = 0;
       sc[lane].emitted = 0;
@@ -649,28 +676,6 @@ __global__ void __launch_bounds__(CellCfg<T>::warps * 32, 5)
         plane_of(f, base + ow, op, omt, orr, sxp, cand, kmax, box, pl[t], pd[t], pj[t]);
     }
     __syncwarp();
-    // each cell's planes by increasing h (ties by index): the clipping order
-    for (int t0 = 0; t0 < total; t0 += 32) {
-      const int t = t0 + lane;
-      const unsigned before = __ballot_sync(kFull, take && slots > 0 && excl <= t0);
-      const unsigned heads = __reduce_or_sync(
-          kFull, (take && slots > 0 && excl > t0 && excl < t0 + 32) ? (1u << (excl - t0)) : 0u);
-      const int idx = __popc(before) + __popc(heads & (0xffffffffu >> (31 - lane))) - 1;
-      const int ow = t < total ? (int)__fns(owners, 0, idx + 1) : 0;
-      const int cm = __shfl_sync(kFull, mt, ow) & kMetaPlanes;
-      const int oex = __shfl_sync(kFull, excl, ow);
-      const int f = t - oex;
-      if (t < total && f < cm) {
-        const T hf = pl[t].w;
-        int rank = 0;
-        for (int g = 0; g < cm; g++) {
-          const T hg = pl[oex + g].w;
-          rank += (hg < hf || (hg == hf && g < f)) ? 1 : 0;
-        }
-        po[oex + rank] = (uint16_t)f;
-      }
-    }
-    __syncwarp();
     // evaluate the slots, 32 per round
     for (int t0 = 0; t0 < total; t0 += 32) {
       const int t = t0 + lane;
@@ -686,13 +691,16 @@ __global__ void __launch_bounds__(CellCfg<T>::warps * 32, 5)
       const V4<T> op = {__shfl_sync(kFull, pw.x, ow), __shfl_sync(kFull, pw.y, ow),
                         __shfl_sync(kFull, pw.z, ow), __shfl_sync(kFull, pw.w, ow)};
       const T orr = __shfl_sync(kFull, rw, ow);
+      const T sox = __shfl_sync(kFull, oxw, ow), soy = __shfl_sync(kFull, oyw, ow),
+              soz = __shfl_sync(kFull, ozw, ow);
       const int cm = omt & kMetaPlanes;
       const int f = t - oex;
       const bool has = inr && f < cm;
       CellAcc<T> a = {};
       Facet<T> fo = {};
       if (has) {
-        fo = facet_eval(pl + oex, po + oex, cm, f, op.w, orr);
+        fo = facet_eval(pl + oex, cm, f, op.w, orr, sox, soy, soz,
+                        sqrt(sox * sox + soy * soy + soz * soz));
         if (fo.overflow) set_error(err, POT_ERR_POLYGON_OVERFLOW, base + ow);
         acc_facet(a, pl[t], pd[t], pj[t], fo);
       }
@@ -732,7 +740,8 @@ __global__ void __launch_bounds__(CellCfg<T>::warps * 32, 5)
       __syncwarp();
     }
     if (take && slots > 0)
-      write_cell(cell, pw, (mt & kMetaEmpty) != 0, sc[lane].neg == 0, sc[lane].a, sc[lane].emitted, o);
+      write_cell(cell, pw, (mt & kMetaEmpty) != 0, sc[lane].neg == 0, sc[lane].a, sc[lane].emitted,
+                 sqrt(oxw * oxw + oyw * oyw + ozw * ozw), o);
     __syncwarp();
     base += ncell;
   }
@@ -752,27 +761,53 @@ __global__ void k_gmax(int64_t ncell, const int32_t* __restrict__ cell_start,
   gmax[c] = m;
 }
 
-// first security radius: 1.25 x the cell's extent in the previous evaluation
-// (Newton changes cells little) or at the last accepted Newton iterate,
+// First security ball of an evaluation.  Centre: kept from the previous
+// evaluation in the same grid order (the Newton solve keeps it fixed), else
+// the hint of the previous solve on these sites (centroid - site, caller
+// order), else the site.  Radius: 1.25 x the cell's extent from that centre
+// in the previous evaluation or at the last accepted Newton iterate,
 // whichever is smaller (a rejected line-search trial can have far larger
-// cells), else 1.5 nu^(1/3); never beyond the ball
+// cells), else 1.25 x the hinted extent, else 1.5 nu^(1/3); capped at
+// r + |o|, where the ball contains the site's ball.
 template <typename T>
 __global__ void k_srad_init(int64_t n, const V4<T>* __restrict__ sxp, const double* __restrict__ snu,
                             const T* __restrict__ rcell, int have_prev,
-                            const T* __restrict__ rcell_acc, int have_acc, T* srad, T* srad_lo,
-                            uint8_t* need) {
+                            const T* __restrict__ rcell_acc, int have_acc,
+                            const int32_t* __restrict__ perm, const T* __restrict__ hint,
+                            int use_hint, T* srad, T* srad_lo, T* soff, uint8_t* need) {
   int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   const T ps = sxp[s].w;
   const T r = ps > T(0) ? sqrt(ps) : T(0);
+  T ox = T(0), oy = T(0), oz = T(0);
+  T prev = T(0);
+  if (have_prev) {
+    ox = soff[3 * s + 0];
+    oy = soff[3 * s + 1];
+    oz = soff[3 * s + 2];
+    prev = rcell[s];
+    if (have_acc && rcell_acc[s] > T(0)) prev = prev > T(0) ? fmin(prev, rcell_acc[s]) : rcell_acc[s];
+  } else if (use_hint) {
+    const int64_t i = perm[s];
+    ox = hint[4 * i + 0];
+    oy = hint[4 * i + 1];
+    oz = hint[4 * i + 2];
+    prev = hint[4 * i + 3];
+    // a centre outside the site's ball is stale
+    if (!(ox * ox + oy * oy + oz * oz < ps)) {
+      ox = oy = oz = T(0);
+      prev = T(0);
+    }
+  }
+  soff[3 * s + 0] = ox;
+  soff[3 * s + 1] = oy;
+  soff[3 * s + 2] = oz;
   T R = r;
-  T prev = have_prev ? rcell[s] : T(0);
-  if (have_acc && rcell_acc[s] > T(0)) prev = prev > T(0) ? fmin(prev, rcell_acc[s]) : rcell_acc[s];
   if (prev > T(0))
     R = T(1.25) * prev;
   else if (snu[s] > 0.0)
     R = T(1.5) * (T)cbrt(snu[s]);
-  srad[s] = fmin(R, r);
+  srad[s] = fmin(R, r + sqrt(ox * ox + oy * oy + oz * oz));
   srad_lo[s] = T(0);
   need[s] = 1;
 }
@@ -785,8 +820,8 @@ __global__ void k_srad_init(int64_t n, const V4<T>* __restrict__ sxp, const doub
 // builds a cell inside that ball.
 template <typename T>
 __global__ void k_need_update(int64_t n, const V4<T>* __restrict__ sxp, const T* __restrict__ rcell,
-                              const int32_t* __restrict__ meta, T* srad, T* srad_lo, uint8_t* need,
-                              int32_t* count) {
+                              const int32_t* __restrict__ meta, const T* __restrict__ soff, T* srad,
+                              T* srad_lo, uint8_t* need, int32_t* count) {
   int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n || !need[s]) return;
   if (meta[s] & kMetaRetry) {  // radius already reduced by the candidate pass
@@ -794,15 +829,16 @@ __global__ void k_need_update(int64_t n, const V4<T>* __restrict__ sxp, const T*
     return;
   }
   const T ps = sxp[s].w;
-  const T r = ps > T(0) ? sqrt(ps) : T(0);
+  const T ox = soff[3 * s + 0], oy = soff[3 * s + 1], oz = soff[3 * s + 2];
+  const T rmax = (ps > T(0) ? sqrt(ps) : T(0)) + sqrt(ox * ox + oy * oy + oz * oz);
   const T R = srad[s];
   const T rc = rcell[s];
-  const bool done = !(ps > T(0)) || R >= r || rc < R * T(1.0 - 1e-5);
+  const bool done = !(ps > T(0)) || R >= rmax || rc < R * T(1.0 - 1e-5);
   if (done) {
     need[s] = 0;
   } else {
     srad_lo[s] = R;
-    srad[s] = fmin(r, fmin(T(2) * R, fmax(T(1.25) * R, T(1.05) * rc)));
+    srad[s] = fmin(rmax, fmin(T(2) * R, fmax(T(1.25) * R, T(1.05) * rc)));
     atomicAdd(count, 1);
   }
 }
@@ -1039,10 +1075,9 @@ int cells_eval(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* dom, 
   note_launch();
   k_gmax<T><<<blocks_for(ncell, 256), 256, 0, st>>>(ncell, ctx->cell_start, w.sxp, w.gmax);
   note_launch();
-  k_srad_init<T><<<blocks_for(n, 256), 256, 0, st>>>(n, w.sxp, ctx->snu, w.rcell,
-                                                      w.have_rcell ? 1 : 0, w.rcell_acc,
-                                                      w.have_acc ? 1 : 0, w.srad, w.srad_lo,
-                                                      ctx->need);
+  k_srad_init<T><<<blocks_for(n, 256), 256, 0, st>>>(
+      n, w.sxp, ctx->snu, w.rcell, w.have_rcell ? 1 : 0, w.rcell_acc, w.have_acc ? 1 : 0, ctx->perm,
+      w.hint, (w.use_hint && w.hint && w.hint_n == n) ? 1 : 0, w.srad, w.srad_lo, w.soff, ctx->need);
   CellOut o;
   o.rcell = w.rcell;
   o.need = ctx->need;
@@ -1063,19 +1098,21 @@ int cells_eval(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* dom, 
     note_launch();
     k_candidates<T><<<blocks_for(n, 256), 256, 0, st>>>(n, w.sxp, ctx->cell_start, w.grid, box,
                                                          w.psi_max, w.gmax, w.srad, w.srad_lo,
-                                                         ctx->need,
+                                                         w.soff, ctx->need,
                                                          ctx->k_max, ctx->cand, ctx->meta, ctx->err);
     note_launch();
     // the no-alloc entry point's context has no events: no timing there
     const bool timed = ctx->ev[6] && ctx->ev[7];
     if (timed) POT_CUDA(cudaEventRecord(ctx->ev[6], st));
-    k_cells<T><<<blocks, CellCfg<T>::warps * 32, 0, st>>>(n, w.sxp, ctx->meta, ctx->cand, ctx->k_max, box,
-                                                   w.stage_vals, o, ctx->err);
+    k_cells<T><<<blocks, CellCfg<T>::warps * 32, 0, st>>>(n, w.sxp, ctx->meta, ctx->cand,
+                                                           ctx->k_max, box, w.stage_vals, w.soff,
+                                                           o, ctx->err);
     if (timed) POT_CUDA(cudaEventRecord(ctx->ev[7], st));
     POT_CUDA(cudaMemsetAsync(ctx->need_count, 0, sizeof(int32_t), st));
     note_launch();
-    k_need_update<T><<<blocks_for(n, 256), 256, 0, st>>>(n, w.sxp, w.rcell, ctx->meta, w.srad,
-                                                          w.srad_lo, ctx->need, ctx->need_count);
+    k_need_update<T><<<blocks_for(n, 256), 256, 0, st>>>(n, w.sxp, w.rcell, ctx->meta, w.soff,
+                                                          w.srad, w.srad_lo, ctx->need,
+                                                          ctx->need_count);
     POT_CUDA(cudaMemcpyAsync(hcount, ctx->need_count, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     POT_CUDA(cudaStreamSynchronize(st));
     float ms = 0.f;
@@ -1196,6 +1233,37 @@ int psi_update(pot_ctx* ctx, cudaStream_t st, int64_t n, double alpha) {
   return POT_OK;
 }
 
+// hint for the next solve on these sites: centroid - site, and the cell's
+// extent from the centroid (<= extent from the security centre + the
+// distance between the two centres), in caller order
+template <typename T>
+__global__ void k_store_hint(int64_t n, const int32_t* __restrict__ perm, const V4<T>* __restrict__ sxp,
+                             const T* __restrict__ cen, const T* __restrict__ soff,
+                             const T* __restrict__ rcell, T* hint) {
+  int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const V4<T> p = sxp[s];
+  const T cx = cen[3 * s + 0] - p.x, cy = cen[3 * s + 1] - p.y, cz = cen[3 * s + 2] - p.z;
+  const T dx = cx - soff[3 * s + 0], dy = cy - soff[3 * s + 1], dz = cz - soff[3 * s + 2];
+  const int64_t i = perm[s];
+  hint[4 * i + 0] = cx;
+  hint[4 * i + 1] = cy;
+  hint[4 * i + 2] = cz;
+  hint[4 * i + 3] = rcell[s] > T(0) ? rcell[s] + sqrt(dx * dx + dy * dy + dz * dz) : T(0);
+}
+
+template <typename T>
+int store_hint(pot_ctx* ctx, cudaStream_t st, int64_t n) {
+  Work<T>& w = ctx->work<T>();
+  if (!w.hint || !w.have_rcell) return POT_OK;
+  note_launch();
+  k_store_hint<T><<<blocks_for(n, 256), 256, 0, st>>>(n, ctx->perm, w.sxp, w.cen, w.soff, w.rcell,
+                                                       w.hint);
+  POT_CUDA(cudaGetLastError());
+  w.hint_n = n;
+  return POT_OK;
+}
+
 #define POT_INST(T)                                                                              \
   template int cells_eval<T>(pot_ctx*, cudaStream_t, int64_t, const pot_domain*, bool);          \
   template int residuals<T>(pot_ctx*, cudaStream_t, int64_t, double*);                          \
@@ -1204,7 +1272,8 @@ int psi_update(pot_ctx* ctx, cudaStream_t st, int64_t n, double alpha) {
   template int csr_user<T>(pot_ctx*, cudaStream_t, int64_t, int32_t*, int32_t*, T*, int64_t,    \
                            int64_t*);                                                           \
   template int unsort_outputs<T>(pot_ctx*, cudaStream_t, int64_t, T*, double*, T*, T*, T*);     \
-  template int psi_update<T>(pot_ctx*, cudaStream_t, int64_t, double);
+  template int psi_update<T>(pot_ctx*, cudaStream_t, int64_t, double);                          \
+  template int store_hint<T>(pot_ctx*, cudaStream_t, int64_t);
 POT_INST(float)
 POT_INST(double)
 

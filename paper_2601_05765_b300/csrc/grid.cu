@@ -172,6 +172,7 @@ int grid_build(pot_ctx* ctx, cudaStream_t st, int64_t n, const T* pos, const T* 
   w.grid_valid = true;
   w.have_rcell = false;
   w.have_acc = false;
+  w.use_hint = false;
   return POT_OK;
 }
 

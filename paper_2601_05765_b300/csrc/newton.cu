@@ -146,6 +146,7 @@ int eval_and_reduce(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* 
   S->passes += ctx->last_passes;
   int64_t site;
   const int code = read_status(ctx, st, &site);  // also clears the device status
+  if (code != POT_OK) S->error_site = site;
   return code != POT_OK ? code : ce;
 }
 
@@ -257,11 +258,13 @@ int newton_solve(pot_ctx* ctx, cudaStream_t st, int64_t n, const T* pos, const d
   double t0 = now_ms();
   POT_CHECK(grid_build<T>(ctx, st, n, pos, psi_inout, targets, dom));
   S->grid_builds++;
-  int status = newton_sorted<T>(ctx, st, n, dom, P, S);
   Work<T>& w = ctx->work<T>();
+  w.use_hint = true;  // security balls start from the last solve's cells
+  int status = newton_sorted<T>(ctx, st, n, dom, P, S);
   if (status == POT_OK || status == POT_ERR_NOT_CONVERGED || status == POT_ERR_LINESEARCH_FAILED) {
     note_launch();
     k_unsort_psi<T><<<blocks_for(n, 256), 256, 0, st>>>(n, ctx->perm, w.psi_base, psi_inout);
+    POT_CHECK(store_hint<T>(ctx, st, n));
   }
   POT_CUDA(cudaStreamSynchronize(st));
   S->status = status;
@@ -283,6 +286,7 @@ int fluid_step(pot_ctx* ctx, cudaStream_t st, int64_t n, T* pos, T* vel, T* psi,
   k_advect<T><<<blocks_for(n, 256), 256, 0, st>>>(n, pos, vel, (T)P->dt, box, (T)P->wall_margin);
   POT_CHECK(grid_build<T>(ctx, st, n, pos, psi, targets, dom));
   S->grid_builds++;
+  ctx->work<T>().use_hint = true;  // security balls start from the last step's cells
   const T* fallback = nullptr;
   if (sizeof(T) == 4 && P->warm_start && ctx->mlp) {
     float* prev = nullptr;
@@ -309,6 +313,7 @@ int fluid_step(pot_ctx* ctx, cudaStream_t st, int64_t n, T* pos, T* vel, T* psi,
     k_velocity<T><<<blocks_for(n, 256), 256, 0, st>>>(
         n, ctx->perm, w.sxp, w.cen, w.psi_base, vel, psi, (T)P->dt, (T)(1.0 / (P->eps * P->eps)),
         (T)P->gravity[0], (T)P->gravity[1], (T)P->gravity[2]);
+    POT_CHECK(store_hint<T>(ctx, st, n));
   }
   POT_CUDA(cudaStreamSynchronize(st));
   S->status = status;

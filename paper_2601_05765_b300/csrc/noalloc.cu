@@ -58,7 +58,8 @@ constexpr size_t oPsiMax = oStage + al(4 * N * kNoAllocK);
 constexpr size_t oNuMax = oPsiMax + al(8);
 constexpr size_t oSrad = oNuMax + al(8);
 constexpr size_t oSradLo = oSrad + al(4 * N);
-constexpr size_t oRcell = oSradLo + al(4 * N);
+constexpr size_t oSoff = oSradLo + al(4 * N);
+constexpr size_t oRcell = oSoff + al(12 * N);
 constexpr size_t oGmax = oRcell + al(4 * N);
 constexpr size_t oNeed = oGmax + al(4 * (kNoAllocGridCap + 1));
 constexpr size_t oNeedCount = oNeed + al(N);
@@ -145,6 +146,7 @@ extern "C" int lgc_compute_cells_noalloc(void* stream, int64_t n, const float* p
   w.nu_max = (float*)(b + oNuMax);
   w.srad = (float*)(b + oSrad);
   w.srad_lo = (float*)(b + oSradLo);
+  w.soff = (float*)(b + oSoff);
   w.rcell = (float*)(b + oRcell);
   w.gmax = (float*)(b + oGmax);
   c.need = (uint8_t*)(b + oNeed);

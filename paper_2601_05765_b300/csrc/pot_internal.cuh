@@ -144,13 +144,17 @@ struct Work {
   T* nu_max = nullptr;      // device scalar: max target volume (grid build)
   T* srad = nullptr;        // per cell: security radius of the current pass
   T* srad_lo = nullptr;     // per cell: largest radius found too small in this evaluation
+  T* soff = nullptr;        // per cell: security ball centre - site (3 per cell)
   T* rcell_acc = nullptr;   // per cell: rcell at the last accepted Newton iterate
-  T* rcell = nullptr;       // per cell: farthest point of the cell from its site
+  T* rcell = nullptr;       // per cell: farthest point of the cell from its security centre
+  T* hint = nullptr;        // caller order: centroid - site and extent from it (4 per site)
   T* gmax = nullptr;        // per grid cell: largest psi of its sites
   GridParams<T> grid{};
   bool grid_valid = false;
   bool have_rcell = false;  // rcell belongs to the current grid order
   bool have_acc = false;    // rcell_acc belongs to the current grid order
+  int64_t hint_n = -1;      // sites the hint was written for (-1: none)
+  bool use_hint = false;    // this grid order's first evaluation starts from the hint
 };
 
 }  // namespace pot
@@ -238,6 +242,10 @@ int grid_build(pot_ctx* ctx, cudaStream_t st, int64_t n, const T* pos, const T* 
 // Cell evaluation in sorted space (cells.cu): candidates + geometry.
 template <typename T>
 int cells_eval(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* dom, bool want_grad);
+// keep the last evaluation's cell centres and extents (caller order) as the
+// security-ball hint of the next Newton solve on the same sites
+template <typename T>
+int store_hint(pot_ctx* ctx, cudaStream_t st, int64_t n);
 
 // FP64 reductions over sorted cells:
 // out = {max |V-nu|/nu, sum (nu-V)^2, min V, #empty, #planes, max planes}.  Host sync.

@@ -66,7 +66,7 @@ class SolveStats(ctypes.Structure):
                 ("ms_cells", ctypes.c_double), ("ms_pcg", ctypes.c_double),
                 ("nnz", ctypes.c_int64), ("mlp_used", ctypes.c_int32),
                 ("mlp_fallback", ctypes.c_int32), ("repairs", ctypes.c_int32),
-                ("passes", ctypes.c_int32)]
+                ("passes", ctypes.c_int32), ("error_site", ctypes.c_int64)]
 
 
 def _as_dict(st):
