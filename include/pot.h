@@ -170,6 +170,16 @@ int64_t pot_kernel_launches(void);
  * Errors: POT_ERR_INVALID_ARG for a NULL context. */
 int pot_cell_kernel_time(pot_ctx* ctx, int reset, int64_t* launches, int64_t* cells, double* ms);
 
+/* State of the last FP32 cell evaluation in this context, per site in the
+ * caller order of that evaluation (n sites, device arrays, any may be
+ * NULL): the security ball (centre offset from the site, 3 values per site,
+ * and radius; Sec. 4's contributing-neighbour problem), the cell's extent
+ * from that centre, and the number of planes (walls + candidate bisectors)
+ * the cell was built from (0 for an empty cell or one that overflowed).
+ * Errors: POT_ERR_INVALID_ARG when n does not match that evaluation. */
+int pot_cell_diagnostics(pot_ctx* ctx, void* stream, int64_t n, float* center_offset,
+                         float* radius, float* extent, int32_t* planes);
+
 /* ---- generalized Laguerre cells (Eq. 1, Sec. 3.2-3.4, Algorithm 2) ------ */
 
 /* Build every generalized Laguerre cell
@@ -229,7 +239,7 @@ int lgc_compute_cells_noalloc(void* stream, int64_t n, const float* pos, const f
 /* Find the weights psi with |C_i(psi)| = targets[i] for all i (partial OT,
  * Sec. 2.2) by damped Newton (Algorithm 1).  A start with empty cells is
  * repaired first: each empty cell's weight is raised to
- * max_j (psi_j - d_ij^2) + 0.1 d*^2, which puts its site inside its own cell
+ * max_j (psi_j - d_ij^2) + 0.25 d*^2, which puts its site inside its own cell
  * (stats->repairs counts them).  Then M u = nu - V(psi) is solved by
  * Jacobi-preconditioned CG (Sec. 7), then the KMT step: alpha = 1, 1/2, ...
  * until min V(psi + alpha u) >= eps0 and

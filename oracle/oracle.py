@@ -166,7 +166,7 @@ NEWTON_EMPTY_CELL_AT_START = 3
 
 def repair_empty(pos, psi, vol, nu):
     """Raise the weight of every empty cell i to
-    max(max_j (psi_j - d_ij^2) + 0.1 d*^2, (nu_i^(1/3) / 2)^2), d* the distance
+    max(max_j (psi_j - d_ij^2) + 0.25 d*^2, (nu_i^(1/3) / 2)^2), d* the distance
     to the maximising site: then every bisector of i has h_ij > 0, so p_i is
     inside its own (non-empty) cell, and each neighbour j keeps h_ji > 0
     (reading: Algorithm 1 needs a start without empty cells; the paper does
@@ -181,7 +181,7 @@ def repair_empty(pos, psi, vol, nu):
         j = int(np.argmax(v))
         cand = psi[i]
         if d2[j] > 0 and np.isfinite(v[j]):
-            cand = max(cand, v[j] + 0.1 * d2[j])
+            cand = max(cand, v[j] + 0.25 * d2[j])
         new[i] = max(cand, 0.25 * np.cbrt(nu[i]) ** 2)
     return new
 
@@ -203,7 +203,7 @@ def newton(pos, nu, psi0, tol=1e-4, max_newton=100, max_halvings=30,
     psi = np.asarray(psi0, np.float64).copy()
     res = cells(pos, psi, lo=lo, hi=hi, nthreads=nthreads)
     vol = res["vol"]
-    for _ in range(8 if repair else 0):
+    for _ in range(32 if repair else 0):
         if vol.min() > 0.0:
             break
         psi = repair_empty(pos, psi, vol, nu)

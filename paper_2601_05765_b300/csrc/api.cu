@@ -146,6 +146,13 @@ extern "C" {
 
 int64_t pot_kernel_launches(void) { return g_launches.load(); }
 
+int pot_cell_diagnostics(pot_ctx* ctx, void* stream, int64_t n, float* center_offset, float* radius,
+                         float* extent, int32_t* planes) {
+  if (!ctx) return POT_ERR_INVALID_ARG;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return POT_ERR_CUDA;
+  return cell_diagnostics(ctx, (cudaStream_t)stream, n, center_offset, radius, extent, planes);
+}
+
 int pot_cell_kernel_time(pot_ctx* ctx, int reset, int64_t* launches, int64_t* cells, double* ms) {
   if (!ctx) return POT_ERR_INVALID_ARG;
   if (launches) *launches = ctx->kc_launches;

@@ -246,7 +246,7 @@ __device__ __forceinline__ void isect(T a1, T b1, T c1, T a2, T b2, T c2, T& x, 
 // rm2 is measured from the security-ball centre p + o (oa = |o|).
 template <typename T>
 __device__ Facet<T> facet_eval(const V4<T>* __restrict__ pl, int m, int fi, T ps, T r, T ox, T oy,
-                               T oz, T oa) {
+                               T oz, T oa, bool want_extent) {
   Facet<T> out = {T(0), T(0), T(0), T(0), T(0), T(0), 0, 0};
   const V4<T> P = pl[fi];
   const T h = P.w;
@@ -348,6 +348,14 @@ __device__ Facet<T> facet_eval(const V4<T>* __restrict__ pl, int m, int fi, T ps
   const T rho3 = rho2 * rho / T(3);
   const T sect_om = sg - h / r;
   T area = T(0), omg = T(0), mx = T(0), my = T(0);
+  // the security-ball centre in the facet's frame (disk centre at h n);
+  // rm2 collects squared distances of the facet's extreme points from it
+  const T ou = ux * ox + uy * oy + uz * oz, ov = vx * ox + vy * oy + vz * oz;
+  const T on = h - (P.x * ox + P.y * oy + P.z * oz);
+  const T on2 = on * on;
+  const T ol = sqrt(ou * ou + ov * ov);
+  const T far2 = (rho + ol) * (rho + ol) + on2;  // the circle's farthest point
+  T rm2 = T(0);
   auto sector = [&](T ax, T ay, T bx, T by) {
     T cr = ax * by - ay * bx;
     T dt = ax * bx + ay * by;
@@ -358,6 +366,21 @@ __device__ Facet<T> facet_eval(const V4<T>* __restrict__ pl, int m, int fi, T ps
     if (na > T(0) && nb > T(0)) {
       mx += rho3 * (by / nb - ay / na);
       my += rho3 * (ax / na - bx / nb);
+      if (!want_extent) return;
+      // the arc from direction a to direction b: its end points, and the
+      // circle's farthest point from the centre when it lies on the arc
+      const T ex = rho * ax / na - ou, ey = rho * ay / na - ov;
+      const T fx = rho * bx / nb - ou, fy = rho * by / nb - ov;
+      rm2 = fmax(rm2, fmax(ex * ex + ey * ey, fx * fx + fy * fy) + on2);
+      if (ol > T(0)) {
+        const T gx = -ou, gy = -ov;  // direction of the farthest point
+        const T c1 = ax * gy - ay * gx, c2 = gx * by - gy * bx;
+        const bool half = dt < T(0) && fabs(cr) <= T(1e-6) * na * nb;
+        if (half || (cr >= T(0) ? (c1 >= T(0) && c2 >= T(0)) : (c1 <= T(0) && c2 <= T(0))))
+          rm2 = fmax(rm2, far2);
+      }
+    } else if (want_extent) {
+      rm2 = fmax(rm2, far2);
     }
   };
   auto tri = [&](T ax, T ay, T bx, T by) {
@@ -371,17 +394,12 @@ __device__ Facet<T> facet_eval(const V4<T>* __restrict__ pl, int m, int fi, T ps
     mx += ta * (ax + bx) * T(1.0 / 3.0);
     my += ta * (ay + by) * T(1.0 / 3.0);
   };
-  // the security-ball centre in the facet's frame (disk centre at h n)
-  const T ou = ux * ox + uy * oy + uz * oz, ov = vx * ox + vy * oy + vz * oz;
-  const T on = h - (P.x * ox + P.y * oy + P.z * oz);
-  const T on2 = on * on;
-  T rm2 = T(0);
   bool arc = false;
   for (int k = 0; k < nl; k++) {
     int k2 = k + 1 == nl ? 0 : k + 1;
     T pxk = px[cur][k], pyk = py[cur][k], qx = px[cur][k2], qy = py[cur][k2];
     const T pk2 = pxk * pxk + pyk * pyk;
-    if (pk2 <= rho2) {  // a polygon vertex inside the disk
+    if (want_extent && pk2 <= rho2) {  // a polygon vertex inside the disk
       const T ex = pxk - ou, ey = pyk - ov;
       rm2 = fmax(rm2, ex * ex + ey * ey + on2);
     }
@@ -415,8 +433,7 @@ __device__ Facet<T> facet_eval(const V4<T>* __restrict__ pl, int m, int fi, T ps
       arc = true;
     }
   }
-  // a facet with an arc reaches the sphere: bound its points by r + |o|
-  out.rm2 = arc ? (r + oa) * (r + oa) : rm2;
+  out.rm2 = rm2;
   out.arc = arc && area > T(0);
   out.area = area;
   out.omega = omg;
@@ -538,7 +555,8 @@ struct CellOut {
 
 template <typename T>
 __device__ __forceinline__ void write_cell(int64_t cell, const V4<T>& p, bool empty, bool inside,
-                                           const CellAcc<T>& a, int cnt, T oa, const CellOut& o) {
+                                           bool qout, bool full, const CellAcc<T>& a, int cnt, T oa,
+                                           const CellOut& o) {
   const T ps = p.w;
   T V = T(0), K = T(0), dg = T(0);
   T cx = p.x, cy = p.y, cz = p.z;
@@ -564,12 +582,22 @@ __device__ __forceinline__ void write_cell(int64_t cell, const V4<T>& p, bool em
       cz += (a.hz - ps * a.nz) * iv;
     }
   }
-  // farthest point of the cell from its security-ball centre, decided
-  // geometrically (|K| carries rounding noise of a few ulp of 4 pi psi):
-  // r + |o| if a facet leaves its disk or if there is no facet at all (a
-  // full ball), else the farthest facet vertex
+  // farthest point of the cell from its security-ball centre c = p + o,
+  // decided geometrically (|K| carries rounding noise of a few ulp of
+  // 4 pi psi): over the facet vertices and, where facets leave their disks,
+  // their circles; the spherical part's farthest point from c is on those
+  // circles or is q = p - r o/|o| (distance r + |o|) when no plane cuts q
+  // off; a cell without facets is the full ball (r + |o| too)
   T rc = T(0);
-  if (!empty && ps > T(0)) rc = a.rm2 > T(0) ? sqrt(a.rm2) : (V > T(0) ? sqrt(ps) + oa : T(0));
+  if (!empty && ps > T(0)) {
+    const T rq = sqrt(ps) + oa;
+    if (full || a.nfac == 0)  // the whole ball (any cell inside it is within rq)
+      rc = V > T(0) ? rq : T(0);
+    else if (a.arc > 0 && !qout && oa > T(0))
+      rc = fmax(sqrt(a.rm2), rq);
+    else
+      rc = sqrt(a.rm2);
+  }
   ((T*)o.rcell)[cell] = rc;
   ((T*)o.vol)[cell] = V;
   ((T*)o.karea)[cell] = K;
@@ -595,6 +623,7 @@ template <typename T>
 struct CellSlot {
   CellAcc<T> a;
   int neg;      // some plane has h < 0 (the site is outside the polytope)
+  int qout;     // some plane excludes the sphere point farthest from the security centre
   int emitted;  // Hessian entries written so far
 };
 
@@ -611,7 +640,7 @@ template <typename T>
 __global__ void __launch_bounds__(CellCfg<T>::warps * 32, 5)
     k_cells(int64_t n, const V4<T>* __restrict__ sxp, const int32_t* __restrict__ meta,
             int32_t* cand, int kmax, Box<T> box, T* stage_vals, const T* __restrict__ soff,
-            CellOut o, int32_t* err) {
+            const T* __restrict__ srad, CellOut o, int32_t* err) {
   constexpr int W = CellCfg<T>::warps;
   __shared__ V4<T> s_pl[W][kPlaneCap];
   __shared__ T s_d[W][kPlaneCap];
@@ -648,14 +677,17 @@ __global__ void __launch_bounds__(CellCfg<T>::warps * 32, 5)
     const unsigned owners = __ballot_sync(kFull, take && slots > 0);
     V4<T> pw = {};
     T rw = T(0), oxw = T(0), oyw = T(0), ozw = T(0);
+    bool fullw = false;  // the security ball contains the site's ball: exact without an extent
     if (take && slots > 0) {
       pw = sxp[cell];
       rw = pw.w > T(0) ? sqrt(pw.w) : T(0);
       oxw = soff[3 * cell + 0];
       oyw = soff[3 * cell + 1];
       ozw = soff[3 * cell + 2];
+      fullw = srad[cell] >= rw + sqrt(oxw * oxw + oyw * oyw + ozw * ozw);
       sc[lane].a = CellAcc<T>{};
       sc[lane].neg = 0;
+      sc[lane].qout = 0;
       sc[lane].emitted = 0;
     }
     // build the window's planes, one slot per lane
@@ -693,6 +725,7 @@ __global__ void __launch_bounds__(CellCfg<T>::warps * 32, 5)
       const T orr = __shfl_sync(kFull, rw, ow);
       const T sox = __shfl_sync(kFull, oxw, ow), soy = __shfl_sync(kFull, oyw, ow),
               soz = __shfl_sync(kFull, ozw, ow);
+      const bool ofull = __shfl_sync(kFull, fullw, ow);
       const int cm = omt & kMetaPlanes;
       const int f = t - oex;
       const bool has = inr && f < cm;
@@ -700,7 +733,7 @@ __global__ void __launch_bounds__(CellCfg<T>::warps * 32, 5)
       Facet<T> fo = {};
       if (has) {
         fo = facet_eval(pl + oex, cm, f, op.w, orr, sox, soy, soz,
-                        sqrt(sox * sox + soy * soy + soz * soz));
+                        sqrt(sox * sox + soy * soy + soz * soz), !ofull);
         if (fo.overflow) set_error(err, POT_ERR_POLYGON_OVERFLOW, base + ow);
         acc_facet(a, pl[t], pd[t], pj[t], fo);
       }
@@ -710,6 +743,12 @@ __global__ void __launch_bounds__(CellCfg<T>::warps * 32, 5)
       seg_reduce(a, lane, hi);
       const unsigned segmask = inr ? ((0xffffffffu >> (31 - hi)) & ~((1u << lo) - 1u)) : 0u;
       const unsigned negm = __ballot_sync(kFull, has && pl[t].w < T(0));
+      // the sphere point farthest from the security centre, q = p - r o/|o|,
+      // is cut off by this plane (clearly: n . (q - p) > h + 1e-6 r)
+      const T soa = sqrt(sox * sox + soy * soy + soz * soz);
+      const unsigned qm = __ballot_sync(
+          kFull, has && soa > T(0) &&
+                     -orr * (pl[t].x * sox + pl[t].y * soy + pl[t].z * soz) > (pl[t].w + T(1e-6) * orr) * soa);
       const bool emit = has && pj[t] >= 0 && fo.area > Real<T>::kEmitArea * op.w;
       const unsigned emm = __ballot_sync(kFull, emit);
       const int done = inr ? sc[ow].emitted : 0;
@@ -735,13 +774,14 @@ __global__ void __launch_bounds__(CellCfg<T>::warps * 32, 5)
         s.nfac += a.nfac;
         s.arc += a.arc;
         sc[ow].neg |= (negm & segmask) != 0u;
+        sc[ow].qout |= (qm & segmask) != 0u;
         sc[ow].emitted = done + __popc(emm & segmask);
       }
       __syncwarp();
     }
     if (take && slots > 0)
-      write_cell(cell, pw, (mt & kMetaEmpty) != 0, sc[lane].neg == 0, sc[lane].a, sc[lane].emitted,
-                 sqrt(oxw * oxw + oyw * oyw + ozw * ozw), o);
+      write_cell(cell, pw, (mt & kMetaEmpty) != 0, sc[lane].neg == 0, sc[lane].qout != 0 && !fullw,
+                 fullw, sc[lane].a, sc[lane].emitted, sqrt(oxw * oxw + oyw * oyw + ozw * ozw), o);
     __syncwarp();
     base += ncell;
   }
@@ -844,10 +884,10 @@ __global__ void k_need_update(int64_t n, const V4<T>* __restrict__ sxp, const T*
 }
 
 // A start with empty cells cannot enter Algorithm 1 (its KMT bound needs
-// min V > 0).  For an empty cell i, psi_i <- max_j (psi_j - d_ij^2) + 0.1 d*^2
+// min V > 0).  For an empty cell i, psi_i <- max_j (psi_j - d_ij^2) + 0.25 d*^2
 // (d* the distance to the maximising site): then h_ij > 0 for every j, so p_i
 // lies strictly inside its own cell, which is no longer empty, while each
-// neighbour keeps h_ji = (2 d^2 - 0.1 d*^2)/(2d) > 0 with respect to i.  Sites
+// neighbour keeps h_ji = (2 d^2 - 0.25 d*^2)/(2d) > 0 with respect to i.  Sites
 // with psi_j - d^2 > psi_i lie within sqrt(psi_max - psi_i); grid cells are
 // skipped when gmax - delta^2 <= psi_i.
 template <typename T>
@@ -893,7 +933,7 @@ __global__ void __launch_bounds__(256)
         }
   }
   T nv = ps;
-  if (best > T(-1e29) && bd2 > T(0)) nv = fmax(nv, best + T(0.1) * bd2);
+  if (best > T(-1e29) && bd2 > T(0)) nv = fmax(nv, best + T(0.25) * bd2);
   // a non-positive weight is an empty ball: give it half the radius of its target
   const T floor = snu[s] > 0.0 ? T(0.25) * (T)cbrt(snu[s] * snu[s]) : T(0);
   nv = fmax(nv, floor);
@@ -1106,7 +1146,7 @@ int cells_eval(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* dom, 
     if (timed) POT_CUDA(cudaEventRecord(ctx->ev[6], st));
     k_cells<T><<<blocks, CellCfg<T>::warps * 32, 0, st>>>(n, w.sxp, ctx->meta, ctx->cand,
                                                            ctx->k_max, box, w.stage_vals, w.soff,
-                                                           o, ctx->err);
+                                                           w.srad, o, ctx->err);
     if (timed) POT_CUDA(cudaEventRecord(ctx->ev[7], st));
     POT_CUDA(cudaMemsetAsync(ctx->need_count, 0, sizeof(int32_t), st));
     note_launch();
@@ -1261,6 +1301,35 @@ int store_hint(pot_ctx* ctx, cudaStream_t st, int64_t n) {
                                                        w.hint);
   POT_CUDA(cudaGetLastError());
   w.hint_n = n;
+  return POT_OK;
+}
+
+__global__ void k_diag(int64_t n, const int32_t* __restrict__ perm, const float* __restrict__ soff,
+                       const float* __restrict__ srad, const float* __restrict__ rcell,
+                       const int32_t* __restrict__ meta, float* off, float* rad, float* ext,
+                       int32_t* planes) {
+  int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const int64_t i = perm[s];
+  if (off) {
+    off[3 * i + 0] = soff[3 * s + 0];
+    off[3 * i + 1] = soff[3 * s + 1];
+    off[3 * i + 2] = soff[3 * s + 2];
+  }
+  if (rad) rad[i] = srad[s];
+  if (ext) ext[i] = rcell[s];
+  if (planes) planes[i] = (meta[s] & kMetaEmpty) ? 0 : (meta[s] & kMetaPlanes);
+}
+
+int cell_diagnostics(pot_ctx* ctx, cudaStream_t st, int64_t n, float* off, float* rad, float* ext,
+                     int32_t* planes) {
+  Work<float>& w = ctx->wf;
+  if (!w.sxp || !w.grid_valid || !w.have_rcell || n <= 0 || n > ctx->n_max) return POT_ERR_INVALID_ARG;
+  note_launch();
+  k_diag<<<blocks_for(n, 256), 256, 0, st>>>(n, ctx->perm, w.soff, w.srad, w.rcell, ctx->meta, off,
+                                              rad, ext, planes);
+  POT_CUDA(cudaGetLastError());
+  POT_CUDA(cudaStreamSynchronize(st));
   return POT_OK;
 }
 

@@ -180,7 +180,7 @@ int newton_sorted(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* do
   // empty cells at the start (sites pushed deep into a heavier neighbour's
   // cell by a fast step): raise their weights until every site is inside its
   // own cell, then start Algorithm 1 from the repaired weights
-  for (int rep = 0; rep < 8 && !(res[2] > 0.0); rep++) {
+  for (int rep = 0; rep < 32 && !(res[2] > 0.0); rep++) {
     int repaired = 0;
     POT_CHECK(repair_empty<T>(ctx, st, n, &repaired));
     if (repaired == 0) break;

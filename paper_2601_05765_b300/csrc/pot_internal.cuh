@@ -246,6 +246,8 @@ int cells_eval(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* dom, 
 // security-ball hint of the next Newton solve on the same sites
 template <typename T>
 int store_hint(pot_ctx* ctx, cudaStream_t st, int64_t n);
+int cell_diagnostics(pot_ctx* ctx, cudaStream_t st, int64_t n, float* off, float* rad, float* ext,
+                     int32_t* planes);
 
 // FP64 reductions over sorted cells:
 // out = {max |V-nu|/nu, sum (nu-V)^2, min V, #empty, #planes, max planes}.  Host sync.

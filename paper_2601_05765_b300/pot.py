@@ -120,6 +120,8 @@ def lib():
         L.pot_cell_kernel_time.argtypes = [P, ctypes.c_int, ctypes.POINTER(I64), ctypes.POINTER(I64),
                                            ctypes.POINTER(ctypes.c_double)]
         L.pot_cell_kernel_time.restype = ctypes.c_int
+        L.pot_cell_diagnostics.argtypes = [P, P, I64, P, P, P, P]
+        L.pot_cell_diagnostics.restype = ctypes.c_int
         for f in (L.pot_mlp_create, L.pot_mlp_destroy, L.pot_mlp_num_params, L.pot_mlp_set_params,
                   L.pot_mlp_get_params, L.pot_mlp_forward, L.pot_mlp_gradients, L.pot_mlp_train_step,
                   L.pot_mlp_check, L.pot_mlp_features, L.pot_mlp_set_history,
@@ -135,6 +137,22 @@ def lib():
 def kernel_launches() -> int:
     """Kernel launches issued by libpot.so so far in this process."""
     return int(lib().pot_kernel_launches())
+
+
+def cell_diagnostics(ctx: "Context", n: int, stream=None) -> dict:
+    """Security ball (centre offset, radius), cell extent from its centre and
+    plane count of every site after the last FP32 cell evaluation of `ctx`
+    (caller order of that evaluation)."""
+    dev = ctx.device
+    out = {"center_offset": torch.empty((n, 3), dtype=torch.float32, device=dev),
+           "radius": torch.empty(n, dtype=torch.float32, device=dev),
+           "extent": torch.empty(n, dtype=torch.float32, device=dev),
+           "planes": torch.empty(n, dtype=torch.int32, device=dev)}
+    code = lib().pot_cell_diagnostics(ctx.handle, _stream(stream), n, _ptr(out["center_offset"]),
+                                      _ptr(out["radius"]), _ptr(out["extent"]), _ptr(out["planes"]))
+    if code != POT_OK:
+        raise PotError(code, "pot_cell_diagnostics")
+    return out
 
 
 def cell_kernel_time(ctx: "Context", reset: bool = False) -> dict:

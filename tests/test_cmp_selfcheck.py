@@ -8,7 +8,7 @@ import torch
 
 from oracle import oracle as O
 from paper_2601_05765_b300 import scenes
-from tests._cmp import compare_cells
+from _cmp import compare_cells
 
 
 def as_gpu_output(ref, psi, nu):

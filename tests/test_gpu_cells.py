@@ -160,3 +160,22 @@ def test_deterministic(ctx):
     b = run(ctx, sc.pos, sc.psi, sc.nu)
     for key in ("volumes", "grad", "centroids", "karea", "row_ptr", "cols", "vals"):
         assert torch.equal(a[key], b[key]), key
+
+
+def test_cell_diagnostics_invariants(ctx):
+    """After an evaluation every cell lies inside its security ball (extent
+    below the radius, or the radius covers the site's ball), standalone
+    evaluations centre the ball on the site, and a cell is built from at
+    least as many planes as it has Hessian entries."""
+    sc = scenes.jittered_block(n_side=10, seed=2)
+    out = run(ctx, sc.pos, sc.psi, sc.nu)
+    dg = pot.cell_diagnostics(ctx, sc.n)
+    ext = to_np(dg["extent"]).astype(np.float64)
+    rad = to_np(dg["radius"]).astype(np.float64)
+    off = to_np(dg["center_offset"]).astype(np.float64)
+    planes = to_np(dg["planes"])
+    r = np.sqrt(sc.psi.astype(np.float64))
+    assert np.all(off == 0.0)
+    assert np.all((ext < rad * (1 - 1e-5)) | (rad >= r * (1 - 1e-6)))
+    rp = to_np(out["row_ptr"]).astype(np.int64)
+    assert np.all(planes >= np.diff(rp) - 1)
