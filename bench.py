@@ -48,10 +48,10 @@ SPLASH_DT = 5e-4
 SMALL_SPACING = 0.032  # ~2000 sites with the splash recipe
 # FP32 FLOP executed (fadd + fmul + 2 ffma) and DRAM bytes per cell processed
 # by k_cells, from an ncu capture of the 536k-site splash at converged weights
-# (the count inside fluid steps agreed to 0.3 %);
+# (an earlier kernel version's count inside fluid steps agreed to 0.3 %);
 # profiles/k_cells_splash_converged.md
-K_CELLS_FLOP_PER_CELL = 14549.0
-K_CELLS_DRAM_BYTES_PER_CELL = 312.0
+K_CELLS_FLOP_PER_CELL = 15462.0
+K_CELLS_DRAM_BYTES_PER_CELL = 413.0
 
 
 def parse():
