@@ -521,7 +521,7 @@ def run_dam(args):
     marks = sorted({k for k in (args.steps // 4, args.steps // 2, 3 * args.steps // 4, args.steps) if k > 0})
     out, snaps = {}, {}
     for prec, dt in (("mixed", torch.float32), ("fp64", torch.float64)):
-        ctx = pot.Context(n, 246, 0, fp32=dt == torch.float32, fp64=dt == torch.float64)
+        ctx = pot.Context(n, 1024, 0, fp32=dt == torch.float32, fp64=dt == torch.float64)
         pos = torch.as_tensor(sc.pos, dtype=dt, device=dev)
         vel = torch.as_tensor(sc.vel, dtype=dt, device=dev)
         psi = torch.as_tensor(sc.psi, dtype=dt, device=dev)

@@ -133,7 +133,7 @@ typedef struct {
 
 /* ---- context ---------------------------------------------------------- */
 
-/* Create a context on `device` for up to n_max sites and k_max (<= 246)
+/* Create a context on `device` for up to n_max sites and k_max (<= 1024)
  * candidate bisectors per cell, and allocate all its workspace.  A cell is
  * built from the bisectors whose plane cuts its ball and meets the cell's
  * security ball (a ball around the cell's previous centroid that the cell

@@ -33,7 +33,7 @@ int alloc(P** p, size_t count) {
 }
 
 template <typename T>
-int alloc_work(Work<T>& w, int64_t n, int64_t k, int64_t gcap) {
+int alloc_work(Work<T>& w, int64_t n, int64_t k, int64_t gcap, int sms) {
   POT_CHECK(alloc(&w.sxp, n));
   POT_CHECK(alloc(&w.psi_base, n));
   POT_CHECK(alloc(&w.vol, n));
@@ -59,6 +59,14 @@ int alloc_work(Work<T>& w, int64_t n, int64_t k, int64_t gcap) {
   POT_CHECK(alloc(&w.rcell_acc, n));
   POT_CHECK(alloc(&w.rcell, n));
   POT_CHECK(alloc(&w.gmax, gcap + 1));
+  // cells with more planes than the cell kernel's shared window exist only
+  // when the lists may hold that many
+  if (k + 6 > kPlaneCap) {
+    w.big_warps = sms * kBigWarpsPerSm;
+    POT_CHECK(alloc(&w.big_pl, (int64_t)w.big_warps * kBigPlanes));
+    POT_CHECK(alloc(&w.big_d, (int64_t)w.big_warps * kBigPlanes));
+    POT_CHECK(alloc(&w.big_j, (int64_t)w.big_warps * kBigPlanes));
+  }
   return POT_OK;
 }
 
@@ -66,7 +74,8 @@ template <typename T>
 void free_work(Work<T>& w) {
   void* ptrs[] = {w.sxp, w.psi_base, w.vol,  w.karea, w.diag, w.cen, w.stage_vals, w.csr_vals,
                   w.u,   w.x,        w.r,    w.z,     w.p0,   w.p1,  w.q,          w.vel_s,
-                  w.psi_max, w.nu_max, w.srad, w.srad_lo, w.soff, w.hint, w.rcell_acc, w.rcell, w.gmax};
+                  w.psi_max, w.nu_max, w.srad, w.srad_lo, w.soff, w.hint, w.rcell_acc, w.rcell, w.gmax,
+                  w.big_pl, w.big_d, w.big_j};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   w = Work<T>();
@@ -208,7 +217,7 @@ int pot_destroy(pot_ctx* ctx) {
   void* ptrs[] = {ctx->keys,     ctx->perm,    ctx->iperm,    ctx->cell_count, ctx->cell_start,
                   ctx->cand,     ctx->meta,    ctx->row_cnt,  ctx->row_ptr,    ctx->ucnt,
                   ctx->csr_cols, ctx->scan_tmp, ctx->snu,     ctx->grad,       ctx->red,
-                  ctx->red_out,  ctx->pcg_red, ctx->pcg_ctl,  ctx->err, ctx->need, ctx->need_count};
+                  ctx->red_out,  ctx->pcg_red, ctx->pcg_ctl,  ctx->err, ctx->need, ctx->need_count, ctx->big_list};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   free_work(ctx->wf);
@@ -264,9 +273,10 @@ int pot_create(pot_ctx** out, int device, int64_t n_max, int32_t k_max, int32_t 
   A(ctx->err, 2);
   A(ctx->need, n);
   A(ctx->need_count, 2);
+  A(ctx->big_list, n);
 #undef A
-  if (s == POT_OK && (ctx->mask & 1)) s = alloc_work(ctx->wf, n, k, ctx->grid_cap);
-  if (s == POT_OK && (ctx->mask & 2)) s = alloc_work(ctx->wd, n, k, ctx->grid_cap);
+  if (s == POT_OK && (ctx->mask & 1)) s = alloc_work(ctx->wf, n, k, ctx->grid_cap, ctx->sm_count);
+  if (s == POT_OK && (ctx->mask & 2)) s = alloc_work(ctx->wd, n, k, ctx->grid_cap, ctx->sm_count);
   if (s == POT_OK && cudaMallocHost((void**)&ctx->h_pinned, 64 * sizeof(double)) != cudaSuccess)
     s = POT_ERR_CUDA;
   for (auto& e : ctx->ev)

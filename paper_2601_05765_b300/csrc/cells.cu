@@ -75,12 +75,16 @@ __device__ __forceinline__ void set_error(int32_t* err, int code, int64_t site) 
 // that cuts it is then a candidate.
 //
 // The first R_i of an evaluation is a guess from the previous evaluation's
-// cells, and a growth step can overshoot, so a list that overflows k_max
-// does not yet mean the cell needs more than k_max planes.  Each cell keeps
-// a bracket: R_lo, the largest radius at which its cell was built and found
+// cells, and a growth step can overshoot (a cell built from too few planes
+// can look almost as wide as its ball), so a list that overflows k_max does
+// not yet mean the cell needs more than k_max planes.  Each cell keeps a
+// bracket: R_lo, the largest radius at which its cell was built and found
 // too small, and the current R_i.  An overflow at R_i retries at the
 // midpoint of (R_lo, R_i) (R_i / 2 while R_lo = 0); only when the bracket has
-// narrowed to 3 % of R_i is the overflow a real capacity error.
+// narrowed to 3 % of R_i is the overflow a real capacity error.  A list that
+// would not fit the cell kernel's shared window (kPlaneCap planes) is
+// bisected the same way, and the cell goes to the big-cell kernel only when
+// its bracket has collapsed.
 //
 // Grid cells are skipped with a lower bound of h over their sites: for
 // |p_i - p_j| >= delta and psi_j <= gmax,  h_ij >= delta/2 - (gmax - psi_i)/(2 delta)
@@ -91,7 +95,8 @@ __global__ void __launch_bounds__(256)
                  GridParams<T> g, Box<T> box, const T* __restrict__ psi_max,
                  const T* __restrict__ gmax, T* __restrict__ srad, const T* __restrict__ srad_lo,
                  const T* __restrict__ soff, const uint8_t* __restrict__ need, int kmax,
-                 int32_t* __restrict__ cand, int32_t* __restrict__ meta, int32_t* err) {
+                 int32_t* __restrict__ cand, int32_t* __restrict__ meta, int32_t* big_count,
+                 int32_t* big_list, int32_t* err) {
   int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n || !need[s]) return;
   const V4<T> p = sxp[s];
@@ -187,7 +192,10 @@ __global__ void __launch_bounds__(256)
   }
   if (empty) {
     meta[s] = kMetaEmpty;
-  } else if (nc > kmax) {
+  } else if (nc > kmax || (nw + nc > kPlaneCap && R - srad_lo[s] > T(0.03) * R)) {
+    // over capacity, or too many planes for the cell kernel's shared window
+    // while a smaller radius may still do: bisect; a cell becomes a big
+    // cell only when its bracket has collapsed
     const T lo = srad_lo[s];
     if (R - lo <= T(0.03) * R) {
       set_error(err, POT_ERR_NEIGHBOUR_OVERFLOW, s);
@@ -198,6 +206,8 @@ __global__ void __launch_bounds__(256)
     }
   } else {
     meta[s] = (nw + nc) | (wmask << kMetaWallShift);
+    // more planes than the cell kernel's shared window: the big-cell kernel
+    if (nw + nc > kPlaneCap) big_list[atomicAdd(big_count, 1)] = (int32_t)s;
   }
 }
 
@@ -244,7 +254,7 @@ __device__ __forceinline__ void isect(T a1, T b1, T c1, T a2, T b2, T c2, T& x, 
 // rounding).
 // Returns area, signed solid angle at the site and first moment (about the site).
 // rm2 is measured from the security-ball centre p + o (oa = |o|).
-template <typename T>
+template <typename T, typename IdT>
 __device__ Facet<T> facet_eval(const V4<T>* __restrict__ pl, int m, int fi, T ps, T r, T ox, T oy,
                                T oz, T oa, bool want_extent) {
   Facet<T> out = {T(0), T(0), T(0), T(0), T(0), T(0), 0, 0};
@@ -259,9 +269,10 @@ __device__ Facet<T> facet_eval(const V4<T>* __restrict__ pl, int m, int fi, T ps
 
   // polygon: line ids (plane index, or kSq + 0..3 for the square around
   // the disk) and vertices; vertex k = intersection of lines k-1 and k
-  constexpr int kSq = 0xfc;
-  static_assert(kPlaneCap <= kSq, "plane indices must stay below the square's line ids");
-  uint8_t lid[2][kMaxLines];
+  constexpr int kSq = sizeof(IdT) == 1 ? 0xfc : 0xfffc;
+  static_assert(sizeof(IdT) == 2 || kPlaneCap <= 0xfc, "plane indices must stay below the square's ids");
+  static_assert(kBigPlanes <= 0xfffc, "plane indices must stay below the square's ids");
+  IdT lid[2][kMaxLines];
   T px[2][kMaxLines], py[2][kMaxLines];
   int cur = 0, nl = 4;
   lid[0][0] = kSq; lid[0][1] = kSq + 1; lid[0][2] = kSq + 2; lid[0][3] = kSq + 3;
@@ -329,7 +340,7 @@ __device__ Facet<T> facet_eval(const V4<T>* __restrict__ pl, int m, int fi, T ps
       py[nx][k] = vy;
       if (k > 0) mr2 = fmax(mr2, vx * vx + vy * vy);
     }
-    lid[nx][cnt] = (uint8_t)gi;
+    lid[nx][cnt] = (IdT)gi;
     T a2, b2, c2;
     line(lid[cur][e], a2, b2, c2);
     isect(a, b, c, a2, b2, c2, px[nx][0], py[nx][0]);
@@ -662,7 +673,8 @@ __global__ void __launch_bounds__(CellCfg<T>::warps * 32, 5)
     const bool todo = valid && o.need[cell];  // cells finished in an earlier pass take no slot
     const int mt = todo ? meta[cell] : 0;
     const int m = mt & kMetaPlanes;
-    const int slots = todo ? (m > 1 ? m : 1) : 0;
+    // cells with more planes than the window are the big-cell kernel's
+    const int slots = (todo && m <= kPlaneCap) ? (m > 1 ? m : 1) : 0;
     int incl = slots;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
@@ -732,7 +744,7 @@ __global__ void __launch_bounds__(CellCfg<T>::warps * 32, 5)
       CellAcc<T> a = {};
       Facet<T> fo = {};
       if (has) {
-        fo = facet_eval(pl + oex, cm, f, op.w, orr, sox, soy, soz,
+        fo = facet_eval<T, uint8_t>(pl + oex, cm, f, op.w, orr, sox, soy, soz,
                         sqrt(sox * sox + soy * soy + soz * soz), !ofull);
         if (fo.overflow) set_error(err, POT_ERR_POLYGON_OVERFLOW, base + ow);
         acc_facet(a, pl[t], pd[t], pj[t], fo);
@@ -784,6 +796,69 @@ __global__ void __launch_bounds__(CellCfg<T>::warps * 32, 5)
                  fullw, sc[lane].a, sc[lane].emitted, sqrt(oxw * oxw + oyw * oyw + ozw * ozw), o);
     __syncwarp();
     base += ncell;
+  }
+}
+
+// Cells with more planes than the shared window (kPlaneCap): one warp per
+// cell, its planes staged in the warp's slice of a global scratch (L1/L2
+// resident), facets in rounds of 32 lanes with per-lane accumulators, one
+// warp reduction at the end.  Line ids of the facet polygons are 16-bit.
+// A fixed grid walks the list the candidate pass built (its length on the
+// device), so no host round trip is needed.
+template <typename T>
+__global__ void __launch_bounds__(128)
+    k_cells_big(const V4<T>* __restrict__ sxp, const int32_t* __restrict__ meta, int32_t* cand,
+                int kmax, Box<T> box, T* stage_vals, const T* __restrict__ soff,
+                const T* __restrict__ srad, const int32_t* __restrict__ big_count,
+                const int32_t* __restrict__ big_list, V4<T>* big_pl, T* big_d, int* big_j,
+                CellOut o, int32_t* err) {
+  const int lane = threadIdx.x & 31;
+  const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+  V4<T>* pl = big_pl + (int64_t)gw * kBigPlanes;
+  T* pd = big_d + (int64_t)gw * kBigPlanes;
+  int* pj = big_j + (int64_t)gw * kBigPlanes;
+  const int count = *big_count;
+  for (int b = gw; b < count; b += nw) {
+    const int64_t cell = big_list[b];
+    const int mt = meta[cell];
+    const int m = mt & kMetaPlanes;
+    const V4<T> p = sxp[cell];
+    const T r = p.w > T(0) ? sqrt(p.w) : T(0);
+    const T ox = soff[3 * cell + 0], oy = soff[3 * cell + 1], oz = soff[3 * cell + 2];
+    const T oa = sqrt(ox * ox + oy * oy + oz * oz);
+    const bool full = srad[cell] >= r + oa;
+    for (int f = lane; f < m; f += 32)
+      plane_of(f, cell, p, mt, r, sxp, cand, kmax, box, pl[f], pd[f], pj[f]);
+    __syncwarp();
+    CellAcc<T> a = {};
+    bool neg = false, qout = false;
+    int emitted = 0;
+    for (int f0 = 0; f0 < m; f0 += 32) {
+      const int f = f0 + lane;
+      const bool has = f < m;
+      Facet<T> fo = {};
+      if (has) {
+        fo = facet_eval<T, uint16_t>(pl, m, f, p.w, r, ox, oy, oz, oa, !full);
+        if (fo.overflow) set_error(err, POT_ERR_POLYGON_OVERFLOW, cell);
+        acc_facet(a, pl[f], pd[f], pj[f], fo);
+        neg |= pl[f].w < T(0);
+        qout |= oa > T(0) && -r * (pl[f].x * ox + pl[f].y * oy + pl[f].z * oz) > (pl[f].w + T(1e-6) * r) * oa;
+      }
+      const bool emit = has && pj[f] >= 0 && fo.area > Real<T>::kEmitArea * p.w;
+      const unsigned em = __ballot_sync(kFull, emit);
+      if (emit) {
+        const int64_t at = cell * kmax + emitted + __popc(em & ((1u << lane) - 1u));
+        cand[at] = pj[f];
+        stage_vals[at] = -fo.area / (T(2) * pd[f]);
+      }
+      emitted += __popc(em);
+    }
+    seg_reduce(a, lane, 31);
+    const bool anyneg = __any_sync(kFull, neg);
+    const bool anyq = __any_sync(kFull, qout);
+    if (lane == 0) write_cell(cell, p, (mt & kMetaEmpty) != 0, !anyneg, anyq && !full, full, a, emitted, oa, o);
+    __syncwarp();
   }
 }
 
@@ -1135,11 +1210,11 @@ int cells_eval(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* dom, 
   int64_t todo = n;  // cells rebuilt in this pass
   for (int pass = 0; pass < kMaxPasses; pass++) {
     ctx->last_passes = pass + 1;
+    POT_CUDA(cudaMemsetAsync(ctx->need_count + 1, 0, sizeof(int32_t), st));
     note_launch();
-    k_candidates<T><<<blocks_for(n, 256), 256, 0, st>>>(n, w.sxp, ctx->cell_start, w.grid, box,
-                                                         w.psi_max, w.gmax, w.srad, w.srad_lo,
-                                                         w.soff, ctx->need,
-                                                         ctx->k_max, ctx->cand, ctx->meta, ctx->err);
+    k_candidates<T><<<blocks_for(n, 256), 256, 0, st>>>(
+        n, w.sxp, ctx->cell_start, w.grid, box, w.psi_max, w.gmax, w.srad, w.srad_lo, w.soff,
+        ctx->need, ctx->k_max, ctx->cand, ctx->meta, ctx->need_count + 1, ctx->big_list, ctx->err);
     note_launch();
     // the no-alloc entry point's context has no events: no timing there
     const bool timed = ctx->ev[6] && ctx->ev[7];
@@ -1147,6 +1222,12 @@ int cells_eval(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* dom, 
     k_cells<T><<<blocks, CellCfg<T>::warps * 32, 0, st>>>(n, w.sxp, ctx->meta, ctx->cand,
                                                            ctx->k_max, box, w.stage_vals, w.soff,
                                                            w.srad, o, ctx->err);
+    if (w.big_warps > 0) {
+      note_launch();
+      k_cells_big<T><<<w.big_warps / 4, 128, 0, st>>>(
+          w.sxp, ctx->meta, ctx->cand, ctx->k_max, box, w.stage_vals, w.soff, w.srad,
+          ctx->need_count + 1, ctx->big_list, w.big_pl, w.big_d, w.big_j, o, ctx->err);
+    }
     if (timed) POT_CUDA(cudaEventRecord(ctx->ev[7], st));
     POT_CUDA(cudaMemsetAsync(ctx->need_count, 0, sizeof(int32_t), st));
     note_launch();

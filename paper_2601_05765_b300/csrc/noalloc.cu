@@ -63,7 +63,8 @@ constexpr size_t oRcell = oSoff + al(12 * N);
 constexpr size_t oGmax = oRcell + al(4 * N);
 constexpr size_t oNeed = oGmax + al(4 * (kNoAllocGridCap + 1));
 constexpr size_t oNeedCount = oNeed + al(N);
-constexpr size_t kScratchBytes = oNeedCount + al(8);
+constexpr size_t oBigList = oNeedCount + al(8);
+constexpr size_t kScratchBytes = oBigList + al(4 * N);
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -151,6 +152,7 @@ extern "C" int lgc_compute_cells_noalloc(void* stream, int64_t n, const float* p
   w.gmax = (float*)(b + oGmax);
   c.need = (uint8_t*)(b + oNeed);
   c.need_count = (int32_t*)(b + oNeedCount);
+  c.big_list = (int32_t*)(b + oBigList);  // unused: 64-plane lists fit the cell kernel's window
 
   // the previous call's status words are stale: clear them
   POT_CUDA(cudaMemcpyAsync(c.err, kErrInit, sizeof(kErrInit), cudaMemcpyHostToDevice, st));

@@ -25,17 +25,19 @@ namespace pot {
 
 constexpr int kWarp = 32;
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kMaxK = 246;         // candidate bisectors per cell (k_max <= 246)
-constexpr int kPlaneCap = kMaxK + 6;
+constexpr int kMaxK = 1024;        // candidate bisectors per cell (k_max <= 1024)
+constexpr int kPlaneCap = 252;     // planes of a cell in the cell kernel's shared window
+constexpr int kBigPlanes = kMaxK + 6;  // planes of a cell in the big-cell kernel
+constexpr int kBigWarpsPerSm = 8;  // warps of the big-cell kernel per SM
 constexpr int kMaxLines = 24;      // edges of one facet polygon
 constexpr int kCellWarps = 4;      // warps per block of the cell kernel
 constexpr int kCellsPerWarp = 32;  // cells per warp task
 
 // meta word written by the candidate kernel
-constexpr int kMetaPlanes = 0x1ff;  // planes (walls + candidates) <= kMaxK + 6
-constexpr int kMetaWallShift = 9;   // 6 wall bits
-constexpr int kMetaEmpty = 1 << 15;
-constexpr int kMetaRetry = 1 << 16;  // candidate list overflowed: redo at a smaller radius
+constexpr int kMetaPlanes = 0x7ff;  // planes (walls + candidates) <= kMaxK + 6
+constexpr int kMetaWallShift = 11;  // 6 wall bits
+constexpr int kMetaEmpty = 1 << 17;
+constexpr int kMetaRetry = 1 << 18;  // candidate list overflowed: redo at a smaller radius
 constexpr int kMaxPasses = 48;       // security-radius passes of one cell evaluation
 
 // device status words: [0] error code (max over sites), [1] smallest site with that error
@@ -148,6 +150,10 @@ struct Work {
   T* rcell_acc = nullptr;   // per cell: rcell at the last accepted Newton iterate
   T* rcell = nullptr;       // per cell: farthest point of the cell from its security centre
   T* hint = nullptr;        // caller order: centroid - site and extent from it (4 per site)
+  V4<T>* big_pl = nullptr;  // big-cell kernel: planes of each warp's cell (kBigPlanes per warp)
+  T* big_d = nullptr;
+  int* big_j = nullptr;
+  int big_warps = 0;        // warps of the big-cell kernel (0: no big cells possible)
   T* gmax = nullptr;        // per grid cell: largest psi of its sites
   GridParams<T> grid{};
   bool grid_valid = false;
@@ -190,7 +196,8 @@ struct pot_ctx {
   int32_t* pcg_ctl = nullptr;     // PCG control words
   int32_t* err = nullptr;         // device status words
   uint8_t* need = nullptr;        // per cell: still to be (re)built in this evaluation
-  int32_t* need_count = nullptr;  // device counter of cells to rebuild
+  int32_t* need_count = nullptr;  // device counters: cells to rebuild, big cells listed
+  int32_t* big_list = nullptr;    // cells with more planes than the shared window holds
   int last_passes = 0;            // security-radius passes of the last cell evaluation
   int64_t kc_launches = 0;        // cell-kernel timer: launches, cells processed, device ms
   int64_t kc_cells = 0;

@@ -45,7 +45,7 @@ def test_host_only_calls(lib):
     # invalid arguments are rejected before any device call
     h = ctypes.c_void_p()
     assert lib.pot_create(ctypes.byref(h), 0, ctypes.c_int64(0), 64, 3) == 1
-    assert lib.pot_create(ctypes.byref(h), 0, ctypes.c_int64(10), 247, 3) == 1
+    assert lib.pot_create(ctypes.byref(h), 0, ctypes.c_int64(10), 1025, 3) == 1
     assert lib.pot_create(ctypes.byref(h), 0, ctypes.c_int64(10), 64, 0) == 1
     assert lib.lgc_compute_cells(None, None, ctypes.c_int64(10), None, None, None, None, None, None,
                                  None, None, None, None) == 1

@@ -179,3 +179,32 @@ def test_cell_diagnostics_invariants(ctx):
     assert np.all((ext < rad * (1 - 1e-5)) | (rad >= r * (1 - 1e-6)))
     rp = to_np(out["row_ptr"]).astype(np.int64)
     assert np.all(planes >= np.diff(rp) - 1)
+
+
+def test_big_cells_against_oracle():
+    """A cell that needs more planes than the cell kernel's shared window
+    (252): in a jittered 14^3 lattice with balls 2.5 spacings wide, one site
+    whose weight exceeds its neighbours' by 12.5 s^2 owns a cell about 3.5
+    spacings wide, bounded by the bisectors of the shell of sites between
+    about 2.3 and 5.5 spacings -- several hundred planes, so it goes through
+    the big-cell kernel.  The central 5^3 cells (the big one, the swallowed
+    empty ones, the shell) against the oracle."""
+    n_side, s = 14, 0.04
+    rng = np.random.default_rng(12)
+    g = np.stack(np.meshgrid(*[np.arange(n_side)] * 3, indexing="ij"), -1).reshape(-1, 3)
+    pos = ((g + 0.5 + rng.uniform(-0.2, 0.2, g.shape)) * s + 0.2).astype(np.float32)
+    n = pos.shape[0]
+    psi = np.full(n, (2.5 * s) ** 2, np.float32)
+    c = int(np.nonzero(np.all(g == n_side // 2, axis=1))[0][0])
+    psi[c] = np.float32(3 * (2.5 * s) ** 2)
+    nu = np.full(n, s ** 3)
+    big = pot.Context(n, 1024, 0, fp64=False)
+    out = run(big, pos, psi, nu)
+    planes = to_np(pot.cell_diagnostics(big, n)["planes"])
+    assert planes[c] > 252, planes[c]
+    q = np.nonzero(np.all(np.abs(g - n_side // 2) <= 2, axis=1))[0]
+    ref = O.cells(pos.astype(np.float64), psi.astype(np.float64), query=q, max_facets=4096)
+    assert np.all(ref["status"] == 0)
+    rep = compare_cells(out, ref, psi, nu, **TOL32)
+    print(rep, int(planes[c]), float(ref["vol"][np.nonzero(q == c)[0][0]] / s ** 3))
+    big.close()
