@@ -84,7 +84,8 @@ __device__ __forceinline__ void set_error(int32_t* err, int code, int64_t site) 
 // narrowed to 3 % of R_i is the overflow a real capacity error.  A list that
 // would not fit the cell kernel's shared window (kPlaneCap planes) is
 // bisected the same way, and the cell goes to the big-cell kernel only when
-// its bracket has collapsed.
+// its bracket has collapsed; from then on (for the rest of the evaluation)
+// it grows without that limit.
 //
 // Grid cells are skipped with a lower bound of h over their sites: for
 // |p_i - p_j| >= delta and psi_j <= gmax,  h_ij >= delta/2 - (gmax - psi_i)/(2 delta)
@@ -94,7 +95,7 @@ __global__ void __launch_bounds__(256)
     k_candidates(int64_t n, const V4<T>* __restrict__ sxp, const int32_t* __restrict__ cell_start,
                  GridParams<T> g, Box<T> box, const T* __restrict__ psi_max,
                  const T* __restrict__ gmax, T* __restrict__ srad, const T* __restrict__ srad_lo,
-                 const T* __restrict__ soff, const uint8_t* __restrict__ need, int kmax,
+                 const T* __restrict__ soff, uint8_t* __restrict__ need, int kmax,
                  int32_t* __restrict__ cand, int32_t* __restrict__ meta, int32_t* big_count,
                  int32_t* big_list, int32_t* err) {
   int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -190,14 +191,19 @@ __global__ void __launch_bounds__(256)
       }
     }
   }
+  const T lo = srad_lo[s];
+  const bool collapsed = R - lo <= T(0.03) * R;
+  // too many planes for the cell kernel's shared window, and not yet known
+  // to need that many in this evaluation
+  const bool soft = nw + nc > kPlaneCap && !(need[s] & kNeedBig);
+  if (!empty && !(nc > kmax) && soft && collapsed) need[s] |= kNeedBig;  // a big cell from now on
   if (empty) {
     meta[s] = kMetaEmpty;
-  } else if (nc > kmax || (nw + nc > kPlaneCap && R - srad_lo[s] > T(0.03) * R)) {
-    // over capacity, or too many planes for the cell kernel's shared window
-    // while a smaller radius may still do: bisect; a cell becomes a big
-    // cell only when its bracket has collapsed
-    const T lo = srad_lo[s];
-    if (R - lo <= T(0.03) * R) {
+  } else if (nc > kmax || (soft && !collapsed)) {
+    // over capacity, or too many planes for the window while a smaller
+    // radius may still do: bisect; a cell becomes a big cell only when its
+    // bracket has collapsed
+    if (collapsed) {
       set_error(err, POT_ERR_NEIGHBOUR_OVERFLOW, s);
       meta[s] = kMetaEmpty;
     } else {

@@ -19,7 +19,7 @@ namespace pot {
 namespace {
 
 constexpr int kPcgThreads = 256;
-constexpr int kTpr = 8;  // threads per CSR row
+constexpr int kTpr = 2;  // threads per CSR row (about 10 entries per row)
 
 // partial-sum arrays (nb doubles each) and scalars at the end of pcg_red
 enum { kPartA = 0, kPartB = 1, kPartC = 2, kParts = 3 };

@@ -39,6 +39,9 @@ constexpr int kMetaWallShift = 11;  // 6 wall bits
 constexpr int kMetaEmpty = 1 << 17;
 constexpr int kMetaRetry = 1 << 18;  // candidate list overflowed: redo at a smaller radius
 constexpr int kMaxPasses = 48;       // security-radius passes of one cell evaluation
+// need[] bits of a cell during an evaluation
+constexpr uint8_t kNeedPending = 1;  // to be (re)built in the next pass
+constexpr uint8_t kNeedBig = 2;      // needs more planes than the cell kernel's window
 
 // device status words: [0] error code (max over sites), [1] smallest site with that error
 enum { kErrCode = 0, kErrSite = 1 };
