@@ -69,6 +69,9 @@ def parse():
     ap.add_argument("--scene", default="cloud", choices=["cloud", "splash"],
                     help="cells mode: the 2^20-site random cloud, or the splash at converged weights")
     ap.add_argument("--spacing", type=float, default=3.224e-3, help="splash lattice spacing")
+    ap.add_argument("--train-splash", action="store_true",
+                    help="warmstart mode: add free-flight samples (small splashes before contact, "
+                         "other seeds) to the dam-break training set")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     return ap.parse_args()
@@ -456,12 +459,25 @@ def run_warmstart(args):
         x, y = W.collect(ctx_t, mlp, col, steps=40, every=2, per_sample=4096, seed=10 + k, dt=2e-3)
         xs.append(x)
         ys.append(y)
+    ctx_t.close()
+    extra = "none"
+    if args.train_splash:
+        # free flight before contact: two balls at spacing 0.01 (about 130k
+        # sites), seeds 40-43, 12 steps of the splash dt
+        for k in range(4):
+            sm = scenes.splash(spacing=0.01, seed=40 + k)
+            ctx_s = pot.Context(sm.n, 246, 0, fp32=True, fp64=False)
+            x, y = W.collect(ctx_s, mlp, sm, steps=12, every=1, per_sample=8192, seed=40 + k,
+                             dt=SPLASH_DT)
+            xs.append(x)
+            ys.append(y)
+            ctx_s.close()
+        extra = "small splashes (spacing 0.01, seeds 40-43, 12 steps before contact)"
     x, y = torch.cat(xs), torch.cat(ys)
     t1 = time.perf_counter()
     hist = W.train(mlp, x, y, epochs=60, batch=8192, lr=1e-3)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
-    ctx_t.close()
 
     def both(ctx, scene, dt, warm):
         res = W.compare(ctx, mlp, scene, steps=args.steps, dt=dt, warm_steps=warm)
@@ -487,7 +503,8 @@ def run_warmstart(args):
                     f"dt {SPLASH_DT}, tol 1e-4, FP32 geometry with FP64 reductions",
         "training": {"samples": int(x.shape[0]), "epochs": len(hist), "loss_first": hist[0],
                      "loss_last": hist[-1], "collect_s": t1 - t0, "train_s": t2 - t1,
-                     "scenes": "dam-break columns 24x24x48, seeds 10-19, 40 steps of dt 2e-3"},
+                     "scenes": "dam-break columns 24x24x48, seeds 10-19, 40 steps of dt 2e-3",
+                     "extra_scenes": extra},
         "plain": plain, "mlp": learned,
         "newton_iters_saved": plain["newton_iters"] - learned["newton_iters"],
         "ms_saved_per_solve": plain["ms_total"] - learned["ms_total"],
