@@ -231,7 +231,13 @@ def newton(pos, nu, psi0, tol=1e-4, max_newton=100, max_halvings=30,
             pt = psi + alpha * u
             rt = cells(pos, pt, lo=lo, hi=hi, nthreads=nthreads)
             vt = rt["vol"]
-            if vt.min() >= eps0 and np.linalg.norm(nu - vt) <= (1.0 - 0.5 * alpha) * gnorm:
+            # KMT decrease in the l2 norm, or in the max relative error that
+            # the stopping test measures (an FP32 evaluation's l2 norm over
+            # many cells reaches its rounding floor before a few worst cells
+            # reach the tolerance)
+            et = float(np.max(np.abs(vt - nu) / nu))
+            if vt.min() >= eps0 and (np.linalg.norm(nu - vt) <= (1.0 - 0.5 * alpha) * gnorm
+                                     or et <= (1.0 - 0.5 * alpha) * err):
                 accepted = True
                 break
             alpha *= 0.5
