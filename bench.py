@@ -3,10 +3,14 @@
 
 One step = one complete fluid step (Sec. 5): advect, grid build, Newton solve
 to 1e-4 worst-cell relative volume error (Algorithm 1: cell geometry, CSR
-Hessian, Jacobi-PCG, KMT line search), centroids, velocity update.  Inputs
-are resident in HBM when the timed region starts; the working set (sites,
-CSR Hessian, candidate lists) is larger than the 126 MB L2, so no flush is
-needed between steps.
+Hessian, Jacobi-PCG, KMT line search), centroids, velocity update.  The
+timed steps are steps 0..K-1 of the run (default K = 100: the balls touch
+near step 10 and are pressed together until the end), from the recipe's
+start state (sites at their cell centroids); the warm-up steps run from the
+same state, which is restored before the timed region.  Inputs are resident
+in HBM when the timed region starts; the working set (sites, CSR Hessian,
+candidate lists) is larger than the 126 MB L2, so no flush is needed between
+steps.
 
 value  = cells/s: sites whose generalized Laguerre cell is solved to 1e-4 per
          second (N x steps / device time), summed over ranks.
@@ -44,7 +48,6 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-SPLASH_DT = 5e-4
 SMALL_SPACING = 0.032  # ~2000 sites with the splash recipe
 # FP32 FLOP executed (fadd + fmul + 2 ffma) and DRAM bytes per cell processed
 # by k_cells, from an ncu capture of the 536k-site splash at converged weights
@@ -57,7 +60,7 @@ K_CELLS_DRAM_BYTES_PER_CELL = 413.0
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="step", choices=["step", "cells", "warmstart", "dam", "solve"],
@@ -179,12 +182,16 @@ def oracle_steps(seconds_budget: float, max_steps: int, seed: int = 3):
     x = sc.pos.astype(np.float64)
     v = sc.vel.astype(np.float64)
     psi = sc.psi.astype(np.float64)
-    # converge the start once (not timed): steps are then warm-started solves
+    # the recipe's start state (not timed): converged weights, sites moved
+    # to their cell centroids, converged again
     psi = O.newton(x, sc.nu, psi, tol=1e-4).psi
+    for _ in range(sc.extra["relax_rounds"]):
+        x = O.cells(x, psi)["cen"].copy()
+        psi = O.newton(x, sc.nu, psi, tol=1e-4).psi
     t0 = time.perf_counter()
     steps = 0
     while steps < max_steps and (time.perf_counter() - t0) < seconds_budget:
-        x, v, nr = O.fluid_step(x, v, psi, sc.nu, dt=SPLASH_DT, tol=1e-4)
+        x, v, nr = O.fluid_step(x, v, psi, sc.nu, dt=sc.extra["dt"], eps=sc.extra["eps"], tol=1e-4)
         psi = nr.psi
         steps += 1
     dt = time.perf_counter() - t0
@@ -203,7 +210,8 @@ def run_reference(args):
         "value": val, "unit": "cells/s", "n_gpus": args.gpus, "steps": steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * dt / max(steps, 1), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"two-ball splash, {n} sites (spacing {SMALL_SPACING}), dt {SPLASH_DT}",
+        "config": {"workload": f"two-ball splash (radius 0.2, \u00b13 m/s), {n} sites "
+                               f"(spacing {SMALL_SPACING}), steps 0..{steps - 1}",
                    "tol": 1e-4},
         "cpu_baseline": {"value": val, "unit": "cells/s", "cores": cores, "kind": "oracle",
                          "sample": f"oracle fluid steps (dense-LU Newton, KMT, tol 1e-4) on the splash "
@@ -268,14 +276,21 @@ def run_ours(args):
     vel = torch.from_numpy(sc.vel).to(dev)
     psi = torch.from_numpy(sc.psi).to(dev)
     nu = torch.from_numpy(sc.nu).to(dev)
-    prm = pot.default_params(dt=SPLASH_DT)
+    prm = pot.default_params(dt=sc.extra["dt"], eps=sc.extra["eps"])
     stream = torch.cuda.current_stream()
 
+    # the recipe's start state (untimed): sites at their cell centroids
+    relax = pot.relax_to_centroids(ctx, pos, psi, nu, sc.extra["relax_rounds"], params=prm)
+    # the state the timed steps start from (step 0 of the run), kept on the
+    # device for the restore after the warm-up and in pinned host memory for
+    # the end-to-end run below, which repeats the same steps from it
+    d0 = [t.clone() for t in (pos, vel, psi)]
+    h0 = [t.cpu().pin_memory() for t in (pos, vel, psi)]
     for _ in range(args.warmup):
         pot.pot_fluid_step(ctx, pos, vel, psi, nu, params=prm)
-    # the state the timed steps start from, kept in pinned host memory: the
-    # end-to-end run below repeats the same steps from it
-    h0 = [t.cpu().pin_memory() for t in (pos, vel, psi)]
+    for t, t0 in zip((pos, vel, psi), d0):
+        t.copy_(t0)
+    del d0
 
     # ---- device-timed region
     gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local]) \
@@ -349,8 +364,13 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32 geometry, f64 reductions", "data": "synthetic",
         "config": {"workload": f"two-ball splash (radius 0.2, \u00b13 m/s), {n} sites per GPU, "
                                f"1e-4 Newton per step",
-                   "sites_per_gpu": n, "dt": SPLASH_DT, "eps": prm.eps, "tol": 1e-4,
-                   "first_timed_step": args.warmup, "parallelism": f"replicas x{world}",
+                   "sites_per_gpu": n, "dt": prm.dt, "eps": prm.eps, "tol": 1e-4,
+                   "timed_steps": f"0..{args.steps - 1} of the run (the warm-up steps are run "
+                                  f"from the same start state, which is then restored)",
+                   "start": f"{sc.extra['relax_rounds']} rounds of sites moved to their cell "
+                            f"centroids (last move: mean {relax['moved_mean'][-1]:.2e}, max "
+                            f"{relax['moved_max'][-1]:.2e})",
+                   "parallelism": f"replicas x{world}",
                    "l2": "working set > 126 MB L2, no flush"},
         "newton_solve_ms": {"median": solve_ms[len(solve_ms) // 2],
                             "p90": solve_ms[min(len(solve_ms) - 1, int(0.9 * len(solve_ms)))]},
@@ -375,10 +395,10 @@ def run_ours(args):
                 "d2h_bytes_per_step": d2h, "steps": "the same steps as the device-timed region"},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        val, steps, nsm, cores, dt = oracle_steps(args.cpu_seconds, 1000)
+        val, steps, nsm, cores, dt = oracle_steps(args.cpu_seconds, 100)
         line["cpu_baseline"] = {"value": val, "unit": "cells/s", "cores": cores, "kind": "oracle",
-                                "sample": f"{steps} oracle fluid steps (dense-LU Newton, KMT, tol 1e-4) "
-                                          f"on the splash recipe at {nsm} sites, {dt:.1f} s"}
+                                "sample": f"oracle fluid steps 0..{steps - 1} (dense-LU Newton, KMT, "
+                                          f"tol 1e-4) of the splash recipe at {nsm} sites, {dt:.1f} s"}
     if rank == 0:
         print(json.dumps(line))
     ctx.close()
@@ -462,25 +482,26 @@ def run_warmstart(args):
     ctx_t.close()
     extra = "none"
     if args.train_splash:
-        # free flight before contact: two balls at spacing 0.01 (about 130k
-        # sites), seeds 40-43, 12 steps of the splash dt
+        # smaller splashes of the same recipe (spacing 0.01, about 65k
+        # sites), seeds 40-43, the first 40 steps (contact near step 10)
         for k in range(4):
             sm = scenes.splash(spacing=0.01, seed=40 + k)
             ctx_s = pot.Context(sm.n, 246, 0, fp32=True, fp64=False)
-            x, y = W.collect(ctx_s, mlp, sm, steps=12, every=1, per_sample=8192, seed=40 + k,
-                             dt=SPLASH_DT)
+            x, y = W.collect(ctx_s, mlp, sm, steps=40, every=2, per_sample=8192, seed=40 + k,
+                             dt=sm.extra["dt"], eps=sm.extra["eps"], relax=sm.extra["relax_rounds"])
             xs.append(x)
             ys.append(y)
             ctx_s.close()
-        extra = "small splashes (spacing 0.01, seeds 40-43, 12 steps before contact)"
+        extra = "small splashes (spacing 0.01, seeds 40-43, steps 0-39, every 2nd)"
     x, y = torch.cat(xs), torch.cat(ys)
     t1 = time.perf_counter()
     hist = W.train(mlp, x, y, epochs=60, batch=8192, lr=1e-3)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
 
-    def both(ctx, scene, dt, warm):
-        res = W.compare(ctx, mlp, scene, steps=args.steps, dt=dt, warm_steps=warm)
+    def both(ctx, scene, dt, warm, eps=0.01, relax=0):
+        res = W.compare(ctx, mlp, scene, steps=args.steps, dt=dt, warm_steps=warm, eps=eps,
+                        relax=relax)
         out = {}
         for k in ("plain", "mlp"):
             out[k] = W.summarize(res[k])
@@ -495,12 +516,13 @@ def run_warmstart(args):
     pot.set_warm_start(ctx_d, None)
     ctx_d.close()
     ctx = pot.Context(sc.n, 246, 0, fp32=True, fp64=False)
-    spl = both(ctx, sc, SPLASH_DT, args.warmup)
+    spl = both(ctx, sc, sc.extra["dt"], args.warmup, sc.extra["eps"], sc.extra["relax_rounds"])
     plain, learned = spl["plain"], spl["mlp"]
     print(json.dumps({
         "metric": "Newton iterations and ms per fluid-step solve, learned vs plain start",
         "workload": f"two-ball splash, {sc.n} sites, steps {args.warmup}..{args.warmup + args.steps - 1}, "
-                    f"dt {SPLASH_DT}, tol 1e-4, FP32 geometry with FP64 reductions",
+                    f"dt {sc.extra['dt']:.4g}, eps {sc.extra['eps']:.4g}, tol 1e-4, FP32 geometry with "
+                    f"FP64 reductions",
         "training": {"samples": int(x.shape[0]), "epochs": len(hist), "loss_first": hist[0],
                      "loss_last": hist[-1], "collect_s": t1 - t0, "train_s": t2 - t1,
                      "scenes": "dam-break columns 24x24x48, seeds 10-19, 40 steps of dt 2e-3",

@@ -333,6 +333,24 @@ def pot_fluid_step(ctx: Context, pos, vel, psi, targets, domain=UNIT_BOX, params
     return s
 
 
+def relax_to_centroids(ctx: Context, pos, psi, targets, rounds: int, domain=UNIT_BOX, params=None):
+    """Start state of a fluid run at rest under the pressure spring of Sec. 5
+    (F_p = (c_i - x_i) / eps^2): solve, then `rounds` times move every site to
+    its cell's centroid and solve again (Lloyd steps of the volume-constrained
+    diagram).  pos and psi are updated in place; returns the solves' stats and
+    the mean and max site-to-centroid distance before each move."""
+    out = {"solves": [pot_newton_solve(ctx, pos, targets, psi, domain=domain, params=params)],
+           "moved_mean": [], "moved_max": []}
+    for _ in range(rounds):
+        cells = lgc_compute_cells(ctx, pos, psi, targets, domain=domain, hessian=False, karea=False)
+        d = (cells["centroids"] - pos).norm(dim=1)
+        out["moved_mean"].append(float(d.mean()))
+        out["moved_max"].append(float(d.max()))
+        pos.copy_(cells["centroids"])
+        out["solves"].append(pot_newton_solve(ctx, pos, targets, psi, domain=domain, params=params))
+    return out
+
+
 # ---------------------------------------------------------------------------
 # learned warm start
 

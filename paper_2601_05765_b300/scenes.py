@@ -120,19 +120,38 @@ def dam_break(nx: int = 63, ny: int = 63, nz: int = 126, width: float = 0.4,
                  extra={"spacing": s})
 
 
+# Spring length and time step of the splash, in units of its lattice spacing
+# s: eps = s / 16 puts each ball's 3 m/s at 0.19 of the spring's signal speed
+# s / eps, and dt = eps / 2 takes 2 steps per radian of the spring's
+# oscillation.  Both scale with s, so every resolution of the recipe sees the
+# same number of steps to contact and the same impact relative to the spring.
+SPLASH_EPS_PER_SPACING = 1.0 / 16.0
+SPLASH_DT_PER_EPS = 0.5
+SPLASH_RELAX_ROUNDS = 3
+
+
 def splash(spacing: float = 3.224e-3, radius: float = 0.2, speed: float = 3.0,
            jitter: float = 0.3, seed: int = 3, fill: float = 0.9,
-           r_factor: float = 0.8,
-           centers=((0.28, 0.5, 0.5), (0.72, 0.5, 0.5))) -> Scene:
-    """Two balls of jittered lattice sites flying at each other.
+           r_factor: float = 0.8, gap: float = 2.0, centers=None) -> Scene:
+    """Two balls of jittered lattice sites flying at each other along x.
 
-    Lattice points (k+0.5)*spacing whose unjittered position lies inside a
-    ball of the given radius around each centre are kept; then every kept site
-    is jittered by U(-jitter, jitter)^3*spacing (one draw, default_rng(seed)).
-    Ball 0 moves with (+speed,0,0), ball 1 with (-speed,0,0).  nu = fill*s^3,
-    psi0 as jittered_block.  The defaults give about 2.0M sites.
+    The balls are centred at (0.5 -/+ (radius + gap*spacing/2), 0.5, 0.5)
+    unless `centers` is given: their surfaces start gap spacings apart and,
+    closing at 2*speed, touch after about gap*spacing/(2*speed*dt) steps
+    (10 with the recipe's dt).  Lattice points (k+0.5)*spacing whose
+    unjittered position lies inside a ball of the given radius around each
+    centre are kept; then every kept site is jittered by
+    U(-jitter, jitter)^3*spacing (one draw, default_rng(seed)).  Ball 0 moves
+    with (+speed,0,0), ball 1 with (-speed,0,0).  nu = fill*s^3, psi0 as
+    jittered_block.  extra holds the recipe's spring length eps, time step dt
+    and the number of rounds that move the sites to their cell centroids
+    before the first step (the spring's rest state).  The defaults give about
+    2.0M sites.
     """
     rng = np.random.default_rng(seed)
+    if centers is None:
+        off = radius + 0.5 * gap * spacing
+        centers = ((0.5 - off, 0.5, 0.5), (0.5 + off, 0.5, 0.5))
     parts, vels = [], []
     for b, c in enumerate(centers):
         c = np.asarray(c, np.float64)
@@ -153,8 +172,11 @@ def splash(spacing: float = 3.224e-3, radius: float = 0.2, speed: float = 3.0,
     pos = pos + rng.uniform(-jitter, jitter, size=(n, 3)) * spacing
     nu = np.full(n, fill * spacing ** 3, dtype=np.float64)
     r = r_factor * _ball_radius_for_volume(nu)
+    eps = SPLASH_EPS_PER_SPACING * spacing
     return Scene(pos=pos.astype(np.float32), psi=(r * r).astype(np.float32), nu=nu,
-                 vel=vel.astype(np.float32), name=f"splash_{n}", extra={"spacing": spacing})
+                 vel=vel.astype(np.float32), name=f"splash_{n}",
+                 extra={"spacing": spacing, "eps": eps, "dt": SPLASH_DT_PER_EPS * eps,
+                        "relax_rounds": SPLASH_RELAX_ROUNDS})
 
 
 def random_subset(n: int, k: int, seed: int) -> np.ndarray:

@@ -57,18 +57,20 @@ def _state(sc, dev):
             torch.from_numpy(sc.psi).to(dev), torch.from_numpy(sc.nu).to(dev))
 
 
-def settle(ctx, pos, vel, psi, nu, prm):
-    """Converge the initial weights (not a sample): a Newton solve in place."""
-    st = pot.pot_newton_solve(ctx, pos, nu, psi, params=prm, check=False)
-    return st
+def settle(ctx, pos, vel, psi, nu, prm, relax=0):
+    """Start state (not a sample): the initial weights converged in place,
+    then `relax` rounds of sites moved to their cell centroids."""
+    if relax > 0:
+        return pot.relax_to_centroids(ctx, pos, psi, nu, relax, params=prm)["solves"][-1]
+    return pot.pot_newton_solve(ctx, pos, nu, psi, params=prm, check=False)
 
 
-def collect(ctx, mlp, scene, steps, every, per_sample, seed, dt, tol=1e-4):
+def collect(ctx, mlp, scene, steps, every, per_sample, seed, dt, tol=1e-4, eps=0.01, relax=0):
     """Samples from `steps` plain-Newton fluid steps of `scene`."""
     dev = ctx.device
     pos, vel, psi, nu = _state(scene, dev)
-    prm = pot.default_params(dt=dt, tol=tol)
-    settle(ctx, pos, vel, psi, nu, prm)
+    prm = pot.default_params(dt=dt, tol=tol, eps=eps)
+    settle(ctx, pos, vel, psi, nu, prm, relax)
     h2 = torch.pow(nu, 2.0 / 3.0).float()
     gen = torch.Generator(device="cpu").manual_seed(seed)
     xs, ys = [], []
@@ -108,13 +110,13 @@ def train(mlp, x, y, epochs, batch=8192, lr=1e-3, seed=0):
     return hist
 
 
-def compare(ctx, mlp, scene, steps, dt, warm_steps=0, tol=1e-4):
+def compare(ctx, mlp, scene, steps, dt, warm_steps=0, tol=1e-4, eps=0.01, relax=0):
     """Run the same fluid steps from the same state with the plain start and
     with the MLP start; returns per-step stats for both."""
     dev = ctx.device
     pos, vel, psi, nu = _state(scene, dev)
-    prm = pot.default_params(dt=dt, tol=tol)
-    settle(ctx, pos, vel, psi, nu, prm)
+    prm = pot.default_params(dt=dt, tol=tol, eps=eps)
+    settle(ctx, pos, vel, psi, nu, prm, relax)
     psi_old = None
     for _ in range(warm_steps):
         psi_old = psi.clone()
@@ -123,7 +125,7 @@ def compare(ctx, mlp, scene, steps, dt, warm_steps=0, tol=1e-4):
     out = {}
     for mode in (0, 1):
         pos, vel, psi = (t.clone() for t in state)
-        p = pot.default_params(dt=dt, tol=tol, warm_start=mode)
+        p = pot.default_params(dt=dt, tol=tol, eps=eps, warm_start=mode)
         pot.set_warm_start(ctx, mlp if mode else None)
         if mode:
             mlp.set_history(psi_old)
