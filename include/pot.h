@@ -106,7 +106,8 @@ typedef struct {
   double gravity[3];    /* (0, 0, -9.81) */
   double wall_margin;   /* sites are clamped to [lo+m, hi-m] (1e-6) */
   int32_t warm_start;   /* 0: previous psi; 1: learned MLP start */
-  int32_t reserved;
+  int32_t substeps;     /* pot_fluid_step takes this many explicit steps of
+                           dt / substeps (0 or 1: one step of dt) */
 } pot_params;
 
 /* Statistics of one Newton solve (and of the solve inside a fluid step). */
@@ -268,6 +269,9 @@ int pot_newton_solve_f64(pot_ctx* ctx, void* stream, int64_t n, const double* po
  *        wall set to 0);
  *   psi <- Newton solve at the new x, warm-started from psi;
  *   v <- v + dt (g + (c_i - x_i) / eps^2)   (pressure spring F_p, Sec. 5).
+ * With params->substeps = k > 1 this is done k times with dt / k, stopping
+ * at the first substep whose solve fails; stats then sums the substeps'
+ * counts and times and keeps their largest start and final errors.
  * pos, vel (n,3) and psi (n) are updated in place. */
 int pot_fluid_step(pot_ctx* ctx, void* stream, int64_t n, float* pos, float* vel, float* psi,
                    const double* targets, const pot_domain* dom, const pot_params* params,

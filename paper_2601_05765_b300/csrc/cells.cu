@@ -310,11 +310,15 @@ __device__ Facet<T> facet_eval(const V4<T>* __restrict__ pl, int m, int fi, T ps
       if (c < T(0)) return out;
       continue;
     }
-    T lr = rho * sqrt(len2);
-    if (c >= lr) continue;            // the disk lies inside this half-plane
-    if (c <= -lr) return out;         // the disk lies outside: no facet
+    // |c| >= rho |(a,b)|: the line misses the disk, which lies inside the
+    // half-plane (c > 0) or outside it (no facet)
+    const T cc = c * c;
+    if (cc >= rho2 * len2) {
+      if (c > T(0)) continue;
+      return out;
+    }
     // every vertex v has a.v <= |(a,b)| |v| < c: the polygon is inside
-    if (c > T(0) && c * c >= len2 * rp2 * T(1.0001)) continue;
+    if (c > T(0) && cc >= len2 * rp2 * T(1.0001)) continue;
     unsigned om = 0;
     for (int k = 0; k < nl; k++)
       if (a * px[cur][k] + b * py[cur][k] > c) om |= 1u << k;

@@ -842,14 +842,15 @@ int pot_mlp_features(pot_ctx* ctx, pot_mlp* mm, void* stream, int64_t n, const f
     box.lo[k] = (float)dom->lo[k];
     box.hi[k] = (float)dom->hi[k];
   }
-  // the positions and velocities the fluid step solves at (same advection rule)
+  // the positions and velocities the (first sub)step solves at (same
+  // advection rule, same step length)
+  const float dt = (float)(prm->substeps > 1 ? prm->dt / prm->substeps : prm->dt);
   note_launch();
-  k_advect_copy<<<blocks_for(n, 256), 256, 0, st>>>(n, pos, vel, mm->pos_tmp, mm->vel_adv,
-                                                     (float)prm->dt, box, (float)prm->wall_margin);
+  k_advect_copy<<<blocks_for(n, 256), 256, 0, st>>>(n, pos, vel, mm->pos_tmp, mm->vel_adv, dt, box,
+                                                     (float)prm->wall_margin);
   POT_CUDA(cudaGetLastError());
   POT_CHECK(grid_build<float>(ctx, st, n, mm->pos_tmp, psi, targets, dom));
-  POT_CHECK(mlp_features_sorted(ctx, mm, st, n, mm->vel_adv, psi, psi_old, (float)prm->dt, ctx->perm,
-                                feat));
+  POT_CHECK(mlp_features_sorted(ctx, mm, st, n, mm->vel_adv, psi, psi_old, dt, ctx->perm, feat));
   POT_CUDA(cudaStreamSynchronize(st));
   return POT_OK;
 }

@@ -277,10 +277,14 @@ int newton_solve(pot_ctx* ctx, cudaStream_t st, int64_t n, const T* pos, const d
   return status;
 }
 
+namespace {
+
+// One explicit step of length dt (Sec. 5): advect and clamp, Newton at the
+// new positions warm-started from psi, velocities from the centroids.
 template <typename T>
-int fluid_step(pot_ctx* ctx, cudaStream_t st, int64_t n, T* pos, T* vel, T* psi,
-               const double* targets, const pot_domain* dom, const pot_params* P,
-               pot_solve_stats* S) {
+int fluid_substep(pot_ctx* ctx, cudaStream_t st, int64_t n, T* pos, T* vel, T* psi,
+                  const double* targets, const pot_domain* dom, const pot_params* P, double dt,
+                  pot_solve_stats* S) {
   double t0 = now_ms();
   Box<T> box;
   for (int k = 0; k < 3; k++) {
@@ -288,7 +292,7 @@ int fluid_step(pot_ctx* ctx, cudaStream_t st, int64_t n, T* pos, T* vel, T* psi,
     box.hi[k] = (T)dom->hi[k];
   }
   note_launch();
-  k_advect<T><<<blocks_for(n, 256), 256, 0, st>>>(n, pos, vel, (T)P->dt, box, (T)P->wall_margin);
+  k_advect<T><<<blocks_for(n, 256), 256, 0, st>>>(n, pos, vel, (T)dt, box, (T)P->wall_margin);
   POT_CHECK(grid_build<T>(ctx, st, n, pos, psi, targets, dom));
   S->grid_builds++;
   ctx->work<T>().use_hint = true;  // security balls start from the last step's cells
@@ -296,7 +300,7 @@ int fluid_step(pot_ctx* ctx, cudaStream_t st, int64_t n, T* pos, T* vel, T* psi,
   if (sizeof(T) == 4 && P->warm_start && ctx->mlp) {
     float* prev = nullptr;
     POT_CHECK(mlp_warm_start(ctx, ctx->mlp, st, n, (const float*)vel, (const float*)psi,
-                             (float)P->dt, &prev));
+                             (float)dt, &prev));
     fallback = (const T*)prev;
   }
   int status = newton_sorted<T>(ctx, st, n, dom, P, S, fallback);
@@ -316,13 +320,55 @@ int fluid_step(pot_ctx* ctx, cudaStream_t st, int64_t n, T* pos, T* vel, T* psi,
     Work<T>& w = ctx->work<T>();
     note_launch();
     k_velocity<T><<<blocks_for(n, 256), 256, 0, st>>>(
-        n, ctx->perm, w.sxp, w.cen, w.psi_base, vel, psi, (T)P->dt, (T)(1.0 / (P->eps * P->eps)),
+        n, ctx->perm, w.sxp, w.cen, w.psi_base, vel, psi, (T)dt, (T)(1.0 / (P->eps * P->eps)),
         (T)P->gravity[0], (T)P->gravity[1], (T)P->gravity[2]);
     POT_CHECK(store_hint<T>(ctx, st, n));
   }
   POT_CUDA(cudaStreamSynchronize(st));
   S->status = status;
   S->ms_total = now_ms() - t0;
+  return status;
+}
+
+}  // namespace
+
+// P->substeps explicit steps of dt / substeps (at least one), stopping at
+// the first that fails; S sums the counts and times of the substeps and
+// keeps the largest start and final errors.
+template <typename T>
+int fluid_step(pot_ctx* ctx, cudaStream_t st, int64_t n, T* pos, T* vel, T* psi,
+               const double* targets, const pot_domain* dom, const pot_params* P,
+               pot_solve_stats* S) {
+  const int k = P->substeps > 1 ? P->substeps : 1;
+  if (k == 1) return fluid_substep<T>(ctx, st, n, pos, vel, psi, targets, dom, P, P->dt, S);
+  const double dt = P->dt / k;
+  pot_solve_stats acc = *S;
+  int status = POT_OK;
+  for (int i = 0; i < k && status == POT_OK; i++) {
+    pot_solve_stats s1;
+    memset(&s1, 0, sizeof(s1));
+    s1.error_site = -1;
+    status = fluid_substep<T>(ctx, st, n, pos, vel, psi, targets, dom, P, dt, &s1);
+    acc.newton_iters += s1.newton_iters;
+    acc.pcg_iters += s1.pcg_iters;
+    acc.halvings += s1.halvings;
+    acc.cell_evals += s1.cell_evals;
+    acc.grid_builds += s1.grid_builds;
+    acc.repairs += s1.repairs;
+    acc.passes += s1.passes;
+    acc.ms_total += s1.ms_total;
+    acc.ms_cells += s1.ms_cells;
+    acc.ms_pcg += s1.ms_pcg;
+    acc.err_start = i == 0 ? s1.err_start : fmax(acc.err_start, s1.err_start);
+    acc.err_max = i == 0 ? s1.err_max : fmax(acc.err_max, s1.err_max);
+    acc.err_l2 = i == 0 ? s1.err_l2 : fmax(acc.err_l2, s1.err_l2);
+    acc.nnz = s1.nnz;
+    acc.mlp_used |= s1.mlp_used;
+    acc.mlp_fallback |= s1.mlp_fallback;
+    if (s1.error_site >= 0) acc.error_site = s1.error_site;
+    acc.status = status;
+  }
+  *S = acc;
   return status;
 }
 

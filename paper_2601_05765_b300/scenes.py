@@ -98,6 +98,15 @@ def uniform_cloud(n: int = 1 << 20, seed: int = 1, subset: int = 10000,
                  extra={"subset": np.sort(sub).astype(np.int64), "R0": r0})
 
 
+# Dam break: fluid step dt = 2e-3; spring length eps = s / 8 keeps the
+# front (about 2 sqrt(g H) = 5.6 m/s for the 0.8 m column) below the
+# spring's signal speed s / eps, and each step is taken as substeps of about
+# eps / 2.
+DAM_DT = 2e-3
+DAM_EPS_PER_SPACING = 1.0 / 8.0
+DAM_RELAX_ROUNDS = 3
+
+
 def dam_break(nx: int = 63, ny: int = 63, nz: int = 126, width: float = 0.4,
               jitter: float = 0.3, seed: int = 2, fill: float = 0.9,
               r_factor: float = 0.8) -> Scene:
@@ -105,6 +114,8 @@ def dam_break(nx: int = 63, ny: int = 63, nz: int = 126, width: float = 0.4,
     [0,width]x[0,width*ny/nx]x[0,s*nz] (z up); nu = fill*s^3, psi0 as jittered_block.
 
     The defaults give 63x63x126 = 500,094 sites in a 0.4 x 0.4 x 0.8 column.
+    extra holds the recipe's step dt, spring length eps, substeps per step
+    and the rounds that move the sites to their cell centroids first.
     """
     rng = np.random.default_rng(seed)
     s = width / nx
@@ -115,9 +126,12 @@ def dam_break(nx: int = 63, ny: int = 63, nz: int = 126, width: float = 0.4,
     pos = ((lat + 0.5) + jit) * s
     nu = np.full(n, fill * s ** 3, dtype=np.float64)
     r = r_factor * _ball_radius_for_volume(nu)
+    eps = DAM_EPS_PER_SPACING * s
     return Scene(pos=pos.astype(np.float32), psi=(r * r).astype(np.float32), nu=nu,
                  vel=np.zeros((n, 3), np.float32), name=f"dam_break_{n}",
-                 extra={"spacing": s})
+                 extra={"spacing": s, "dt": DAM_DT, "eps": eps,
+                        "substeps": max(1, int(round(DAM_DT / (0.5 * eps)))),
+                        "relax_rounds": DAM_RELAX_ROUNDS})
 
 
 # Spring length and time step of the splash, in units of its lattice spacing

@@ -119,3 +119,33 @@ def test_fluid_step_matches_oracle(ctx, dtype):
     r = math.sqrt(float(psi0.max()))
     atol = 2e-3 / 1e-4 * r * (1e-9 if dtype == torch.float64 else 2e-3)
     np.testing.assert_allclose(gv, v1, rtol=0, atol=atol)
+
+
+def test_fluid_substeps_match_oracle_steps(ctx):
+    """substeps = 3 equals three oracle fluid steps of dt / 3 (FP64, solved
+    far below the tolerance), and the stats sum the substeps."""
+    sc = scenes.dam_break(nx=10, ny=10, nz=20, width=0.16, seed=5)
+    dev = ctx.device
+    r0 = O.newton(sc.pos.astype(np.float64), sc.nu, sc.psi.astype(np.float64), tol=1e-10)
+    x = sc.pos.astype(np.float64)
+    v = np.zeros_like(x)
+    v[:, 0] = 0.5
+    psi0 = r0.psi.copy()
+    pos, vel, psi = tens(x, torch.float64, dev), tens(v, torch.float64, dev), tens(psi0, torch.float64, dev)
+    prm = pot.default_params(tol=1e-10, dt=3e-3, eps=4e-3, substeps=3)
+    st = pot.pot_fluid_step(ctx, pos, vel, psi, tens(sc.nu, torch.float64, dev), params=prm)
+    assert st["status"] == 0 and st["grid_builds"] == 3 and st["err_max"] <= 1e-10
+    one = pot.pot_fluid_step(ctx, tens(x, torch.float64, dev), tens(v, torch.float64, dev),
+                             tens(psi0, torch.float64, dev), tens(sc.nu, torch.float64, dev),
+                             params=pot.default_params(tol=1e-10, dt=1e-3, eps=4e-3))
+    assert one["grid_builds"] == 1 and st["newton_iters"] >= one["newton_iters"]
+    p = psi0
+    for _ in range(3):
+        x, v, nr = O.fluid_step(x, v, p, sc.nu, dt=1e-3, eps=4e-3, tol=1e-11)
+        p = nr.psi
+    # positions take dt times velocities that carry the centroid error
+    np.testing.assert_allclose(pos.cpu().numpy(), x, rtol=0, atol=1e-11)
+    # velocity = dt/eps^2 * centroid offset, centroids agree to ~1e-9 r
+    r = math.sqrt(float(psi0.max()))
+    np.testing.assert_allclose(vel.cpu().numpy(), v, rtol=0, atol=3 * 1e-3 / 1.6e-5 * r * 1e-9)
+    np.testing.assert_allclose(psi.cpu().numpy(), p, rtol=0, atol=1e-8 * float(np.max(p)))
