@@ -50,11 +50,10 @@ sys.path.insert(0, ROOT)
 
 SMALL_SPACING = 0.032  # ~2000 sites with the splash recipe
 # FP32 FLOP executed (fadd + fmul + 2 ffma) and DRAM bytes per cell processed
-# by k_cells, from an ncu capture of the 536k-site splash at converged weights
-# (an earlier kernel version's count inside fluid steps agreed to 0.3 %);
-# profiles/k_cells_splash_converged.md
-K_CELLS_FLOP_PER_CELL = 15462.0
-K_CELLS_DRAM_BYTES_PER_CELL = 413.0
+# by k_cells, from an ncu capture of the splash recipe at 536k sites, step 30
+# (the bench's run in miniature); profiles/k_cells_splash_536k_step30.md
+K_CELLS_FLOP_PER_CELL = 10049.0
+K_CELLS_DRAM_BYTES_PER_CELL = 387.0
 
 
 def parse():
@@ -461,15 +460,18 @@ def run_cells(args):
 def run_warmstart(args):
     """Learned warm start against the plain start on the splash.
 
-    Training: plain-Newton fluid steps on dam-break columns (the dam-break
-    recipe at spacing 0.4/24, 24 x 24 x 48 sites, seeds 10-19, 40 steps of
-    dt 2e-3 each, every 2nd step 4096 sampled sites), Adam on the library's
-    tensor-core kernels.  Evaluation: after `warmup` plain steps, the same
-    `steps` splash steps from the same state with the plain start (previous
-    weights) and with the MLP start (its history seeded with the weights one
-    step earlier), both FP32 geometry with FP64 reductions at tol 1e-4; the
-    same comparison on a dam-break column of an unseen seed (in the training
-    distribution) is reported beside it."""
+    Training: plain-Newton fluid substeps on dam-break columns (the
+    dam-break recipe at spacing 0.4/24, 24 x 24 x 48 sites, seeds 10-19:
+    spring s/8, its 2e-3 steps as substeps, the first 40 steps, every 2nd
+    substep 4096 sampled sites), Adam on the library's tensor-core kernels.
+    Every sample is one substep: the model predicts the weights of the next
+    solve, which is what the fluid step asks it for.  Evaluation: after
+    `warmup` plain steps, the same `steps` splash steps from the same state
+    with the plain start (previous weights) and with the MLP start (its
+    history seeded with the weights one step earlier), both FP32 geometry
+    with FP64 reductions at tol 1e-4; the same comparison over substeps of a
+    dam-break column of an unseen seed (in the training distribution) is
+    reported beside it."""
     import torch
 
     from paper_2601_05765_b300 import pot, scenes
@@ -482,8 +484,14 @@ def run_warmstart(args):
     mlp = pot.Mlp(max(sc.n, 65536), 0)
     mlp.set_params(W.init_params(0, device=dev))
     xs, ys = [], []
+    def sub(scene):
+        e = scene.extra
+        return e["dt"] / e["substeps"], e["eps"], e["substeps"], e["relax_rounds"]
+
     for k, col in enumerate(cols):
-        x, y = W.collect(ctx_t, mlp, col, steps=40, every=2, per_sample=4096, seed=10 + k, dt=2e-3)
+        dts, eps, nsub, relax = sub(col)
+        x, y = W.collect(ctx_t, mlp, col, steps=40 * nsub, every=2, per_sample=4096, seed=10 + k,
+                         dt=dts, eps=eps, relax=relax)
         xs.append(x)
         ys.append(y)
     ctx_t.close()
@@ -519,7 +527,8 @@ def run_warmstart(args):
     # in distribution: a dam-break column of an unseen seed, 3x the sites
     dam = scenes.dam_break(nx=36, ny=36, nz=72, width=0.4, seed=20)
     ctx_d = pot.Context(dam.n, 246, 0, fp32=True, fp64=False)
-    held = both(ctx_d, dam, 2e-3, 12)
+    dts, eps_d, nsub_d, relax_d = sub(dam)
+    held = both(ctx_d, dam, dts, 12 * nsub_d, eps_d, relax_d)
     pot.set_warm_start(ctx_d, None)
     ctx_d.close()
     ctx = pot.Context(sc.n, 246, 0, fp32=True, fp64=False)
@@ -532,13 +541,15 @@ def run_warmstart(args):
                     f"FP64 reductions",
         "training": {"samples": int(x.shape[0]), "epochs": len(hist), "loss_first": hist[0],
                      "loss_last": hist[-1], "collect_s": t1 - t0, "train_s": t2 - t1,
-                     "scenes": "dam-break columns 24x24x48, seeds 10-19, 40 steps of dt 2e-3",
+                     "scenes": "dam-break columns 24x24x48, seeds 10-19, the substeps of their "
+                               "first 40 steps of 2e-3",
                      "extra_scenes": extra},
         "plain": plain, "mlp": learned,
         "newton_iters_saved": plain["newton_iters"] - learned["newton_iters"],
         "ms_saved_per_solve": plain["ms_total"] - learned["ms_total"],
         "holdout_dam_break": {"workload": f"dam-break column 36x36x72 ({dam.n} sites), seed 20, "
-                                          f"steps 12..{12 + args.steps - 1}, dt 2e-3",
+                                          f"substeps {12 * nsub_d}..{12 * nsub_d + args.steps - 1} "
+                                          f"of {dts:.3g}, eps {eps_d:.3g}",
                               "plain": held["plain"], "mlp": held["mlp"],
                               "newton_iters_saved": held["plain"]["newton_iters"] - held["mlp"]["newton_iters"],
                               "ms_saved_per_solve": held["plain"]["ms_total"] - held["mlp"]["ms_total"]}}))
