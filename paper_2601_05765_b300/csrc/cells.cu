@@ -377,39 +377,49 @@ __device__ Facet<T> facet_eval(const V4<T>* __restrict__ pl, int m, int fi, T ps
   const T ol = sqrt(ou * ou + ov * ov);
   const T far2 = (rho + ol) * (rho + ol) + on2;  // the circle's farthest point
   T rm2 = T(0);
-  auto sector = [&](T ax, T ay, T bx, T by) {
-    T cr = ax * by - ay * bx;
-    T dt = ax * bx + ay * by;
-    T phi = atan2(cr, dt);
+  // Each polygon edge p -> q splits at its crossings x1, x2 with the circle
+  // into an arc piece p -> x1 (a sector of the disk), the chord piece
+  // x1 -> x2 (a triangle with the disk centre) and an arc piece x2 -> q;
+  // pieces that do not occur (real == false) add exact zeros.  Every lane
+  // runs all three pieces of each edge, so the lanes of a warp do not
+  // diverge on which pieces their edges have.
+  auto sector = [&](T ax, T ay, T bx, T by, bool real) {
+    const T cr = real ? ax * by - ay * bx : T(0);
+    const T dt = ax * bx + ay * by;
+    const T phi = atan2(cr, dt);
     area += T(0.5) * rho2 * phi;
     omg += phi * sect_om;
-    T na = sqrt(ax * ax + ay * ay), nb = sqrt(bx * bx + by * by);
-    if (na > T(0) && nb > T(0)) {
-      mx += rho3 * (by / nb - ay / na);
-      my += rho3 * (ax / na - bx / nb);
-      if (!want_extent) return;
-      // the arc from direction a to direction b: its end points, and the
-      // circle's farthest point from the centre when it lies on the arc
-      const T ex = rho * ax / na - ou, ey = rho * ay / na - ov;
-      const T fx = rho * bx / nb - ou, fy = rho * by / nb - ov;
-      rm2 = fmax(rm2, fmax(ex * ex + ey * ey, fx * fx + fy * fy) + on2);
-      if (ol > T(0)) {
-        const T gx = -ou, gy = -ov;  // direction of the farthest point
-        const T c1 = ax * gy - ay * gx, c2 = gx * by - gy * bx;
-        const bool half = dt < T(0) && fabs(cr) <= T(1e-6) * na * nb;
-        if (half || (cr >= T(0) ? (c1 >= T(0) && c2 >= T(0)) : (c1 <= T(0) && c2 <= T(0))))
-          rm2 = fmax(rm2, far2);
-      }
-    } else if (want_extent) {
+    const T na = sqrt(ax * ax + ay * ay), nb = sqrt(bx * bx + by * by);
+    const bool dirs = na > T(0) && nb > T(0);
+    const T ina = dirs ? T(1) / na : T(0), inb = dirs ? T(1) / nb : T(0);
+    if (real && dirs) {
+      mx += rho3 * (by * inb - ay * ina);
+      my += rho3 * (ax * ina - bx * inb);
+    }
+    if (!want_extent || !real) return;
+    if (!dirs) {
       rm2 = fmax(rm2, far2);
+      return;
+    }
+    // the arc from direction a to direction b: its end points, and the
+    // circle's farthest point from the centre when it lies on the arc
+    const T ex = rho * ax * ina - ou, ey = rho * ay * ina - ov;
+    const T fx = rho * bx * inb - ou, fy = rho * by * inb - ov;
+    rm2 = fmax(rm2, fmax(ex * ex + ey * ey, fx * fx + fy * fy) + on2);
+    if (ol > T(0)) {
+      const T gx = -ou, gy = -ov;  // direction of the farthest point
+      const T c1 = ax * gy - ay * gx, c2 = gx * by - gy * bx;
+      const bool half = dt < T(0) && fabs(cr) <= T(1e-6) * na * nb;
+      if (half || (cr >= T(0) ? (c1 >= T(0) && c2 >= T(0)) : (c1 <= T(0) && c2 <= T(0))))
+        rm2 = fmax(rm2, far2);
     }
   };
-  auto tri = [&](T ax, T ay, T bx, T by) {
-    T cr = ax * by - ay * bx;
-    T dt = ax * bx + ay * by;
-    T la = sqrt(ax * ax + ay * ay + h2), lb = sqrt(bx * bx + by * by + h2);
-    T den = la * lb + ah * (la + lb) + dt + h2;
-    T ta = T(0.5) * cr;
+  auto tri = [&](T ax, T ay, T bx, T by, bool real) {
+    const T cr = real ? ax * by - ay * bx : T(0);
+    const T dt = ax * bx + ay * by;
+    const T la = sqrt(ax * ax + ay * ay + h2), lb = sqrt(bx * bx + by * by + h2);
+    const T den = la * lb + ah * (la + lb) + dt + h2;
+    const T ta = T(0.5) * cr;
     area += ta;
     omg += sg * T(2) * atan2(cr, den);
     mx += ta * (ax + bx) * T(1.0 / 3.0);
@@ -428,31 +438,25 @@ __device__ Facet<T> facet_eval(const V4<T>* __restrict__ pl, int m, int fi, T ps
     T a2 = dx * dx + dy * dy;
     if (a2 == T(0)) continue;
     T b2 = pxk * dx + pyk * dy;
-    T c2 = pxk * pxk + pyk * pyk - rho2;
+    T c2 = pk2 - rho2;
     T disc = b2 * b2 - a2 * c2;
-    if (disc <= T(0)) {
-      sector(pxk, pyk, qx, qy);
-      arc = true;
-      continue;
+    // no crossing: the whole edge is an arc piece (t1 = t2 = 1)
+    T t1 = T(1), t2 = T(1);
+    if (disc > T(0)) {
+      const T sq = sqrt(disc);
+      t1 = fmin(fmax((-b2 - sq) / a2, T(0)), T(1));
+      t2 = fmin(fmax((-b2 + sq) / a2, T(0)), T(1));
     }
-    T sq = sqrt(disc);
-    T t1 = (-b2 - sq) / a2, t2 = (-b2 + sq) / a2;
-    t1 = fmin(fmax(t1, T(0)), T(1));
-    t2 = fmin(fmax(t2, T(0)), T(1));
     // a clamped crossing is the vertex itself, exactly
     T x1 = t1 == T(0) ? pxk : (t1 == T(1) ? qx : pxk + t1 * dx);
     T y1 = t1 == T(0) ? pyk : (t1 == T(1) ? qy : pyk + t1 * dy);
     T x2 = t2 == T(0) ? pxk : (t2 == T(1) ? qx : pxk + t2 * dx);
     T y2 = t2 == T(0) ? pyk : (t2 == T(1) ? qy : pyk + t2 * dy);
-    if (t1 > T(0)) {
-      sector(pxk, pyk, x1, y1);
-      arc = true;
-    }
-    if (t2 > t1) tri(x1, y1, x2, y2);
-    if (t2 < T(1)) {
-      sector(x2, y2, qx, qy);
-      arc = true;
-    }
+    const bool s1 = t1 > T(0), s2 = t2 < T(1);
+    sector(pxk, pyk, x1, y1, s1);
+    tri(x1, y1, x2, y2, t2 > t1);
+    sector(x2, y2, qx, qy, s2);
+    arc = arc || s1 || s2;
   }
   out.rm2 = rm2;
   out.arc = arc && area > T(0);
