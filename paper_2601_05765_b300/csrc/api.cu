@@ -220,6 +220,10 @@ int pot_destroy(pot_ctx* ctx) {
                   ctx->red_out,  ctx->pcg_red, ctx->pcg_ctl,  ctx->err, ctx->need, ctx->need_count, ctx->big_list};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  for (int k = 0; k < 2; k++) {
+    if (ctx->pcg_exec[k]) cudaGraphExecDestroy(ctx->pcg_exec[k]);
+    if (ctx->pcg_graph[k]) cudaGraphDestroy(ctx->pcg_graph[k]);
+  }
   free_work(ctx->wf);
   free_work(ctx->wd);
   if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);

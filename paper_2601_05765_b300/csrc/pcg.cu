@@ -11,8 +11,17 @@
 // then over blocks by the last block to finish (an arrival counter after a
 // memory fence), which adds the block partials in index order and publishes
 // the scalars and the decisions (converged, breakdown) for the next kernel.
-// The result is deterministic and no block re-reads all partials.  The
-// host checks the done flag once per chunk of iterations.
+// The result is deterministic and no block re-reads all partials.
+//
+// The iterations run as a CUDA graph: a while node whose body is the two
+// kernels, built once per context, precision and row count (the tolerance
+// and iteration cap live in device memory, set by k_pcg_init).  Thread 0 of
+// k_update's block 0 alone ends the loop (cudaGraphSetConditional): when an
+// earlier kernel has set the done flag, or when its own trip counter passes
+// the cap + 1, so the loop ends even if the done flag were never set.  The
+// host waits once per solve.  Without the graph (its construction failed)
+// the same kernels run in chunks from the host, which checks the done flag
+// once per chunk.
 #include "pot_internal.cuh"
 
 namespace pot {
@@ -23,9 +32,9 @@ constexpr int kTpr = 2;  // threads per CSR row (about 10 entries per row)
 
 // partial-sum arrays (nb doubles each) and scalars at the end of pcg_red
 enum { kPartA = 0, kPartB = 1, kPartC = 2, kParts = 3 };
-enum { kRZ = 0, kRZP = 1, kPQ = 2, kRR = 3, kRR0 = 4, kScalars = 8 };
-// control words
-enum { kDone = 0, kIt = 1, kBreak = 2, kIters = 3, kArrive = 4 };
+enum { kRZ = 0, kRZP = 1, kPQ = 2, kRR = 3, kRR0 = 4, kRtol2 = 5, kScalars = 8 };
+// control words (ctx->pcg_ctl holds 8)
+enum { kDone = 0, kIt = 1, kBreak = 2, kIters = 3, kArrive = 4, kTrips = 5, kMaxIt = 6 };
 
 // Block sum of v (fixed shape) into thread 0's return value.
 __device__ __forceinline__ double block_sum(double v) {
@@ -93,14 +102,16 @@ __global__ void __launch_bounds__(kPcgThreads)
       scal[kRZP] = 1.0;
       scal[kRR] = trr;
       scal[kRR0] = trr;
+      scal[kRtol2] = rtol2;
       ctl[kIt] = 0;
       ctl[kBreak] = 0;
       ctl[kIters] = 0;
+      ctl[kTrips] = 0;
+      ctl[kMaxIt] = max_iter;
       ctl[kDone] = (trr <= 0.0 || max_iter <= 0) ? 1 : 0;
       ctl[kArrive] = 0;
     }
   }
-  (void)rtol2;
 }
 
 template <typename T>
@@ -154,12 +165,20 @@ __global__ void __launch_bounds__(kPcgThreads)
   }
 }
 
-template <typename T>
+template <typename T, bool kGraph>
 __global__ void __launch_bounds__(kPcgThreads)
     k_update(int64_t n, const T* __restrict__ diag, T* x, T* r, T* z, const T* __restrict__ pa,
              const T* __restrict__ pb, const T* __restrict__ q, double* part, double* scal,
-             int nb, int32_t* ctl, double rtol2, int max_iter) {
+             int nb, int32_t* ctl, cudaGraphConditionalHandle loop) {
+  if (kGraph && blockIdx.x == 0 && threadIdx.x == 0) {
+    // the only writer of the loop condition and of the trip counter
+    const int trips = ctl[kTrips] + 1;
+    ctl[kTrips] = trips;
+    if (ctl[kDone] || trips > ctl[kMaxIt] + 1) cudaGraphSetConditional(loop, 0u);
+  }
   if (ctl[kDone]) return;
+  const double rtol2 = scal[kRtol2];
+  const int max_iter = ctl[kMaxIt];
   const int it = ctl[kIt];
   const T alpha = (T)(scal[kRZ] / scal[kPQ]);
   const T* __restrict__ p = (it & 1) ? pa : pb;
@@ -196,6 +215,64 @@ __global__ void __launch_bounds__(kPcgThreads)
 int pcg_blocks(int sm_count) { return sm_count * kPcgMaxBlocksPerSm; }
 size_t pcg_red_len(int sm_count) { return (size_t)kParts * pcg_blocks(sm_count) + kScalars; }
 
+namespace {
+
+// The while-node graph of the PCG iterations for n rows (see the top).
+template <typename T>
+int build_graph(pot_ctx* ctx, int64_t n, int nb, double* part, double* scal) {
+  const int k = sizeof(T) == 4 ? 0 : 1;
+  if (ctx->pcg_exec[k]) cudaGraphExecDestroy(ctx->pcg_exec[k]);
+  if (ctx->pcg_graph[k]) cudaGraphDestroy(ctx->pcg_graph[k]);
+  ctx->pcg_exec[k] = nullptr;
+  ctx->pcg_graph[k] = nullptr;
+  ctx->pcg_graph_n[k] = -1;
+  Work<T>& w = ctx->work<T>();
+  cudaGraph_t g = nullptr;
+  POT_CUDA(cudaGraphCreate(&g, 0));
+  ctx->pcg_graph[k] = g;
+  cudaGraphConditionalHandle loop;
+  POT_CUDA(cudaGraphConditionalHandleCreate(&loop, g, 1u, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = loop;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cnode;
+  POT_CUDA(cudaGraphAddNode(&cnode, g, nullptr, nullptr, 0, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  // kernel arguments (copied into the graph when the nodes are added)
+  int64_t an = n;
+  const int32_t* row_ptr = ctx->row_ptr;
+  const int32_t* cols = ctx->csr_cols;
+  const T* vals = w.csr_vals;
+  const T* diag = w.diag;
+  const T* zc = w.z;
+  T *x = w.u, *r = w.r, *z = w.z, *pa = w.p0, *pb = w.p1, *q = w.q;
+  const T *pac = w.p0, *pbc = w.p1, *qc = w.q;
+  int anb = nb;
+  int32_t* ctl = ctx->pcg_ctl;
+  void* a1[] = {&an, &row_ptr, &cols, &vals, &diag, &zc, &pa, &pb, &q, &part, &scal, &anb, &ctl};
+  cudaKernelNodeParams k1 = {};
+  k1.func = (void*)k_spmv<T>;
+  k1.gridDim = dim3(nb);
+  k1.blockDim = dim3(kPcgThreads);
+  k1.kernelParams = a1;
+  cudaGraphNode_t n1, n2;
+  POT_CUDA(cudaGraphAddKernelNode(&n1, body, nullptr, 0, &k1));
+  void* a2[] = {&an, &diag, &x, &r, &z, &pac, &pbc, &qc, &part, &scal, &anb, &ctl, &loop};
+  cudaKernelNodeParams k2 = {};
+  k2.func = (void*)k_update<T, true>;
+  k2.gridDim = dim3(nb);
+  k2.blockDim = dim3(kPcgThreads);
+  k2.kernelParams = a2;
+  POT_CUDA(cudaGraphAddKernelNode(&n2, body, &n1, 1, &k2));
+  POT_CUDA(cudaGraphInstantiate(&ctx->pcg_exec[k], g, 0));
+  ctx->pcg_graph_n[k] = n;
+  return POT_OK;
+}
+
+}  // namespace
+
 template <typename T>
 int pcg_solve(pot_ctx* ctx, cudaStream_t st, int64_t n, int64_t nnz_off, double rtol, int max_iter,
               int chunk, int* iters, double* rel_res) {
@@ -218,22 +295,38 @@ int pcg_solve(pot_ctx* ctx, cudaStream_t st, int64_t n, int64_t nnz_off, double 
   note_launch();
   k_pcg_init<T><<<nb, kPcgThreads, 0, st>>>(n, ctx->grad, w.diag, w.u, w.r, w.z, w.p0, part, scal,
                                             nb, ctx->pcg_ctl, rtol2, max_iter);
-  int launched = 0;
+  POT_CUDA(cudaGetLastError());
   int32_t* hctl = (int32_t*)(ctx->h_pinned + 16);
-  for (;;) {
-    for (int k = 0; k < chunk; k++) {
-      note_launch();
-      k_spmv<T><<<nb, kPcgThreads, 0, st>>>(n, ctx->row_ptr, ctx->csr_cols, w.csr_vals, w.diag,
-                                            w.z, w.p0, w.p1, w.q, part, scal, nb, ctx->pcg_ctl);
-      note_launch();
-      k_update<T><<<nb, kPcgThreads, 0, st>>>(n, w.diag, w.u, w.r, w.z, w.p0, w.p1, w.q, part,
-                                              scal, nb, ctx->pcg_ctl, rtol2, max_iter);
-    }
-    launched += chunk;
-    POT_CUDA(cudaGetLastError());
-    POT_CUDA(cudaMemcpyAsync(hctl, ctx->pcg_ctl, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  const int gk = sizeof(T) == 4 ? 0 : 1;
+  bool graph = ctx->pcg_exec[gk] && ctx->pcg_graph_n[gk] == n;
+  if (!graph) {
+    graph = build_graph<T>(ctx, n, nb, part, scal) == POT_OK;
+    if (!graph) cudaGetLastError();  // clear it: the chunked loop below runs instead
+  }
+  if (graph) {
+    POT_CUDA(cudaGraphLaunch(ctx->pcg_exec[gk], st));
+    POT_CUDA(cudaMemcpyAsync(hctl, ctx->pcg_ctl, 8 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     POT_CUDA(cudaStreamSynchronize(st));
-    if (hctl[kDone] || launched > max_iter + chunk) break;
+    // launches: the kernels of every trip of the loop
+    note_launches(2 * (int64_t)hctl[kTrips]);
+  } else {
+    int launched = 0;
+    for (;;) {
+      for (int k = 0; k < chunk; k++) {
+        note_launch();
+        k_spmv<T><<<nb, kPcgThreads, 0, st>>>(n, ctx->row_ptr, ctx->csr_cols, w.csr_vals, w.diag,
+                                              w.z, w.p0, w.p1, w.q, part, scal, nb, ctx->pcg_ctl);
+        note_launch();
+        k_update<T, false><<<nb, kPcgThreads, 0, st>>>(n, w.diag, w.u, w.r, w.z, w.p0, w.p1, w.q,
+                                                       part, scal, nb, ctx->pcg_ctl,
+                                                       cudaGraphConditionalHandle{});
+      }
+      launched += chunk;
+      POT_CUDA(cudaGetLastError());
+      POT_CUDA(cudaMemcpyAsync(hctl, ctx->pcg_ctl, 8 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+      POT_CUDA(cudaStreamSynchronize(st));
+      if (hctl[kDone] || launched > max_iter + chunk) break;
+    }
   }
   *iters = hctl[kDone] ? hctl[kIters] : hctl[kIt];
   if (rel_res) *rel_res = -1.0;

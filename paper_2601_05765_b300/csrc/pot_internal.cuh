@@ -197,6 +197,11 @@ struct pot_ctx {
   double* red_out = nullptr;      // reduction results (device)
   double* pcg_red = nullptr;      // PCG reduction partials
   int32_t* pcg_ctl = nullptr;     // PCG control words
+  // PCG iteration loop as a CUDA graph with a device-side while node, one
+  // per precision ([0] float, [1] double), built for pcg_graph_n rows
+  cudaGraph_t pcg_graph[2] = {nullptr, nullptr};
+  cudaGraphExec_t pcg_exec[2] = {nullptr, nullptr};
+  int64_t pcg_graph_n[2] = {-1, -1};
   int32_t* err = nullptr;         // device status words
   uint8_t* need = nullptr;        // per cell: still to be (re)built in this evaluation
   int32_t* need_count = nullptr;  // device counters: cells to rebuild, big cells listed
@@ -235,6 +240,7 @@ namespace pot {
 // kernel launches issued by this library in this process (pot_kernel_launches)
 extern std::atomic<long long> g_launches;
 inline void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+inline void note_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 inline int blocks_for(int64_t n, int threads) { return (int)((n + threads - 1) / threads); }
 
