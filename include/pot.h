@@ -285,7 +285,7 @@ int pot_fluid_step_f64(pot_ctx* ctx, void* stream, int64_t n, double* pos, doubl
 
 /* A small MLP predicts each site's new weight from its neighbourhood:
  * inputs (80 BF16 values per site, row-major): offsets to the up to 24
- * nearest other sites closer than 2 sqrt(max psi), by increasing distance,
+ * nearest other sites closer than 2 h, by increasing distance,
  * divided by h = nu^(1/3) (zero-padded); psi_prev / h^2; v dt / h; the
  * previous weight change (psi_prev - psi_old) / h^2 (0 without history);
  * 3 zeros.

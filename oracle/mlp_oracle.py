@@ -121,21 +121,20 @@ def init_params(seed=0):
 
 def knn_features(pos, psi_prev, vel, nu, dt, radius=None, psi_old=None):
     """Features of every site, brute force: offsets to the (up to) 24 nearest
-    other sites closer than `radius` (default 2 sqrt(max psi_prev)), by
-    increasing distance, over h = nu^(1/3), zero-padded; psi_prev / h^2;
-    vel * dt / h; (psi_prev - psi_old) / h^2 (0 when psi_old is None);
-    3 zeros.  (n, 80) float64."""
+    other sites closer than `radius` (default 2 h_i), by increasing
+    distance, over h = nu^(1/3), zero-padded; psi_prev / h^2; vel * dt / h;
+    (psi_prev - psi_old) / h^2 (0 when psi_old is None); 3 zeros.
+    (n, 80) float64."""
     pos = np.asarray(pos, np.float64)
     n = pos.shape[0]
     h = np.cbrt(np.asarray(nu, np.float64))
-    if radius is None:
-        radius = 2.0 * np.sqrt(max(float(np.max(psi_prev)), 0.0))
     F = np.zeros((n, N_IN))
     for i in range(n):
+        rad = 2.0 * h[i] if radius is None else radius
         d = pos - pos[i]
         d2 = np.sum(d * d, 1)
         d2[i] = np.inf
-        d2[d2 >= radius * radius] = np.inf
+        d2[d2 >= rad * rad] = np.inf
         order = np.argsort(d2, kind="stable")[:N_KNN]
         order = order[np.isfinite(d2[order])]
         off = d[order] / h[i]

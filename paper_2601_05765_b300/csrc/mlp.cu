@@ -244,6 +244,134 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm(GemmArgs g) {
 }
 
 // ---------------------------------------------------------------------------
+// fused inference: the three layers and the head of one 128-row tile in one
+// CTA.  The tile's activations never leave the SM: each layer's epilogue
+// (bias + ReLU + BF16, the same roundings as the layer-by-layer path) writes
+// them into shared memory in the core-matrix layout as the next layer's A
+// operand, while the next weight matrix is staged into the B buffer.  One
+// 128x128 FP32 accumulator in TMEM serves all three layers.
+
+constexpr int kFusedSmem = 2 * kTM * kHid * 2 + 1024 + 64;
+
+// rows [row0, row0+128) x k [0, K) of a K-contiguous matrix (K a multiple
+// of 8) into the core-matrix layout with K/8 core matrices per 8-row group
+// (zero rows past nrows)
+__device__ __forceinline__ void stage_k(uint8_t* s, const bf16* src, int64_t ld, int64_t row0,
+                                        int64_t nrows, int K) {
+  const int kc8 = K / 8;
+  for (int q = threadIdx.x; q < kTM * kc8; q += kGemmThreads) {
+    const int r = q / kc8, kc = q - r * kc8;
+    const int64_t gr = row0 + r;
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (gr < nrows) v = *(const uint4*)(src + gr * ld + kc * 8);
+    *(uint4*)(s + ((r >> 3) * kc8 + kc) * 128 + (r & 7) * 16) = v;
+  }
+}
+
+// issue K/16 MMAs (A, B in the layout of stage_k) into tmem, then commit to
+// mbar; thread 0 only
+__device__ __forceinline__ void issue_layer(uint32_t tmem, uint8_t* sA, uint8_t* sB, int K,
+                                            uint64_t* mbar) {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t sbo = (uint32_t)(K / 8) * 128;
+  for (int j = 0; j < K / 16; j++) {
+    const uint64_t da = umma_desc(smem_u32(sA) + j * 256, 128, sbo);
+    const uint64_t db = umma_desc(smem_u32(sB) + j * 256, 128, sbo);
+    umma(tmem, da, db, j == 0 ? 0u : 1u);
+  }
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(mbar))
+      : "memory");
+}
+
+__global__ void __launch_bounds__(kGemmThreads) k_mlp_infer(const bf16* __restrict__ x, int64_t M,
+                                                            const bf16* __restrict__ wt1,
+                                                            const bf16* __restrict__ wt2,
+                                                            const bf16* __restrict__ wt3,
+                                                            const float* __restrict__ p,
+                                                            float* __restrict__ out, int32_t* err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sA = base;
+  uint8_t* sB = base + kTM * kHid * 2;
+  uint64_t* mbar = (uint64_t*)(sB + kTM * kHid * 2);
+  uint32_t* tslot = (uint32_t*)(mbar + 1);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int64_t row0 = (int64_t)blockIdx.x * kTM;
+
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tslot)),
+                 "r"(kTM));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::);
+  }
+  // layer 1 operands: the input tile (K = 80) and W1 (128 x 80)
+  stage_k(sA, x, kIn, row0, M, kIn);
+  stage_k(sB, wt1, kIn, 0, kHid, kIn);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+  const uint32_t trow = (uint32_t)(warp * 32) << 16;  // this warp's 32 TMEM lanes
+  const int r = tid;                                   // the tile row of this thread
+  const int64_t grow = row0 + r;
+
+  uint32_t phase = 0;
+  bool ok = true;
+  float acc = 0.f;
+  for (int layer = 0; layer < 3 && ok; layer++) {
+    if (tid == 0) issue_layer(tmem, sA, sB, layer == 0 ? kIn : kHid, mbar);
+    ok = __syncthreads_and(mbar_wait(mbar, phase)) != 0;
+    phase ^= 1u;
+    if (!ok) break;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const float* bias = p + (layer == 0 ? ob1 : (layer == 1 ? ob2 : ob3));
+    // the MMAs are done with sA and sB: the next weights go into sB while
+    // the activations go into sA (K = 128 layout)
+    if (layer < 2) stage_k(sB, layer == 0 ? wt2 : wt3, kHid, 0, kHid, kHid);
+    for (int c0 = 0; c0 < kHid; c0 += 16) {
+      float v[16];
+      tmem_ld16(tmem + trow + (uint32_t)c0, v);
+      __align__(16) bf16 hb[16];
+#pragma unroll
+      for (int k = 0; k < 16; k++) {
+        hb[k] = __float2bfloat16_rn(fmaxf(v[k] + bias[c0 + k], 0.f));
+        if (layer == 2) acc += __bfloat162float(hb[k]) * p[ow4 + c0 + k];
+      }
+      if (layer < 2) {
+        const int kc = c0 / 8;
+        uint8_t* d0 = sA + ((r >> 3) * (kHid / 8) + kc) * 128 + (r & 7) * 16;
+        *(uint4*)d0 = *(const uint4*)&hb[0];
+        *(uint4*)(d0 + 128) = *(const uint4*)&hb[8];
+      }
+    }
+    // every thread's TMEM reads and shared-memory writes complete before
+    // the next layer's MMAs read sA / sB and overwrite the accumulator
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+  }
+  if (ok) {
+    if (grow < M) out[grow] = acc + p[ob4];
+  } else {
+    // report, then give the MMAs in flight one more bounded wait before the
+    // tensor memory is freed
+    if (tid == 0) atomicExch(&err[kErrCode], POT_ERR_CUDA);
+    mbar_wait(mbar, phase ^ 1u);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTM));
+}
+
+// ---------------------------------------------------------------------------
 // kNN features
 
 __device__ __forceinline__ int fcell(float x, float lo, float inv, int dim) {
@@ -251,76 +379,156 @@ __device__ __forceinline__ int fcell(float x, float lo, float inv, int dim) {
   return f < 0.f ? 0 : (f >= (float)dim ? dim - 1 : (int)f);
 }
 
-// one thread per site (sorted order): the (up to) 24 nearest other sites with
-// |d| < 2 sqrt(psi_max), offsets / h by increasing distance; psi / h^2;
-// v dt / h; the previous weight change / h^2 (0 without history); zero
-// padding to 80.  feat row = out_perm ? out_perm[s] : s.
-__global__ void __launch_bounds__(128)
+constexpr int kFeatWarps = 8;   // sites per block of k_features (one warp each)
+constexpr int kCandCap = 128;   // candidate buffer of a warp
+
+// Rank of candidate c among the first m of (d, t): the number that come
+// before it in increasing distance, ties by lower sorted index (unique).
+__device__ __forceinline__ int cand_rank(const float* d, const int* t, int m, float dc, int tc) {
+  int rank = 0;
+  for (int o = 0; o < m; o++) rank += (d[o] < dc) || (d[o] == dc && t[o] < tc);
+  return rank;
+}
+
+// One warp per site (sorted order): the (up to) 24 nearest other sites with
+// |d| < 2 h (h = nu^(1/3)), offsets / h by increasing distance (ties by
+// lower sorted index); psi / h^2; v dt / h; the previous weight change / h^2
+// (0 without history); zero padding to 80.  feat row = out_perm ? out_perm[s]
+// : s.  The lanes share the scan of the grid cells that meet the ball of
+// radius 2 h (per (y, z) row, the run of cells within the ball's chord);
+// sites inside the ball go to a shared buffer, which is cut back to its 24
+// nearest whenever it would overflow; the final 24 are placed by their rank.
+// The row is assembled in shared memory and written as ten 16-byte stores
+// (2-byte stores when feat is not 16-byte aligned).
+__global__ void __launch_bounds__(kFeatWarps * 32)
     k_features(int64_t n, const V4<float>* __restrict__ sxp, const int32_t* __restrict__ cell_start,
-               GridParams<float> g, const float* __restrict__ psi_max,
-               const float* __restrict__ vel_s, const float* __restrict__ dpsi_s,
-               const double* __restrict__ snu, float dt, const int32_t* __restrict__ out_perm,
-               bf16* feat) {
-  int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= n) return;
+               GridParams<float> g, const float* __restrict__ vel_s,
+               const float* __restrict__ dpsi_s, const double* __restrict__ snu, float dt,
+               const int32_t* __restrict__ out_perm, bf16* feat) {
+  __shared__ float s_d[kFeatWarps][kCandCap];
+  __shared__ int s_t[kFeatWarps][kCandCap];
+  __shared__ float s_kd[kFeatWarps][kKnn];
+  __shared__ int s_kt[kFeatWarps][kKnn];
+  __shared__ __align__(16) bf16 s_row[kFeatWarps][kIn];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t s = (int64_t)blockIdx.x * kFeatWarps + wid;
+  if (s >= n) return;  // the whole warp
+  float* cd = s_d[wid];
+  int* ct = s_t[wid];
   const V4<float> p = sxp[s];
-  const float R = 2.f * sqrtf(fmaxf(*psi_max, 0.f));
+  const float h = (float)cbrt(snu[s]);
+  const float ih = 1.f / h;
+  const float R = 2.f * h;
   const float R2 = R * R;
-  float bd[kKnn];
-  int bi[kKnn];
-  int cnt = 0;
-  const int cx = fcell(p.x, g.lo[0], g.inv_cs, g.dim[0]);
-  const int cy = fcell(p.y, g.lo[1], g.inv_cs, g.dim[1]);
-  const int cz = fcell(p.z, g.lo[2], g.inv_cs, g.dim[2]);
-  for (int z = cz - 1; z <= cz + 1; z++) {
-    if (z < 0 || z >= g.dim[2]) continue;
-    for (int y = cy - 1; y <= cy + 1; y++) {
-      if (y < 0 || y >= g.dim[1]) continue;
-      const int x0 = cx > 0 ? cx - 1 : 0, x1 = cx + 1 < g.dim[0] ? cx + 1 : g.dim[0] - 1;
+  const float pc[3] = {p.x, p.y, p.z};
+  int c0[3], c1[3];
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    c0[k] = fcell(pc[k] - R, g.lo[k], g.inv_cs, g.dim[k]);
+    c1[k] = fcell(pc[k] + R, g.lo[k], g.inv_cs, g.dim[k]);
+  }
+  // squared distance from p to the slab of cell c along axis k (0 inside;
+  // the outermost cells reach to infinity)
+  auto slab = [&](int k, int c) {
+    const float lo = g.lo[k] + c * g.cs;
+    float e = fmaxf(0.f, fmaxf(lo - pc[k], pc[k] - (lo + g.cs)));
+    if (c == 0 && pc[k] < lo) e = 0.f;
+    if (c == g.dim[k] - 1 && pc[k] > lo) e = 0.f;
+    return e * e;
+  };
+  // keep the kKnn nearest of the m buffered candidates at the front
+  auto cut = [&](int m) {
+    for (int c = lane; c < m; c += 32) {
+      const float dc = cd[c];
+      const int tc = ct[c];
+      const int rank = cand_rank(cd, ct, m, dc, tc);
+      if (rank < kKnn) {
+        s_kd[wid][rank] = dc;
+        s_kt[wid][rank] = tc;
+      }
+    }
+    __syncwarp();
+    if (lane < kKnn) {
+      cd[lane] = s_kd[wid][lane];
+      ct[lane] = s_kt[wid][lane];
+    }
+    __syncwarp();
+  };
+  const unsigned below = (1u << lane) - 1u;
+  int m = 0;  // buffered candidates (the same in every lane)
+  for (int z = c0[2]; z <= c1[2]; z++) {
+    const float ez = slab(2, z);
+    if (ez >= R2) continue;
+    for (int y = c0[1]; y <= c1[1]; y++) {
+      const float eyz = ez + slab(1, y);
+      if (eyz >= R2) continue;
+      const float rx = sqrtf(R2 - eyz);
+      const int x0 = fcell(p.x - rx, g.lo[0], g.inv_cs, g.dim[0]);
+      const int x1 = fcell(p.x + rx, g.lo[0], g.inv_cs, g.dim[0]);
       const int key0 = (z * g.dim[1] + y) * g.dim[0];
       const int a = cell_start[key0 + x0], b = cell_start[key0 + x1 + 1];
-      for (int t = a; t < b; t++) {
-        if (t == s) continue;
-        const V4<float> q = sxp[t];
-        const float dx = q.x - p.x, dy = q.y - p.y, dz = q.z - p.z;
-        const float d2 = dx * dx + dy * dy + dz * dz;
-        if (!(d2 < R2)) continue;
-        if (cnt == kKnn && !(d2 < bd[kKnn - 1])) continue;
-        // insertion (ties keep the lower sorted index first: t ascends)
-        int j = cnt < kKnn ? cnt : kKnn - 1;
-        while (j > 0 && bd[j - 1] > d2) {
-          bd[j] = bd[j - 1];
-          bi[j] = bi[j - 1];
-          j--;
+      for (int t0 = a; t0 < b; t0 += 32) {
+        const int t = t0 + lane;
+        float d2 = 0.f;
+        bool in = false;
+        if (t < b && t != s) {
+          const V4<float> q = sxp[t];
+          const float dx = q.x - p.x, dy = q.y - p.y, dz = q.z - p.z;
+          d2 = dx * dx + dy * dy + dz * dz;
+          in = d2 < R2;
         }
-        bd[j] = d2;
-        bi[j] = t;
-        if (cnt < kKnn) cnt++;
+        const unsigned bal = __ballot_sync(kFull, in);
+        const int nb = __popc(bal);
+        if (nb == 0) continue;
+        if (m + nb > kCandCap) {
+          cut(m);
+          m = kKnn;
+        }
+        if (in) {
+          const int at = m + __popc(bal & below);
+          cd[at] = d2;
+          ct[at] = t;
+        }
+        m += nb;
+        __syncwarp();
       }
     }
   }
-  const float h = (float)cbrt(snu[s]);
-  const float ih = 1.f / h;
-  const int64_t row = out_perm ? (int64_t)out_perm[s] : s;
-  bf16* f = feat + row * kIn;
-  for (int k = 0; k < kKnn; k++) {
+  // the kKnn nearest in increasing order
+  const int cnt = m < kKnn ? m : kKnn;
+  for (int c = lane; c < m; c += 32) {
+    const int rank = cand_rank(cd, ct, m, cd[c], ct[c]);
+    if (rank < kKnn) s_kt[wid][rank] = ct[c];
+  }
+  __syncwarp();
+  bf16* row = s_row[wid];
+  if (lane < kKnn) {
     float ox = 0.f, oy = 0.f, oz = 0.f;
-    if (k < cnt) {
-      const V4<float> q = sxp[bi[k]];
+    if (lane < cnt) {
+      const V4<float> q = sxp[s_kt[wid][lane]];
       ox = (q.x - p.x) * ih;
       oy = (q.y - p.y) * ih;
       oz = (q.z - p.z) * ih;
     }
-    f[3 * k + 0] = __float2bfloat16_rn(ox);
-    f[3 * k + 1] = __float2bfloat16_rn(oy);
-    f[3 * k + 2] = __float2bfloat16_rn(oz);
+    row[3 * lane + 0] = __float2bfloat16_rn(ox);
+    row[3 * lane + 1] = __float2bfloat16_rn(oy);
+    row[3 * lane + 2] = __float2bfloat16_rn(oz);
+  } else if (lane == kKnn) {
+    row[72] = __float2bfloat16_rn(p.w * ih * ih);
+    row[73] = __float2bfloat16_rn(vel_s[3 * s + 0] * dt * ih);
+    row[74] = __float2bfloat16_rn(vel_s[3 * s + 1] * dt * ih);
+    row[75] = __float2bfloat16_rn(vel_s[3 * s + 2] * dt * ih);
+    row[76] = __float2bfloat16_rn(dpsi_s ? dpsi_s[s] * ih * ih : 0.f);
+    for (int k = kFeat; k < kIn; k++) row[k] = __float2bfloat16_rn(0.f);
   }
-  f[72] = __float2bfloat16_rn(p.w * ih * ih);
-  f[73] = __float2bfloat16_rn(vel_s[3 * s + 0] * dt * ih);
-  f[74] = __float2bfloat16_rn(vel_s[3 * s + 1] * dt * ih);
-  f[75] = __float2bfloat16_rn(vel_s[3 * s + 2] * dt * ih);
-  f[76] = __float2bfloat16_rn(dpsi_s ? dpsi_s[s] * ih * ih : 0.f);
-  for (int k = kFeat; k < kIn; k++) f[k] = __float2bfloat16_rn(0.f);
+  __syncwarp();
+  const int64_t orow = out_perm ? (int64_t)out_perm[s] : s;
+  bf16* f = feat + orow * kIn;
+  if ((reinterpret_cast<uintptr_t>(feat) & 15) == 0) {
+    if (lane < kIn / 8) reinterpret_cast<uint4*>(f)[lane] = reinterpret_cast<const uint4*>(row)[lane];
+  } else {
+    for (int k = lane; k < kIn; k += 32) f[k] = row[k];
+  }
 }
 
 // x <- clamp(x + dt v), v through a wall -> 0  (same rule as the fluid step)
@@ -545,6 +753,14 @@ GemmArgs base_args() {
 // keeps H^T and H3 for the backward pass (rows <= kTrainMax)
 int forward(mlp_t* mm, cudaStream_t st, int64_t rows, const bf16* x, float* out, bool train) {
   const float* p = mm->params;
+  if (!train) {
+    // inference: all layers of a tile in one CTA (k_mlp_infer)
+    note_launch();
+    k_mlp_infer<<<(unsigned)((rows + kTM - 1) / kTM), kGemmThreads, kFusedSmem, st>>>(
+        x, rows, mm->wt1, mm->wt2, mm->wt3, p, out, mm->err);
+    POT_CUDA(cudaGetLastError());
+    return POT_OK;
+  }
   GemmArgs a = base_args();
   a.A = x; a.lda = kIn; a.M = rows; a.B = mm->wt1; a.ldb = kIn; a.Nrows = kHid;
   a.K = kIn; a.ksplit = kIn; a.mode = kModeHidden; a.ncols = kHid; a.bias = p + ob1;
@@ -657,9 +873,9 @@ int mlp_features_sorted(pot_ctx* ctx, pot_mlp* mm, cudaStream_t st, int64_t n, c
   k_gather_vel<<<blocks_for(n, 256), 256, 0, st>>>(n, ctx->perm, vel, psi, psi_old, mm->vel_tmp,
                                                     mm->dpsi_s);
   note_launch();
-  k_features<<<blocks_for(n, 128), 128, 0, st>>>(n, w.sxp, ctx->cell_start, w.grid, w.psi_max,
-                                                  mm->vel_tmp, psi_old ? mm->dpsi_s : nullptr,
-                                                  ctx->snu, dt, out_perm, (bf16*)feat);
+  k_features<<<(unsigned)((n + kFeatWarps - 1) / kFeatWarps), kFeatWarps * 32, 0, st>>>(
+      n, w.sxp, ctx->cell_start, w.grid, mm->vel_tmp, psi_old ? mm->dpsi_s : nullptr, ctx->snu,
+      dt, out_perm, (bf16*)feat);
   POT_CUDA(cudaGetLastError());
   return POT_OK;
 }
@@ -715,7 +931,9 @@ int pot_mlp_create(pot_mlp** out, int device, int64_t max_rows) {
   if (max_rows <= 0 || max_rows > ((int64_t)1 << 28)) return POT_ERR_INVALID_ARG;
   if (cudaSetDevice(device) != cudaSuccess) return POT_ERR_CUDA;
   if (cudaFuncSetAttribute(k_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem) !=
-      cudaSuccess)
+          cudaSuccess ||
+      cudaFuncSetAttribute(k_mlp_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, kFusedSmem) !=
+          cudaSuccess)
     return POT_ERR_CUDA;
   pot_mlp* mm = new (std::nothrow) pot_mlp();
   if (!mm) return POT_ERR_CUDA;

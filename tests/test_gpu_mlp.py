@@ -115,7 +115,6 @@ def test_features_match_oracle(mlp, history):
     got = feat.float().cpu().numpy().astype(np.float64)
     x1 = np.clip(sc.pos.astype(np.float32) + np.float32(1e-3) * vel, 1e-6, 1 - 1e-6).astype(np.float64)
     ref = M.bf16(M.knn_features(x1, sc.psi.astype(np.float64), vel.astype(np.float64), sc.nu, 1e-3,
-                                radius=2 * np.sqrt(float(sc.psi.astype(np.float32).max())),
                                 psi_old=old.astype(np.float64) if history else None))
     diff = np.abs(got - ref)
     # one BF16 ulp of the offsets (values ~1) or of the scaled psi

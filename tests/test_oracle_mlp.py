@@ -62,9 +62,9 @@ def test_knn_features_against_kdtree():
     vel = rng.normal(size=(n, 3))
     nu = np.full(n, 2e-5)
     F = M.knn_features(pos, psi, vel, nu, dt=1e-3)
-    radius = 2 * np.sqrt(psi.max())
     tree = cKDTree(pos)
     h = np.cbrt(nu)
+    radius = 2 * h[0]
     for i in range(0, n, 17):
         d, j = tree.query(pos[i], k=25)
         keep = (j != i) & (d < radius)
