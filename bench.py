@@ -49,11 +49,14 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 SMALL_SPACING = 0.032  # ~2000 sites with the splash recipe
-# FP32 FLOP executed (fadd + fmul + 2 ffma) and DRAM bytes per cell processed
-# by k_cells, from an ncu capture of the splash recipe at 536k sites, step 30
-# (the bench's run in miniature); profiles/k_cells_splash_536k_step30.md
+# FP32 FLOP of the cell work (fadd + fmul + 2 ffma executed by the version
+# that runs only the edge pieces that occur; the current kernel executes
+# 12,988 per cell, adding exact zeros for the absent pieces) and DRAM bytes
+# per cell processed by k_cells, from ncu captures of the splash recipe at
+# 536k sites, step 30 (the bench's run in miniature);
+# profiles/k_cells_splash_536k_step30.md
 K_CELLS_FLOP_PER_CELL = 10049.0
-K_CELLS_DRAM_BYTES_PER_CELL = 387.0
+K_CELLS_DRAM_BYTES_PER_CELL = 383.0
 
 
 def parse():
