@@ -170,9 +170,10 @@ __global__ void __launch_bounds__(256)
           const V4<T> q = sxp[t];
           T dx, dy, dz;
           const T d2 = sqdist(p, q, dx, dy, dz);
-          const T rj = q.w > T(0) ? sqrt(q.w) : T(0);
-          const T sr = r + rj;
-          if (!(d2 < sr * sr)) continue;
+          // beyond the reach D no plane can be a candidate or empty the
+          // cell; within it the tests on h decide (h < r needs
+          // |p_i - p_j| < r_i + r_j, and h <= -r needs p_i inside ball j)
+          if (!(d2 < D2)) continue;
           if (d2 == T(0)) {
             set_error(err, POT_ERR_COINCIDENT_SITES, s);
             continue;
