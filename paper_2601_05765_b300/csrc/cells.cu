@@ -222,6 +222,11 @@ __global__ void __launch_bounds__(256)
 // facet geometry
 
 template <typename T>
+struct alignas(2 * sizeof(T)) P2 {
+  T x, y;
+};
+
+template <typename T>
 struct Facet {
   T area, omega, mx, my, mz;
   T rm2;  // squared distance from the site of the facet's farthest point
@@ -280,13 +285,14 @@ __device__ Facet<T> facet_eval(const V4<T>* __restrict__ pl, int m, int fi, T ps
   static_assert(sizeof(IdT) == 2 || kPlaneCap <= 0xfc, "plane indices must stay below the square's ids");
   static_assert(kBigPlanes <= 0xfffc, "plane indices must stay below the square's ids");
   IdT lid[2][kMaxLines];
-  T px[2][kMaxLines], py[2][kMaxLines];
+  // vertex coordinates as (x, y) pairs: one 8-byte local access per vertex
+  P2<T> pv[2][kMaxLines];
   int cur = 0, nl = 4;
   lid[0][0] = kSq; lid[0][1] = kSq + 1; lid[0][2] = kSq + 2; lid[0][3] = kSq + 3;
-  px[0][0] = -B; py[0][0] = -B;
-  px[0][1] = B;  py[0][1] = -B;
-  px[0][2] = B;  py[0][2] = B;
-  px[0][3] = -B; py[0][3] = B;
+  pv[0][0] = P2<T>{-B, -B};
+  pv[0][1] = P2<T>{B, -B};
+  pv[0][2] = P2<T>{B, B};
+  pv[0][3] = P2<T>{-B, B};
 
   auto line = [&](int id, T& a, T& b, T& c) {
     if (id >= kSq) {
@@ -321,8 +327,10 @@ __device__ Facet<T> facet_eval(const V4<T>* __restrict__ pl, int m, int fi, T ps
     // every vertex v has a.v <= |(a,b)| |v| < c: the polygon is inside
     if (c > T(0) && cc >= len2 * rp2 * T(1.0001)) continue;
     unsigned om = 0;
-    for (int k = 0; k < nl; k++)
-      if (a * px[cur][k] + b * py[cur][k] > c) om |= 1u << k;
+    for (int k = 0; k < nl; k++) {
+      const P2<T> v = pv[cur][k];
+      if (a * v.x + b * v.y > c) om |= 1u << k;
+    }
     if (om == 0) continue;
     const unsigned full = (1u << nl) - 1u;
     if (om == full) return out;
@@ -346,20 +354,24 @@ __device__ Facet<T> facet_eval(const V4<T>* __restrict__ pl, int m, int fi, T ps
       int idx = e + k;
       if (idx >= nl) idx -= nl;
       lid[nx][k] = lid[cur][idx];
-      const T vx = px[cur][idx], vy = py[cur][idx];
-      px[nx][k] = vx;
-      py[nx][k] = vy;
+      const P2<T> v = pv[cur][idx];
+      const T vx = v.x, vy = v.y;
+      pv[nx][k] = v;
       if (k > 0) mr2 = fmax(mr2, vx * vx + vy * vy);
     }
     lid[nx][cnt] = (IdT)gi;
     T a2, b2, c2;
     line(lid[cur][e], a2, b2, c2);
-    isect(a, b, c, a2, b2, c2, px[nx][0], py[nx][0]);
+    T x0, y0;
+    isect(a, b, c, a2, b2, c2, x0, y0);
+    pv[nx][0] = P2<T>{x0, y0};
     int sm1 = s == 0 ? nl - 1 : s - 1;
     line(lid[cur][sm1], a2, b2, c2);
-    isect(a2, b2, c2, a, b, c, px[nx][cnt], py[nx][cnt]);
-    mr2 = fmax(mr2, px[nx][0] * px[nx][0] + py[nx][0] * py[nx][0]);
-    rp2 = fmax(mr2, px[nx][cnt] * px[nx][cnt] + py[nx][cnt] * py[nx][cnt]);
+    T x1, y1;
+    isect(a2, b2, c2, a, b, c, x1, y1);
+    pv[nx][cnt] = P2<T>{x1, y1};
+    mr2 = fmax(mr2, x0 * x0 + y0 * y0);
+    rp2 = fmax(mr2, x1 * x1 + y1 * y1);
     nl = cnt + 1;
     cur = nx;
   }
@@ -429,7 +441,8 @@ __device__ Facet<T> facet_eval(const V4<T>* __restrict__ pl, int m, int fi, T ps
   bool arc = false;
   for (int k = 0; k < nl; k++) {
     int k2 = k + 1 == nl ? 0 : k + 1;
-    T pxk = px[cur][k], pyk = py[cur][k], qx = px[cur][k2], qy = py[cur][k2];
+    const P2<T> vk = pv[cur][k], vq = pv[cur][k2];
+    T pxk = vk.x, pyk = vk.y, qx = vq.x, qy = vq.y;
     const T pk2 = pxk * pxk + pyk * pyk;
     if (want_extent && pk2 <= rho2) {  // a polygon vertex inside the disk
       const T ex = pxk - ou, ey = pyk - ov;
