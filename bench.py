@@ -521,7 +521,7 @@ def run_warmstart(args):
         res = W.compare(ctx, mlp, scene, steps=args.steps, dt=dt, warm_steps=warm, eps=eps,
                         relax=relax)
         out = {}
-        for k in ("plain", "mlp"):
+        for k in ("plain", "extrapolated", "mlp"):
             out[k] = W.summarize(res[k])
             ms = sorted(st["ms_total"] for st in res[k])
             out[k]["ms_total_median"] = ms[len(ms) // 2]
@@ -547,13 +547,14 @@ def run_warmstart(args):
                      "scenes": "dam-break columns 24x24x48, seeds 10-19, the substeps of their "
                                "first 40 steps of 2e-3",
                      "extra_scenes": extra},
-        "plain": plain, "mlp": learned,
+        "plain": plain, "extrapolated": spl["extrapolated"], "mlp": learned,
         "newton_iters_saved": plain["newton_iters"] - learned["newton_iters"],
         "ms_saved_per_solve": plain["ms_total"] - learned["ms_total"],
         "holdout_dam_break": {"workload": f"dam-break column 36x36x72 ({dam.n} sites), seed 20, "
                                           f"substeps {12 * nsub_d}..{12 * nsub_d + args.steps - 1} "
                                           f"of {dts:.3g}, eps {eps_d:.3g}",
-                              "plain": held["plain"], "mlp": held["mlp"],
+                              "plain": held["plain"], "extrapolated": held["extrapolated"],
+                              "mlp": held["mlp"],
                               "newton_iters_saved": held["plain"]["newton_iters"] - held["mlp"]["newton_iters"],
                               "ms_saved_per_solve": held["plain"]["ms_total"] - held["mlp"]["ms_total"]}}))
     pot.set_warm_start(ctx, None)

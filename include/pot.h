@@ -105,7 +105,8 @@ typedef struct {
   double eps;           /* spring length of the pressure force (0.01, Sec. 5) */
   double gravity[3];    /* (0, 0, -9.81) */
   double wall_margin;   /* sites are clamped to [lo+m, hi-m] (1e-6) */
-  int32_t warm_start;   /* 0: previous psi; 1: learned MLP start */
+  int32_t warm_start;   /* 0: previous psi; 1: learned MLP start; 2: psi
+                           extrapolated from the previous two steps */
   int32_t substeps;     /* pot_fluid_step takes this many explicit steps of
                            dt / substeps (0 or 1: one step of dt) */
 } pot_params;
@@ -269,6 +270,12 @@ int pot_newton_solve_f64(pot_ctx* ctx, void* stream, int64_t n, const double* po
  *        wall set to 0);
  *   psi <- Newton solve at the new x, warm-started from psi;
  *   v <- v + dt (g + (c_i - x_i) / eps^2)   (pressure spring F_p, Sec. 5).
+ * With params->warm_start = 2, Newton starts from psi + (psi - psi_prev),
+ * psi_prev the weights at the start of the previous pot_fluid_step on this
+ * context with the same n (none after pot_create, pot_clear_history or a
+ * pot_newton_solve: then from psi); a start with an empty cell or a geometry
+ * error, or from which Newton does not converge, falls back to psi (stats:
+ * mlp_used / mlp_fallback).
  * With params->substeps = k > 1 this is done k times with dt / k, stopping
  * at the first substep whose solve fails; stats then sums the substeps'
  * counts and times and keeps their largest start and final errors.
@@ -280,6 +287,10 @@ int pot_fluid_step(pot_ctx* ctx, void* stream, int64_t n, float* pos, float* vel
 int pot_fluid_step_f64(pot_ctx* ctx, void* stream, int64_t n, double* pos, double* vel,
                        double* psi, const double* targets, const pot_domain* dom,
                        const pot_params* params, pot_solve_stats* stats);
+
+/* Forget the weight history of warm_start = 2 (a new run on the same
+ * context).  Errors: POT_ERR_INVALID_ARG for a NULL context. */
+int pot_clear_history(pot_ctx* ctx);
 
 /* ---- learned warm start (not in the paper) ------------------------------- */
 

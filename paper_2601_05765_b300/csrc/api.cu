@@ -56,6 +56,8 @@ int alloc_work(Work<T>& w, int64_t n, int64_t k, int64_t gcap, int sms) {
   POT_CHECK(alloc(&w.srad_lo, n));
   POT_CHECK(alloc(&w.soff, 3 * n));
   POT_CHECK(alloc(&w.hint, 4 * n));
+  POT_CHECK(alloc(&w.psi_hist, n));
+  POT_CHECK(alloc(&w.psi_fb, n));
   POT_CHECK(alloc(&w.rcell_acc, n));
   POT_CHECK(alloc(&w.rcell, n));
   POT_CHECK(alloc(&w.gmax, gcap + 1));
@@ -75,7 +77,7 @@ void free_work(Work<T>& w) {
   void* ptrs[] = {w.sxp, w.psi_base, w.vol,  w.karea, w.diag, w.cen, w.stage_vals, w.csr_vals,
                   w.u,   w.x,        w.r,    w.z,     w.p0,   w.p1,  w.q,          w.vel_s,
                   w.psi_max, w.nu_max, w.srad, w.srad_lo, w.soff, w.hint, w.rcell_acc, w.rcell, w.gmax,
-                  w.big_pl, w.big_d, w.big_j};
+                  w.big_pl, w.big_d, w.big_j, w.psi_hist, w.psi_fb};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   w = Work<T>();
@@ -191,6 +193,13 @@ void pot_default_params(pot_params* p) {
   p->gravity[2] = -9.81;
   p->wall_margin = 1e-6;
   p->warm_start = 0;
+}
+
+int pot_clear_history(pot_ctx* ctx) {
+  if (!ctx) return POT_ERR_INVALID_ARG;
+  ctx->wf.hist_n = -1;
+  ctx->wd.hist_n = -1;
+  return POT_OK;
 }
 
 const char* pot_status_string(int status) {

@@ -85,6 +85,36 @@ __global__ void k_velocity(int64_t n, const int32_t* __restrict__ perm,
   psi[o] = psi_base[s];
 }
 
+// Extrapolated start (Sec. 5 steps are smooth in time): psi_start =
+// psi^k + (psi^k - psi^{k-1}), from the weights at the start of this step
+// (psi, caller order) and of the previous one (hist); a non-positive value
+// keeps psi^k.  The plain start psi^k is kept in fb (sorted) for the
+// fallback; the largest new weight raises psi_max.
+template <typename T>
+__global__ void k_extrapolate(int64_t n, const int32_t* __restrict__ perm, const T* __restrict__ psi,
+                              const T* __restrict__ hist, V4<T>* sxp, T* psi_base, T* fb,
+                              T* psi_max) {
+  int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  T v = T(0);
+  if (s < n) {
+    const int64_t o = perm[s];
+    const T p = psi[o];
+    v = p + (p - hist[o]);
+    if (!(v > T(0))) v = p;
+    fb[s] = p;
+    sxp[s].w = v;
+    psi_base[s] = v;
+  }
+  T m = v > T(0) ? v : T(0);
+  for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_down_sync(kFull, m, off));
+  if ((threadIdx.x & 31) == 0 && m > T(0)) {
+    if (sizeof(T) == 4)
+      atomicMax((int*)psi_max, __float_as_int((float)m));
+    else
+      atomicMax((unsigned long long*)psi_max, (unsigned long long)__double_as_longlong((double)m));
+  }
+}
+
 // psi <- src (sorted), the current weights for evaluation and the base;
 // psi_max follows (reset by the caller)
 template <typename T>
@@ -265,6 +295,7 @@ int newton_solve(pot_ctx* ctx, cudaStream_t st, int64_t n, const T* pos, const d
   S->grid_builds++;
   Work<T>& w = ctx->work<T>();
   w.use_hint = true;  // security balls start from the last solve's cells
+  w.hist_n = -1;      // weights from outside a run of fluid steps: no history
   int status = newton_sorted<T>(ctx, st, n, dom, P, S);
   if (status == POT_OK || status == POT_ERR_NOT_CONVERGED || status == POT_ERR_LINESEARCH_FAILED) {
     note_launch();
@@ -297,11 +328,23 @@ int fluid_substep(pot_ctx* ctx, cudaStream_t st, int64_t n, T* pos, T* vel, T* p
   S->grid_builds++;
   ctx->work<T>().use_hint = true;  // security balls start from the last step's cells
   const T* fallback = nullptr;
-  if (sizeof(T) == 4 && P->warm_start && ctx->mlp) {
+  if (sizeof(T) == 4 && P->warm_start == 1 && ctx->mlp) {
     float* prev = nullptr;
     POT_CHECK(mlp_warm_start(ctx, ctx->mlp, st, n, (const float*)vel, (const float*)psi,
                              (float)dt, &prev));
     fallback = (const T*)prev;
+  } else if (P->warm_start == 2) {
+    Work<T>& w = ctx->work<T>();
+    if (w.hist_n == n) {
+      note_launch();
+      k_extrapolate<T><<<blocks_for(n, 256), 256, 0, st>>>(n, ctx->perm, psi, w.psi_hist, w.sxp,
+                                                           w.psi_base, w.psi_fb, w.psi_max);
+      POT_CUDA(cudaGetLastError());
+      fallback = w.psi_fb;
+    }
+    // this step's starting weights are the next step's history
+    POT_CUDA(cudaMemcpyAsync(w.psi_hist, psi, n * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    w.hist_n = n;
   }
   int status = newton_sorted<T>(ctx, st, n, dom, P, S, fallback);
   if (fallback && S->mlp_used &&

@@ -122,6 +122,8 @@ def lib():
         L.pot_cell_kernel_time.restype = ctypes.c_int
         L.pot_cell_diagnostics.argtypes = [P, P, I64, P, P, P, P]
         L.pot_cell_diagnostics.restype = ctypes.c_int
+        L.pot_clear_history.argtypes = [P]
+        L.pot_clear_history.restype = ctypes.c_int
         for f in (L.pot_mlp_create, L.pot_mlp_destroy, L.pot_mlp_num_params, L.pot_mlp_set_params,
                   L.pot_mlp_get_params, L.pot_mlp_forward, L.pot_mlp_gradients, L.pot_mlp_train_step,
                   L.pot_mlp_check, L.pot_mlp_features, L.pot_mlp_set_history,
@@ -331,6 +333,13 @@ def pot_fluid_step(ctx: Context, pos, vel, psi, targets, domain=UNIT_BOX, params
     if check and code != POT_OK:
         raise PotError(code, "pot_fluid_step", s)
     return s
+
+
+def clear_history(ctx: Context):
+    """Forget the weight history of the extrapolated start (warm_start = 2)."""
+    code = lib().pot_clear_history(ctx.handle)
+    if code != POT_OK:
+        raise PotError(code, "pot_clear_history")
 
 
 def relax_to_centroids(ctx: Context, pos, psi, targets, rounds: int, domain=UNIT_BOX, params=None):

@@ -111,28 +111,33 @@ def train(mlp, x, y, epochs, batch=8192, lr=1e-3, seed=0):
 
 
 def compare(ctx, mlp, scene, steps, dt, warm_steps=0, tol=1e-4, eps=0.01, relax=0):
-    """Run the same fluid steps from the same state with the plain start and
-    with the MLP start; returns per-step stats for both."""
+    """Run the same fluid steps from the same state with the plain start
+    (previous weights), the extrapolated start (warm_start 2) and the MLP
+    start; returns per-step stats of each.  The warm-up steps run with the
+    extrapolated start, which leaves the weight history of the last one in
+    the context (their converged weights are those of the plain start, to
+    the tolerance)."""
     dev = ctx.device
     pos, vel, psi, nu = _state(scene, dev)
-    prm = pot.default_params(dt=dt, tol=tol, eps=eps)
+    prm = pot.default_params(dt=dt, tol=tol, eps=eps, warm_start=2)
     settle(ctx, pos, vel, psi, nu, prm, relax)
+    pot.clear_history(ctx)
     psi_old = None
     for _ in range(warm_steps):
         psi_old = psi.clone()
         pot.pot_fluid_step(ctx, pos, vel, psi, nu, params=prm)
     state = (pos.clone(), vel.clone(), psi.clone())
     out = {}
-    for mode in (0, 1):
+    for mode, name in ((0, "plain"), (2, "extrapolated"), (1, "mlp")):
         pos, vel, psi = (t.clone() for t in state)
         p = pot.default_params(dt=dt, tol=tol, eps=eps, warm_start=mode)
-        pot.set_warm_start(ctx, mlp if mode else None)
-        if mode:
+        pot.set_warm_start(ctx, mlp if mode == 1 else None)
+        if mode == 1:
             mlp.set_history(psi_old)
         stats = []
         for _ in range(steps):
             stats.append(pot.pot_fluid_step(ctx, pos, vel, psi, nu, params=p, check=False))
-        out["mlp" if mode else "plain"] = stats
+        out[name] = stats
     pot.set_warm_start(ctx, None)
     return out
 

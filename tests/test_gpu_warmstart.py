@@ -66,3 +66,29 @@ def test_trained_model_starts_closer(setup):
     assert learned["fallback_rate"] == 0.0 and learned["used_rate"] == 1.0
     assert learned["newton_iters"] <= plain["newton_iters"] - 0.5, (learned, plain)
     assert learned["pcg_iters"] < plain["pcg_iters"], (learned, plain)
+
+
+def test_extrapolated_start(setup):
+    """warm_start 2: the first step after clear_history starts from the
+    previous weights, later ones from psi + (psi - psi_prev); every step
+    converges to the tolerance, and in FP64 far below it the weights equal
+    the plain start's (the solution does not depend on the start)."""
+    ctx, _ = setup
+    sc = column(19)
+    dev = ctx.device
+    res = {}
+    for ws in (0, 2):
+        ctx64 = pot.Context(sc.n, 128, 0, fp32=False, fp64=True)
+        pos, vel, psi, nu = (torch.as_tensor(a, dtype=torch.float64, device=dev)
+                             for a in (sc.pos, sc.vel, sc.psi, sc.nu))
+        prm = pot.default_params(dt=DT, tol=1e-10, warm_start=ws)
+        pot.pot_newton_solve(ctx64, pos, nu, psi, params=prm)
+        pot.clear_history(ctx64)
+        stats = [pot.pot_fluid_step(ctx64, pos, vel, psi, nu, params=prm) for _ in range(6)]
+        assert all(s["status"] == 0 and s["err_max"] <= 1e-10 for s in stats)
+        res[ws] = (psi.cpu().numpy(), stats)
+        ctx64.close()
+    used = [s["mlp_used"] for s in res[2][1]]
+    assert used[0] == 0 and all(u == 1 for u in used[1:]), used
+    assert sum(s["newton_iters"] for s in res[2][1]) <= sum(s["newton_iters"] for s in res[0][1])
+    np.testing.assert_allclose(res[2][0], res[0][0], rtol=0, atol=1e-8 * float(np.max(res[0][0])))
