@@ -356,8 +356,9 @@ int pot_mlp_features(pot_ctx* ctx, pot_mlp* mlp, void* stream, int64_t n, const 
 int pot_mlp_set_history(pot_mlp* mlp, void* stream, int64_t n, const float* psi_old);
 
 /* Attach a model to a context (NULL detaches; the context does not own it).
- * pot_fluid_step then starts Newton from the MLP's prediction (its change
- * clamped to |dpsi| <= h^2) when params->warm_start is 1, and falls back to
+ * pot_fluid_step then starts Newton from psi + (psi - psi_old) + h^2 y, y
+ * the MLP's output clamped to [-1, 1] (psi_old from the history; without it
+ * that term is 0), when params->warm_start is 1, and falls back to
  * plain Newton from the previous weights when the prediction fails the KMT
  * precondition (an empty cell, or a geometry error) or when Newton from it
  * does not converge (stats: mlp_used / mlp_fallback).  FP32 path only. */

@@ -566,17 +566,20 @@ __global__ void k_gather_vel(int64_t n, const int32_t* __restrict__ perm, const 
   if (psi_old) dpsi_s[s] = psi[i] - psi_old[i];
 }
 
-// psi_pred = psi_prev + h^2 out, written as the Newton start; psi_prev kept
+// psi_pred = psi_prev + dpsi + h^2 out, written as the Newton start: the
+// network corrects the linear extrapolation by the last weight change dpsi
+// (0 without history); psi_prev kept
 __global__ void k_apply_warm(int64_t n, const float* __restrict__ out, const double* __restrict__ snu,
-                             V4<float>* sxp, float* psi_base, float* psi_prev, float* psi_max) {
+                             const float* __restrict__ dpsi, V4<float>* sxp, float* psi_base,
+                             float* psi_prev, float* psi_max) {
   int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   float v = 0.f;
   if (s < n) {
     const float prev = sxp[s].w;
     const float h = (float)cbrt(snu[s]);
-    // a loose guard against extrapolation: at most h^2 of change per step
-    v = prev + h * h * fminf(fmaxf(out[s], -1.f), 1.f);
-    if (!(v == v)) v = prev;  // a NaN prediction keeps the previous weight
+    // a loose guard on the correction: at most h^2 per step
+    v = prev + (dpsi ? dpsi[s] : 0.f) + h * h * fminf(fmaxf(out[s], -1.f), 1.f);
+    if (!(v > 0.f)) v = prev;  // a NaN or non-positive start keeps the previous weight
     psi_prev[s] = prev;
     sxp[s].w = v;
     psi_base[s] = v;
@@ -894,8 +897,8 @@ int mlp_warm_start(pot_ctx* ctx, pot_mlp* mm, cudaStream_t st, int64_t n, const 
   POT_CHECK(forward(mm, st, n, mm->x, mm->out, false));
   Work<float>& w = ctx->wf;
   note_launch();
-  k_apply_warm<<<blocks_for(n, 256), 256, 0, st>>>(n, mm->out, ctx->snu, w.sxp, w.psi_base,
-                                                     mm->psi_prev, w.psi_max);
+  k_apply_warm<<<blocks_for(n, 256), 256, 0, st>>>(n, mm->out, ctx->snu, hist ? mm->dpsi_s : nullptr,
+                                                     w.sxp, w.psi_base, mm->psi_prev, w.psi_max);
   POT_CUDA(cudaGetLastError());
   POT_CHECK(check_err(mm, st));
   *psi_prev = mm->psi_prev;

@@ -4,7 +4,9 @@ Data: plain-Newton fluid steps on dam-break columns (seeded); every `every`
 steps, the features at the state the step solves at (positions advanced by
 dt v and clamped, previous weights psi^k, velocities, the change
 psi^k - psi^{k-1}) and the converged weights psi^{k+1} of `per_sample` random
-sites give samples (x, y = (psi^{k+1} - psi^k) / h^2), h = nu^(1/3).
+sites give samples (x, y = (psi^{k+1} - psi^k - (psi^k - psi^{k-1})) / h^2,
+the departure from the linear extrapolation; without psi^{k-1} the plain
+change), h = nu^(1/3).
 
 Training: Adam on the mean squared error, shuffled batches, all kernels in
 libpot.so (tensor-core forward and back-propagation).  Evaluation: the same
@@ -78,6 +80,7 @@ def collect(ctx, mlp, scene, steps, every, per_sample, seed, dt, tol=1e-4, eps=0
     for k in range(steps):
         take = k % every == 0
         psi_prev = psi.clone()
+        hist = psi_old
         if take:
             feat = pot.pot_mlp_features(ctx, mlp, pos, vel, psi, nu, params=prm, psi_old=psi_old)
         psi_old = psi_prev
@@ -87,7 +90,11 @@ def collect(ctx, mlp, scene, steps, every, per_sample, seed, dt, tol=1e-4, eps=0
         if take:
             idx = torch.randperm(scene.n, generator=gen)[:per_sample].to(dev)
             xs.append(feat[idx])
-            ys.append(((psi - psi_prev) / h2)[idx])
+            # the target: the new weight's departure from the linear
+            # extrapolation psi^k + (psi^k - psi^{k-1}) (plain change without
+            # history), as the fluid step applies it
+            lin = psi_prev if hist is None else 2.0 * psi_prev - hist
+            ys.append(((psi - lin) / h2)[idx])
     return torch.cat(xs), torch.cat(ys)
 
 

@@ -3,7 +3,8 @@ MLP-started fluid step against the plain start (previous weights).
 
 The warm start only changes where Newton starts, so correctness is the
 converged result (checked in test_gpu_newton.py); what is checked here is
-that (a) a model whose output is 0 reproduces the plain start exactly, and
+that (a) a model whose output is 0 reproduces the extrapolated start
+(psi + (psi - psi_prev)) exactly, and
 (b) a model trained on a few dam-break steps needs fewer Newton and PCG
 iterations than the start from the previous weights on unseen steps of
 another seed, with no fallback and every step converged.  (The worst-cell
@@ -37,14 +38,16 @@ def setup():
     ctx.close()
 
 
-def test_zero_model_is_the_plain_start(setup):
+def test_zero_model_is_the_extrapolated_start(setup):
+    """The network corrects the linear extrapolation: with its output 0 the
+    learned start is the extrapolated start (warm_start 2) exactly."""
     ctx, mlp = setup
     mlp.set_params(torch.zeros(pot.Mlp.num_params(), dtype=torch.float32, device=ctx.device))
     res = W.compare(ctx, mlp, column(19), steps=3, dt=DT, warm_steps=2)
-    for a, b in zip(res["plain"], res["mlp"]):
+    for a, b in zip(res["extrapolated"], res["mlp"]):
         assert a["status"] == 0 and b["status"] == 0
-        assert b["mlp_used"] == 1 and b["mlp_fallback"] == 0
-        assert b["err_start"] == pytest.approx(a["err_start"], rel=1e-6)
+        assert a["mlp_used"] == 1 and b["mlp_used"] == 1 and b["mlp_fallback"] == 0
+        assert b["err_start"] == a["err_start"]
         assert b["newton_iters"] == a["newton_iters"]
 
 
