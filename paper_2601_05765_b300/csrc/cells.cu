@@ -138,59 +138,72 @@ __global__ void __launch_bounds__(256)
   int nc = 0;
   bool empty = false;
   const int64_t row = s * (int64_t)kmax;
-  for (int cz = c0[2]; cz <= c1[2] && !empty; cz++) {
+  // One flat loop over the box of grid cells (x fastest, then y, then z)
+  // and their sites: each pass tests one site or opens the next cell, so
+  // the lanes of a warp stay on the same short path instead of diverging on
+  // nested loop bounds.  Candidates come out in ascending sorted index.
+  const int nxr = c1[0] - c0[0] + 1, nyr = c1[1] - c0[1] + 1, nzr = c1[2] - c0[2] + 1;
+  int ix = 0, iy = 0, iz = 0;  // the next cell to open
+  int t = 0, b = 0;            // the open cell's sites [t, b)
+  while (!empty) {
+    if (t < b) {
+      if (t != s) {
+        const V4<T> q = sxp[t];
+        T dx, dy, dz;
+        const T d2 = sqdist(p, q, dx, dy, dz);
+        // beyond the reach D no plane can be a candidate or empty the
+        // cell; within it the tests on h decide (h < r needs
+        // |p_i - p_j| < r_i + r_j, and h <= -r needs p_i inside ball j)
+        if (d2 < D2) {
+          if (d2 == T(0)) {
+            set_error(err, POT_ERR_COINCIDENT_SITES, s);
+          } else {
+            T d;
+            const T h = fix_zero(plane_offset(d2, ps, q.w, d), r);
+            if (h <= -r) {
+              empty = true;
+            } else if (h < r && h - (dx * ox + dy * oy + dz * oz) / d < R) {
+              if (nc < kmax) cand[row + nc] = t;
+              nc++;
+            }
+          }
+        }
+      }
+      t++;
+      continue;
+    }
+    if (iz >= nzr) break;
+    const int cx = c0[0] + ix, cy = c0[1] + iy, cz = c0[2] + iz;
+    if (++ix == nxr) {
+      ix = 0;
+      if (++iy == nyr) {
+        iy = 0;
+        iz++;
+      }
+    }
     const T zlo = g.lo[2] + cz * g.cs;
     T ez = fmax(T(0), fmax(zlo - p.z, p.z - (zlo + g.cs)));
     if (cz == 0 && p.z < zlo) ez = T(0);
     if (cz == g.dim[2] - 1 && p.z > zlo) ez = T(0);
-    for (int cy = c0[1]; cy <= c1[1] && !empty; cy++) {
-      const T ylo = g.lo[1] + cy * g.cs;
-      T ey = fmax(T(0), fmax(ylo - p.y, p.y - (ylo + g.cs)));
-      if (cy == 0 && p.y < ylo) ey = T(0);
-      if (cy == g.dim[1] - 1 && p.y > ylo) ey = T(0);
-      const T eyz = ey * ey + ez * ez;
-      if (eyz >= D2) continue;
-      for (int cx = c0[0]; cx <= c1[0] && !empty; cx++) {
-        const T xlo = g.lo[0] + cx * g.cs;
-        T ex = fmax(T(0), fmax(xlo - p.x, p.x - (xlo + g.cs)));
-        if (cx == 0 && p.x < xlo) ex = T(0);
-        if (cx == g.dim[0] - 1 && p.x > xlo) ex = T(0);
-        const T dl2 = ex * ex + eyz;
-        if (dl2 >= D2) continue;
-        const int key = (cz * g.dim[1] + cy) * g.dim[0] + cx;
-        if (dl2 > T(0)) {
-          const T dl = sqrt(dl2);
-          const T c = gmax[key] - ps;
-          const T hmin = c >= T(0) ? T(0.5) * dl - c / (T(2) * dl) : T(0.5) * dl;
-          if (hmin >= Re) continue;
-        }
-        const int a = cell_start[key], b = cell_start[key + 1];
-        for (int t = a; t < b; t++) {
-          if (t == s) continue;
-          const V4<T> q = sxp[t];
-          T dx, dy, dz;
-          const T d2 = sqdist(p, q, dx, dy, dz);
-          // beyond the reach D no plane can be a candidate or empty the
-          // cell; within it the tests on h decide (h < r needs
-          // |p_i - p_j| < r_i + r_j, and h <= -r needs p_i inside ball j)
-          if (!(d2 < D2)) continue;
-          if (d2 == T(0)) {
-            set_error(err, POT_ERR_COINCIDENT_SITES, s);
-            continue;
-          }
-          T d;
-          const T h = fix_zero(plane_offset(d2, ps, q.w, d), r);
-          if (h <= -r) {
-            empty = true;
-            break;
-          }
-          if (h < r && h - (dx * ox + dy * oy + dz * oz) / d < R) {
-            if (nc < kmax) cand[row + nc] = t;
-            nc++;
-          }
-        }
-      }
+    const T ylo = g.lo[1] + cy * g.cs;
+    T ey = fmax(T(0), fmax(ylo - p.y, p.y - (ylo + g.cs)));
+    if (cy == 0 && p.y < ylo) ey = T(0);
+    if (cy == g.dim[1] - 1 && p.y > ylo) ey = T(0);
+    const T xlo = g.lo[0] + cx * g.cs;
+    T ex = fmax(T(0), fmax(xlo - p.x, p.x - (xlo + g.cs)));
+    if (cx == 0 && p.x < xlo) ex = T(0);
+    if (cx == g.dim[0] - 1 && p.x > xlo) ex = T(0);
+    const T dl2 = ex * ex + ey * ey + ez * ez;
+    if (dl2 >= D2) continue;
+    const int key = (cz * g.dim[1] + cy) * g.dim[0] + cx;
+    if (dl2 > T(0)) {
+      const T dl = sqrt(dl2);
+      const T c = gmax[key] - ps;
+      const T hmin = c >= T(0) ? T(0.5) * dl - c / (T(2) * dl) : T(0.5) * dl;
+      if (hmin >= Re) continue;
     }
+    t = cell_start[key];
+    b = cell_start[key + 1];
   }
   const T lo = srad_lo[s];
   const bool collapsed = R - lo <= T(0.03) * R;
