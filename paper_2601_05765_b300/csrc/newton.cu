@@ -241,9 +241,10 @@ int newton_sorted(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* do
     POT_CHECK(csr_compact<T>(ctx, st, n, &nnz_off));
     S->nnz = nnz_off + n;
     // inexact Newton: the linear residual only needs to be small against
-    // the distance still to go to the tolerance
+    // the distance still to go to the tolerance, and far from it no smaller
+    // than the error the next Newton step leaves anyway (about err^2)
     double rtol = P->pcg_rtol;
-    if (!(rtol > 0.0)) rtol = fmin(0.1, fmax(1e-7, 0.1 * P->tol / err));
+    if (!(rtol > 0.0)) rtol = fmin(0.1, fmax(1e-7, fmax(0.1 * P->tol / err, 0.02 * err)));
     int iters = 0;
     {
       EvTimer tm(ctx, 1, st);
