@@ -255,16 +255,27 @@ constexpr int kFusedSmem = 2 * kTM * kHid * 2 + 1024 + 64;
 
 // rows [row0, row0+128) x k [0, K) of a K-contiguous matrix (K a multiple
 // of 8) into the core-matrix layout with K/8 core matrices per 8-row group
-// (zero rows past nrows)
+// (zero rows past nrows).  Each thread issues all of its 16-byte loads
+// before its shared-memory stores, so they are in flight together.
+template <int K>
 __device__ __forceinline__ void stage_k(uint8_t* s, const bf16* src, int64_t ld, int64_t row0,
-                                        int64_t nrows, int K) {
-  const int kc8 = K / 8;
-  for (int q = threadIdx.x; q < kTM * kc8; q += kGemmThreads) {
+                                        int64_t nrows) {
+  constexpr int kc8 = K / 8;
+  constexpr int kPer = kTM * kc8 / kGemmThreads;
+  static_assert(kTM * kc8 % kGemmThreads == 0, "whole 16-byte chunks per thread");
+  uint4 v[kPer];
+#pragma unroll
+  for (int i = 0; i < kPer; i++) {
+    const int q = threadIdx.x + i * kGemmThreads;
     const int r = q / kc8, kc = q - r * kc8;
     const int64_t gr = row0 + r;
-    uint4 v = make_uint4(0, 0, 0, 0);
-    if (gr < nrows) v = *(const uint4*)(src + gr * ld + kc * 8);
-    *(uint4*)(s + ((r >> 3) * kc8 + kc) * 128 + (r & 7) * 16) = v;
+    v[i] = gr < nrows ? *(const uint4*)(src + gr * ld + kc * 8) : make_uint4(0, 0, 0, 0);
+  }
+#pragma unroll
+  for (int i = 0; i < kPer; i++) {
+    const int q = threadIdx.x + i * kGemmThreads;
+    const int r = q / kc8, kc = q - r * kc8;
+    *(uint4*)(s + ((r >> 3) * kc8 + kc) * 128 + (r & 7) * 16) = v[i];
   }
 }
 
@@ -311,8 +322,8 @@ __global__ void __launch_bounds__(kGemmThreads) k_mlp_infer(const bf16* __restri
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::);
   }
   // layer 1 operands: the input tile (K = 80) and W1 (128 x 80)
-  stage_k(sA, x, kIn, row0, M, kIn);
-  stage_k(sB, wt1, kIn, 0, kHid, kIn);
+  stage_k<kIn>(sA, x, kIn, row0, M);
+  stage_k<kIn>(sB, wt1, kIn, 0, kHid);
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -334,7 +345,7 @@ __global__ void __launch_bounds__(kGemmThreads) k_mlp_infer(const bf16* __restri
     const float* bias = p + (layer == 0 ? ob1 : (layer == 1 ? ob2 : ob3));
     // the MMAs are done with sA and sB: the next weights go into sB while
     // the activations go into sA (K = 128 layout)
-    if (layer < 2) stage_k(sB, layer == 0 ? wt2 : wt3, kHid, 0, kHid, kHid);
+    if (layer < 2) stage_k<kHid>(sB, layer == 0 ? wt2 : wt3, kHid, 0, kHid);
     for (int c0 = 0; c0 < kHid; c0 += 16) {
       float v[16];
       tmem_ld16(tmem + trow + (uint32_t)c0, v);
