@@ -14,8 +14,10 @@ Contents, each citing the paper passage it follows:
   repair_empty()  raise the weights of empty cells until each site is inside
                   its own cell, before Algorithm 1 (not in the paper: its
                   precondition, no empty cell at the start, made to hold).
-  fluid_step()    Gallouet-Merigot explicit step of Sec. 5 (pressure spring,
-                  gravity, symplectic update), no viscosity/surface tension.
+  fluid_step()    Gallouet-Merigot step of Sec. 5 (pressure spring, gravity,
+                  symplectic update); with viscosity or surface tension the
+                  semi-implicit velocity solve of Eq. 4 over the P1
+                  Laplacian of Eq. 3 (laplacian_weights, viscous_velocity).
   mlp_*()         FP64 reference of the learned warm-start MLP (not in the
                   paper): forward, backward, Adam, on BF16-rounded operands.
 
@@ -272,12 +274,47 @@ def velocity_update(x1, v, cen, dt, eps=0.01, g=(0.0, 0.0, -9.81)):
                                              + (np.asarray(cen, np.float64) - x1) / (eps * eps))
 
 
+def laplacian_weights(res, psi):
+    """Dense weights w_ij = |B_ij| / (2 d_ij) of the P1 Laplacian (Eq. 3) over
+    the restricted bisector facets of a full evaluation: the off-diagonal
+    of M = -grad^2 K with its sign flipped (walls and the free surface add
+    nothing)."""
+    n = res["vol"].shape[0]
+    _, rows = hessian_entries(res, psi)
+    w = np.zeros((n, n))
+    for i in range(n):
+        cols, vals = rows[i]
+        w[i, cols] = -vals
+    return w
+
+
+def viscous_velocity(x1, v, cen, w, dt, eps, g, mu, gamma):
+    """Semi-implicit velocity update with viscosity and surface tension
+    (Sec. 5, Eq. 4, unit mass):
+    (I/dt + mu (D - W)) v^{k+1} = v^k/dt + F_p + F_g + F_t,
+    F_p = (c - x)/eps^2, F_g = g, F_t = gamma L x, (L u)_i = sum_j w_ij (u_j - u_i),
+    D = diag(sum_j w_ij); one dense solve for the three components."""
+    x1 = np.asarray(x1, np.float64)
+    d = w.sum(axis=1)
+    lap_x = w @ x1 - d[:, None] * x1
+    b = (np.asarray(v, np.float64) / dt + (np.asarray(cen, np.float64) - x1) / (eps * eps)
+         + np.asarray(g, np.float64)[None, :] + gamma * lap_x)
+    a = np.diag(1.0 / dt + mu * d) - mu * w
+    return np.linalg.solve(a, b)
+
+
 def fluid_step(pos, vel, psi, nu, dt, eps=0.01, g=(0.0, 0.0, -9.81), tol=1e-4,
-               max_newton=100, nthreads=0):
-    """One explicit fluid step: advect + clamp, Newton at x^{k+1} warm-started
-    from psi, centroids of the converged cells, velocity update."""
+               max_newton=100, nthreads=0, mu=0.0, gamma=0.0):
+    """One fluid step: advect + clamp, Newton at x^{k+1} warm-started from
+    psi, centroids of the converged cells, velocity update -- explicit, or
+    semi-implicit with viscosity mu and surface tension gamma (Eq. 4) when
+    either is non-zero."""
     x1, v = advect_and_clamp(pos, vel, dt)
     nr = newton(x1, nu, psi, tol=tol, max_newton=max_newton, nthreads=nthreads)
     cen = nr.res["cen"]
-    v1 = velocity_update(x1, v, cen, dt, eps=eps, g=g)
+    if mu == 0.0 and gamma == 0.0:
+        v1 = velocity_update(x1, v, cen, dt, eps=eps, g=g)
+    else:
+        w = laplacian_weights(nr.res, nr.psi)
+        v1 = viscous_velocity(x1, v, cen, w, dt, eps, g, mu, gamma)
     return x1, v1, nr

@@ -129,3 +129,59 @@ def test_empty_cell_repair_puts_sites_inside_their_cells():
     ref = O.newton(pos, sc.nu, sc.psi.astype(np.float64), tol=1e-10)
     assert nr.status == O.NEWTON_OK
     np.testing.assert_allclose(nr.psi, ref.psi, rtol=1e-8)
+
+
+def _viscous_setup(seed=8):
+    from paper_2601_05765_b300 import scenes
+    sc = scenes.dam_break(nx=6, ny=6, nz=8, width=0.12, seed=seed)
+    x = sc.pos.astype(np.float64)
+    nr = O.newton(x, sc.nu, sc.psi.astype(np.float64), tol=1e-10)
+    assert nr.status == O.NEWTON_OK
+    w = O.laplacian_weights(nr.res, nr.psi)
+    rng = np.random.default_rng(seed)
+    v = rng.normal(size=x.shape)
+    return x, v, nr.res["cen"], w
+
+
+def test_viscous_update_pins():
+    """Eq. 4 against what the algebra fixes: the weights are symmetric and
+    non-negative; without viscosity and surface tension the solve is the
+    explicit update; a uniform velocity field under no force is left
+    unchanged; the Laplacian terms conserve momentum (the total velocity
+    change is dt times the summed pressure and gravity forces); viscosity
+    never adds kinetic energy to the explicit update; surface tension pulls
+    a free blob inwards."""
+    x, v, cen, w = _viscous_setup()
+    n = x.shape[0]
+    dt, eps, g = 1e-3, 0.01, np.array([0.0, 0.0, -9.81])
+    np.testing.assert_allclose(w, w.T, rtol=1e-9, atol=1e-15)
+    assert np.all(w >= 0) and np.all(np.diag(w) == 0) and w.sum() > 0
+    explicit = O.velocity_update(x, v, cen, dt, eps=eps, g=g)
+    np.testing.assert_allclose(O.viscous_velocity(x, v, cen, w, dt, eps, g, 0.0, 0.0), explicit,
+                               rtol=1e-12, atol=1e-12)
+    u = np.tile([0.3, -0.2, 0.1], (n, 1))
+    np.testing.assert_allclose(O.viscous_velocity(x, u, x, w, dt, eps, 0 * g, 50.0, 0.0), u,
+                               rtol=1e-12, atol=1e-12)
+    v1 = O.viscous_velocity(x, v, cen, w, dt, eps, g, 50.0, 3.0)
+    np.testing.assert_allclose(v1.sum(0), explicit.sum(0), rtol=1e-9, atol=1e-9)
+    vv = O.viscous_velocity(x, v, cen, w, dt, eps, g, 50.0, 0.0)
+    assert np.sum(vv ** 2) < np.sum(explicit ** 2)
+    # surface tension alone, no other force, at rest: the blob contracts
+    vt = O.viscous_velocity(x, np.zeros_like(v), x, w, dt, eps, 0 * g, 0.0, 3.0)
+    assert np.sum(vt * (x - x.mean(0))) < 0
+
+
+def test_viscous_update_against_graph_laplacian():
+    """L u built site by site from its definition (sum_j w_ij (u_j - u_i))
+    equals the matrix form the solve uses, and the solution satisfies the
+    system row by row."""
+    x, v, cen, w = _viscous_setup(9)
+    n = x.shape[0]
+    dt, eps, g, mu, gamma = 1e-3, 0.01, np.array([0.0, 0.0, -9.81]), 20.0, 2.0
+    v1 = O.viscous_velocity(x, v, cen, w, dt, eps, g, mu, gamma)
+    for i in range(0, n, 7):
+        lap_v = sum(w[i, j] * (v1[j] - v1[i]) for j in range(n) if w[i, j] > 0)
+        lap_x = sum(w[i, j] * (x[j] - x[i]) for j in range(n) if w[i, j] > 0)
+        lhs = v1[i] / dt - mu * lap_v
+        rhs = v[i] / dt + (cen[i] - x[i]) / eps ** 2 + g + gamma * lap_x
+        np.testing.assert_allclose(lhs, rhs, rtol=1e-9, atol=1e-6)
