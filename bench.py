@@ -75,6 +75,8 @@ def parse():
     ap.add_argument("--scene", default="cloud", choices=["cloud", "splash"],
                     help="cells mode: the 2^20-site random cloud, or the splash at converged weights")
     ap.add_argument("--spacing", type=float, default=3.224e-3, help="splash lattice spacing")
+    ap.add_argument("--mu", type=float, default=0.0, help="dam mode: viscosity (Eq. 4)")
+    ap.add_argument("--gamma", type=float, default=0.0, help="dam mode: surface tension")
     ap.add_argument("--advance", type=int, default=0,
                     help="cells mode, splash: fluid steps taken from the recipe's start state "
                          "before the timed calls")
@@ -605,7 +607,7 @@ def run_dam(args):
         psi = torch.as_tensor(sc.psi, dtype=dt, device=dev)
         nu = torch.as_tensor(sc.nu, dtype=torch.float64, device=dev)
         prm = pot.default_params(dt=sc.extra["dt"], eps=sc.extra["eps"],
-                                 substeps=sc.extra["substeps"])
+                                 substeps=sc.extra["substeps"], mu=args.mu, gamma=args.gamma)
         pot.relax_to_centroids(ctx, pos, psi, nu, sc.extra["relax_rounds"], params=prm)
         stats, snaps[prec] = [], {}
         for k in range(1, args.steps + 1):
@@ -618,6 +620,8 @@ def run_dam(args):
                      "newton_iters_mean": float(np.mean([st["newton_iters"] for st in stats])),
                      "pcg_iters_mean": float(np.mean([st["pcg_iters"] for st in stats])),
                      "step_ms": _pcts([st["ms_total"] for st in stats]),
+                     "viscosity_ms": _pcts([st["ms_visc"] for st in stats]),
+                     "viscosity_pcg_iters_mean": float(np.mean([st["visc_iters"] for st in stats])),
                      "err_max_per_step": _pcts([st["err_max"] for st in stats]),
                      "newton_iters_per_step": [st["newton_iters"] for st in stats]}
         ctx.close()
@@ -635,6 +639,7 @@ def run_dam(args):
     print(json.dumps({"metric": "dam break, mixed precision against FP64 on the GPU",
                       "workload": f"dam-break column 63x63x126 ({n} sites), dt 2e-3 as "
                                   f"{sc.extra['substeps']} substeps, eps {sc.extra['eps']:.3g}, "
+                                  f"viscosity {args.mu:g}, surface tension {args.gamma:g}, "
                                   f"{args.steps} steps, tol 1e-4",
                       "mixed": out["mixed"], "fp64": out["fp64"],
                       "speedup_mixed_over_fp64": out["fp64"]["step_ms"]["median"] / out["mixed"]["step_ms"]["median"],

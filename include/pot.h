@@ -109,6 +109,8 @@ typedef struct {
                            extrapolated from the previous two steps */
   int32_t substeps;     /* pot_fluid_step takes this many explicit steps of
                            dt / substeps (0 or 1: one step of dt) */
+  double mu;            /* viscosity (Eq. 4; 0: none) */
+  double gamma;         /* surface tension (Sec. 5; 0: none) */
 } pot_params;
 
 /* Statistics of one Newton solve (and of the solve inside a fluid step). */
@@ -131,6 +133,9 @@ typedef struct {
   int32_t repairs;     /* empty cells at the start whose weight was raised */
   int32_t passes;      /* security-ball passes over all cell evaluations */
   int64_t error_site;  /* caller index of a site behind the last cell error, else -1 */
+  int32_t visc_iters;  /* PCG iterations of the viscosity solves (fluid step) */
+  int32_t reserved;
+  double ms_visc;      /* host wall time of the viscosity / surface-tension update */
 } pot_solve_stats;
 
 /* ---- context ---------------------------------------------------------- */
@@ -270,6 +275,12 @@ int pot_newton_solve_f64(pot_ctx* ctx, void* stream, int64_t n, const double* po
  *        wall set to 0);
  *   psi <- Newton solve at the new x, warm-started from psi;
  *   v <- v + dt (g + (c_i - x_i) / eps^2)   (pressure spring F_p, Sec. 5).
+ * With params->mu > 0 or params->gamma > 0 the velocity update is the
+ * semi-implicit one of Eq. 4 (unit mass) over the P1 Laplacian of Eq. 3,
+ * whose weights |B_ij| / (2 d_ij) come from the converged cells:
+ *   (I/dt + mu (D - W)) v <- v/dt + (c - x)/eps^2 + g + gamma L x,
+ * one Jacobi-PCG solve per component (relative residual 1e-6 in FP32,
+ * 1e-11 in FP64); walls and the free surface add no Laplacian terms.
  * With params->warm_start = 2, Newton starts from psi + (psi - psi_prev),
  * psi_prev the weights at the start of the previous pot_fluid_step on this
  * context with the same n (none after pot_create, pot_clear_history or a

@@ -99,7 +99,8 @@ int check_ctx(pot_ctx* ctx, int64_t n, int need) {
 
 bool check_params(const pot_params* p) {
   return p && p->tol > 0.0 && p->max_newton >= 0 && p->max_halvings >= 0 && p->max_pcg > 0 &&
-         p->pcg_chunk > 0 && isfinite(p->dt) && p->eps > 0.0 && p->substeps >= 0;
+         p->pcg_chunk > 0 && isfinite(p->dt) && p->eps > 0.0 && p->substeps >= 0 &&
+         p->mu >= 0.0 && p->gamma >= 0.0 && isfinite(p->mu) && isfinite(p->gamma);
 }
 
 template <typename T, typename CSR>

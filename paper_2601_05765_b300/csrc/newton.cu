@@ -115,6 +115,66 @@ __global__ void k_extrapolate(int64_t n, const int32_t* __restrict__ perm, const
   }
 }
 
+// Semi-implicit velocity update with viscosity and surface tension (Sec. 5,
+// Eq. 4, unit mass) over the P1 Laplacian of Eq. 3, whose weights
+// w_ij = |B_ij| / (2 d_ij) are the converged cells' off-diagonal Hessian
+// entries with the sign flipped (vals = -w):
+//   (I/dt + mu (D - W)) v^{k+1} = v^k/dt + (c - x)/eps^2 + g + gamma L x,
+//   D = diag(sum_j w_ij), (L x)_i = sum_j w_ij (x_j - x_i).
+// This kernel forms the right-hand side per sorted site (into b, 3 per
+// site) and the system's diagonal (into diag).
+template <typename T>
+__global__ void k_visc_rhs(int64_t n, const int32_t* __restrict__ perm,
+                           const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ cols,
+                           const T* __restrict__ vals, const V4<T>* __restrict__ sxp,
+                           const T* cen, const T* __restrict__ vel, T dt, T inv_eps2, T gx, T gy,
+                           T gz, T mu, T gamma, T* b, T* diag) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const V4<T> p = sxp[i];
+  T wsum = T(0), lx = T(0), ly = T(0), lz = T(0);
+  for (int k = row_ptr[i]; k < row_ptr[i + 1]; k++) {
+    const T wij = -vals[k];
+    const V4<T> q = sxp[cols[k]];
+    wsum += wij;
+    lx += wij * (q.x - p.x);
+    ly += wij * (q.y - p.y);
+    lz += wij * (q.z - p.z);
+  }
+  const int64_t o = perm[i];
+  const T bx = vel[3 * o + 0] / dt + (cen[3 * i + 0] - p.x) * inv_eps2 + gx + gamma * lx;
+  const T by = vel[3 * o + 1] / dt + (cen[3 * i + 1] - p.y) * inv_eps2 + gy + gamma * ly;
+  const T bz = vel[3 * o + 2] / dt + (cen[3 * i + 2] - p.z) * inv_eps2 + gz + gamma * lz;
+  b[3 * i + 0] = bx;
+  b[3 * i + 1] = by;
+  b[3 * i + 2] = bz;
+  diag[i] = T(1) / dt + mu * wsum;
+}
+
+// off-diagonal of the system: mu (-w_ij) = mu vals
+template <typename T>
+__global__ void k_scale_vals(int64_t nnz, T* vals, T mu) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < nnz) vals[k] *= mu;
+}
+
+// component c of b (sorted) as the PCG right-hand side
+template <typename T>
+__global__ void k_visc_b(int64_t n, const T* __restrict__ b, int c, double* rhs) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) rhs[i] = (double)b[3 * i + c];
+}
+
+// component c of the new velocity (caller order): the solution u, or dt b
+// when there is no viscosity (the system is then I/dt)
+template <typename T>
+__global__ void k_visc_store(int64_t n, const int32_t* __restrict__ perm, const T* __restrict__ u,
+                             const T* __restrict__ b, int c, T dt, T* vel) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  vel[3 * (int64_t)perm[i] + c] = u ? u[i] : dt * b[3 * i + c];
+}
+
 // psi <- src (sorted), the current weights for evaluation and the base;
 // psi_max follows (reset by the caller)
 template <typename T>
@@ -362,10 +422,50 @@ int fluid_substep(pot_ctx* ctx, cudaStream_t st, int64_t n, T* pos, T* vel, T* p
   }
   if (status == POT_OK || status == POT_ERR_NOT_CONVERGED || status == POT_ERR_LINESEARCH_FAILED) {
     Work<T>& w = ctx->work<T>();
-    note_launch();
-    k_velocity<T><<<blocks_for(n, 256), 256, 0, st>>>(
-        n, ctx->perm, w.sxp, w.cen, w.psi_base, vel, psi, (T)dt, (T)(1.0 / (P->eps * P->eps)),
-        (T)P->gravity[0], (T)P->gravity[1], (T)P->gravity[2]);
+    const bool viscous = P->mu > 0.0 || P->gamma > 0.0;
+    if (viscous) {
+      // Eq. 4 over the converged cells: right-hand side from the old
+      // velocities, the weights written out (k_velocity with dt = 0 leaves
+      // the velocities alone), then one solve per component
+      const double tv = now_ms();
+      int64_t nnz_off = 0;
+      POT_CHECK(csr_compact<T>(ctx, st, n, &nnz_off));
+      note_launch();
+      k_visc_rhs<T><<<blocks_for(n, 256), 256, 0, st>>>(
+          n, ctx->perm, ctx->row_ptr, ctx->csr_cols, w.csr_vals, w.sxp, w.cen, vel, (T)dt,
+          (T)(1.0 / (P->eps * P->eps)), (T)P->gravity[0], (T)P->gravity[1], (T)P->gravity[2],
+          (T)P->mu, (T)P->gamma, w.vel_s, w.diag);
+      if (P->mu > 0.0 && nnz_off > 0) {
+        note_launch();
+        k_scale_vals<T><<<blocks_for(nnz_off, 256), 256, 0, st>>>(nnz_off, w.csr_vals, (T)P->mu);
+      }
+      POT_CUDA(cudaGetLastError());
+      note_launch();
+      k_velocity<T><<<blocks_for(n, 256), 256, 0, st>>>(
+          n, ctx->perm, w.sxp, w.cen, w.psi_base, vel, psi, T(0), T(0), T(0), T(0), T(0));
+      for (int c = 0; c < 3; c++) {
+        if (P->mu > 0.0) {
+          note_launch();
+          k_visc_b<T><<<blocks_for(n, 256), 256, 0, st>>>(n, w.vel_s, c, ctx->grad);
+          int iters = 0;
+          const double rtol = sizeof(T) == 4 ? 1e-6 : 1e-11;
+          POT_CHECK(pcg_solve<T>(ctx, st, n, nnz_off, rtol, P->max_pcg, P->pcg_chunk, &iters,
+                                 nullptr));
+          S->visc_iters += iters;
+        }
+        note_launch();
+        k_visc_store<T><<<blocks_for(n, 256), 256, 0, st>>>(n, ctx->perm, P->mu > 0.0 ? w.u : nullptr,
+                                                            w.vel_s, c, (T)dt, vel);
+      }
+      POT_CUDA(cudaGetLastError());
+      POT_CUDA(cudaStreamSynchronize(st));
+      S->ms_visc += now_ms() - tv;
+    } else {
+      note_launch();
+      k_velocity<T><<<blocks_for(n, 256), 256, 0, st>>>(
+          n, ctx->perm, w.sxp, w.cen, w.psi_base, vel, psi, (T)dt, (T)(1.0 / (P->eps * P->eps)),
+          (T)P->gravity[0], (T)P->gravity[1], (T)P->gravity[2]);
+    }
     POT_CHECK(store_hint<T>(ctx, st, n));
   }
   POT_CUDA(cudaStreamSynchronize(st));
@@ -403,6 +503,8 @@ int fluid_step(pot_ctx* ctx, cudaStream_t st, int64_t n, T* pos, T* vel, T* psi,
     acc.ms_total += s1.ms_total;
     acc.ms_cells += s1.ms_cells;
     acc.ms_pcg += s1.ms_pcg;
+    acc.visc_iters += s1.visc_iters;
+    acc.ms_visc += s1.ms_visc;
     acc.err_start = i == 0 ? s1.err_start : fmax(acc.err_start, s1.err_start);
     acc.err_max = i == 0 ? s1.err_max : fmax(acc.err_max, s1.err_max);
     acc.err_l2 = i == 0 ? s1.err_l2 : fmax(acc.err_l2, s1.err_l2);

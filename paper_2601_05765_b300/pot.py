@@ -54,7 +54,7 @@ class Params(ctypes.Structure):
                 ("pcg_chunk", ctypes.c_int32), ("pcg_rtol", ctypes.c_double),
                 ("dt", ctypes.c_double), ("eps", ctypes.c_double), ("gravity", ctypes.c_double * 3),
                 ("wall_margin", ctypes.c_double), ("warm_start", ctypes.c_int32),
-                ("substeps", ctypes.c_int32)]
+                ("substeps", ctypes.c_int32), ("mu", ctypes.c_double), ("gamma", ctypes.c_double)]
 
 
 class SolveStats(ctypes.Structure):
@@ -66,7 +66,9 @@ class SolveStats(ctypes.Structure):
                 ("ms_cells", ctypes.c_double), ("ms_pcg", ctypes.c_double),
                 ("nnz", ctypes.c_int64), ("mlp_used", ctypes.c_int32),
                 ("mlp_fallback", ctypes.c_int32), ("repairs", ctypes.c_int32),
-                ("passes", ctypes.c_int32), ("error_site", ctypes.c_int64)]
+                ("passes", ctypes.c_int32), ("error_site", ctypes.c_int64),
+                ("visc_iters", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("ms_visc", ctypes.c_double)]
 
 
 def _as_dict(st):

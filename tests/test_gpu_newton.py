@@ -149,3 +149,34 @@ def test_fluid_substeps_match_oracle_steps(ctx):
     r = math.sqrt(float(psi0.max()))
     np.testing.assert_allclose(vel.cpu().numpy(), v, rtol=0, atol=3 * 1e-3 / 1.6e-5 * r * 1e-9)
     np.testing.assert_allclose(psi.cpu().numpy(), p, rtol=0, atol=1e-8 * float(np.max(p)))
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_viscous_fluid_step_matches_oracle(ctx, dtype):
+    """Eq. 4 (viscosity and surface tension over the P1 Laplacian of the
+    converged cells) against the oracle's dense solve, one fluid step of a
+    dam-break column with a strong coupling (dt mu sum_j w_ij ~ 0.4)."""
+    sc = scenes.dam_break(nx=10, ny=10, nz=20, width=0.16, seed=2)
+    dev = ctx.device
+    npdt = np.float64 if dtype == torch.float64 else np.float32
+    r0 = O.newton(sc.pos.astype(npdt).astype(np.float64), sc.nu, sc.psi.astype(np.float64), tol=1e-10)
+    psi0 = r0.psi.astype(npdt)
+    rng = np.random.default_rng(4)
+    vel0 = (rng.normal(size=sc.pos.shape) * 0.3).astype(npdt)
+    pos, vel, psi = tens(sc.pos.astype(npdt), dtype, dev), tens(vel0, dtype, dev), tens(psi0, dtype, dev)
+    mu, gamma = 2000.0, 500.0
+    tol = 1e-10 if dtype == torch.float64 else 1e-4
+    prm = pot.default_params(tol=tol, dt=2e-3, mu=mu, gamma=gamma)
+    st = pot.pot_fluid_step(ctx, pos, vel, psi, tens(sc.nu, torch.float64, dev), params=prm)
+    assert st["status"] == 0 and (st["visc_iters"] > 0)
+    x1, v1, nr = O.fluid_step(sc.pos.astype(npdt).astype(np.float64), vel0.astype(np.float64),
+                              psi0.astype(np.float64), sc.nu, dt=2e-3, tol=1e-11, mu=mu, gamma=gamma)
+    explicit = O.velocity_update(x1, O.advect_and_clamp(sc.pos.astype(npdt).astype(np.float64),
+                                                        vel0.astype(np.float64), 2e-3)[1],
+                                 nr.res["cen"], 2e-3)
+    gv = vel.cpu().numpy().astype(np.float64)
+    # the viscous update differs from the explicit one by far more than the tolerance
+    assert np.max(np.abs(v1 - explicit)) > 1e-2
+    scale = float(np.max(np.abs(v1)))
+    atol = 1e-9 * scale if dtype == torch.float64 else 2e-3 * scale
+    np.testing.assert_allclose(gv, v1, rtol=0, atol=atol)
