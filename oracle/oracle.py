@@ -18,12 +18,15 @@ Contents, each citing the paper passage it follows:
                   symplectic update); with viscosity or surface tension the
                   semi-implicit velocity solve of Eq. 4 over the P1
                   Laplacian of Eq. 3 (laplacian_weights, viscous_velocity).
+  render_depth()  first point of each camera ray inside the fluid (the union
+                  of the balls inside the box), with the free-surface culling
+                  of Sec. 6's first-cell search; brute force over all balls.
   mlp_*()         FP64 reference of the learned warm-start MLP (not in the
                   paper): forward, backward, Adam, on BF16-rounded operands.
 
 Parity pins: tests/test_oracle_geometry.py, tests/test_oracle_newton.py,
-tests/test_oracle_mlp.py (closed forms, Monte Carlo, finite differences,
-invariants).  Functions without such a pin say "parity unpinned" below.
+tests/test_oracle_mlp.py, tests/test_oracle_render.py (closed forms, Monte
+Carlo, finite differences, invariants).  Functions without such a pin say "parity unpinned" below.
 """
 from __future__ import annotations
 
@@ -318,3 +321,71 @@ def fluid_step(pos, vel, psi, nu, dt, eps=0.01, g=(0.0, 0.0, -9.81), tol=1e-4,
         w = laplacian_weights(nr.res, nr.psi)
         v1 = viscous_velocity(x1, v, cen, w, dt, eps, g, mu, gamma)
     return x1, v1, nr
+
+
+# ---------------------------------------------------------------------------
+# first hit of camera rays (Sec. 6, finding the first cell)
+
+
+def camera_rays(origin, forward, up, fov_y, width, height):
+    """Pinhole camera: unit directions (height, width, 3) of the rays through
+    the pixel centres; row 0 at the top.  right = forward x up (normalised),
+    the image's up = right x forward, tan of the half angles fov_y / 2 and
+    that times width / height."""
+    f = np.asarray(forward, np.float64)
+    f = f / np.linalg.norm(f)
+    r = np.cross(f, np.asarray(up, np.float64))
+    r = r / np.linalg.norm(r)
+    u = np.cross(r, f)
+    tv = math.tan(0.5 * fov_y)
+    th = tv * width / height
+    sx = ((np.arange(width) + 0.5) / width * 2.0 - 1.0) * th
+    sy = (1.0 - (np.arange(height) + 0.5) / height * 2.0) * tv
+    d = f[None, None, :] + sx[None, :, None] * r[None, None, :] + sy[:, None, None] * u[None, None, :]
+    return d / np.linalg.norm(d, axis=2, keepdims=True)
+
+
+def render_depth(pos, psi, origin, forward, up, fov_y, width, height, karea=None,
+                 lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0)):
+    """Depth and normal of the first point of each camera ray inside the
+    fluid, brute force over all balls.  The fluid (the union of the
+    generalized Laguerre cells of Eq. 1) is the union of the balls inside the
+    box: a point of ball j lies in the cell of the site of least power
+    distance, which is inside that site's own ball.  Its first point along a
+    ray lies on a sphere whose cell has a free surface, so with `karea` the
+    balls of cells with |K| = 0 are skipped (the paper's free-surface
+    impostors).  depth: t of the hit (-1 when none); normal: unit outward
+    normal of the hit sphere (0 when none)."""
+    pos = np.asarray(pos, np.float64)
+    psi = np.asarray(psi, np.float64)
+    o = np.asarray(origin, np.float64)
+    d = camera_rays(origin, forward, up, fov_y, width, height).reshape(-1, 3)
+    lo = np.asarray(lo, np.float64)
+    hi = np.asarray(hi, np.float64)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        ta = (lo[None, :] - o[None, :]) / d
+        tb = (hi[None, :] - o[None, :]) / d
+    t0 = np.max(np.minimum(ta, tb), axis=1).clip(min=0.0)
+    t1 = np.min(np.maximum(ta, tb), axis=1)
+    keep = psi > 0
+    if karea is not None:
+        keep &= np.asarray(karea, np.float64) > 0
+    p, r2 = pos[keep], psi[keep]
+    best = np.full(d.shape[0], np.inf)
+    arg = np.full(d.shape[0], -1)
+    for k in range(p.shape[0]):
+        b = d @ (p[k] - o)
+        c = np.dot(p[k] - o, p[k] - o) - r2[k]
+        disc = b * b - c
+        ok = disc >= 0
+        sq = np.sqrt(np.where(ok, disc, 0.0))
+        t = np.maximum(b - sq, t0)
+        hit = ok & (t < np.minimum(b + sq, t1)) & (t < best)
+        best = np.where(hit, t, best)
+        arg = np.where(hit, k, arg)
+    depth = np.where(np.isfinite(best), best, -1.0)
+    normal = np.zeros_like(d)
+    h = arg >= 0
+    x = o[None, :] + best[h, None] * d[h]
+    normal[h] = (x - p[arg[h]]) / np.sqrt(r2[arg[h]])[:, None]
+    return depth.reshape(height, width), normal.reshape(height, width, 3)

@@ -1,0 +1,48 @@
+"""The oracle's first-hit rendering against closed forms: a ball straight
+ahead is hit at distance D - r with the normal facing the camera; rays miss
+exactly outside its silhouette (tan of the angle to the centre > r /
+sqrt(D^2 - r^2)); a nearer ball occludes a farther one; the box clips the
+union of balls; culling by the free-surface area keeps the first hit."""
+import math
+
+import numpy as np
+
+from oracle import oracle as O
+
+
+def test_single_ball_straight_ahead():
+    o, f, up = (0.5, 0.5, -1.0), (0.0, 0.0, 1.0), (0.0, 1.0, 0.0)
+    p = np.array([[0.5, 0.5, 0.5]])
+    r = 0.2
+    depth, normal = O.render_depth(p, [r * r], o, f, up, math.radians(30), 41, 31)
+    # the centre pixel's ray is the axis: distance 1.5 - 0.2
+    assert abs(depth[15, 20] - 1.3) < 1e-12
+    np.testing.assert_allclose(normal[15, 20], [0.0, 0.0, -1.0], atol=1e-12)
+    d = O.camera_rays(o, f, up, math.radians(30), 41, 31)
+    cosang = d[..., 2]
+    tan = np.sqrt(1 - cosang ** 2) / cosang
+    inside = tan < r / math.sqrt(1.5 ** 2 - r ** 2)
+    edge = np.abs(tan - r / math.sqrt(1.5 ** 2 - r ** 2)) < 1e-9
+    assert np.all((depth >= 0) == inside | edge)
+    # every hit lies on the sphere
+    x = np.asarray(o)[None, None, :] + depth[..., None] * d
+    rr = np.linalg.norm(x - p[0], axis=2)
+    assert np.all(np.abs(rr[depth >= 0] - r) < 1e-12)
+
+
+def test_occlusion_box_and_culling():
+    o, f, up = (0.5, 0.5, -1.0), (0.0, 0.0, 1.0), (0.0, 1.0, 0.0)
+    p = np.array([[0.5, 0.5, 0.7], [0.5, 0.5, 0.3]])
+    psi = np.array([0.1 ** 2, 0.05 ** 2])
+    depth, _ = O.render_depth(p, psi, o, f, up, math.radians(20), 11, 11)
+    assert abs(depth[5, 5] - (1.3 - 0.05)) < 1e-12  # the nearer, smaller ball
+    # a ball sticking out of the box: the hit is the box face z = 0
+    depth, normal = O.render_depth(np.array([[0.5, 0.5, 0.05]]), [0.1 ** 2], o, f, up,
+                                   math.radians(10), 5, 5)
+    assert abs(depth[2, 2] - 1.0) < 1e-12
+    # a ball without free surface hidden inside a bigger one: culling keeps the hit
+    p = np.array([[0.5, 0.5, 0.5], [0.5, 0.5, 0.45]])
+    psi = np.array([0.2 ** 2, 0.1 ** 2])
+    a, _ = O.render_depth(p, psi, o, f, up, math.radians(20), 9, 9)
+    b, _ = O.render_depth(p, psi, o, f, up, math.radians(20), 9, 9, karea=[1.0, 0.0])
+    np.testing.assert_array_equal(a, b)
