@@ -66,7 +66,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="step",
-                    choices=["step", "cells", "warmstart", "dam", "solve", "robust"],
+                    choices=["step", "cells", "warmstart", "dam", "solve", "robust", "render"],
                     help="step: fluid steps on the splash; cells: lgc_compute_cells alone; "
                          "warmstart: train the warm-start MLP on dam-break columns, then run the "
                          "same splash steps from the plain and the learned start; dam: the 500k "
@@ -684,6 +684,51 @@ def run_robust(args):
     ctx.close()
 
 
+def run_render(args):
+    """First hit of camera rays (pot_render_depth) on the 2M splash after
+    `advance` fluid steps from the recipe's start state: a 1920 x 1080 depth
+    and normal image, median of `steps` frames after `warmup`, with the
+    balls of cells without free surface skipped and without."""
+    import math
+
+    import torch
+
+    from paper_2601_05765_b300 import pot, scenes
+    dev = torch.device("cuda", 0)
+    sc = scenes.splash(spacing=args.spacing, seed=3)
+    n = sc.n
+    ctx = pot.Context(n, 246, 0, fp32=True, fp64=False)
+    pos, vel, psi, nu = (torch.from_numpy(a).to(dev) for a in (sc.pos, sc.vel, sc.psi, sc.nu))
+    prm = pot.default_params(dt=sc.extra["dt"], eps=sc.extra["eps"])
+    pot.relax_to_centroids(ctx, pos, psi, nu, sc.extra["relax_rounds"], params=prm)
+    for _ in range(args.advance):
+        pot.pot_fluid_step(ctx, pos, vel, psi, nu, params=prm)
+    karea = pot.lgc_compute_cells(ctx, pos, psi, nu, hessian=False)["karea"]
+    cam = dict(origin=(0.5, -0.9, 0.8), forward=(0.0, 1.0, -0.55), up=(0.0, 0.0, 1.0),
+               fov_y=math.radians(40), width=1920, height=1080)
+    out = {}
+    for name, ka in (("culled", karea), ("all_balls", None)):
+        for _ in range(args.warmup):
+            pot.render_depth(ctx, pos, psi, karea=ka, **cam)
+        times = []
+        for _ in range(args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            depth, _ = pot.render_depth(ctx, pos, psi, karea=ka, **cam)
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        times.sort()
+        ms = times[len(times) // 2]
+        out[name] = {"ms_per_frame": ms, "rays_per_s": 1920 * 1080 / (ms / 1e3),
+                     "hit_fraction": float((depth >= 0).float().mean())}
+    print(json.dumps({"metric": "camera rays per second, first hit on the fluid (pot_render_depth)",
+                      "workload": f"two-ball splash, {n} sites, step {args.advance}, 1920 x 1080, "
+                                  f"grid build included",
+                      "free_surface_cells": int((karea > 0).sum()), **out}))
+    ctx.close()
+
+
 def run_solve(args):
     """The 1000-site jittered block solved to 1e-4 from psi0 (single Newton
     solve), FP64 and mixed precision on the GPU; the FP64 oracle's Newton
@@ -741,6 +786,8 @@ def main():
         run_dam(args)
     elif args.mode == "robust":
         run_robust(args)
+    elif args.mode == "render":
+        run_render(args)
     elif args.mode == "solve":
         run_solve(args)
     else:

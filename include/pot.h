@@ -375,6 +375,37 @@ int pot_mlp_set_history(pot_mlp* mlp, void* stream, int64_t n, const float* psi_
  * does not converge (stats: mlp_used / mlp_fallback).  FP32 path only. */
 int pot_set_warm_start(pot_ctx* ctx, pot_mlp* mlp);
 
+/* ---- first hit of camera rays (Sec. 6, finding the first cell) -------- */
+
+/* Pinhole camera: rays from origin through the pixel centres; right =
+ * forward x up, the image's up = right x forward; fov_y the vertical field
+ * of view in radians, the horizontal one from width / height; row 0 at the
+ * top. */
+typedef struct {
+  double origin[3];
+  double forward[3];
+  double up[3];
+  double fov_y;
+  int32_t width, height;
+} pot_camera;
+
+/* Depth and normal of the first point of each camera ray inside the fluid:
+ * the union of the generalized Laguerre cells of Eq. 1, which is the union
+ * of the balls B(p_i, sqrt(psi_i)) inside the box dom.  pos (n,3), psi (n),
+ * karea (n, optional: the cells' free-surface areas |K_i|, e.g. from
+ * lgc_compute_cells; balls of cells with |K_i| = 0 are skipped, which leaves
+ * the first hit unchanged) are device arrays in caller order.  depth
+ * (height x width, row-major): the ray parameter t of the hit (the distance
+ * from the origin), -1 when the ray misses; normal (3 per pixel, optional):
+ * unit outward normal of the sphere hit, 0 when none.  Device buffers
+ * written on `stream`; no graphics API.  Uses ctx's FP32 grid workspace.
+ * Errors: POT_ERR_INVALID_ARG (NULL pointers, n out of range, an FP64-only
+ * context, width or height <= 0, fov_y outside (0, 3.14), degenerate
+ * forward/up), POT_ERR_CUDA. */
+int pot_render_depth(pot_ctx* ctx, void* stream, int64_t n, const float* pos, const float* psi,
+                     const float* karea, const pot_domain* dom, const pot_camera* cam,
+                     float* depth, float* normal);
+
 #ifdef __cplusplus
 }
 #endif

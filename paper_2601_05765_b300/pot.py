@@ -71,6 +71,12 @@ class SolveStats(ctypes.Structure):
                 ("ms_visc", ctypes.c_double)]
 
 
+class Camera(ctypes.Structure):
+    _fields_ = [("origin", ctypes.c_double * 3), ("forward", ctypes.c_double * 3),
+                ("up", ctypes.c_double * 3), ("fov_y", ctypes.c_double),
+                ("width", ctypes.c_int32), ("height", ctypes.c_int32)]
+
+
 def _as_dict(st):
     return {name: getattr(st, name) for name, _ in st._fields_}
 
@@ -126,6 +132,9 @@ def lib():
         L.pot_cell_diagnostics.restype = ctypes.c_int
         L.pot_clear_history.argtypes = [P]
         L.pot_clear_history.restype = ctypes.c_int
+        L.pot_render_depth.argtypes = [P, P, I64, P, P, P, ctypes.POINTER(Domain),
+                                       ctypes.POINTER(Camera), P, P]
+        L.pot_render_depth.restype = ctypes.c_int
         for f in (L.pot_mlp_create, L.pot_mlp_destroy, L.pot_mlp_num_params, L.pot_mlp_set_params,
                   L.pot_mlp_get_params, L.pot_mlp_forward, L.pot_mlp_gradients, L.pot_mlp_train_step,
                   L.pot_mlp_check, L.pot_mlp_features, L.pot_mlp_set_history,
@@ -335,6 +344,31 @@ def pot_fluid_step(ctx: Context, pos, vel, psi, targets, domain=UNIT_BOX, params
     if check and code != POT_OK:
         raise PotError(code, "pot_fluid_step", s)
     return s
+
+
+def render_depth(ctx: Context, pos, psi, origin, forward, up, fov_y, width, height, karea=None,
+                 domain=UNIT_BOX, normals=True, stream=None):
+    """First point of each camera ray inside the fluid (pot_render_depth):
+    depth (height, width) with -1 for a miss, and unit normals
+    (height, width, 3) when `normals`."""
+    n = int(pos.shape[0])
+    dev = ctx.device
+    pos = _dev(pos, torch.float32, (n, 3), "pos", dev)
+    psi = _dev(psi, torch.float32, (n,), "psi", dev)
+    if karea is not None:
+        karea = _dev(karea, torch.float32, (n,), "karea", dev)
+    cam = Camera()
+    for k in range(3):
+        cam.origin[k], cam.forward[k], cam.up[k] = float(origin[k]), float(forward[k]), float(up[k])
+    cam.fov_y, cam.width, cam.height = float(fov_y), int(width), int(height)
+    depth = torch.empty((height, width), dtype=torch.float32, device=dev)
+    normal = torch.empty((height, width, 3), dtype=torch.float32, device=dev) if normals else None
+    code = lib().pot_render_depth(ctx.handle, _stream(stream), n, _ptr(pos), _ptr(psi), _ptr(karea),
+                                  ctypes.byref(_domain(domain)), ctypes.byref(cam), _ptr(depth),
+                                  _ptr(normal))
+    if code != POT_OK:
+        raise PotError(code, "pot_render_depth")
+    return depth, normal
 
 
 def clear_history(ctx: Context):
