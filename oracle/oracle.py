@@ -291,23 +291,28 @@ def laplacian_weights(res, psi):
     return w
 
 
-def viscous_velocity(x1, v, cen, w, dt, eps, g, mu, gamma):
+def viscous_velocity(x1, v, cen, w, dt, eps, g, mu, gamma, factors=None):
     """Semi-implicit velocity update with viscosity and surface tension
     (Sec. 5, Eq. 4, unit mass):
-    (I/dt + mu (D - W)) v^{k+1} = v^k/dt + F_p + F_g + F_t,
+    (I/dt + (D_mu - W_mu)) v^{k+1} = v^k/dt + F_p + F_g + F_t,
     F_p = (c - x)/eps^2, F_g = g, F_t = gamma L x, (L u)_i = sum_j w_ij (u_j - u_i),
-    D = diag(sum_j w_ij); one dense solve for the three components."""
+    W_mu = mu_ij w_ij with mu_ij = mu (f_i + f_j) / 2 (per-site factors f for
+    several fluids, the per-pair coefficients of Sec. 5; all 1 by default),
+    D_mu = diag(sum_j mu_ij w_ij); one dense solve for the three components."""
     x1 = np.asarray(x1, np.float64)
+    n = x1.shape[0]
+    f = np.ones(n) if factors is None else np.asarray(factors, np.float64)
+    wm = mu * 0.5 * (f[:, None] + f[None, :]) * w
     d = w.sum(axis=1)
     lap_x = w @ x1 - d[:, None] * x1
     b = (np.asarray(v, np.float64) / dt + (np.asarray(cen, np.float64) - x1) / (eps * eps)
          + np.asarray(g, np.float64)[None, :] + gamma * lap_x)
-    a = np.diag(1.0 / dt + mu * d) - mu * w
+    a = np.diag(1.0 / dt + wm.sum(axis=1)) - wm
     return np.linalg.solve(a, b)
 
 
 def fluid_step(pos, vel, psi, nu, dt, eps=0.01, g=(0.0, 0.0, -9.81), tol=1e-4,
-               max_newton=100, nthreads=0, mu=0.0, gamma=0.0):
+               max_newton=100, nthreads=0, mu=0.0, gamma=0.0, factors=None):
     """One fluid step: advect + clamp, Newton at x^{k+1} warm-started from
     psi, centroids of the converged cells, velocity update -- explicit, or
     semi-implicit with viscosity mu and surface tension gamma (Eq. 4) when
@@ -319,7 +324,7 @@ def fluid_step(pos, vel, psi, nu, dt, eps=0.01, g=(0.0, 0.0, -9.81), tol=1e-4,
         v1 = velocity_update(x1, v, cen, dt, eps=eps, g=g)
     else:
         w = laplacian_weights(nr.res, nr.psi)
-        v1 = viscous_velocity(x1, v, cen, w, dt, eps, g, mu, gamma)
+        v1 = viscous_velocity(x1, v, cen, w, dt, eps, g, mu, gamma, factors)
     return x1, v1, nr
 
 

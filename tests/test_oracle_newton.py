@@ -185,3 +185,23 @@ def test_viscous_update_against_graph_laplacian():
         lhs = v1[i] / dt - mu * lap_v
         rhs = v[i] / dt + (cen[i] - x[i]) / eps ** 2 + g + gamma * lap_x
         np.testing.assert_allclose(lhs, rhs, rtol=1e-9, atol=1e-6)
+
+
+def test_viscous_factors_pins():
+    """Per-site viscosity factors (mu_ij = mu (f_i + f_j) / 2): all ones is
+    the single-fluid update; the system stays symmetric with zero row sums
+    off the I/dt part, so momentum is conserved; a site of factor 0 among
+    factor-0 neighbours moves as without viscosity."""
+    x, v, cen, w = _viscous_setup(10)
+    n = x.shape[0]
+    dt, eps, g = 1e-3, 0.01, np.array([0.0, 0.0, -9.81])
+    one = O.viscous_velocity(x, v, cen, w, dt, eps, g, 50.0, 1.0)
+    np.testing.assert_allclose(O.viscous_velocity(x, v, cen, w, dt, eps, g, 50.0, 1.0, np.ones(n)),
+                               one, rtol=1e-12, atol=1e-12)
+    f = np.random.default_rng(3).uniform(0.1, 2.0, n)
+    vf = O.viscous_velocity(x, v, cen, w, dt, eps, g, 50.0, 1.0, f)
+    explicit = O.velocity_update(x, v, cen, dt, eps=eps, g=g)
+    lap_x_sum = (w @ x - w.sum(1)[:, None] * x).sum(0)
+    np.testing.assert_allclose(vf.sum(0), explicit.sum(0) + dt * 1.0 * lap_x_sum, rtol=1e-9, atol=1e-9)
+    zero = O.viscous_velocity(x, v, cen, w, dt, eps, g, 50.0, 0.0, np.zeros(n))
+    np.testing.assert_allclose(zero, explicit, rtol=1e-12, atol=1e-12)
