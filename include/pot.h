@@ -303,6 +303,13 @@ int pot_fluid_step_f64(pot_ctx* ctx, void* stream, int64_t n, double* pos, doubl
  * context).  Errors: POT_ERR_INVALID_ARG for a NULL context. */
 int pot_clear_history(pot_ctx* ctx);
 
+/* Several fluids (Sec. 5's per-pair viscosity coefficients): per-site
+ * factors f (device, n floats, caller order, owned by the caller and read by
+ * every later viscous pot_fluid_step with this n) make the pair coefficient
+ * mu_ij = params->mu (f_i + f_j) / 2.  NULL clears them (mu_ij = mu).
+ * Errors: POT_ERR_INVALID_ARG (NULL context; n out of range with factors). */
+int pot_set_viscosity_factors(pot_ctx* ctx, int64_t n, const float* factors);
+
 /* ---- learned warm start (not in the paper) ------------------------------- */
 
 /* A small MLP predicts each site's new weight from its neighbourhood:

@@ -196,6 +196,13 @@ void pot_default_params(pot_params* p) {
   p->warm_start = 0;
 }
 
+int pot_set_viscosity_factors(pot_ctx* ctx, int64_t n, const float* factors) {
+  if (!ctx || (factors && (n <= 0 || n > ctx->n_max))) return POT_ERR_INVALID_ARG;
+  ctx->visc_factors = factors;
+  ctx->visc_factors_n = factors ? n : -1;
+  return POT_OK;
+}
+
 int pot_clear_history(pot_ctx* ctx) {
   if (!ctx) return POT_ERR_INVALID_ARG;
   ctx->wf.hist_n = -1;

@@ -123,20 +123,27 @@ __global__ void k_extrapolate(int64_t n, const int32_t* __restrict__ perm, const
 //   D = diag(sum_j w_ij), (L x)_i = sum_j w_ij (x_j - x_i).
 // This kernel forms the right-hand side per sorted site (into b, 3 per
 // site) and the system's diagonal (into diag).
+// With per-site factors f (several fluids), mu_ij = mu (f_i + f_j) / 2 (the
+// per-pair coefficients of Sec. 5); the row's entries become the system's
+// off-diagonal -mu_ij w_ij in place (each thread owns its row).
 template <typename T>
 __global__ void k_visc_rhs(int64_t n, const int32_t* __restrict__ perm,
                            const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ cols,
-                           const T* __restrict__ vals, const V4<T>* __restrict__ sxp,
-                           const T* cen, const T* __restrict__ vel, T dt, T inv_eps2, T gx, T gy,
-                           T gz, T mu, T gamma, T* b, T* diag) {
+                           T* vals, const V4<T>* __restrict__ sxp, const T* cen,
+                           const T* __restrict__ vel, const float* __restrict__ factors, T dt,
+                           T inv_eps2, T gx, T gy, T gz, T mu, T gamma, T* b, T* diag) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const V4<T> p = sxp[i];
-  T wsum = T(0), lx = T(0), ly = T(0), lz = T(0);
+  const T fi = factors ? (T)factors[perm[i]] : T(1);
+  T msum = T(0), lx = T(0), ly = T(0), lz = T(0);
   for (int k = row_ptr[i]; k < row_ptr[i + 1]; k++) {
     const T wij = -vals[k];
-    const V4<T> q = sxp[cols[k]];
-    wsum += wij;
+    const int j = cols[k];
+    const V4<T> q = sxp[j];
+    const T mij = factors ? mu * T(0.5) * (fi + (T)factors[perm[j]]) : mu;
+    msum += mij * wij;
+    vals[k] = -mij * wij;
     lx += wij * (q.x - p.x);
     ly += wij * (q.y - p.y);
     lz += wij * (q.z - p.z);
@@ -148,14 +155,7 @@ __global__ void k_visc_rhs(int64_t n, const int32_t* __restrict__ perm,
   b[3 * i + 0] = bx;
   b[3 * i + 1] = by;
   b[3 * i + 2] = bz;
-  diag[i] = T(1) / dt + mu * wsum;
-}
-
-// off-diagonal of the system: mu (-w_ij) = mu vals
-template <typename T>
-__global__ void k_scale_vals(int64_t nnz, T* vals, T mu) {
-  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < nnz) vals[k] *= mu;
+  diag[i] = T(1) / dt + msum;
 }
 
 // component c of b (sorted) as the PCG right-hand side
@@ -432,13 +432,10 @@ int fluid_substep(pot_ctx* ctx, cudaStream_t st, int64_t n, T* pos, T* vel, T* p
       POT_CHECK(csr_compact<T>(ctx, st, n, &nnz_off));
       note_launch();
       k_visc_rhs<T><<<blocks_for(n, 256), 256, 0, st>>>(
-          n, ctx->perm, ctx->row_ptr, ctx->csr_cols, w.csr_vals, w.sxp, w.cen, vel, (T)dt,
+          n, ctx->perm, ctx->row_ptr, ctx->csr_cols, w.csr_vals, w.sxp, w.cen, vel,
+          ctx->visc_factors_n == n ? ctx->visc_factors : nullptr, (T)dt,
           (T)(1.0 / (P->eps * P->eps)), (T)P->gravity[0], (T)P->gravity[1], (T)P->gravity[2],
           (T)P->mu, (T)P->gamma, w.vel_s, w.diag);
-      if (P->mu > 0.0 && nnz_off > 0) {
-        note_launch();
-        k_scale_vals<T><<<blocks_for(nnz_off, 256), 256, 0, st>>>(nnz_off, w.csr_vals, (T)P->mu);
-      }
       POT_CUDA(cudaGetLastError());
       note_launch();
       k_velocity<T><<<blocks_for(n, 256), 256, 0, st>>>(

@@ -175,6 +175,8 @@ struct pot_mlp;
 
 struct pot_ctx {
   pot_mlp* mlp = nullptr;  // learned warm-start model (pot_set_warm_start), not owned
+  const float* visc_factors = nullptr;  // per-site viscosity factors (caller's, caller order)
+  int64_t visc_factors_n = -1;          // sites they were given for
   int device = 0;
   int64_t n_max = 0;
   int32_t k_max = 0;

@@ -132,6 +132,8 @@ def lib():
         L.pot_cell_diagnostics.restype = ctypes.c_int
         L.pot_clear_history.argtypes = [P]
         L.pot_clear_history.restype = ctypes.c_int
+        L.pot_set_viscosity_factors.argtypes = [P, I64, P]
+        L.pot_set_viscosity_factors.restype = ctypes.c_int
         L.pot_render_depth.argtypes = [P, P, I64, P, P, P, ctypes.POINTER(Domain),
                                        ctypes.POINTER(Camera), P, P]
         L.pot_render_depth.restype = ctypes.c_int
@@ -369,6 +371,22 @@ def render_depth(ctx: Context, pos, psi, origin, forward, up, fov_y, width, heig
     if code != POT_OK:
         raise PotError(code, "pot_render_depth")
     return depth, normal
+
+
+def set_viscosity_factors(ctx: Context, factors):
+    """Per-site viscosity factors (mu_ij = mu (f_i + f_j) / 2) for later
+    viscous fluid steps; None clears them.  The tensor must stay alive while
+    they are in use (the library keeps its pointer)."""
+    if factors is None:
+        code = lib().pot_set_viscosity_factors(ctx.handle, 0, None)
+        ctx._visc_factors = None
+    else:
+        n = int(factors.shape[0])
+        factors = _dev(factors, torch.float32, (n,), "factors", ctx.device)
+        ctx._visc_factors = factors
+        code = lib().pot_set_viscosity_factors(ctx.handle, n, _ptr(factors))
+    if code != POT_OK:
+        raise PotError(code, "pot_set_viscosity_factors")
 
 
 def clear_history(ctx: Context):

@@ -180,3 +180,28 @@ def test_viscous_fluid_step_matches_oracle(ctx, dtype):
     scale = float(np.max(np.abs(v1)))
     atol = 1e-9 * scale if dtype == torch.float64 else 2e-3 * scale
     np.testing.assert_allclose(gv, v1, rtol=0, atol=atol)
+
+
+def test_viscous_factors_match_oracle(ctx):
+    """Two fluids: per-site viscosity factors (mu_ij = mu (f_i + f_j) / 2),
+    the lower half of the column 20x more viscous, against the oracle (FP64)."""
+    sc = scenes.dam_break(nx=10, ny=10, nz=20, width=0.16, seed=2)
+    dev = ctx.device
+    x0 = sc.pos.astype(np.float64)
+    r0 = O.newton(x0, sc.nu, sc.psi.astype(np.float64), tol=1e-10)
+    rng = np.random.default_rng(6)
+    vel0 = rng.normal(size=sc.pos.shape) * 0.3
+    f = np.where(x0[:, 2] < 0.08, 2.0, 0.1)
+    pos, vel, psi = tens(x0, torch.float64, dev), tens(vel0, torch.float64, dev), tens(r0.psi, torch.float64, dev)
+    pot.set_viscosity_factors(ctx, torch.as_tensor(f, dtype=torch.float32, device=dev))
+    try:
+        prm = pot.default_params(tol=1e-10, dt=2e-3, mu=2000.0, gamma=100.0)
+        st = pot.pot_fluid_step(ctx, pos, vel, psi, tens(sc.nu, torch.float64, dev), params=prm)
+    finally:
+        pot.set_viscosity_factors(ctx, None)
+    assert st["status"] == 0
+    x1, v1, _ = O.fluid_step(x0, vel0, r0.psi, sc.nu, dt=2e-3, tol=1e-11, mu=2000.0, gamma=100.0,
+                             factors=f.astype(np.float32).astype(np.float64))
+    _, v_one, _ = O.fluid_step(x0, vel0, r0.psi, sc.nu, dt=2e-3, tol=1e-11, mu=2000.0, gamma=100.0)
+    assert np.max(np.abs(v1 - v_one)) > 1e-2  # the factors matter
+    np.testing.assert_allclose(vel.cpu().numpy(), v1, rtol=0, atol=1e-9 * float(np.max(np.abs(v1))))
