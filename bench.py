@@ -77,6 +77,7 @@ def parse():
     ap.add_argument("--spacing", type=float, default=3.224e-3, help="splash lattice spacing")
     ap.add_argument("--mu", type=float, default=0.0, help="dam mode: viscosity (Eq. 4)")
     ap.add_argument("--gamma", type=float, default=0.0, help="dam mode: surface tension")
+    ap.add_argument("--mu-wall", type=float, default=0.0, help="dam mode: no-slip wall viscosity")
     ap.add_argument("--advance", type=int, default=0,
                     help="cells mode, splash: fluid steps taken from the recipe's start state "
                          "before the timed calls")
@@ -607,7 +608,8 @@ def run_dam(args):
         psi = torch.as_tensor(sc.psi, dtype=dt, device=dev)
         nu = torch.as_tensor(sc.nu, dtype=torch.float64, device=dev)
         prm = pot.default_params(dt=sc.extra["dt"], eps=sc.extra["eps"],
-                                 substeps=sc.extra["substeps"], mu=args.mu, gamma=args.gamma)
+                                 substeps=sc.extra["substeps"], mu=args.mu, gamma=args.gamma,
+                                 mu_wall=args.mu_wall)
         pot.relax_to_centroids(ctx, pos, psi, nu, sc.extra["relax_rounds"], params=prm)
         stats, snaps[prec] = [], {}
         for k in range(1, args.steps + 1):
@@ -639,7 +641,7 @@ def run_dam(args):
     print(json.dumps({"metric": "dam break, mixed precision against FP64 on the GPU",
                       "workload": f"dam-break column 63x63x126 ({n} sites), dt 2e-3 as "
                                   f"{sc.extra['substeps']} substeps, eps {sc.extra['eps']:.3g}, "
-                                  f"viscosity {args.mu:g}, surface tension {args.gamma:g}, "
+                                  f"viscosity {args.mu:g}, surface tension {args.gamma:g}, wall viscosity {args.mu_wall:g}, "
                                   f"{args.steps} steps, tol 1e-4",
                       "mixed": out["mixed"], "fp64": out["fp64"],
                       "speedup_mixed_over_fp64": out["fp64"]["step_ms"]["median"] / out["mixed"]["step_ms"]["median"],

@@ -111,6 +111,7 @@ typedef struct {
                            dt / substeps (0 or 1: one step of dt) */
   double mu;            /* viscosity (Eq. 4; 0: none) */
   double gamma;         /* surface tension (Sec. 5; 0: none) */
+  double mu_wall;       /* fluid-wall affinity of the viscosity (walls at rest; 0: none) */
 } pot_params;
 
 /* Statistics of one Newton solve (and of the solve inside a fluid step). */
@@ -280,7 +281,9 @@ int pot_newton_solve_f64(pot_ctx* ctx, void* stream, int64_t n, const double* po
  * whose weights |B_ij| / (2 d_ij) come from the converged cells:
  *   (I/dt + mu (D - W)) v <- v/dt + (c - x)/eps^2 + g + gamma L x,
  * one Jacobi-PCG solve per component (relative residual 1e-6 in FP32,
- * 1e-11 in FP64); walls and the free surface add no Laplacian terms.
+ * 1e-11 in FP64); params->mu_wall > 0 adds walls at rest, mu_wall times the
+ * cell's wall facets' weight |B_iw| / (2 h_iw) on the diagonal (Sec. 5's
+ * fluid-boundary term); the free surface adds no Laplacian term.
  * With params->warm_start = 2, Newton starts from psi + (psi - psi_prev),
  * psi_prev the weights at the start of the previous pot_fluid_step on this
  * context with the same n (none after pot_create, pot_clear_history or a

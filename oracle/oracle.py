@@ -291,14 +291,30 @@ def laplacian_weights(res, psi):
     return w
 
 
-def viscous_velocity(x1, v, cen, w, dt, eps, g, mu, gamma, factors=None):
+def wall_weights(res, pos, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0)):
+    """Per cell, the walls' P1 Laplacian weight sum_w |B_iw| / (2 h_iw) (Eq. 3
+    with the wall as the neighbour, Sec. 5's fluid-boundary term without the
+    volume factor): wall facet areas over twice the site's distance to the
+    wall (walls in the order -x, +x, -y, +y, -z, +z)."""
+    pos = np.asarray(pos, np.float64)
+    lo = np.asarray(lo, np.float64)
+    hi = np.asarray(hi, np.float64)
+    h = np.stack([pos[:, 0] - lo[0], hi[0] - pos[:, 0], pos[:, 1] - lo[1], hi[1] - pos[:, 1],
+                  pos[:, 2] - lo[2], hi[2] - pos[:, 2]], axis=1)
+    a = res["wall_area"]
+    return np.sum(np.where(a > 0, a / (2.0 * np.where(h > 0, h, np.inf)), 0.0), axis=1)
+
+
+def viscous_velocity(x1, v, cen, w, dt, eps, g, mu, gamma, factors=None, wall_w=None,
+                     mu_wall=0.0):
     """Semi-implicit velocity update with viscosity and surface tension
     (Sec. 5, Eq. 4, unit mass):
     (I/dt + (D_mu - W_mu)) v^{k+1} = v^k/dt + F_p + F_g + F_t,
     F_p = (c - x)/eps^2, F_g = g, F_t = gamma L x, (L u)_i = sum_j w_ij (u_j - u_i),
     W_mu = mu_ij w_ij with mu_ij = mu (f_i + f_j) / 2 (per-site factors f for
     several fluids, the per-pair coefficients of Sec. 5; all 1 by default),
-    D_mu = diag(sum_j mu_ij w_ij); one dense solve for the three components."""
+    D_mu = diag(sum_j mu_ij w_ij); walls at rest add mu_wall * wall_w to the
+    diagonal (no-slip); one dense solve for the three components."""
     x1 = np.asarray(x1, np.float64)
     n = x1.shape[0]
     f = np.ones(n) if factors is None else np.asarray(factors, np.float64)
@@ -307,12 +323,13 @@ def viscous_velocity(x1, v, cen, w, dt, eps, g, mu, gamma, factors=None):
     lap_x = w @ x1 - d[:, None] * x1
     b = (np.asarray(v, np.float64) / dt + (np.asarray(cen, np.float64) - x1) / (eps * eps)
          + np.asarray(g, np.float64)[None, :] + gamma * lap_x)
-    a = np.diag(1.0 / dt + wm.sum(axis=1)) - wm
+    dw = np.zeros(n) if wall_w is None else mu_wall * np.asarray(wall_w, np.float64)
+    a = np.diag(1.0 / dt + wm.sum(axis=1) + dw) - wm
     return np.linalg.solve(a, b)
 
 
 def fluid_step(pos, vel, psi, nu, dt, eps=0.01, g=(0.0, 0.0, -9.81), tol=1e-4,
-               max_newton=100, nthreads=0, mu=0.0, gamma=0.0, factors=None):
+               max_newton=100, nthreads=0, mu=0.0, gamma=0.0, factors=None, mu_wall=0.0):
     """One fluid step: advect + clamp, Newton at x^{k+1} warm-started from
     psi, centroids of the converged cells, velocity update -- explicit, or
     semi-implicit with viscosity mu and surface tension gamma (Eq. 4) when
@@ -320,11 +337,12 @@ def fluid_step(pos, vel, psi, nu, dt, eps=0.01, g=(0.0, 0.0, -9.81), tol=1e-4,
     x1, v = advect_and_clamp(pos, vel, dt)
     nr = newton(x1, nu, psi, tol=tol, max_newton=max_newton, nthreads=nthreads)
     cen = nr.res["cen"]
-    if mu == 0.0 and gamma == 0.0:
+    if mu == 0.0 and gamma == 0.0 and mu_wall == 0.0:
         v1 = velocity_update(x1, v, cen, dt, eps=eps, g=g)
     else:
         w = laplacian_weights(nr.res, nr.psi)
-        v1 = viscous_velocity(x1, v, cen, w, dt, eps, g, mu, gamma, factors)
+        ww = wall_weights(nr.res, x1) if mu_wall > 0.0 else None
+        v1 = viscous_velocity(x1, v, cen, w, dt, eps, g, mu, gamma, factors, ww, mu_wall)
     return x1, v1, nr
 
 

@@ -541,6 +541,7 @@ __device__ __forceinline__ void plane_of(int f, int64_t cell, const V4<T>& p, in
 template <typename T>
 struct CellAcc {
   T hA, om, nx, ny, nz, hx, hy, hz, dg, rm2;
+  T wg;      // sum over wall facets of |B| / (2 h): the walls' P1 Laplacian weight
   int nfac;  // facets of positive area
   int arc;   // facets with a circular edge
 };
@@ -556,7 +557,10 @@ __device__ __forceinline__ void acc_facet(CellAcc<T>& a, const V4<T>& pl, T pd, 
   a.hx += pl.w * fo.mx;
   a.hy += pl.w * fo.my;
   a.hz += pl.w * fo.mz;
-  if (pj >= 0) a.dg += fo.area / (T(2) * pd);
+  if (pj >= 0)
+    a.dg += fo.area / (T(2) * pd);
+  else
+    a.wg += fo.area / (T(2) * pl.w);
   a.rm2 = fmax(a.rm2, fo.rm2);
   a.nfac += fo.area > T(0) ? 1 : 0;
   a.arc += fo.arc;
@@ -584,6 +588,7 @@ __device__ __forceinline__ void seg_reduce(CellAcc<T>& a, int lane, int last) {
   a.hy = seg_sum(a.hy, lane, last);
   a.hz = seg_sum(a.hz, lane, last);
   a.dg = seg_sum(a.dg, lane, last);
+  a.wg = seg_sum(a.wg, lane, last);
 #pragma unroll
   for (int off = 1; off < 32; off <<= 1) {
     T t = __shfl_down_sync(kFull, a.rm2, off);
@@ -603,6 +608,7 @@ struct CellOut {
   int32_t* row_cnt;
   double* grad;
   const double* snu;
+  void* wallw;  // the walls' Laplacian weight per cell (optional)
 };
 
 template <typename T>
@@ -660,6 +666,7 @@ __device__ __forceinline__ void write_cell(int64_t cell, const V4<T>& p, bool em
   cen[3 * cell + 2] = cz;
   o.row_cnt[cell] = cnt;
   if (o.grad) o.grad[cell] = o.snu[cell] - (double)V;
+  if (o.wallw) ((T*)o.wallw)[cell] = empty ? T(0) : a.wg;
 }
 
 // Warps per block of the cell kernel: the plane window of every warp lives in
@@ -823,6 +830,7 @@ __global__ void __launch_bounds__(CellCfg<T>::warps * 32, 5)
         s.hy += a.hy;
         s.hz += a.hz;
         s.dg += a.dg;
+        s.wg += a.wg;
         s.rm2 = fmax(s.rm2, a.rm2);
         s.nfac += a.nfac;
         s.arc += a.arc;
@@ -1239,6 +1247,7 @@ int cells_eval(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* dom, 
   o.need = ctx->need;
   o.vol = w.vol;
   o.karea = w.karea;
+  o.wallw = w.wallw;
   o.diag = w.diag;
   o.cen = w.cen;
   o.row_cnt = ctx->row_cnt;

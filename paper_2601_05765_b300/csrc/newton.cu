@@ -119,8 +119,9 @@ __global__ void k_extrapolate(int64_t n, const int32_t* __restrict__ perm, const
 // Eq. 4, unit mass) over the P1 Laplacian of Eq. 3, whose weights
 // w_ij = |B_ij| / (2 d_ij) are the converged cells' off-diagonal Hessian
 // entries with the sign flipped (vals = -w):
-//   (I/dt + mu (D - W)) v^{k+1} = v^k/dt + (c - x)/eps^2 + g + gamma L x,
-//   D = diag(sum_j w_ij), (L x)_i = sum_j w_ij (x_j - x_i).
+//   (I/dt + mu (D - W) + mu_wall Dw) v^{k+1} = v^k/dt + (c - x)/eps^2 + g + gamma L x,
+//   D = diag(sum_j w_ij), (L x)_i = sum_j w_ij (x_j - x_i), Dw = diag of the
+//   wall facets' weights |B_iw| / (2 h_iw) (walls at rest: no-slip).
 // This kernel forms the right-hand side per sorted site (into b, 3 per
 // site) and the system's diagonal (into diag).
 // With per-site factors f (several fluids), mu_ij = mu (f_i + f_j) / 2 (the
@@ -130,8 +131,9 @@ template <typename T>
 __global__ void k_visc_rhs(int64_t n, const int32_t* __restrict__ perm,
                            const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ cols,
                            T* vals, const V4<T>* __restrict__ sxp, const T* cen,
-                           const T* __restrict__ vel, const float* __restrict__ factors, T dt,
-                           T inv_eps2, T gx, T gy, T gz, T mu, T gamma, T* b, T* diag) {
+                           const T* __restrict__ vel, const float* __restrict__ factors,
+                           const T* __restrict__ wallw, T mu_wall, T dt, T inv_eps2, T gx, T gy,
+                           T gz, T mu, T gamma, T* b, T* diag) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const V4<T> p = sxp[i];
@@ -155,7 +157,8 @@ __global__ void k_visc_rhs(int64_t n, const int32_t* __restrict__ perm,
   b[3 * i + 0] = bx;
   b[3 * i + 1] = by;
   b[3 * i + 2] = bz;
-  diag[i] = T(1) / dt + msum;
+  // no-slip walls: the wall facets' Laplacian weight towards zero velocity
+  diag[i] = T(1) / dt + msum + mu_wall * wallw[i];
 }
 
 // component c of b (sorted) as the PCG right-hand side
@@ -422,7 +425,8 @@ int fluid_substep(pot_ctx* ctx, cudaStream_t st, int64_t n, T* pos, T* vel, T* p
   }
   if (status == POT_OK || status == POT_ERR_NOT_CONVERGED || status == POT_ERR_LINESEARCH_FAILED) {
     Work<T>& w = ctx->work<T>();
-    const bool viscous = P->mu > 0.0 || P->gamma > 0.0;
+    const bool viscous = P->mu > 0.0 || P->gamma > 0.0 || P->mu_wall > 0.0;
+    const bool solve = P->mu > 0.0 || P->mu_wall > 0.0;
     if (viscous) {
       // Eq. 4 over the converged cells: right-hand side from the old
       // velocities, the weights written out (k_velocity with dt = 0 leaves
@@ -433,7 +437,7 @@ int fluid_substep(pot_ctx* ctx, cudaStream_t st, int64_t n, T* pos, T* vel, T* p
       note_launch();
       k_visc_rhs<T><<<blocks_for(n, 256), 256, 0, st>>>(
           n, ctx->perm, ctx->row_ptr, ctx->csr_cols, w.csr_vals, w.sxp, w.cen, vel,
-          ctx->visc_factors_n == n ? ctx->visc_factors : nullptr, (T)dt,
+          ctx->visc_factors_n == n ? ctx->visc_factors : nullptr, w.wallw, (T)P->mu_wall, (T)dt,
           (T)(1.0 / (P->eps * P->eps)), (T)P->gravity[0], (T)P->gravity[1], (T)P->gravity[2],
           (T)P->mu, (T)P->gamma, w.vel_s, w.diag);
       POT_CUDA(cudaGetLastError());
@@ -441,7 +445,7 @@ int fluid_substep(pot_ctx* ctx, cudaStream_t st, int64_t n, T* pos, T* vel, T* p
       k_velocity<T><<<blocks_for(n, 256), 256, 0, st>>>(
           n, ctx->perm, w.sxp, w.cen, w.psi_base, vel, psi, T(0), T(0), T(0), T(0), T(0));
       for (int c = 0; c < 3; c++) {
-        if (P->mu > 0.0) {
+        if (solve) {
           note_launch();
           k_visc_b<T><<<blocks_for(n, 256), 256, 0, st>>>(n, w.vel_s, c, ctx->grad);
           int iters = 0;
@@ -451,7 +455,7 @@ int fluid_substep(pot_ctx* ctx, cudaStream_t st, int64_t n, T* pos, T* vel, T* p
           S->visc_iters += iters;
         }
         note_launch();
-        k_visc_store<T><<<blocks_for(n, 256), 256, 0, st>>>(n, ctx->perm, P->mu > 0.0 ? w.u : nullptr,
+        k_visc_store<T><<<blocks_for(n, 256), 256, 0, st>>>(n, ctx->perm, solve ? w.u : nullptr,
                                                             w.vel_s, c, (T)dt, vel);
       }
       POT_CUDA(cudaGetLastError());

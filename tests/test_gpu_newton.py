@@ -205,3 +205,32 @@ def test_viscous_factors_match_oracle(ctx):
     _, v_one, _ = O.fluid_step(x0, vel0, r0.psi, sc.nu, dt=2e-3, tol=1e-11, mu=2000.0, gamma=100.0)
     assert np.max(np.abs(v1 - v_one)) > 1e-2  # the factors matter
     np.testing.assert_allclose(vel.cpu().numpy(), v1, rtol=0, atol=1e-9 * float(np.max(np.abs(v1))))
+
+
+@pytest.mark.parametrize("dtype,mu", [(torch.float64, 0.0), (torch.float32, 2000.0)])
+def test_wall_viscosity_matches_oracle(ctx, dtype, mu):
+    """The fluid-boundary term (Sec. 5, walls at rest): mu_wall times the
+    walls' P1 Laplacian weight sum_w |B_iw| / (2 h_iw) on the diagonal of
+    Eq. 4, alone (the bulk viscosity off) and with the bulk viscosity, against
+    the oracle's dense solve on a dam-break column standing in a box corner."""
+    sc = scenes.dam_break(nx=10, ny=10, nz=20, width=0.16, seed=2)
+    dev = ctx.device
+    npdt = np.float64 if dtype == torch.float64 else np.float32
+    x0 = sc.pos.astype(npdt).astype(np.float64)
+    r0 = O.newton(x0, sc.nu, sc.psi.astype(np.float64), tol=1e-10)
+    psi0 = r0.psi.astype(npdt)
+    rng = np.random.default_rng(8)
+    vel0 = (rng.normal(size=sc.pos.shape) * 0.3).astype(npdt)
+    pos, vel, psi = tens(x0, dtype, dev), tens(vel0, dtype, dev), tens(psi0, dtype, dev)
+    mu_wall = 1e4
+    tol = 1e-10 if dtype == torch.float64 else 1e-4
+    prm = pot.default_params(tol=tol, dt=2e-3, mu=mu, gamma=0.0, mu_wall=mu_wall)
+    st = pot.pot_fluid_step(ctx, pos, vel, psi, tens(sc.nu, torch.float64, dev), params=prm)
+    assert st["status"] == 0 and st["visc_iters"] > 0
+    args = (x0, vel0.astype(np.float64), psi0.astype(np.float64), sc.nu)
+    _, v1, _ = O.fluid_step(*args, dt=2e-3, tol=1e-11, mu=mu, mu_wall=mu_wall)
+    _, v_free, _ = O.fluid_step(*args, dt=2e-3, tol=1e-11, mu=mu)
+    assert np.max(np.abs(v1 - v_free)) > 1e-2  # the walls matter
+    scale = float(np.max(np.abs(v1)))
+    atol = 1e-9 * scale if dtype == torch.float64 else 2e-3 * scale
+    np.testing.assert_allclose(vel.cpu().numpy().astype(np.float64), v1, rtol=0, atol=atol)

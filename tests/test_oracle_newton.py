@@ -205,3 +205,23 @@ def test_viscous_factors_pins():
     np.testing.assert_allclose(vf.sum(0), explicit.sum(0) + dt * 1.0 * lap_x_sum, rtol=1e-9, atol=1e-9)
     zero = O.viscous_velocity(x, v, cen, w, dt, eps, g, 50.0, 0.0, np.zeros(n))
     np.testing.assert_allclose(zero, explicit, rtol=1e-12, atol=1e-12)
+
+
+def test_wall_weights_closed_form_and_no_slip():
+    """A lone ball cut by the floor at height h: its wall facet is the disk
+    of radius sqrt(psi - h^2), weight pi (psi - h^2) / (2 h); a stiff wall
+    affinity brings that site's velocity to rest (no-slip) while a site away
+    from the walls keeps its explicit update."""
+    pos = np.array([[0.5, 0.5, 0.05], [0.5, 0.5, 0.5]])
+    psi = np.array([0.08 ** 2, 0.05 ** 2])
+    res = O.cells(pos, psi)
+    ww = O.wall_weights(res, pos)
+    assert abs(ww[0] - math.pi * (psi[0] - 0.05 ** 2) / (2 * 0.05)) < 1e-12
+    assert ww[1] == 0.0
+    w = O.laplacian_weights(res, psi)
+    v = np.array([[1.0, 0.0, 0.0], [1.0, 0.0, 0.0]])
+    out = O.viscous_velocity(pos, v, res["cen"], w, 1e-3, 0.01, np.zeros(3), 0.0, 0.0,
+                             wall_w=ww, mu_wall=1e13)
+    assert np.max(np.abs(out[0])) < 1e-6
+    expl = O.velocity_update(pos, v, res["cen"], 1e-3, eps=0.01, g=(0.0, 0.0, 0.0))
+    np.testing.assert_allclose(out[1], expl[1], rtol=1e-12, atol=1e-12)
