@@ -56,7 +56,7 @@ SMALL_SPACING = 0.032  # ~2000 sites with the splash recipe
 # 536k sites, step 30 (the bench's run in miniature);
 # profiles/k_cells_splash_536k_step30.md
 K_CELLS_FLOP_PER_CELL = 10049.0
-K_CELLS_DRAM_BYTES_PER_CELL = 380.0
+K_CELLS_DRAM_BYTES_PER_CELL = 385.0
 
 
 def parse():

@@ -17,6 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libpot.so")
 
 POT_OK = 0
+POT_ERR_INVALID_ARG = 1
 STATUS = {
     0: "POT_OK", 1: "POT_ERR_INVALID_ARG", 2: "POT_ERR_CUDA", 3: "POT_ERR_NEIGHBOUR_OVERFLOW",
     4: "POT_ERR_COINCIDENT_SITES", 5: "POT_ERR_EMPTY_CELL_AT_START", 6: "POT_ERR_NOT_CONVERGED",
