@@ -136,6 +136,8 @@ __global__ void __launch_bounds__(kPcgThreads)
     T pi = T(0);
     if (i < n) {
       const int a = row_ptr[i], e = row_ptr[i + 1];
+      // unrolled so that the loads of several entries are in flight at once
+#pragma unroll 4
       for (int k = a + sub; k < e; k += kTpr) {
         const int j = cols[k];
         acc += vals[k] * (z[j] + beta * pold[j]);
@@ -166,7 +168,7 @@ __global__ void __launch_bounds__(kPcgThreads)
 }
 
 template <typename T, bool kGraph>
-__global__ void __launch_bounds__(kPcgThreads)
+__global__ void __launch_bounds__(kPcgThreads, kPcgMaxBlocksPerSm)
     k_update(int64_t n, const T* __restrict__ diag, T* x, T* r, T* z, const T* __restrict__ pa,
              const T* __restrict__ pb, const T* __restrict__ q, double* part, double* scal,
              int nb, int32_t* ctl, cudaGraphConditionalHandle loop) {
