@@ -225,3 +225,23 @@ def test_wall_weights_closed_form_and_no_slip():
     assert np.max(np.abs(out[0])) < 1e-6
     expl = O.velocity_update(pos, v, res["cen"], 1e-3, eps=0.01, g=(0.0, 0.0, 0.0))
     np.testing.assert_allclose(out[1], expl[1], rtol=1e-12, atol=1e-12)
+
+
+def test_wall_weights_two_walls_clip_each_other():
+    """A ball in the edge between the floor and the -x wall, both at distance
+    h: each wall's disk (radius rho = sqrt(psi - h^2), centre at distance h
+    from the other wall) loses the circular segment beyond the other wall,
+    rho^2 acos(h / rho) - h sqrt(rho^2 - h^2); the weight is twice that
+    clipped area over 2 h."""
+    h, r = 0.05, 0.08
+    pos = np.array([[h, 0.5, h]])
+    psi = np.array([r * r])
+    res = O.cells(pos, psi)
+    rho2 = r * r - h * h
+    rho = math.sqrt(rho2)
+    seg = rho2 * math.acos(h / rho) - h * math.sqrt(rho2 - h * h)
+    area = math.pi * rho2 - seg
+    np.testing.assert_allclose(res["wall_area"][0, [0, 4]], [area, area], rtol=1e-10)
+    assert np.all(res["wall_area"][0, [1, 2, 3, 5]] == 0.0)
+    ww = O.wall_weights(res, pos)
+    assert abs(ww[0] - 2 * area / (2 * h)) < 1e-10 * ww[0]
