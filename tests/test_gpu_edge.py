@@ -85,3 +85,29 @@ def test_single_site_fluid_step_is_free_fall(ctx, mu):
     np.testing.assert_allclose(pos.cpu().numpy(), x, rtol=0, atol=1e-12)
     np.testing.assert_allclose(vel.cpu().numpy(), v, rtol=0, atol=1e-9)
     assert abs(float(psi[0]) - r * r) <= 1e-12 * r * r
+
+
+def test_single_site_in_a_box_edge_with_wall_viscosity(ctx):
+    """One ball cut by the floor and the -x wall (two wall facets clipping
+    each other), no-slip wall viscosity on: the GPU fluid step against the
+    oracle's (Eq. 4 with the walls' Laplacian weight on the diagonal)."""
+    from oracle import oracle as O
+    dev = ctx.device
+    h, r = 0.05, 0.08
+    x0 = np.array([[h, 0.5, h]])
+    v0 = np.array([[0.2, 0.1, -0.3]])
+    nu = O.cells(x0, np.array([r * r]))["vol"]
+    pos = torch.tensor(x0, dtype=torch.float64, device=dev)
+    vel = torch.tensor(v0, dtype=torch.float64, device=dev)
+    psi = torch.tensor([r * r], dtype=torch.float64, device=dev)
+    tgt = torch.tensor(nu, dtype=torch.float64, device=dev)
+    dt, eps, mu_wall = 1e-3, 0.01, 50.0
+    prm = pot.default_params(tol=1e-12, dt=dt, eps=eps, mu_wall=mu_wall)
+    st = pot.pot_fluid_step(ctx, pos, vel, psi, tgt, params=prm)
+    assert st["status"] == 0 and st["visc_iters"] > 0
+    x1, v1, _ = O.fluid_step(x0, v0, np.array([r * r]), nu, dt=dt, eps=eps, tol=1e-12,
+                             mu_wall=mu_wall)
+    _, v_free, _ = O.fluid_step(x0, v0, np.array([r * r]), nu, dt=dt, eps=eps, tol=1e-12)
+    assert np.max(np.abs(v1 - v_free)) > 1e-3  # the walls matter
+    np.testing.assert_allclose(pos.cpu().numpy(), x1, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(vel.cpu().numpy(), v1, rtol=0, atol=1e-9 * float(np.max(np.abs(v1))))
