@@ -243,22 +243,28 @@ def measured_peaks():
     return 6400.0, "fallback"
 
 
-def k_cells_roofline(kc, clocks, sm_count):
+def k_cells_roofline(kc, clocks, sm_count, fp32_peak=None):
     """ALU roofline of the cell kernel from its live event timings.
 
     Work per cell = FP32 FLOP executed per processed cell (fadd + fmul +
-    2 ffma) counted by ncu on the splash at converged weights; peak = SMs x
-    128 FP32 lanes x 2 FLOP x the median SM clock sampled during the timed
-    region.  Traffic per launch = DRAM bytes per processed cell from the same
-    capture x cells per launch."""
+    2 ffma) counted by ncu on the splash at converged weights; peak = the
+    FP32 FMA throughput measured on this GPU by the library's FMA-chain
+    kernel (else SMs x 128 FP32 lanes x 2 FLOP x the median SM clock sampled
+    during the timed region).  Traffic per launch = DRAM bytes per processed
+    cell from the same capture x cells per launch."""
     if not kc["launches"] or kc["ms"] <= 0:
         return None
     mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2032.0
-    peak = sm_count * 128 * 2 * mhz * 1e6 / 1e12
+    if fp32_peak:
+        peak = fp32_peak
+        kind = "measured: FP32 FMA chains on this GPU (pot_measure_fp32_peak, best of 5)"
+    else:
+        peak = sm_count * 128 * 2 * mhz * 1e6 / 1e12
+        kind = f"derived: {sm_count} SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz (median under load)"
     cells_per_launch = kc["cells"] / kc["launches"]
     launch_ms = kc["ms"] / kc["launches"]
     out = {"kernel": "k_cells", "bound": "alu", "unit": "TFLOP/s", "peak": peak,
-           "peak_kind": f"derived: {sm_count} SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz (median under load)",
+           "peak_kind": kind,
            "cells_per_launch": cells_per_launch, "launch_ms": launch_ms, "launches": kc["launches"],
            "flop_per_cell": K_CELLS_FLOP_PER_CELL, "achieved": None, "frac": None, "traffic": None}
     if K_CELLS_FLOP_PER_CELL:
@@ -266,6 +272,78 @@ def k_cells_roofline(kc, clocks, sm_count):
         out["frac"] = out["achieved"] / peak
     if K_CELLS_DRAM_BYTES_PER_CELL:
         out["traffic"] = K_CELLS_DRAM_BYTES_PER_CELL * cells_per_launch
+    return out
+
+
+def secondary(dev, cpu_baseline=True):
+    """The other workloads' headline numbers, each within a few seconds:
+    the FP32 FMA peak; lgc_compute_cells on the 2^20-site random cloud
+    (median of 20 calls after 3 warm-ups, grid build reported separately);
+    the 1000-site jittered block solved to 1e-4 from psi0 in mixed precision
+    and in FP64 (median of 5 after 1 warm-up); and the oracle on the cloud's
+    10k-cell subset, single-threaded and on all host cores."""
+    import numpy as np
+    import torch
+
+    from paper_2601_05765_b300 import pot, scenes
+    out = {"fp32_peak_tflops": pot.measure_fp32_peak(dev)["tflops"]}
+    stream = torch.cuda.current_stream()
+    sc = scenes.uniform_cloud(n=1 << 20, seed=1)
+    ctx = pot.Context(sc.n, 128, dev.index, fp32=True, fp64=False)
+    pos, psi, nu = (torch.from_numpy(a).to(dev) for a in (sc.pos, sc.psi, sc.nu))
+    for _ in range(3):
+        pot.lgc_compute_cells(ctx, pos, psi, nu)
+    times, st = [], []
+    for _ in range(20):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st.append(pot.lgc_compute_cells(ctx, pos, psi, nu)["stats"])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ctx.close()
+    times.sort()
+    med = times[len(times) // 2]
+    out["cells_per_s_cloud"] = {
+        "value": sc.n / (med / 1e3), "unit": "cells/s", "ms_per_call_median": med,
+        "ms_grid": statistics.mean(x["ms_grid"] for x in st),
+        "ms_cells": statistics.mean(x["ms_cells"] for x in st),
+        "ms_csr": statistics.mean(x["ms_csr"] for x in st),
+        "workload": "lgc_compute_cells (grid, candidates, cells, CSR Hessian) on the 2^20-site "
+                    "random cloud (positions U(0,1)^3 seed 1, r = U(0.4,1.2) (3/(4 pi N))^(1/3)), "
+                    "median of 20 calls"}
+    blk = scenes.jittered_block()
+    solve = {}
+    for prec, dt in (("mixed", torch.float32), ("fp64", torch.float64)):
+        ctx = pot.Context(blk.n, 246, dev.index, fp32=dt == torch.float32, fp64=dt == torch.float64)
+        p = torch.as_tensor(blk.pos, dtype=dt, device=dev)
+        n_ = torch.as_tensor(blk.nu, dtype=torch.float64, device=dev)
+        ts, it = [], None
+        for k in range(6):
+            ps = torch.as_tensor(blk.psi, dtype=dt, device=dev)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            it = pot.pot_newton_solve(ctx, p, n_, ps)
+            torch.cuda.synchronize()
+            if k:
+                ts.append(1e3 * (time.perf_counter() - t0))
+        ctx.close()
+        ts.sort()
+        solve[prec] = {"ms": ts[len(ts) // 2], "newton_iters": it["newton_iters"],
+                       "pcg_iters": it["pcg_iters"], "err_max": it["err_max"]}
+    out["solve_1000_ms"] = {**solve, "workload": "jittered 10x10x10 block (spacing 0.05, seed 0), "
+                                                 "psi0 = (0.8 r_nu)^2, Newton to 1e-4, host wall time"}
+    if cpu_baseline:
+        from oracle import oracle as O
+        q = sc.extra["subset"]
+        res = {}
+        for name, nt in (("1_thread", 1), ("all_cores", 0)):
+            t0 = time.perf_counter()
+            O.cells(sc.pos.astype(np.float64), sc.psi.astype(np.float64), query=q, nthreads=nt)
+            res[name] = len(q) / (time.perf_counter() - t0)
+        out["cpu_baseline_cloud"] = {"unit": "cells/s", "kind": "oracle", "cores_all": O.max_threads(),
+                                     **res, "sample": f"oracle cells of the cloud's {len(q)}-cell "
+                                                      f"subset (seed 1001)"}
     return out
 
 
@@ -379,6 +457,9 @@ def run_ours(args):
                    "start": f"{sc.extra['relax_rounds']} rounds of sites moved to their cell "
                             f"centroids (last move: mean {relax['moved_mean'][-1]:.2e}, max "
                             f"{relax['moved_max'][-1]:.2e})",
+                   "recipe": f"splash: two balls of radius 0.2 centred at (0.5 -/+ (0.2 + s), 0.5, 0.5), "
+                             f"+/-3 m/s along x, lattice spacing s = {args.spacing:g} jittered by 0.3 s "
+                             f"(seed {3 + rank}), nu = 0.9 s^3, spring eps = s/16, dt = eps/2",
                    "parallelism": f"replicas x{world}",
                    "l2": "working set > 126 MB L2, no flush"},
         "newton_solve_ms": {"median": solve_ms[len(solve_ms) // 2],
@@ -393,7 +474,7 @@ def run_ours(args):
         "nnz": nnz,
         "max_err": max(s["err_max"] for s in stats),
         "status": sorted({s["status"] for s in stats}),
-        "roofline": k_cells_roofline(kc, clocks, sm_count),
+        "roofline": None,
         "roofline_pcg": {"kernel": "PCG iteration (k_spmv + k_update)", "bound": "hbm",
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak if achieved else None, "traffic": None,
@@ -403,6 +484,14 @@ def run_ours(args):
         "e2e": {"value": units_e2e / T_e2e, "unit": "cells/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": "the same steps as the device-timed region"},
     }
+    ctx.close()
+    # the other workloads (rank 0 only; untimed for `value`)
+    fp32_peak = None
+    if rank == 0:
+        sec = secondary(dev, cpu_baseline=world == 1 and not args.no_cpu_baseline)
+        fp32_peak = sec["fp32_peak_tflops"]
+        line.update(sec)
+    line["roofline"] = k_cells_roofline(kc, clocks, sm_count, fp32_peak)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         val, steps, nsm, cores, dt = oracle_steps(args.cpu_seconds, 100)
         line["cpu_baseline"] = {"value": val, "unit": "cells/s", "cores": cores, "kind": "oracle",
@@ -410,7 +499,6 @@ def run_ours(args):
                                           f"tol 1e-4) of the splash recipe at {nsm} sites, {dt:.1f} s"}
     if rank == 0:
         print(json.dumps(line))
-    ctx.close()
 
 
 def run_cells(args):

@@ -169,6 +169,16 @@ void pot_default_params(pot_params* p);
  * (all contexts and devices), for launch accounting by callers. */
 int64_t pot_kernel_launches(void);
 
+/* FP32 FMA throughput of the current device in TFLOP/s (not in the paper:
+ * the denominator of the cell kernel's roofline, whose work is FP32
+ * arithmetic).  Runs one warm-up and five timed launches of a kernel of
+ * independent FMA chains on `stream` at full occupancy (CUDA events, best
+ * launch; 2 FLOP per FMA); ms_out (optional) gets that launch's time.
+ * sink: a caller-owned device buffer of at least (SM count x 8) floats that
+ * the kernel never writes in practice (it only writes an impossible value).
+ * Errors: POT_ERR_INVALID_ARG (NULL sink or tflops), POT_ERR_CUDA. */
+int pot_measure_fp32_peak(void* stream, float* sink, double* tflops, double* ms_out);
+
 /* Device time of the cell kernel (clipping, restriction and analytic
  * quantities, Sec. 3.2-3.4) accumulated over this context's evaluations since
  * the last reset, measured with CUDA events on the caller's stream around each
@@ -225,17 +235,18 @@ int lgc_compute_cells_f64(pot_ctx* ctx, void* stream, int64_t n, const double* p
  * grad, centroids, karea; same meaning, layout and FP32/FP64 split), with
  * no context and no allocation: all scratch memory is one file-scope device
  * array inside libpot.so sized for n <= 8192 sites and 64 cutting bisectors
- * per cell (about 4.9 MB, held by every GPU that loads the library until the
- * process exits).  The caller passes device inputs and outputs as usual;
+ * per cell (5,300,736 bytes, held by every GPU that loads the library until
+ * the process exits).  The caller passes device inputs and outputs as usual;
  * centroids, karea and grad may be NULL.
  *  - n > 8192 returns POT_ERR_TOO_LARGE before any device work.
  *  - The first call on each device looks up the array's device address with
  *    that device current (the calling thread's current device is used);
- *    make that first call before any stream capture.
+ *    make that first call before any stream capture.  `stream` must belong
+ *    to the current device (POT_ERR_INVALID_ARG otherwise).
  *  - Every call shares the array and overwrites the previous call's
  *    contents; calls whose work overlaps on the GPU race on it (a host mutex
  *    serialises calls from several threads, and each call waits for its own
- *    stream before returning).
+ *    stream before returning, also when it returns an error).
  * Errors: as lgc_compute_cells (no POT_ERR_CAPACITY), plus POT_ERR_TOO_LARGE.
  * Timing fields of stats stay 0. */
 int lgc_compute_cells_noalloc(void* stream, int64_t n, const float* pos, const float* psi,
@@ -256,7 +267,11 @@ int lgc_compute_cells_noalloc(void* stream, int64_t n, const float* pos, const f
  * max_i |V_i - nu_i| / nu_i <= params->tol.
  * psi_inout: start (must give non-empty cells) in, solution out.
  * Mixed precision: FP32 geometry and matrix, FP64 residuals, PCG dot
- * products and KMT test.  Errors: POT_ERR_EMPTY_CELL_AT_START (if the repair
+ * products and KMT test.  This entry point stops at 0.9 params->tol on its
+ * FP32-evaluated error, a margin for the FP32 rounding of the volumes (about
+ * 1e-6 of the target), so the weights meet params->tol in exact arithmetic;
+ * its KMT test also accepts the same decrease of the max relative error (the
+ * l2 norm of an FP32 evaluation stalls at its rounding floor).  Errors: POT_ERR_EMPTY_CELL_AT_START (if the repair
  * fails),
  * POT_ERR_NOT_CONVERGED, POT_ERR_LINESEARCH_FAILED, geometry errors.
  * psi_inout holds the last accepted iterate on NOT_CONVERGED. */
@@ -264,7 +279,8 @@ int pot_newton_solve(pot_ctx* ctx, void* stream, int64_t n, const float* pos, co
                      float* psi_inout, const pot_domain* dom, const pot_params* params,
                      pot_solve_stats* stats);
 
-/* Same with FP64 geometry, matrix and PCG vectors. */
+/* Same with FP64 geometry, matrix and PCG vectors; stops at params->tol and
+ * takes the l2 KMT test alone. */
 int pot_newton_solve_f64(pot_ctx* ctx, void* stream, int64_t n, const double* pos,
                          const double* targets, double* psi_inout, const pot_domain* dom,
                          const pot_params* params, pot_solve_stats* stats);

@@ -18,7 +18,7 @@
  *   centroid: int_C (x-p) dx = 1/4 sum_f h_f int_{B_f}(x-p) dA
  *                              - 1/4 psi_i sum_f n_f |B_f|
  *
- * Readings of the paper taken here (each is listed in the design doc):
+ * Readings of the paper taken here (where it is garbled, ambiguous or silent):
  *   - the pyramid volume is h|B|/3 (the field F=(x-p)/3 of Sec. 3.2 gives the
  *     1/3 that the printed h|B| and sqrt(psi)|K| drop);
  *   - h_f is the scalar signed distance (|d|^2 + psi_i - psi_j) / (2|d|);

@@ -8,7 +8,8 @@
 //   - the Newton system is M u = nu - V(psi), M = -grad^2 K (Eq. 2);
 //   - the KMT step halves alpha from 1 until min V(psi + alpha u) >= eps0 and
 //     ||nu - V(psi + alpha u)||_2 <= (1 - alpha/2) ||nu - V(psi)||_2, with
-//     eps0 = 1/2 min(min nu, min V(psi_start));
+//     eps0 = 1/2 min(min nu, min V(psi_start)); the FP32-geometry path also
+//     accepts that decrease of the max relative error (see the line search);
 //   - the start is the given psi (psi = 0 would give empty cells);
 //   - convergence: max_i |V_i - nu_i| / nu_i <= tol (relative, Sec. 7).
 #include <chrono>
@@ -18,6 +19,9 @@
 
 namespace pot {
 namespace {
+
+// stopping test of the FP32-geometry path: err <= kMixedStop * tol
+constexpr double kMixedStop = 0.9;
 
 template <typename T>
 __global__ void k_accept(int64_t n, const V4<T>* __restrict__ sxp, T* base) {
@@ -293,12 +297,17 @@ int newton_sorted(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* do
   POT_CUDA(cudaMemcpyAsync(ctx->h_pinned, ctx->red_out, sizeof(double), cudaMemcpyDeviceToHost, st));
   POT_CUDA(cudaStreamSynchronize(st));
   const double eps0 = 0.5 * fmin(ctx->h_pinned[0], res[2]);
+  // The FP32-geometry path stops at kMixedStop * tol on its FP32-evaluated
+  // error: the margin of 0.1 tol (1e-5 at tol = 1e-4) covers the rounding
+  // of the FP32 volumes (measured against the FP64 oracle at about 1e-6 of
+  // the target, ten times below it), so that the volumes meet tol exactly
+  const double tol_stop = sizeof(T) == 4 ? kMixedStop * P->tol : P->tol;
   double err = res[0], gnorm = sqrt(res[1]);
   for (int it = 0;; it++) {
     S->newton_iters = it;
     S->err_max = err;
     S->err_l2 = gnorm;
-    if (err <= P->tol) return POT_OK;
+    if (err <= tol_stop) return POT_OK;
     if (it >= P->max_newton) return POT_ERR_NOT_CONVERGED;
     int64_t nnz_off = 0;
     POT_CHECK(csr_compact<T>(ctx, st, n, &nnz_off));
@@ -325,12 +334,16 @@ int newton_sorted(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* do
       const int code = eval_and_reduce<T>(ctx, st, n, dom, res, S);
       if (code != POT_OK && code != POT_ERR_NEIGHBOUR_OVERFLOW && code != POT_ERR_POLYGON_OVERFLOW)
         return code;
-      // KMT decrease in the l2 norm, or in the max relative error that the
-      // stopping test measures: an FP32 evaluation's l2 norm over many
-      // cells reaches its rounding floor (about 1e-6 nu per cell) before a
-      // few worst cells reach the tolerance
+      // KMT: a sufficient decrease of the l2 norm (FP64 path: the test of
+      // Algorithm 1 as read, nothing else).  The FP32-geometry path also
+      // accepts the same decrease of the max relative error that the
+      // stopping test measures: its l2 norm over many cells reaches the FP32
+      // rounding floor (about 1e-6 nu per cell) while a few worst cells are
+      // still above the tolerance, where the l2 test alone stalls
       const double fac = 1.0 - 0.5 * alpha;
-      if (code == POT_OK && res[2] >= eps0 && (sqrt(res[1]) <= fac * gnorm || res[0] <= fac * err)) {
+      const bool l2_ok = sqrt(res[1]) <= fac * gnorm;
+      const bool max_ok = sizeof(T) == 4 && res[0] <= fac * err;
+      if (code == POT_OK && res[2] >= eps0 && (l2_ok || max_ok)) {
         accepted = true;
         break;
       }

@@ -12,10 +12,12 @@
 // Host code cannot use the array's name as a device address, so the first
 // call on each device asks the runtime for the address (cudaGetSymbolAddress)
 // with that device current and caches it; make that first call before any
-// stream capture.  Every call shares the array and the next call overwrites
-// it: the status words are cleared at the start of each call and the grid
-// counts are cleared by the grid build.  Calls that overlap on the GPU race
-// on the array; a host mutex serialises calls made from several threads.
+// stream capture.  The stream must belong to the current device.  Every call
+// shares the array and the next call overwrites it: the status words are
+// cleared at the start of each call and the grid counts are cleared by the
+// grid build.  Calls that overlap on the GPU race on the array; a host mutex
+// serialises calls made from several threads, and each call waits for its
+// stream before it returns, on every return path.
 #include <mutex>
 
 #include "pot_internal.cuh"
@@ -65,6 +67,8 @@ constexpr size_t oNeed = oGmax + al(4 * (kNoAllocGridCap + 1));
 constexpr size_t oNeedCount = oNeed + al(N);
 constexpr size_t oBigList = oNeedCount + al(8);
 constexpr size_t kScratchBytes = oBigList + al(4 * N);
+// the size the header states (5,300,736 bytes, about 5.3 MB)
+static_assert(kScratchBytes == 5300736, "update the scratch size stated in pot.h");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -84,6 +88,17 @@ int scratch_base(int dev, unsigned char** out) {
   *out = (unsigned char*)g_noalloc_base[dev];
   return POT_OK;
 }
+
+// Waits for the call's stream on every return path once device work has
+// been enqueued, so that the next call (after the mutex is released) never
+// overlaps this one on the shared array, whatever status this one returns.
+struct StreamDrain {
+  cudaStream_t st;
+  bool armed = false;
+  ~StreamDrain() {
+    if (armed) cudaStreamSynchronize(st);
+  }
+};
 
 }  // namespace
 }  // namespace pot
@@ -105,9 +120,18 @@ extern "C" int lgc_compute_cells_noalloc(void* stream, int64_t n, const float* p
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return POT_ERR_CUDA;
+  cudaStream_t st = (cudaStream_t)stream;
+  // the array's address belongs to the current device: the stream must too
+  // (the legacy default stream follows the current device)
+  if (st != nullptr) {
+    int sdev = -1;
+    if (cudaStreamGetDevice(st, &sdev) != cudaSuccess) return POT_ERR_INVALID_ARG;
+    if (sdev != dev) return POT_ERR_INVALID_ARG;
+  }
   unsigned char* b = nullptr;
   POT_CHECK(scratch_base(dev, &b));
-  cudaStream_t st = (cudaStream_t)stream;
+  // declared after the lock, so it drains the stream before the unlock
+  StreamDrain drain{st};
 
   // a context shell whose buffers all point into the scratch array
   pot_ctx c;
@@ -155,6 +179,7 @@ extern "C" int lgc_compute_cells_noalloc(void* stream, int64_t n, const float* p
   c.big_list = (int32_t*)(b + oBigList);  // unused: 64-plane lists fit the cell kernel's window
 
   // the previous call's status words are stale: clear them
+  drain.armed = true;
   POT_CUDA(cudaMemcpyAsync(c.err, kErrInit, sizeof(kErrInit), cudaMemcpyHostToDevice, st));
   POT_CHECK(grid_build<float>(&c, st, n, pos, psi, targets, dom));
   const int ce = cells_eval<float>(&c, st, n, dom, grad != nullptr);

@@ -139,6 +139,9 @@ def lib():
         L.pot_render_depth.argtypes = [P, P, I64, P, P, P, ctypes.POINTER(Domain),
                                        ctypes.POINTER(Camera), P, P]
         L.pot_render_depth.restype = ctypes.c_int
+        L.pot_measure_fp32_peak.argtypes = [P, P, ctypes.POINTER(ctypes.c_double),
+                                            ctypes.POINTER(ctypes.c_double)]
+        L.pot_measure_fp32_peak.restype = ctypes.c_int
         for f in (L.pot_mlp_create, L.pot_mlp_destroy, L.pot_mlp_num_params, L.pot_mlp_set_params,
                   L.pot_mlp_get_params, L.pot_mlp_forward, L.pot_mlp_gradients, L.pot_mlp_train_step,
                   L.pot_mlp_check, L.pot_mlp_features, L.pot_mlp_set_history,
@@ -154,6 +157,19 @@ def lib():
 def kernel_launches() -> int:
     """Kernel launches issued by libpot.so so far in this process."""
     return int(lib().pot_kernel_launches())
+
+
+def measure_fp32_peak(device=None, stream=None) -> dict:
+    """FP32 FMA throughput of the current device (TFLOP/s), measured by the
+    library's FMA-chain kernel (best of five launches)."""
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else device
+    sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    sink = torch.empty(sm * 8, dtype=torch.float32, device=dev)
+    tf, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    code = lib().pot_measure_fp32_peak(_stream(stream), _ptr(sink), ctypes.byref(tf), ctypes.byref(ms))
+    if code != POT_OK:
+        raise PotError(code, "pot_measure_fp32_peak")
+    return {"tflops": float(tf.value), "ms": float(ms.value)}
 
 
 def cell_diagnostics(ctx: "Context", n: int, stream=None) -> dict:

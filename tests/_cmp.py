@@ -51,7 +51,11 @@ def compare_cells(out, ref, psi, nu, tol_v, tol_h, tol_c=None, tol_floor=None,
     ev = np.abs(v_gpu - ref["vol"]) / base
     worst = int(np.argmax(ev))
     assert ev.max() <= tol_v, f"volume rel err {ev.max():.3e} at site {q[worst]}"
-    report = {"vol_max_rel": float(ev.max())}
+    # cells that pass only because of the floor: the plain relative test
+    # |dV| <= tol_v V_ref would fail them
+    plain = np.abs(v_gpu - ref["vol"]) > tol_v * ref["vol"]
+    report = {"cells": int(q.shape[0]), "vol_max_rel": float(ev.max()),
+              "vol_floor_cells": int(np.sum(plain))}
     if nu is not None:
         g = to_np(out["grad"])[q]
         nb = np.maximum(np.asarray(nu)[q], ref["vol"]) + (tol_floor / tol_v) * ball
@@ -84,6 +88,7 @@ def compare_hessian(out, ref, psi, tol_h, floor_h=1e-2):
     diag_ref, rows_ref = O.hessian_entries(ref, psi)
     amb = 0
     worst = 0.0
+    floor_rows = 0  # rows that pass only because of the floor (|M_ii| < floor_h r_i)
     for k, i in enumerate(q):
         gc = cols[rp[i]:rp[i + 1]]
         gv = vals[rp[i]:rp[i + 1]]
@@ -116,4 +121,6 @@ def compare_hessian(out, ref, psi, tol_h, floor_h=1e-2):
             e = max(e, abs(v - rmap[c]) / scale)
         worst = max(worst, e)
         assert e <= tol_h, f"row {i}: Hessian rel err {e:.3e}"
-    return {"hess_max_rel": worst, "ambiguous_facets": amb}
+        if scale > abs(diag_ref[k]) and e * scale > tol_h * abs(diag_ref[k]):
+            floor_rows += 1
+    return {"hess_max_rel": worst, "ambiguous_facets": amb, "hess_floor_rows": floor_rows}

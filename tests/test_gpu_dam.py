@@ -26,7 +26,7 @@ def check_subset(ctx, pos, psi, nu, q):
     rep = compare_cells(out, ref, s32, to_np(nu), **TOL32)
     nu_q = to_np(nu)[q]
     rep["oracle_vol_err"] = float(np.max(np.abs(ref["vol"] - nu_q) / nu_q))
-    assert rep["oracle_vol_err"] <= 1.5e-4, rep
+    assert rep["oracle_vol_err"] <= 1e-4, rep
     return rep
 
 

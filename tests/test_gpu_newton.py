@@ -53,7 +53,7 @@ def test_block_mixed_precision(ctx):
     got = psi.cpu().numpy().astype(np.float64)
     v = O.cells(sc.pos.astype(np.float64), got)["vol"]
     err = np.max(np.abs(v - sc.nu) / sc.nu)
-    assert err <= 1.5e-4, err  # FP32 geometry error on top of the 1e-4 tolerance
+    assert err <= 1e-4, err  # the mixed solve stops at 0.9 tol: room for the FP32 error
     ref = O.newton(sc.pos.astype(np.float64), sc.nu, sc.psi.astype(np.float64), tol=1e-10)
     np.testing.assert_allclose(got, ref.psi, rtol=2e-3)
 

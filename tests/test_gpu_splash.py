@@ -29,7 +29,7 @@ def check_subset(ctx, pos, psi, nu, q):
     # plus the FP32 geometry error
     nu_q = to_np(nu)[q]
     rep["oracle_vol_err"] = float(np.max(np.abs(ref["vol"] - nu_q) / nu_q))
-    assert rep["oracle_vol_err"] <= 1.5e-4, rep
+    assert rep["oracle_vol_err"] <= 1e-4, rep
     return rep
 
 

@@ -27,13 +27,17 @@ def noalloc_fn():
     return f
 
 
-def call_noalloc(pos, psi, nu):
+def outputs(n, dev):
+    return {"volumes": torch.empty(n, dtype=torch.float32, device=dev),
+            "grad": torch.empty(n, dtype=torch.float64, device=dev),
+            "centroids": torch.empty((n, 3), dtype=torch.float32, device=dev),
+            "karea": torch.empty(n, dtype=torch.float32, device=dev)}
+
+
+def call_noalloc(pos, psi, nu, out=None):
     n = pos.shape[0]
-    dev = pos.device
-    out = {"volumes": torch.empty(n, dtype=torch.float32, device=dev),
-           "grad": torch.empty(n, dtype=torch.float64, device=dev),
-           "centroids": torch.empty((n, 3), dtype=torch.float32, device=dev),
-           "karea": torch.empty(n, dtype=torch.float32, device=dev)}
+    if out is None:
+        out = outputs(n, pos.device)
     st = pot.CellStats()
     dom = pot._domain(pot.UNIT_BOX)
     code = noalloc_fn()(ctypes.c_void_p(torch.cuda.current_stream().cuda_stream), n,
@@ -75,6 +79,27 @@ def test_noalloc_matches_context_entry_point_twice():
         assert st.n_empty == ref["stats"]["n_empty"]
         assert st.max_planes == ref["stats"]["max_planes"]
     ctx.close()
+
+
+def test_noalloc_allocates_nothing():
+    """After a first call (which looks up the array's address), a call
+    leaves the device's free memory unchanged: torch's own counters would
+    not see a cudaMalloc inside the library, the driver's free count does."""
+    dev = torch.device("cuda", 0)
+    sc = scenes.uniform_cloud(n=MAX_SITES, seed=22)
+    pos = torch.from_numpy(sc.pos).to(dev)
+    psi = torch.from_numpy(sc.psi).to(dev)
+    nu = torch.from_numpy(sc.nu).to(dev)
+    out = outputs(sc.n, dev)
+    code, _, _ = call_noalloc(pos, psi, nu, out)
+    assert code == 0
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info(dev)
+    code, _, _ = call_noalloc(pos, psi, nu, out)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info(dev)
+    assert code == 0
+    assert free1 == free0, (free0, free1)
 
 
 def test_noalloc_rejects_too_many_sites():
