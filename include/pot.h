@@ -235,7 +235,7 @@ int lgc_compute_cells_f64(pot_ctx* ctx, void* stream, int64_t n, const double* p
  * grad, centroids, karea; same meaning, layout and FP32/FP64 split), with
  * no context and no allocation: all scratch memory is one file-scope device
  * array inside libpot.so sized for n <= 8192 sites and 64 cutting bisectors
- * per cell (5,300,736 bytes, held by every GPU that loads the library until
+ * per cell (5,333,504 bytes, held by every GPU that loads the library until
  * the process exits).  The caller passes device inputs and outputs as usual;
  * centroids, karea and grad may be NULL.
  *  - n > 8192 returns POT_ERR_TOO_LARGE before any device work.

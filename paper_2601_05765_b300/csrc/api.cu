@@ -62,9 +62,9 @@ int alloc_work(Work<T>& w, int64_t n, int64_t k, int64_t gcap, int sms) {
   POT_CHECK(alloc(&w.rcell_acc, n));
   POT_CHECK(alloc(&w.rcell, n));
   POT_CHECK(alloc(&w.gmax, gcap + 1));
-  // cells with more planes than the cell kernel's shared window exist only
-  // when the lists may hold that many
-  if (k + 6 > kPlaneCap) {
+  // cells with more planes than the cell kernel takes (kSmallPlanes) exist
+  // only when the lists may hold that many
+  if (k + 6 > kSmallPlanes) {
     w.big_warps = sms * kBigWarpsPerSm;
     POT_CHECK(alloc(&w.big_pl, (int64_t)w.big_warps * kBigPlanes));
     POT_CHECK(alloc(&w.big_d, (int64_t)w.big_warps * kBigPlanes));
@@ -236,7 +236,8 @@ int pot_destroy(pot_ctx* ctx) {
   void* ptrs[] = {ctx->keys,     ctx->perm,    ctx->iperm,    ctx->cell_count, ctx->cell_start,
                   ctx->cand,     ctx->meta,    ctx->row_cnt,  ctx->row_ptr,    ctx->ucnt,
                   ctx->csr_cols, ctx->scan_tmp, ctx->snu,     ctx->grad,       ctx->red,
-                  ctx->red_out,  ctx->pcg_red, ctx->pcg_ctl,  ctx->err, ctx->need, ctx->need_count, ctx->big_list};
+                  ctx->red_out,  ctx->pcg_red, ctx->pcg_ctl,  ctx->err, ctx->need, ctx->need_count, ctx->big_list,
+                  ctx->fix_list};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int k = 0; k < 2; k++) {
@@ -295,8 +296,9 @@ int pot_create(pot_ctx** out, int device, int64_t n_max, int32_t k_max, int32_t 
   A(ctx->pcg_ctl, 8);
   A(ctx->err, 2);
   A(ctx->need, n);
-  A(ctx->need_count, 2);
+  A(ctx->need_count, 4);
   A(ctx->big_list, n);
+  if (precision_mask & 1) A(ctx->fix_list, n);
 #undef A
   if (s == POT_OK && (ctx->mask & 1)) s = alloc_work(ctx->wf, n, k, ctx->grid_cap, ctx->sm_count);
   if (s == POT_OK && (ctx->mask & 2)) s = alloc_work(ctx->wd, n, k, ctx->grid_cap, ctx->sm_count);

@@ -81,11 +81,12 @@ __device__ __forceinline__ void set_error(int32_t* err, int code, int64_t site) 
 // bracket: R_lo, the largest radius at which its cell was built and found
 // too small, and the current R_i.  An overflow at R_i retries at the
 // midpoint of (R_lo, R_i) (R_i / 2 while R_lo = 0); only when the bracket has
-// narrowed to 3 % of R_i is the overflow a real capacity error.  A list that
-// would not fit the cell kernel's shared window (kPlaneCap planes) is
-// bisected the same way, and the cell goes to the big-cell kernel only when
-// its bracket has collapsed; from then on (for the rest of the evaluation)
-// it grows without that limit.
+// narrowed to 3 % of R_i is the overflow a real capacity error.  A list of
+// more than kPlaneCap planes is bisected the same way (a smaller radius may
+// still give a short list), and only when its bracket has collapsed does the
+// cell keep that many; from then on (for the rest of the evaluation) it grows
+// without that limit.  Cells of more than kSmallPlanes planes go to the
+// big-cell kernel.
 //
 // Grid cells are skipped with a lower bound of h over their sites: for
 // |p_i - p_j| >= delta and psi_j <= gmax,  h_ij >= delta/2 - (gmax - psi_i)/(2 delta)
@@ -226,8 +227,8 @@ __global__ void __launch_bounds__(256)
     }
   } else {
     meta[s] = (nw + nc) | (wmask << kMetaWallShift);
-    // more planes than the cell kernel's shared window: the big-cell kernel
-    if (nw + nc > kPlaneCap) big_list[atomicAdd(big_count, 1)] = (int32_t)s;
+    // more planes than the cell kernel's crossing sets hold: the big-cell kernel
+    if (nw + nc > kSmallPlanes) big_list[atomicAdd(big_count, 1)] = (int32_t)s;
   }
 }
 
@@ -497,9 +498,11 @@ __device__ Facet<T> facet_eval(const V4<T>* __restrict__ pl, int m, int fi, T ps
 
 // Plane f of cell `cell` (walls first in order -x,+x,-y,+y,-z,+z, then the
 // candidate bisectors in ascending sorted index).
-template <typename T>
+// S is the storage type of sxp (the FP64 re-evaluation of FP32 cells widens
+// the stored float values exactly).
+template <typename T, typename S = T>
 __device__ __forceinline__ void plane_of(int f, int64_t cell, const V4<T>& p, int mt, T r,
-                                         const V4<T>* __restrict__ sxp,
+                                         const V4<S>* __restrict__ sxp,
                                          const int32_t* __restrict__ cand, int kmax,
                                          const Box<T>& box, V4<T>& pl, T& pd, int& pj) {
   int wmask = (mt >> kMetaWallShift) & 63;
@@ -523,7 +526,8 @@ __device__ __forceinline__ void plane_of(int f, int64_t cell, const V4<T>& p, in
     pj = -1;
   } else {
     int t = cand[cell * kmax + (f - nw)];
-    const V4<T> q = sxp[t];
+    const V4<S> qs = sxp[t];
+    const V4<T> q = {T(qs.x), T(qs.y), T(qs.z), T(qs.w)};
     T dx, dy, dz;
     T d2 = sqdist(p, q, dx, dy, dz);
     T d;
@@ -609,10 +613,26 @@ struct CellOut {
   double* grad;
   const double* snu;
   void* wallw;  // the walls' Laplacian weight per cell (optional)
+  int32_t* fix_count;  // FP32 kernels: ill-conditioned cells for the FP64 pass (NULL: none)
+  int32_t* fix_list;
 };
 
-template <typename T>
-__device__ __forceinline__ void write_cell(int64_t cell, const V4<T>& p, bool empty, bool inside,
+// An FP32 cell whose rounding can exceed the parity bounds is recomputed in
+// FP64 (k_cells_fix64).  The FP32 volume carries an absolute error of a few
+// ulp of the ball volume when a spherical part is present (r|K|/3 with
+// |K| = psi (4 pi [inside] - sum Omega)) or when the site is outside its
+// polytope (pyramids of both signs): about 2e-7 of the ball, so a cell below
+// 1/20 of its ball could miss 1e-5 relative.  The Hessian diagonal carries
+// r times the solid-angle rounding, about 2e-6 r: a diagonal below 0.1 r
+// could miss 1e-5 relative.  Cells without a spherical part and with the
+// site inside are sums of positive pyramids: well conditioned.
+constexpr float kFixBallOverVol = 20.0f;
+constexpr float kFixDiagOverR = 0.1f;
+
+// T: arithmetic of the cell, S: storage type of the outputs.  Returns true
+// when an FP32 cell is ill-conditioned (see above).
+template <typename T, typename S = T>
+__device__ __forceinline__ bool write_cell(int64_t cell, const V4<T>& p, bool empty, bool inside,
                                            bool qout, bool full, const CellAcc<T>& a, int cnt, T oa,
                                            const CellOut& o) {
   const T ps = p.w;
@@ -656,22 +676,62 @@ __device__ __forceinline__ void write_cell(int64_t cell, const V4<T>& p, bool em
     else
       rc = sqrt(a.rm2);
   }
-  ((T*)o.rcell)[cell] = rc;
-  ((T*)o.vol)[cell] = V;
-  ((T*)o.karea)[cell] = K;
-  ((T*)o.diag)[cell] = dg;
-  T* cen = (T*)o.cen;
-  cen[3 * cell + 0] = cx;
-  cen[3 * cell + 1] = cy;
-  cen[3 * cell + 2] = cz;
+  ((S*)o.rcell)[cell] = (S)rc;
+  ((S*)o.vol)[cell] = (S)V;
+  ((S*)o.karea)[cell] = (S)K;
+  ((S*)o.diag)[cell] = (S)dg;
+  S* cen = (S*)o.cen;
+  cen[3 * cell + 0] = (S)cx;
+  cen[3 * cell + 1] = (S)cy;
+  cen[3 * cell + 2] = (S)cz;
   o.row_cnt[cell] = cnt;
-  if (o.grad) o.grad[cell] = o.snu[cell] - (double)V;
-  if (o.wallw) ((T*)o.wallw)[cell] = empty ? T(0) : a.wg;
+  if (o.grad) o.grad[cell] = o.snu[cell] - (double)(S)V;
+  if (o.wallw) ((S*)o.wallw)[cell] = empty ? S(0) : (S)a.wg;
+  if (sizeof(T) != 4 || empty || !(ps > T(0)) || (K == T(0) && inside)) return false;
+  const T r = sqrt(ps);
+  const T ball = T(4.0 * 3.14159265358979323846 / 3.0) * ps * r;
+  return V * T(kFixBallOverVol) < ball || dg < T(kFixDiagOverR) * r;
 }
 
-// Warps per block of the cell kernel: the plane window of every warp lives in
-// static shared memory (kPlaneCap planes of 16 or 32 bytes plus distance and
-// index), so the FP64 kernel runs half as many warps per block.
+// Append an ill-conditioned FP32 cell to the FP64 list and put its full
+// plane list back into its candidate row (the cell kernel rewrote the row in
+// place into its Hessian columns): j of its bisector planes, in plane order
+// after the walls.
+__device__ __forceinline__ void flag_fix(int64_t cell, int m, int nw, const int* pj, int kmax,
+                                         int32_t* cand, int32_t* fix_count, int32_t* fix_list) {
+  fix_list[atomicAdd(fix_count, 1)] = (int32_t)cell;
+  for (int f = nw; f < m; f++) cand[cell * kmax + (f - nw)] = pj[f];
+}
+
+// ---------------------------------------------------------------------------
+// cell kernel (cells of at most kSmallPlanes planes)
+//
+// A restricted facet B_f is the disk of plane f (centre h_f n_f, radius
+// rho_f = sqrt(psi - h_f^2)) cut by the half-planes that the other planes
+// trace on it (Sec. 3.4).  Only the lines that cross the disk matter: a plane
+// whose line misses the disk keeps all of it or none (the facet is empty).
+// Whether the line of two planes f and g crosses the ball is symmetric in f
+// and g -- the line's distance from the site is below r --, so it is decided
+// once per pair of planes.
+//
+// With the crossing lines G_f, the boundary of B_f is a cycle of chord
+// segments and circular arcs, and area, solid angle at the site (Sec. 3.3)
+// and first moment are sums over it of fan pieces from the disk centre: a
+// triangle per segment, a sector per arc.  Each crossing line g gives one
+// task: its chord [-w, w] (direction with the facet on its left) clipped by
+// the other lines of G_f is the segment of g on the boundary, when not empty;
+// if the end of the chord survives the clipping, an arc starts there and
+// runs counter-clockwise to the nearest chord start of a line of G_f (the
+// first point where the circle leaves the facet).  A line whose whole chord
+// lies behind the arc's start does not end it; the start of a line whose
+// cut-off arc contains the arc's start (possible only where three boundary
+// pieces meet, within rounding) ends it at once.  A facet crossed by no line
+// is its whole disk.  No polygon is stored: every task runs in registers on
+// the planes in the warp's shared window.
+constexpr int kWin = 128;  // plane slots of a warp's window
+
+// Warps per block: the window of every warp lives in static shared memory,
+// so the FP64 kernel runs half as many warps per block.
 template <typename T>
 struct CellCfg {
   static constexpr int warps = sizeof(T) == 4 ? kCellWarps : kCellWarps / 2;
@@ -686,30 +746,300 @@ struct CellSlot {
   int emitted;  // Hessian entries written so far
 };
 
-// One warp per task of up to 32 consecutive cells (grid order).  The task is
-// processed in windows: as many of its cells as have all their planes fit in
-// the warp's kPlaneCap-slot buffer (a cell with no plane takes one slot).
-// The window's planes are built first, then the flat list of its
-// (cell, plane) slots is evaluated 32 at a time, one lane per slot; a cell's
-// slots may span several rounds.  After each round a segmented warp sum per
-// cell is added, in round order, to the cell's accumulator in shared memory
-// (deterministic), and the facets with positive area are written to the
-// cell's Hessian row in plane order.  Finally one lane per cell writes it.
+
+// Monotone stand-in for the counter-clockwise angle in [0, 2 pi) between
+// two directions, from their cross and dot products: 0 at the same
+// direction, 2 opposite, approaching 4 just behind.
+__device__ __forceinline__ float fast_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double fast_div(double a, double b) { return a / b; }
+__device__ __forceinline__ float rsqrt_t(float a) { return rsqrtf(a); }
+__device__ __forceinline__ double rsqrt_t(double a) { return 1.0 / sqrt(a); }
+
 template <typename T>
-__global__ void __launch_bounds__(CellCfg<T>::warps * 32, 5)
+__device__ __forceinline__ T pangle(T cr, T dt) {
+  const T s = fabs(cr) + fabs(dt);
+  const T x = s > T(0) ? fast_div(dt, s) : T(1);
+  return cr >= T(0) ? T(1) - x : T(3) + x;
+}
+
+// Line-decision tolerances of the task kernel (relative to the disk radius):
+// a line whose half chord is below kTangent rho touches the disk (it cuts a
+// cap of area below 1e-9 rho^2, none of the facet, or all of it); two lines
+// within kCoincide (angle, and offset relative to rho) are one line.
+template <typename T>
+struct LineTol;
+template <>
+struct LineTol<float> {
+  static constexpr float kTangent2 = 1e-6f;  // (1e-3)^2
+  static constexpr float kCoincide = 4e-6f;
+};
+template <>
+struct LineTol<double> {
+  static constexpr double kTangent2 = 1e-14;
+  static constexpr double kCoincide = 1e-12;
+};
+
+// A crossing line of a facet in the facet's frame, staged in shared memory
+// by its task for the other tasks of the same facet: unit normal (a, b) and
+// offset c (the facet is on the side a x + b y <= c), chord start S and end
+// Q (counter-clockwise: the facet lies on the left of S -> Q), plane index
+// within the cell and whether it crosses the disk by more than a touch.
+template <typename T>
+struct LineRec {
+  T a, b, c, sx, sy, qx, qy;
+  int gl;  // plane index | live << 8
+};
+
+template <typename T>
+struct TaskOut {
+  T area, om, mx, my, rm2;
+  int arc;
+};
+
+// Frame of facet f: the disk and the security-ball centre in it.
+template <typename T>
+struct FacetFrame {
+  T h, rho2, rho, ux, uy, uz, vx, vy, vz, sect_om, ou, ov, on2, ol, far2;
+};
+
+template <typename T>
+__device__ __forceinline__ FacetFrame<T> facet_frame(const V4<T>& P, T ps, T r, T ox, T oy, T oz) {
+  FacetFrame<T> F;
+  F.h = P.w;
+  F.rho2 = ps - P.w * P.w;
+  F.rho = F.rho2 > T(0) ? sqrt(F.rho2) : T(0);
+  onb(P.x, P.y, P.z, F.ux, F.uy, F.uz, F.vx, F.vy, F.vz);
+  F.sect_om = (P.w >= T(0) ? T(1) : T(-1)) - P.w / r;
+  F.ou = F.ux * ox + F.uy * oy + F.uz * oz;
+  F.ov = F.vx * ox + F.vy * oy + F.vz * oz;
+  const T on = P.w - (P.x * ox + P.y * oy + P.z * oz);
+  F.on2 = on * on;
+  F.ol = sqrt(F.ou * F.ou + F.ov * F.ov);
+  F.far2 = (F.rho + F.ol) * (F.rho + F.ol) + F.on2;  // the circle's farthest point
+  return F;
+}
+
+// Line of plane G in the frame of facet plane P (unit normal, offset), its
+// chord and liveness.
+template <typename T>
+__device__ __forceinline__ LineRec<T> line_rec(const V4<T>& P, const FacetFrame<T>& F, const V4<T>& G,
+                                               int g) {
+  LineRec<T> L;
+  const T a = F.ux * G.x + F.uy * G.y + F.uz * G.z, b = F.vx * G.x + F.vy * G.y + F.vz * G.z;
+  const T c = G.w - F.h * (P.x * G.x + P.y * G.y + P.z * G.z);
+  const T il = rsqrt_t(a * a + b * b);
+  L.a = a * il;
+  L.b = b * il;
+  L.c = c * il;
+  const T w2 = F.rho2 - L.c * L.c;
+  const bool live = w2 > LineTol<T>::kTangent2 * F.rho2;
+  const T w = live ? sqrt(w2) : T(0);
+  // foot c (a, b), direction (-b, a)
+  L.sx = L.c * L.a + w * L.b;
+  L.sy = L.c * L.b - w * L.a;
+  L.qx = L.c * L.a - w * L.b;
+  L.qy = L.c * L.b + w * L.a;
+  L.gl = g | (live ? 256 : 0);
+  return L;
+}
+
+// One task of facet f: its line `own` (rec[me]) among the facet's lines
+// rec[lo..hi], or the facet's whole disk when no line crosses it (own.gl <
+// 0).  Moments are in the facet frame about the disk centre; rm2 is the
+// squared distance of the task's farthest boundary point from the security
+// centre, when want_extent.
+template <typename T>
+__device__ __forceinline__ TaskOut<T> facet_task(const FacetFrame<T>& F, const LineRec<T>* rec,
+                                                 int me, int lo, int hi, int lowest,
+                                                 bool want_extent) {
+  TaskOut<T> out = {T(0), T(0), T(0), T(0), T(0), 0};
+  constexpr T kPi = T(3.14159265358979323846);
+  if (!(F.rho2 > T(0))) return out;
+  if (lo > hi) {  // no line crosses the disk: the whole disk
+    out.area = kPi * F.rho2;
+    out.om = T(2) * kPi * F.sect_om;
+    out.arc = 1;
+    out.rm2 = want_extent ? F.far2 : T(0);
+    return out;
+  }
+  const LineRec<T> G = rec[me];
+  const int g = G.gl & 255;
+  const bool own_live = (G.gl & 256) != 0;
+  // a touching line with the disk centre on its far side leaves no facet
+  if (!own_live && !(G.c > T(0))) return out;
+  const T Fx = G.c * G.a, Fy = G.c * G.b, dx = -G.b, dy = G.a;
+  const T w2 = F.rho2 - G.c * G.c;
+  const T w = own_live ? sqrt(w2) : T(0);
+  T t0 = -w, t1 = w;
+  bool none = !own_live, dead = false, other_live = false;
+  // the chord end B = Q, where an arc starts if it survives; the nearest
+  // chord start ahead of it: first g's own
+  const T Bx = G.qx, By = G.qy;
+  T ecr = Bx * G.sy - By * G.sx, edt = Bx * G.sx + By * G.sy;
+  T Ex = G.sx, Ey = G.sy;
+  T best = pangle(ecr, edt);
+  for (int j = lo; j <= hi; j++) {
+    if (j == me) continue;
+    const LineRec<T> K = rec[j];
+    if (!(K.gl & 256)) {  // k touches the disk: all of it or none
+      if (!(K.c > T(0))) dead = true;
+      continue;
+    }
+    other_live = true;
+    if (!own_live) continue;
+    const T s = K.a * dx + K.b * dy;    // sin of the angle between the lines
+    const T e = K.c - (K.a * Fx + K.b * Fy);  // distance of g's foot from line k
+    if (fabs(s) <= LineTol<T>::kCoincide && fabs(e) <= LineTol<T>::kCoincide * F.rho) {
+      // one line: the lower plane index carries it; opposite half-planes
+      // leave no area
+      if (K.a * G.a + K.b * G.b < T(0) || (K.gl & 255) < g) none = true;
+      continue;
+    }
+    if (s > T(0))
+      t1 = fmin(t1, e / s);
+    else if (s < T(0))
+      t0 = fmax(t0, e / s);
+    else if (e < T(0))
+      none = true;
+    const T scr = Bx * K.sy - By * K.sx, sdt = Bx * K.sx + By * K.sy;
+    T ps_ = pangle(scr, sdt);
+    // the arc start inside k's cut-off arc (from its start to its end):
+    // only within rounding, where the arc has no length
+    if (pangle(Bx * K.qy - By * K.qx, Bx * K.qx + By * K.qy) < ps_) ps_ = T(0);
+    if (ps_ < best) {
+      best = ps_;
+      ecr = scr;
+      edt = sdt;
+      Ex = K.sx;
+      Ey = K.sy;
+    }
+  }
+  if (dead) return out;
+  if (!own_live) {
+    // touching lines only: the whole disk, counted by the lowest one
+    if (!other_live && g == lowest) {
+      out.area = kPi * F.rho2;
+      out.om = T(2) * kPi * F.sect_om;
+      out.arc = 1;
+      out.rm2 = want_extent ? F.far2 : T(0);
+    }
+    return out;
+  }
+  if (none || !(t0 < t1)) return out;
+  // the segment of g on the boundary: triangle piece from the disk centre
+  const T Ax = Fx + t0 * dx, Ay = Fy + t0 * dy;
+  const T Cx = Fx + t1 * dx, Cy = Fy + t1 * dy;
+  {
+    const T ah = fabs(F.h), h2 = F.h * F.h;
+    const T cr = Ax * Cy - Ay * Cx;
+    const T dt = Ax * Cx + Ay * Cy;
+    const T la = sqrt(Ax * Ax + Ay * Ay + h2), lb = sqrt(Cx * Cx + Cy * Cy + h2);
+    const T den = la * lb + ah * (la + lb) + dt + h2;
+    const T ta = T(0.5) * cr;
+    out.area = ta;
+    out.om = (F.h >= T(0) ? T(2) : T(-2)) * atan2(cr, den);
+    out.mx = ta * (Ax + Cx) * T(1.0 / 3.0);
+    out.my = ta * (Ay + Cy) * T(1.0 / 3.0);
+    if (want_extent) {
+      const T ex = Ax - F.ou, ey = Ay - F.ov, fx = Cx - F.ou, fy = Cy - F.ov;
+      out.rm2 = fmax(ex * ex + ey * ey, fx * fx + fy * fy) + F.on2;
+    }
+  }
+  if (t1 == w && best > T(0)) {
+    // the arc from the chord end B to E, counter-clockwise
+    // (the angle from the same cross and dot products that ranked E)
+    T phi = atan2(ecr, edt);
+    if (phi < T(0)) phi += T(2) * kPi;
+    out.area += T(0.5) * F.rho2 * phi;
+    out.om += phi * F.sect_om;
+    out.mx += F.rho2 * T(1.0 / 3.0) * (Ey - By);
+    out.my += F.rho2 * T(1.0 / 3.0) * (Bx - Ex);
+    out.arc = 1;
+    // the circle's farthest point from the security centre, if on the arc
+    if (want_extent && F.ol > T(0)) {
+      const T gx = -F.rho * F.ou / F.ol, gy = -F.rho * F.ov / F.ol;
+      if (pangle(Bx * gy - By * gx, Bx * gx + By * gy) <= best) out.rm2 = fmax(out.rm2, F.far2);
+    }
+  }
+  return out;
+}
+
+// A warp's window: the planes of consecutive cells, the crossing sets, the
+// task prefix and the per-facet sums of the tasks.
+template <typename T>
+struct Window {
+  V4<T> pl[kWin];   // plane (n, h) of each slot
+  T pd[kWin];       // distance to the neighbour (0 for a wall)
+  int pj[kWin];     // neighbour (sorted index), -1 for a wall
+  unsigned mask[kWin];  // lines crossing the slot's disk (bit = plane of the same cell)
+  int tpre[kWin + 1];   // first task of each slot
+  uint8_t owner[kWin];  // window cell of each slot
+  uint8_t dead[kWin];   // a plane keeps none of the slot's disk
+  T fa[kWin], fo[kWin], fx[kWin], fy[kWin], fr[kWin];  // facet area, solid angle, moment, extent
+  uint8_t farc[kWin];
+  LineRec<T> rec[32];  // the lines of the current round's tasks
+  int cex[33];      // first slot of each window cell
+  int cpp[33];      // first plane pair of each window cell
+  CellSlot<T> sc[32];
+};
+
+template <typename T>
+__device__ __forceinline__ T seg_max(T v, int lane, int last) {
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    T t = __shfl_down_sync(kFull, v, off);
+    if (lane + off <= last) v = fmax(v, t);
+  }
+  return v;
+}
+
+// inclusive warp prefix sum
+__device__ __forceinline__ int warp_incl(int v, int lane) {
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    int t = __shfl_up_sync(kFull, v, off);
+    if (lane >= off) v += t;
+  }
+  return v;
+}
+
+// last index i in [0, n) with a[i] <= x (a ascending, a[0] <= x)
+__device__ __forceinline__ int last_le(const int* a, int n, int x) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (a[mid] <= x)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+// One warp per task of up to 32 consecutive cells (grid order), processed in
+// windows: as many of its cells as have all their planes fit in the warp's
+// kWin slots.  Per window: (A) one lane per slot builds a plane; (B) one
+// lane per pair of planes of a cell decides whether their line crosses the
+// ball (then each is in the other's crossing set) or else whether one keeps
+// none of the other's disk; (C) one lane per task (facet, crossing line)
+// integrates its segment and arc, and a segmented warp sum per facet is
+// added, in round order, to the facet's sums in shared memory; (D) one lane
+// per slot turns its facet into the cell's pyramid, moment and Hessian
+// terms, writes the facet to the cell's Hessian row in plane order when its
+// area counts, and a segmented warp sum per cell is added to the cell's
+// accumulator; (E) one lane per cell writes it.  All sums are in a fixed
+// order (deterministic).  Cells of more than kSmallPlanes planes are the
+// big-cell kernel's.
+template <typename T>
+__global__ void __launch_bounds__(CellCfg<T>::warps * 32)
     k_cells(int64_t n, const V4<T>* __restrict__ sxp, const int32_t* __restrict__ meta,
             int32_t* cand, int kmax, Box<T> box, T* stage_vals, const T* __restrict__ soff,
             const T* __restrict__ srad, CellOut o, int32_t* err) {
   constexpr int W = CellCfg<T>::warps;
-  __shared__ V4<T> s_pl[W][kPlaneCap];
-  __shared__ T s_d[W][kPlaneCap];
-  __shared__ int s_j[W][kPlaneCap];
-  __shared__ CellSlot<T> s_cell[W][32];
+  __shared__ Window<T> s_win[W];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  V4<T>* pl = s_pl[wid];
-  T* pd = s_d[wid];
-  int* pj = s_j[wid];
-  CellSlot<T>* sc = s_cell[wid];
+  Window<T>& S = s_win[wid];
+  (void)err;
   const int64_t c0 = ((int64_t)blockIdx.x * W + wid) * kCellsPerWarp;
   if (c0 >= n) return;
   const int64_t c1 = c0 + kCellsPerWarp < n ? c0 + kCellsPerWarp : n;
@@ -721,134 +1051,263 @@ __global__ void __launch_bounds__(CellCfg<T>::warps * 32, 5)
     const bool todo = valid && o.need[cell];  // cells finished in an earlier pass take no slot
     const int mt = todo ? meta[cell] : 0;
     const int m = mt & kMetaPlanes;
-    // cells with more planes than the window are the big-cell kernel's
-    const int slots = (todo && m <= kPlaneCap) ? (m > 1 ? m : 1) : 0;
-    int incl = slots;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      int t = __shfl_up_sync(kFull, incl, off);
-      if (lane >= off) incl += t;
-    }
+    const bool mine = todo && m <= kSmallPlanes;  // larger cells are the big-cell kernel's
+    const int slots = mine ? m : 0;
+    const int incl = warp_incl(slots, lane);
     const int excl = incl - slots;
-    // a prefix of the cells (m <= kPlaneCap, so the first always fits)
-    const bool take = valid && incl <= kPlaneCap;
+    // a prefix of the cells (m <= kSmallPlanes <= kWin, so the first always fits)
+    const bool take = valid && incl <= kWin;
     const int ncell = __popc(__ballot_sync(kFull, take));
     const int total = __shfl_sync(kFull, incl, ncell - 1);
-    const unsigned owners = __ballot_sync(kFull, take && slots > 0);
+    const int np = take ? slots * (slots - 1) / 2 : 0;
+    const int pincl = warp_incl(np, lane);
     V4<T> pw = {};
     T rw = T(0), oxw = T(0), oyw = T(0), ozw = T(0);
     bool fullw = false;  // the security ball contains the site's ball: exact without an extent
-    if (take && slots > 0) {
+    if (take && mine) {
       pw = sxp[cell];
       rw = pw.w > T(0) ? sqrt(pw.w) : T(0);
       oxw = soff[3 * cell + 0];
       oyw = soff[3 * cell + 1];
       ozw = soff[3 * cell + 2];
       fullw = srad[cell] >= rw + sqrt(oxw * oxw + oyw * oyw + ozw * ozw);
-      sc[lane].a = CellAcc<T>{};
-      sc[lane].neg = 0;
-      sc[lane].qout = 0;
-      sc[lane].emitted = 0;
+      S.sc[lane].a = CellAcc<T>{};
+      S.sc[lane].neg = 0;
+      S.sc[lane].qout = 0;
+      S.sc[lane].emitted = 0;
     }
-    // build the window's planes, one slot per lane
+    if (lane < ncell) {
+      S.cex[lane] = excl;
+      S.cpp[lane] = pincl - np;
+    }
+    if (lane == ncell - 1) {
+      S.cex[ncell] = total;
+      S.cpp[ncell] = pincl;
+    }
+    __syncwarp();
+    const int ptot = S.cpp[ncell];
+
+    // (A) the window's planes, one slot per lane
     for (int t0 = 0; t0 < total; t0 += 32) {
       const int t = t0 + lane;
-      const unsigned before = __ballot_sync(kFull, take && slots > 0 && excl <= t0);
-      const unsigned heads = __reduce_or_sync(
-          kFull, (take && slots > 0 && excl > t0 && excl < t0 + 32) ? (1u << (excl - t0)) : 0u);
-      const int idx = __popc(before) + __popc(heads & (0xffffffffu >> (31 - lane))) - 1;
-      const int ow = t < total ? (int)__fns(owners, 0, idx + 1) : 0;
+      const int ow = t < total ? last_le(S.cex, ncell, t) : 0;
       const int omt = __shfl_sync(kFull, mt, ow);
-      const int oex = __shfl_sync(kFull, excl, ow);
       const V4<T> op = {__shfl_sync(kFull, pw.x, ow), __shfl_sync(kFull, pw.y, ow),
                         __shfl_sync(kFull, pw.z, ow), __shfl_sync(kFull, pw.w, ow)};
       const T orr = __shfl_sync(kFull, rw, ow);
-      const int f = t - oex;
-      if (t < total && f < (omt & kMetaPlanes))
-        plane_of(f, base + ow, op, omt, orr, sxp, cand, kmax, box, pl[t], pd[t], pj[t]);
+      if (t < total) {
+        plane_of(t - S.cex[ow], base + ow, op, omt, orr, sxp, cand, kmax, box, S.pl[t], S.pd[t],
+                 S.pj[t]);
+        S.owner[t] = (uint8_t)ow;
+        S.mask[t] = 0u;
+        S.dead[t] = 0;
+        S.fa[t] = T(0);
+        S.fo[t] = T(0);
+        S.fx[t] = T(0);
+        S.fy[t] = T(0);
+        S.fr[t] = T(0);
+        S.farc[t] = 0;
+      }
     }
     __syncwarp();
-    // evaluate the slots, 32 per round
+
+    // (B) pairs of planes of each cell: k-th pair of a cell of mc planes is
+    // (f, f + s mod mc), s = k / mc + 1, f = k mod mc (each unordered pair once)
+    for (int p0 = 0; p0 < ptot; p0 += 32) {
+      const int p = p0 + lane;
+      const int c = p < ptot ? last_le(S.cpp, ncell, p) : 0;
+      const T psc = __shfl_sync(kFull, pw.w, c);
+      if (p < ptot) {
+        const int k = p - S.cpp[c];
+        const int sb = S.cex[c];
+        const int mc = S.cex[c + 1] - sb;
+        const int s = k / mc + 1;
+        const int f = k - (s - 1) * mc;
+        int g = f + s;
+        if (g >= mc) g -= mc;
+        const V4<T> F = S.pl[sb + f], G = S.pl[sb + g];
+        const T cxx = F.y * G.z - F.z * G.y, cyy = F.z * G.x - F.x * G.z, czz = F.x * G.y - F.y * G.x;
+        const T len2 = cxx * cxx + cyy * cyy + czz * czz;  // 1 - (n_f . n_g)^2
+        const T cs = F.x * G.x + F.y * G.y + F.z * G.z;
+        const T cf = G.w - F.w * cs;  // g's line offset in f's plane: > 0 keeps f's disk centre
+        const T cg = F.w - G.w * cs;
+        bool cross = false;
+        if (len2 > T(0)) {
+          // the line of f and g crosses the open ball iff
+          // h_f^2 - 2 cs h_f h_g + h_g^2 < psi (1 - cs^2)
+          const T lhs = cs >= T(0)
+                            ? (F.w - G.w) * (F.w - G.w) + T(2) * (len2 / (T(1) + cs)) * F.w * G.w
+                            : (F.w + G.w) * (F.w + G.w) - T(2) * (len2 / (T(1) - cs)) * F.w * G.w;
+          cross = lhs < psc * len2;
+        }
+        if (cross) {
+          atomicOr(&S.mask[sb + f], 1u << g);
+          atomicOr(&S.mask[sb + g], 1u << f);
+        } else {
+          const bool parallel = !(len2 > T(0));
+          if (parallel ? cf < T(0) : !(cf > T(0))) S.dead[sb + f] = 1;
+          if (parallel ? cg < T(0) : !(cg > T(0))) S.dead[sb + g] = 1;
+        }
+      }
+    }
+    __syncwarp();
+
+    // (C) tasks: a live facet has one per crossing line, or one for its
+    // whole disk; first the task prefix over the slots
+    int carry = 0;
+    for (int t0 = 0; t0 < total; t0 += 32) {
+      const int t = t0 + lane;
+      int nt = 0;
+      if (t < total && !S.dead[t]) {
+        const int pc = __popc(S.mask[t]);
+        nt = pc > 0 ? pc : 1;
+      }
+      const int inc = warp_incl(nt, lane);
+      if (t < total) S.tpre[t] = carry + inc - nt;
+      carry += __shfl_sync(kFull, inc, 31);
+    }
+    if (lane == 0) S.tpre[total] = carry;
+    __syncwarp();
+    const int ttot = carry;
+    // rounds of whole facets (a facet has at most kSmallPlanes - 1 tasks):
+    // each task stages its line for the other tasks of its facet
+    for (int R = 0; R < ttot;) {
+      const int Rend = S.tpre[last_le(S.tpre, total + 1, R + 32)];
+      const int q = R + lane;
+      const bool act = q < Rend;
+      const int slot = act ? last_le(S.tpre, total, q) : 0;
+      const int c = act ? S.owner[slot] : 0;
+      const T psc = __shfl_sync(kFull, pw.w, c);
+      const T orr = __shfl_sync(kFull, rw, c);
+      const T sox = __shfl_sync(kFull, oxw, c), soy = __shfl_sync(kFull, oyw, c),
+              soz = __shfl_sync(kFull, ozw, c);
+      const bool ofull = __shfl_sync(kFull, fullw, c);
+      const int head = act ? S.tpre[slot] - R : lane;
+      const int last = act ? S.tpre[slot + 1] - 1 - R : lane;
+      FacetFrame<T> fr = {};
+      unsigned M = 0u;
+      if (act) {
+        const int sb = S.cex[c];
+        const V4<T> P = S.pl[slot];
+        fr = facet_frame(P, psc, orr, sox, soy, soz);
+        M = S.mask[slot];
+        if (M) {
+          const int g = (int)__fns(M, 0, q - S.tpre[slot] + 1);
+          S.rec[lane] = line_rec(P, fr, S.pl[sb + g], g);
+        }
+      }
+      __syncwarp();
+      TaskOut<T> tk = {T(0), T(0), T(0), T(0), T(0), 0};
+      if (act)
+        tk = M ? facet_task(fr, S.rec, lane, head, last, __ffs(M) - 1, !ofull)
+               : facet_task(fr, S.rec, lane, 1, 0, 0, !ofull);
+      tk.area = seg_sum(tk.area, lane, last);
+      tk.om = seg_sum(tk.om, lane, last);
+      tk.mx = seg_sum(tk.mx, lane, last);
+      tk.my = seg_sum(tk.my, lane, last);
+      tk.rm2 = seg_max(tk.rm2, lane, last);
+      tk.arc = seg_sum(tk.arc, lane, last);
+      if (act && lane == head) {
+        S.fa[slot] = tk.area;
+        S.fo[slot] = tk.om;
+        S.fx[slot] = tk.mx;
+        S.fy[slot] = tk.my;
+        S.fr[slot] = tk.rm2;
+        S.farc[slot] = tk.arc > 0 ? 1 : 0;
+      }
+      __syncwarp();
+      R = Rend;
+    }
+
+    // (D) facets: pyramid, moment and Hessian terms per slot, emission, and
+    // a segmented sum per cell
     for (int t0 = 0; t0 < total; t0 += 32) {
       const int t = t0 + lane;
       const bool inr = t < total;
-      const unsigned before = __ballot_sync(kFull, take && slots > 0 && excl <= t0);
-      const unsigned heads = __reduce_or_sync(
-          kFull, (take && slots > 0 && excl > t0 && excl < t0 + 32) ? (1u << (excl - t0)) : 0u);
-      const int idx = __popc(before) + __popc(heads & (0xffffffffu >> (31 - lane))) - 1;
-      const int ow = inr ? (int)__fns(owners, 0, idx + 1) : 0;
-      const int omt = __shfl_sync(kFull, mt, ow);
-      const int oex = __shfl_sync(kFull, excl, ow);
-      const int osl = __shfl_sync(kFull, slots, ow);
-      const V4<T> op = {__shfl_sync(kFull, pw.x, ow), __shfl_sync(kFull, pw.y, ow),
-                        __shfl_sync(kFull, pw.z, ow), __shfl_sync(kFull, pw.w, ow)};
+      const int ow = inr ? S.owner[t] : 0;
+      const T ops = __shfl_sync(kFull, pw.w, ow);
       const T orr = __shfl_sync(kFull, rw, ow);
       const T sox = __shfl_sync(kFull, oxw, ow), soy = __shfl_sync(kFull, oyw, ow),
               soz = __shfl_sync(kFull, ozw, ow);
-      const bool ofull = __shfl_sync(kFull, fullw, ow);
-      const int cm = omt & kMetaPlanes;
-      const int f = t - oex;
-      const bool has = inr && f < cm;
       CellAcc<T> a = {};
-      Facet<T> fo = {};
-      if (has) {
-        fo = facet_eval<T, uint8_t>(pl + oex, cm, f, op.w, orr, sox, soy, soz,
-                        sqrt(sox * sox + soy * soy + soz * soz), !ofull);
-        if (fo.overflow) set_error(err, POT_ERR_POLYGON_OVERFLOW, base + ow);
-        acc_facet(a, pl[t], pd[t], pj[t], fo);
+      bool neg = false, qo = false, emit = false;
+      T area = T(0);
+      if (inr) {
+        const V4<T> P = S.pl[t];
+        area = S.fa[t];
+        Facet<T> fo = {};
+        fo.area = area;
+        fo.omega = S.fo[t];
+        fo.rm2 = S.fr[t];
+        fo.arc = S.farc[t] && area > T(0);
+        T ux, uy, uz, vx, vy, vz;
+        onb(P.x, P.y, P.z, ux, uy, uz, vx, vy, vz);
+        const T mx = S.fx[t], my = S.fy[t];
+        fo.mx = P.w * P.x * area + ux * mx + vx * my;
+        fo.my = P.w * P.y * area + uy * mx + vy * my;
+        fo.mz = P.w * P.z * area + uz * mx + vz * my;
+        acc_facet(a, P, S.pd[t], S.pj[t], fo);
+        neg = P.w < T(0);
+        // the sphere point farthest from the security centre, q = p - r o/|o|,
+        // is cut off by this plane (clearly: n . (q - p) > h + 1e-6 r)
+        const T soa = sqrt(sox * sox + soy * soy + soz * soz);
+        qo = soa > T(0) && -orr * (P.x * sox + P.y * soy + P.z * soz) > (P.w + T(1e-6) * orr) * soa;
+        emit = S.pj[t] >= 0 && area > Real<T>::kEmitArea * ops;
       }
-      // this round's part of the owner's slots: lanes [lo, hi]
-      const int lo = inr ? max(oex - t0, 0) : lane;
-      const int hi = inr ? min(oex + osl - 1 - t0, 31) : lane;
+      const int cs0 = S.cex[ow];
+      const int lo = inr ? max(cs0 - t0, 0) : lane;
+      const int hi = inr ? min(S.cex[ow + 1] - 1 - t0, 31) : lane;
       seg_reduce(a, lane, hi);
       const unsigned segmask = inr ? ((0xffffffffu >> (31 - hi)) & ~((1u << lo) - 1u)) : 0u;
-      const unsigned negm = __ballot_sync(kFull, has && pl[t].w < T(0));
-      // the sphere point farthest from the security centre, q = p - r o/|o|,
-      // is cut off by this plane (clearly: n . (q - p) > h + 1e-6 r)
-      const T soa = sqrt(sox * sox + soy * soy + soz * soz);
-      const unsigned qm = __ballot_sync(
-          kFull, has && soa > T(0) &&
-                     -orr * (pl[t].x * sox + pl[t].y * soy + pl[t].z * soz) > (pl[t].w + T(1e-6) * orr) * soa);
-      const bool emit = has && pj[t] >= 0 && fo.area > Real<T>::kEmitArea * op.w;
+      const unsigned negm = __ballot_sync(kFull, neg);
+      const unsigned qm = __ballot_sync(kFull, qo);
       const unsigned emm = __ballot_sync(kFull, emit);
-      const int done = inr ? sc[ow].emitted : 0;
+      const int done = inr ? S.sc[ow].emitted : 0;
       if (emit) {
         const int rank = done + __popc(emm & segmask & ((1u << lane) - 1u));
         const int64_t at = (base + ow) * kmax + rank;
-        cand[at] = pj[t];
-        stage_vals[at] = -fo.area / (T(2) * pd[t]);
+        cand[at] = S.pj[t];
+        stage_vals[at] = -area / (T(2) * S.pd[t]);
       }
       __syncwarp();
       if (inr && lane == lo) {
-        CellAcc<T>& s = sc[ow].a;
-        s.hA += a.hA;
-        s.om += a.om;
-        s.nx += a.nx;
-        s.ny += a.ny;
-        s.nz += a.nz;
-        s.hx += a.hx;
-        s.hy += a.hy;
-        s.hz += a.hz;
-        s.dg += a.dg;
-        s.wg += a.wg;
-        s.rm2 = fmax(s.rm2, a.rm2);
-        s.nfac += a.nfac;
-        s.arc += a.arc;
-        sc[ow].neg |= (negm & segmask) != 0u;
-        sc[ow].qout |= (qm & segmask) != 0u;
-        sc[ow].emitted = done + __popc(emm & segmask);
+        CellAcc<T>& sa = S.sc[ow].a;
+        sa.hA += a.hA;
+        sa.om += a.om;
+        sa.nx += a.nx;
+        sa.ny += a.ny;
+        sa.nz += a.nz;
+        sa.hx += a.hx;
+        sa.hy += a.hy;
+        sa.hz += a.hz;
+        sa.dg += a.dg;
+        sa.wg += a.wg;
+        sa.rm2 = fmax(sa.rm2, a.rm2);
+        sa.nfac += a.nfac;
+        sa.arc += a.arc;
+        S.sc[ow].neg |= (negm & segmask) != 0u;
+        S.sc[ow].qout |= (qm & segmask) != 0u;
+        S.sc[ow].emitted = done + __popc(emm & segmask);
       }
       __syncwarp();
     }
-    if (take && slots > 0)
-      write_cell(cell, pw, (mt & kMetaEmpty) != 0, sc[lane].neg == 0, sc[lane].qout != 0 && !fullw,
-                 fullw, sc[lane].a, sc[lane].emitted, sqrt(oxw * oxw + oyw * oyw + ozw * ozw), o);
+
+    // (E) the window's cells
+    if (take && mine) {
+      const bool fix =
+          write_cell(cell, pw, (mt & kMetaEmpty) != 0, S.sc[lane].neg == 0,
+                     S.sc[lane].qout != 0 && !fullw, fullw, S.sc[lane].a, S.sc[lane].emitted,
+                     sqrt(oxw * oxw + oyw * oyw + ozw * ozw), o);
+      if (fix && o.fix_list)
+        flag_fix(cell, m, __popc((mt >> kMetaWallShift) & 63), S.pj + excl, kmax, cand,
+                 o.fix_count, o.fix_list);
+    }
     __syncwarp();
     base += ncell;
   }
 }
 
-// Cells with more planes than the shared window (kPlaneCap): one warp per
+// Cells with more planes than the cell kernel takes (kSmallPlanes): one warp per
 // cell, its planes staged in the warp's slice of a global scratch (L1/L2
 // resident), facets in rounds of 32 lanes with per-lane accumulators, one
 // warp reduction at the end.  Line ids of the facet polygons are 16-bit.
@@ -906,7 +1365,86 @@ __global__ void __launch_bounds__(128)
     seg_reduce(a, lane, 31);
     const bool anyneg = __any_sync(kFull, neg);
     const bool anyq = __any_sync(kFull, qout);
-    if (lane == 0) write_cell(cell, p, (mt & kMetaEmpty) != 0, !anyneg, anyq && !full, full, a, emitted, oa, o);
+    if (lane == 0) {
+      const bool fix = write_cell(cell, p, (mt & kMetaEmpty) != 0, !anyneg, anyq && !full, full, a,
+                                  emitted, oa, o);
+      if (fix && o.fix_list && m <= kPlaneCap)
+        flag_fix(cell, m, __popc((mt >> kMetaWallShift) & 63), pj, kmax, cand, o.fix_count,
+                 o.fix_list);
+    }
+    __syncwarp();
+  }
+}
+
+// FP64 re-evaluation of the FP32 cells that write_cell found ill-conditioned
+// (list built by the cell kernels of the same pass, their candidate rows
+// restored): one warp per cell, the planes rebuilt in FP64 from the stored
+// float sites (widened exactly, as the FP64 oracle reads them) into the
+// warp's shared window, the facets in rounds of 32 lanes, and the cell's
+// outputs and Hessian row rewritten (stored as float).  The emission
+// threshold and the security-ball decisions stay those of the FP32 pass.
+constexpr int kFixWarps = 4;
+
+__global__ void __launch_bounds__(kFixWarps * 32)
+    k_cells_fix64(const V4<float>* __restrict__ sxp, const int32_t* __restrict__ meta,
+                  int32_t* cand, int kmax, Box<double> box, float* stage_vals,
+                  const float* __restrict__ soff, const float* __restrict__ srad, CellOut o,
+                  int32_t* err) {
+  __shared__ V4<double> s_pl[kFixWarps][kPlaneCap];
+  __shared__ double s_d[kFixWarps][kPlaneCap];
+  __shared__ int s_j[kFixWarps][kPlaneCap];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  V4<double>* pl = s_pl[wid];
+  double* pd = s_d[wid];
+  int* pj = s_j[wid];
+  const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+  const int count = *o.fix_count;
+  for (int b = gw; b < count; b += nwarps) {
+    const int64_t cell = o.fix_list[b];
+    const int mt = meta[cell];
+    const int m = mt & kMetaPlanes;
+    const V4<float> ps = sxp[cell];
+    const V4<double> p = {ps.x, ps.y, ps.z, ps.w};
+    const double r = p.w > 0.0 ? sqrt(p.w) : 0.0;
+    const float oxf = soff[3 * cell + 0], oyf = soff[3 * cell + 1], ozf = soff[3 * cell + 2];
+    // the security-ball decision exactly as the FP32 pass took it
+    const float rf = ps.w > 0.f ? sqrtf(ps.w) : 0.f;
+    const bool full = srad[cell] >= rf + sqrtf(oxf * oxf + oyf * oyf + ozf * ozf);
+    const double ox = oxf, oy = oyf, oz = ozf;
+    const double oa = sqrt(ox * ox + oy * oy + oz * oz);
+    for (int f = lane; f < m; f += 32)
+      plane_of<double, float>(f, cell, p, mt, r, sxp, cand, kmax, box, pl[f], pd[f], pj[f]);
+    __syncwarp();
+    CellAcc<double> a = {};
+    bool neg = false, qout = false;
+    int emitted = 0;
+    for (int f0 = 0; f0 < m; f0 += 32) {
+      const int f = f0 + lane;
+      const bool has = f < m;
+      Facet<double> fo = {};
+      if (has) {
+        fo = facet_eval<double, uint8_t>(pl, m, f, p.w, r, ox, oy, oz, oa, !full);
+        if (fo.overflow) set_error(err, POT_ERR_POLYGON_OVERFLOW, cell);
+        acc_facet(a, pl[f], pd[f], pj[f], fo);
+        neg |= pl[f].w < 0.0;
+        qout |= oa > 0.0 && -r * (pl[f].x * ox + pl[f].y * oy + pl[f].z * oz) > (pl[f].w + 1e-6 * r) * oa;
+      }
+      const bool emit = has && pj[f] >= 0 && fo.area > (double)Real<float>::kEmitArea * p.w;
+      const unsigned em = __ballot_sync(kFull, emit);
+      if (emit) {
+        const int64_t at = cell * kmax + emitted + __popc(em & ((1u << lane) - 1u));
+        cand[at] = pj[f];
+        stage_vals[at] = (float)(-fo.area / (2.0 * pd[f]));
+      }
+      emitted += __popc(em);
+    }
+    seg_reduce(a, lane, 31);
+    const bool anyneg = __any_sync(kFull, neg);
+    const bool anyq = __any_sync(kFull, qout);
+    if (lane == 0)
+      write_cell<double, float>(cell, p, (mt & kMetaEmpty) != 0, !anyneg, anyq && !full, full, a,
+                                emitted, oa, o);
     __syncwarp();
   }
 }
@@ -1253,6 +1791,15 @@ int cells_eval(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* dom, 
   o.row_cnt = ctx->row_cnt;
   o.grad = want_grad ? ctx->grad : nullptr;
   o.snu = ctx->snu;
+  // FP32: ill-conditioned cells are listed for the FP64 re-evaluation
+  const bool fix64 = sizeof(T) == 4 && ctx->fix_list != nullptr;
+  o.fix_count = fix64 ? ctx->need_count + 2 : nullptr;
+  o.fix_list = fix64 ? ctx->fix_list : nullptr;
+  Box<double> box64;
+  for (int k = 0; k < 3; k++) {
+    box64.lo[k] = dom->lo[k];
+    box64.hi[k] = dom->hi[k];
+  }
   const int64_t warps = (n + kCellsPerWarp - 1) / kCellsPerWarp;
   const int blocks = (int)((warps + CellCfg<T>::warps - 1) / CellCfg<T>::warps);
   int32_t* hcount = (int32_t*)(ctx->h_pinned + 24);
@@ -1260,7 +1807,7 @@ int cells_eval(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* dom, 
   int64_t todo = n;  // cells rebuilt in this pass
   for (int pass = 0; pass < kMaxPasses; pass++) {
     ctx->last_passes = pass + 1;
-    POT_CUDA(cudaMemsetAsync(ctx->need_count + 1, 0, sizeof(int32_t), st));
+    POT_CUDA(cudaMemsetAsync(ctx->need_count + 1, 0, (fix64 ? 2 : 1) * sizeof(int32_t), st));
     note_launch();
     k_candidates<T><<<blocks_for(n, 256), 256, 0, st>>>(
         n, w.sxp, ctx->cell_start, w.grid, box, w.psi_max, w.gmax, w.srad, w.srad_lo, w.soff,
@@ -1277,6 +1824,13 @@ int cells_eval(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* dom, 
       k_cells_big<T><<<w.big_warps / 4, 128, 0, st>>>(
           w.sxp, ctx->meta, ctx->cand, ctx->k_max, box, w.stage_vals, w.soff, w.srad,
           ctx->need_count + 1, ctx->big_list, w.big_pl, w.big_d, w.big_j, o, ctx->err);
+    }
+    if (fix64) {
+      // a fixed grid walks the list (its length stays on the device)
+      note_launch();
+      k_cells_fix64<<<ctx->sm_count * 3, kFixWarps * 32, 0, st>>>(
+          (const V4<float>*)w.sxp, ctx->meta, ctx->cand, ctx->k_max, box64, (float*)w.stage_vals,
+          (const float*)w.soff, (const float*)w.srad, o, ctx->err);
     }
     if (timed) POT_CUDA(cudaEventRecord(ctx->ev[7], st));
     POT_CUDA(cudaMemsetAsync(ctx->need_count, 0, sizeof(int32_t), st));

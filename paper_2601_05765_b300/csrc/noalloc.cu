@@ -65,10 +65,11 @@ constexpr size_t oRcell = oSoff + al(12 * N);
 constexpr size_t oGmax = oRcell + al(4 * N);
 constexpr size_t oNeed = oGmax + al(4 * (kNoAllocGridCap + 1));
 constexpr size_t oNeedCount = oNeed + al(N);
-constexpr size_t oBigList = oNeedCount + al(8);
-constexpr size_t kScratchBytes = oBigList + al(4 * N);
-// the size the header states (5,300,736 bytes, about 5.3 MB)
-static_assert(kScratchBytes == 5300736, "update the scratch size stated in pot.h");
+constexpr size_t oBigList = oNeedCount + al(16);
+constexpr size_t oFixList = oBigList + al(4 * N);
+constexpr size_t kScratchBytes = oFixList + al(4 * N);
+// the size the header states (5,333,504 bytes, about 5.3 MB)
+static_assert(kScratchBytes == 5333504, "update the scratch size stated in pot.h");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -177,6 +178,7 @@ extern "C" int lgc_compute_cells_noalloc(void* stream, int64_t n, const float* p
   c.need = (uint8_t*)(b + oNeed);
   c.need_count = (int32_t*)(b + oNeedCount);
   c.big_list = (int32_t*)(b + oBigList);  // unused: 64-plane lists fit the cell kernel's window
+  c.fix_list = (int32_t*)(b + oFixList);
 
   // the previous call's status words are stale: clear them
   drain.armed = true;

@@ -26,7 +26,8 @@ namespace pot {
 constexpr int kWarp = 32;
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kMaxK = 1024;        // candidate bisectors per cell (k_max <= 1024)
-constexpr int kPlaneCap = 252;     // planes of a cell in the cell kernel's shared window
+constexpr int kPlaneCap = 252;     // planes of a cell kept without bisecting its security radius
+constexpr int kSmallPlanes = 32;   // planes of a cell in the cell kernel (32-bit crossing sets)
 constexpr int kBigPlanes = kMaxK + 6;  // planes of a cell in the big-cell kernel
 constexpr int kBigWarpsPerSm = 8;  // warps of the big-cell kernel per SM
 constexpr int kMaxLines = 24;      // edges of one facet polygon
@@ -210,8 +211,9 @@ struct pot_ctx {
   int64_t pcg_graph_n[2] = {-1, -1};
   int32_t* err = nullptr;         // device status words
   uint8_t* need = nullptr;        // per cell: still to be (re)built in this evaluation
-  int32_t* need_count = nullptr;  // device counters: cells to rebuild, big cells listed
+  int32_t* need_count = nullptr;  // device counters: cells to rebuild, big cells, FP64 cells listed
   int32_t* big_list = nullptr;    // cells with more planes than the shared window holds
+  int32_t* fix_list = nullptr;    // FP32 cells re-evaluated in FP64 (ill-conditioned)
   int last_passes = 0;            // security-radius passes of the last cell evaluation
   int64_t kc_launches = 0;        // cell-kernel timer: launches, cells processed, device ms
   int64_t kc_cells = 0;
