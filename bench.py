@@ -85,6 +85,8 @@ def parse():
                     help="warmstart mode: add free-flight samples (small splashes before contact, "
                          "other seeds) to the dam-break training set")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the other workloads' numbers (FP32 peak, 2^20 cloud, 1000-site solve)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     return ap.parse_args()
 
@@ -487,7 +489,7 @@ def run_ours(args):
     ctx.close()
     # the other workloads (rank 0 only; untimed for `value`)
     fp32_peak = None
-    if rank == 0:
+    if rank == 0 and not args.no_extras:
         sec = secondary(dev, cpu_baseline=world == 1 and not args.no_cpu_baseline)
         fp32_peak = sec["fp32_peak_tflops"]
         line.update(sec)

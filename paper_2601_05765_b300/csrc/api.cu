@@ -61,6 +61,9 @@ int alloc_work(Work<T>& w, int64_t n, int64_t k, int64_t gcap, int sms) {
   POT_CHECK(alloc(&w.psi_fb, n));
   POT_CHECK(alloc(&w.rcell_acc, n));
   POT_CHECK(alloc(&w.rcell, n));
+  POT_CHECK(alloc(&w.vlist, n * (int64_t)kVerletCap));
+  POT_CHECK(alloc(&w.vcount, n));
+  POT_CHECK(alloc(&w.vreach, n));
   POT_CHECK(alloc(&w.gmax, gcap + 1));
   // cells with more planes than the cell kernel takes (kSmallPlanes) exist
   // only when the lists may hold that many
@@ -78,7 +81,8 @@ void free_work(Work<T>& w) {
   void* ptrs[] = {w.sxp, w.psi_base, w.vol,  w.karea, w.diag, w.cen, w.stage_vals, w.csr_vals,
                   w.u,   w.x,        w.r,    w.z,     w.p0,   w.p1,  w.q,          w.vel_s,
                   w.psi_max, w.nu_max, w.srad, w.srad_lo, w.soff, w.hint, w.rcell_acc, w.rcell, w.gmax,
-                  w.big_pl, w.big_d, w.big_j, w.psi_hist, w.psi_fb, w.wallw};
+                  w.big_pl, w.big_d, w.big_j, w.psi_hist, w.psi_fb, w.wallw, w.vlist, w.vcount,
+                  w.vreach};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   w = Work<T>();

@@ -91,6 +91,15 @@ __device__ __forceinline__ void set_error(int32_t* err, int code, int64_t site) 
 // Grid cells are skipped with a lower bound of h over their sites: for
 // |p_i - p_j| >= delta and psi_j <= gmax,  h_ij >= delta/2 - (gmax - psi_i)/(2 delta)
 // (increasing in the distance when gmax >= psi_i), and h_ij >= delta/2 otherwise.
+// Per-site neighbour lists of the candidate pass (kVerletCap sorted indices
+// per site, their count and the reach they were built with; reach 0: none).
+template <typename T>
+struct VerletList {
+  int32_t* list;
+  int32_t* count;
+  T* reach;
+};
+
 template <typename T>
 __global__ void __launch_bounds__(256)
     k_candidates(int64_t n, const V4<T>* __restrict__ sxp, const int32_t* __restrict__ cell_start,
@@ -98,7 +107,7 @@ __global__ void __launch_bounds__(256)
                  const T* __restrict__ gmax, T* __restrict__ srad, const T* __restrict__ srad_lo,
                  const T* __restrict__ soff, uint8_t* __restrict__ need, int kmax,
                  int32_t* __restrict__ cand, int32_t* __restrict__ meta, int32_t* big_count,
-                 int32_t* big_list, int32_t* err) {
+                 int32_t* big_list, int32_t* err, VerletList<T> vl) {
   int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n || !need[s]) return;
   const V4<T> p = sxp[s];
@@ -129,22 +138,60 @@ __global__ void __launch_bounds__(256)
   const T pmx = *psi_max;
   const T D = fmin(Re + sqrt(fmax(Re * Re - ps + pmx, T(0))), r + sqrt(pmx));
   const T D2 = D * D;
+  int nc = 0;
+  bool empty = false;
+  const int64_t row = s * (int64_t)kmax;
+  // the tests of one site t within the reach D: beyond it no plane can be
+  // a candidate or empty the cell; within it the tests on h decide (h < r
+  // needs |p_i - p_j| < r_i + r_j, and h <= -r needs p_i inside ball j)
+  auto test = [&](int t, const V4<T>& q, T d2, T dx, T dy, T dz) {
+    if (d2 == T(0)) {
+      set_error(err, POT_ERR_COINCIDENT_SITES, s);
+    } else {
+      T d;
+      const T h = fix_zero(plane_offset(d2, ps, q.w, d), r);
+      if (h <= -r) {
+        empty = true;
+      } else if (h < r && h - (dx * ox + dy * oy + dz * oz) / d < R) {
+        if (nc < kmax) cand[row + nc] = t;
+        nc++;
+      }
+    }
+  };
+  // The site's neighbour list (all sites within a reach Dv, ascending), kept
+  // across the evaluations of one grid order: while the reach D stays within
+  // Dv it holds every site the tests can take, so they run over it instead
+  // of the grid.  Otherwise the grid walk below rebuilds it with reach
+  // kVerletReach D.
+  const bool use_list = vl.list != nullptr && D <= vl.reach[s];
+  const bool build = vl.list != nullptr && !use_list;
+  const int64_t vrow = s * (int64_t)kVerletCap;
+  if (use_list) {
+    const int cnt = vl.count[s];
+    for (int k = 0; k < cnt && !empty; k++) {
+      const int t = vl.list[vrow + k];
+      const V4<T> q = sxp[t];
+      T dx, dy, dz;
+      const T d2 = sqdist(p, q, dx, dy, dz);
+      if (d2 < D2) test(t, q, d2, dx, dy, dz);
+    }
+  }
+  const T Dw = build ? T(kVerletReach) * D : D;  // reach of the grid walk
+  const T Dw2 = Dw * Dw;
   int c0[3], c1[3];
   const T pc[3] = {p.x, p.y, p.z};
 #pragma unroll
   for (int k = 0; k < 3; k++) {
-    c0[k] = cell_coord(pc[k] - D, g.lo[k], g.inv_cs, g.dim[k]);
-    c1[k] = cell_coord(pc[k] + D, g.lo[k], g.inv_cs, g.dim[k]);
+    c0[k] = cell_coord(pc[k] - Dw, g.lo[k], g.inv_cs, g.dim[k]);
+    c1[k] = cell_coord(pc[k] + Dw, g.lo[k], g.inv_cs, g.dim[k]);
   }
-  int nc = 0;
-  bool empty = false;
-  const int64_t row = s * (int64_t)kmax;
+  int nv = 0;
   // One flat loop over the box of grid cells (x fastest, then y, then z)
   // and their sites: each pass tests one site or opens the next cell, so
   // the lanes of a warp stay on the same short path instead of diverging on
   // nested loop bounds.  Candidates come out in ascending sorted index.
   const int nxr = c1[0] - c0[0] + 1, nyr = c1[1] - c0[1] + 1, nzr = c1[2] - c0[2] + 1;
-  int ix = 0, iy = 0, iz = 0;  // the next cell to open
+  int ix = 0, iy = 0, iz = use_list ? nzr : 0;  // the next cell to open (none with a list)
   int t = 0, b = 0;            // the open cell's sites [t, b)
   while (!empty) {
     if (t < b) {
@@ -152,22 +199,12 @@ __global__ void __launch_bounds__(256)
         const V4<T> q = sxp[t];
         T dx, dy, dz;
         const T d2 = sqdist(p, q, dx, dy, dz);
-        // beyond the reach D no plane can be a candidate or empty the
-        // cell; within it the tests on h decide (h < r needs
-        // |p_i - p_j| < r_i + r_j, and h <= -r needs p_i inside ball j)
-        if (d2 < D2) {
-          if (d2 == T(0)) {
-            set_error(err, POT_ERR_COINCIDENT_SITES, s);
-          } else {
-            T d;
-            const T h = fix_zero(plane_offset(d2, ps, q.w, d), r);
-            if (h <= -r) {
-              empty = true;
-            } else if (h < r && h - (dx * ox + dy * oy + dz * oz) / d < R) {
-              if (nc < kmax) cand[row + nc] = t;
-              nc++;
-            }
+        if (d2 < Dw2) {
+          if (build) {
+            if (nv < kVerletCap) vl.list[vrow + nv] = t;
+            nv++;
           }
+          if (d2 < D2) test(t, q, d2, dx, dy, dz);
         }
       }
       t++;
@@ -195,9 +232,11 @@ __global__ void __launch_bounds__(256)
     if (cx == 0 && p.x < xlo) ex = T(0);
     if (cx == g.dim[0] - 1 && p.x > xlo) ex = T(0);
     const T dl2 = ex * ex + ey * ey + ez * ez;
-    if (dl2 >= D2) continue;
+    if (dl2 >= Dw2) continue;
     const int key = (cz * g.dim[1] + cy) * g.dim[0] + cx;
-    if (dl2 > T(0)) {
+    // (a list takes every site within its reach: no bound on h there, the
+    // weights change between evaluations)
+    if (dl2 > T(0) && !build) {
       const T dl = sqrt(dl2);
       const T c = gmax[key] - ps;
       const T hmin = c >= T(0) ? T(0.5) * dl - c / (T(2) * dl) : T(0.5) * dl;
@@ -205,6 +244,12 @@ __global__ void __launch_bounds__(256)
     }
     t = cell_start[key];
     b = cell_start[key + 1];
+  }
+  if (build) {
+    // a walk cut short (empty cell) or a list over capacity is no list
+    const bool ok = !empty && nv <= kVerletCap;
+    vl.count[s] = ok ? nv : 0;
+    vl.reach[s] = ok ? Dw : T(0);
   }
   const T lo = srad_lo[s];
   const bool collapsed = R - lo <= T(0.03) * R;
@@ -728,7 +773,7 @@ __device__ __forceinline__ void flag_fix(int64_t cell, int m, int nw, const int*
 // pieces meet, within rounding) ends it at once.  A facet crossed by no line
 // is its whole disk.  No polygon is stored: every task runs in registers on
 // the planes in the warp's shared window.
-constexpr int kWin = 128;  // plane slots of a warp's window
+constexpr int kWin = 96;  // plane slots of a warp's window
 
 // Warps per block: the window of every warp lives in static shared memory,
 // so the FP64 kernel runs half as many warps per block.
@@ -803,13 +848,13 @@ struct FacetFrame {
 };
 
 template <typename T>
-__device__ __forceinline__ FacetFrame<T> facet_frame(const V4<T>& P, T ps, T r, T ox, T oy, T oz) {
+__device__ __forceinline__ FacetFrame<T> facet_frame(const V4<T>& P, T ps, T ir, T ox, T oy, T oz) {
   FacetFrame<T> F;
   F.h = P.w;
   F.rho2 = ps - P.w * P.w;
   F.rho = F.rho2 > T(0) ? sqrt(F.rho2) : T(0);
   onb(P.x, P.y, P.z, F.ux, F.uy, F.uz, F.vx, F.vy, F.vz);
-  F.sect_om = (P.w >= T(0) ? T(1) : T(-1)) - P.w / r;
+  F.sect_om = (P.w >= T(0) ? T(1) : T(-1)) - P.w * ir;
   F.ou = F.ux * ox + F.uy * oy + F.uz * oz;
   F.ov = F.vx * ox + F.vy * oy + F.vz * oz;
   const T on = P.w - (P.x * ox + P.y * oy + P.z * oz);
@@ -896,9 +941,9 @@ __device__ __forceinline__ TaskOut<T> facet_task(const FacetFrame<T>& F, const L
       continue;
     }
     if (s > T(0))
-      t1 = fmin(t1, e / s);
+      t1 = fmin(t1, fast_div(e, s));
     else if (s < T(0))
-      t0 = fmax(t0, e / s);
+      t0 = fmax(t0, fast_div(e, s));
     else if (e < T(0))
       none = true;
     const T scr = Bx * K.sy - By * K.sx, sdt = Bx * K.sx + By * K.sy;
@@ -1031,7 +1076,7 @@ __device__ __forceinline__ int last_le(const int* a, int n, int x) {
 // order (deterministic).  Cells of more than kSmallPlanes planes are the
 // big-cell kernel's.
 template <typename T>
-__global__ void __launch_bounds__(CellCfg<T>::warps * 32)
+__global__ void __launch_bounds__(CellCfg<T>::warps * 32, sizeof(T) == 4 ? 6 : 2)
     k_cells(int64_t n, const V4<T>* __restrict__ sxp, const int32_t* __restrict__ meta,
             int32_t* cand, int kmax, Box<T> box, T* stage_vals, const T* __restrict__ soff,
             const T* __restrict__ srad, CellOut o, int32_t* err) {
@@ -1062,11 +1107,12 @@ __global__ void __launch_bounds__(CellCfg<T>::warps * 32)
     const int np = take ? slots * (slots - 1) / 2 : 0;
     const int pincl = warp_incl(np, lane);
     V4<T> pw = {};
-    T rw = T(0), oxw = T(0), oyw = T(0), ozw = T(0);
+    T rw = T(0), irw = T(0), oxw = T(0), oyw = T(0), ozw = T(0);
     bool fullw = false;  // the security ball contains the site's ball: exact without an extent
     if (take && mine) {
       pw = sxp[cell];
       rw = pw.w > T(0) ? sqrt(pw.w) : T(0);
+      irw = rw > T(0) ? T(1) / rw : T(0);
       oxw = soff[3 * cell + 0];
       oyw = soff[3 * cell + 1];
       ozw = soff[3 * cell + 2];
@@ -1178,7 +1224,7 @@ __global__ void __launch_bounds__(CellCfg<T>::warps * 32)
       const int slot = act ? last_le(S.tpre, total, q) : 0;
       const int c = act ? S.owner[slot] : 0;
       const T psc = __shfl_sync(kFull, pw.w, c);
-      const T orr = __shfl_sync(kFull, rw, c);
+      const T oir = __shfl_sync(kFull, irw, c);
       const T sox = __shfl_sync(kFull, oxw, c), soy = __shfl_sync(kFull, oyw, c),
               soz = __shfl_sync(kFull, ozw, c);
       const bool ofull = __shfl_sync(kFull, fullw, c);
@@ -1189,7 +1235,7 @@ __global__ void __launch_bounds__(CellCfg<T>::warps * 32)
       if (act) {
         const int sb = S.cex[c];
         const V4<T> P = S.pl[slot];
-        fr = facet_frame(P, psc, orr, sox, soy, soz);
+        fr = facet_frame(P, psc, oir, sox, soy, soz);
         M = S.mask[slot];
         if (M) {
           const int g = (int)__fns(M, 0, q - S.tpre[slot] + 1);
@@ -1800,6 +1846,10 @@ int cells_eval(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* dom, 
     box64.lo[k] = dom->lo[k];
     box64.hi[k] = dom->hi[k];
   }
+  // neighbour lists: kept across the evaluations of one grid order when the
+  // caller asked for them (a Newton solve), invalidated by the grid build
+  VerletList<T> vl = {nullptr, nullptr, nullptr};
+  if (w.verlet && w.vlist) vl = {w.vlist, w.vcount, w.vreach};
   const int64_t warps = (n + kCellsPerWarp - 1) / kCellsPerWarp;
   const int blocks = (int)((warps + CellCfg<T>::warps - 1) / CellCfg<T>::warps);
   int32_t* hcount = (int32_t*)(ctx->h_pinned + 24);
@@ -1811,7 +1861,8 @@ int cells_eval(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* dom, 
     note_launch();
     k_candidates<T><<<blocks_for(n, 256), 256, 0, st>>>(
         n, w.sxp, ctx->cell_start, w.grid, box, w.psi_max, w.gmax, w.srad, w.srad_lo, w.soff,
-        ctx->need, ctx->k_max, ctx->cand, ctx->meta, ctx->need_count + 1, ctx->big_list, ctx->err);
+        ctx->need, ctx->k_max, ctx->cand, ctx->meta, ctx->need_count + 1, ctx->big_list, ctx->err,
+        vl);
     note_launch();
     // the no-alloc entry point's context has no events: no timing there
     const bool timed = ctx->ev[6] && ctx->ev[7];

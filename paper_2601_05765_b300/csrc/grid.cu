@@ -168,6 +168,8 @@ int grid_build(pot_ctx* ctx, cudaStream_t st, int64_t n, const T* pos, const T* 
   k_gather<T><<<blocks_for(n, 256), 256, 0, st>>>(ctx->perm, n, pos, psi, targets, w.sxp,
                                                   w.psi_base, ctx->snu, ctx->iperm);
   POT_CUDA(cudaGetLastError());
+  // the candidate pass's neighbour lists belong to the previous order
+  if (w.vreach) POT_CUDA(cudaMemsetAsync(w.vreach, 0, sizeof(T) * n, st));
   w.grid = g;
   w.grid_valid = true;
   w.have_rcell = false;

@@ -254,8 +254,24 @@ int eval_and_reduce(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* 
 // start fails the KMT precondition -- an empty cell (the bound eps0 needs
 // min V > 0) or a geometry error.
 template <typename T>
+int newton_sorted_impl(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* dom,
+                       const pot_params* P, pot_solve_stats* S, const T* psi_fallback);
+
+// The evaluations of one solve share the grid order: the candidate pass
+// keeps its neighbour lists across them.
+template <typename T>
 int newton_sorted(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* dom,
                   const pot_params* P, pot_solve_stats* S, const T* psi_fallback = nullptr) {
+  Work<T>& w = ctx->work<T>();
+  w.verlet = true;
+  const int status = newton_sorted_impl<T>(ctx, st, n, dom, P, S, psi_fallback);
+  w.verlet = false;
+  return status;
+}
+
+template <typename T>
+int newton_sorted_impl(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* dom,
+                       const pot_params* P, pot_solve_stats* S, const T* psi_fallback) {
   Work<T>& w = ctx->work<T>();
   double res[6];
   if (psi_fallback) {

@@ -28,6 +28,8 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kMaxK = 1024;        // candidate bisectors per cell (k_max <= 1024)
 constexpr int kPlaneCap = 252;     // planes of a cell kept without bisecting its security radius
 constexpr int kSmallPlanes = 32;   // planes of a cell in the cell kernel (32-bit crossing sets)
+constexpr int kVerletCap = 160;    // sites of a neighbour list of the candidate pass
+constexpr float kVerletReach = 1.2f;  // a list's reach over the reach it was built for
 constexpr int kBigPlanes = kMaxK + 6;  // planes of a cell in the big-cell kernel
 constexpr int kBigWarpsPerSm = 8;  // warps of the big-cell kernel per SM
 constexpr int kMaxLines = 24;      // edges of one facet polygon
@@ -169,6 +171,10 @@ struct Work {
   T* psi_fb = nullptr;      // plain start kept while an extrapolated one is tried (sorted)
   int64_t hist_n = -1;      // sites psi_hist was written for (-1: none)
   bool use_hint = false;    // this grid order's first evaluation starts from the hint
+  int32_t* vlist = nullptr; // candidate pass: per-site neighbour lists (kVerletCap per site)
+  int32_t* vcount = nullptr;
+  T* vreach = nullptr;      // reach each list was built with (0: none; cleared by the grid build)
+  bool verlet = false;      // evaluations of the current solve keep and reuse the lists
 };
 
 }  // namespace pot
