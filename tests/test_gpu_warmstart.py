@@ -7,7 +7,8 @@ that (a) a model whose output is 0 reproduces the extrapolated start
 (psi + (psi - psi_prev)) exactly, and
 (b) a model trained on a few dam-break steps needs fewer Newton and PCG
 iterations than the start from the previous weights on unseen steps of
-another seed, with no fallback and every step converged.  (The worst-cell
+another seed, with no fallback and every step converged, and is not worse
+than the linear extrapolation it corrects.  (The worst-cell
 start error is not the measure: the prediction moves most cells much closer
 and a few outliers further.)"""
 import numpy as np
@@ -65,10 +66,21 @@ def test_trained_model_starts_closer(setup):
     assert hist[-1] < 0.1 * hist[0]
     res = W.compare(ctx, mlp, column(19), steps=8, dt=DT, warm_steps=12)
     plain, learned = W.summarize(res["plain"]), W.summarize(res["mlp"])
-    assert plain["all_converged"] and learned["all_converged"]
+    extrap = W.summarize(res["extrapolated"])
+    print("Newton / PCG iterations per step: plain", plain["newton_iters"], plain["pcg_iters"],
+          "extrapolated", extrap["newton_iters"], extrap["pcg_iters"],
+          "learned", learned["newton_iters"], learned["pcg_iters"])
+    assert plain["all_converged"] and learned["all_converged"] and extrap["all_converged"]
     assert learned["fallback_rate"] == 0.0 and learned["used_rate"] == 1.0
+    # the gain over the method without the network (plain Newton from the
+    # previous weights) ...
     assert learned["newton_iters"] <= plain["newton_iters"] - 0.5, (learned, plain)
     assert learned["pcg_iters"] < plain["pcg_iters"], (learned, plain)
+    # ... and against the free linear extrapolation of the weights, which the
+    # network corrects: not worse by more than a quarter of a Newton
+    # iteration per step (on these columns the two are close; the splash
+    # comparison is in bench.py --mode warmstart)
+    assert learned["newton_iters"] <= extrap["newton_iters"] + 0.25, (learned, extrap)
 
 
 def test_extrapolated_start(setup):
