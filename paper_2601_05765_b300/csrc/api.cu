@@ -297,7 +297,7 @@ int pot_create(pot_ctx** out, int device, int64_t n_max, int32_t k_max, int32_t 
   A(ctx->red, 6 * kRedBlocks);
   A(ctx->red_out, 8);
   A(ctx->pcg_red, pcg_red_len(ctx->sm_count));
-  A(ctx->pcg_ctl, 8);
+  A(ctx->pcg_ctl, kPcgCtlWords);
   A(ctx->err, 2);
   A(ctx->need, n);
   A(ctx->need_count, 4);

@@ -319,6 +319,7 @@ int mlp_warm_start(pot_ctx* ctx, pot_mlp* mm, cudaStream_t st, int64_t n, const 
 
 // PCG (pcg.cu): solve M u = grad (sorted space) into work.u
 constexpr int kPcgMaxBlocksPerSm = 8;
+constexpr int kPcgCtlWords = 16;    // ctx->pcg_ctl
 int pcg_blocks(int sm_count);       // largest grid of the PCG kernels
 size_t pcg_red_len(int sm_count);   // doubles of ctx->pcg_red
 template <typename T>
