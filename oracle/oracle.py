@@ -17,7 +17,9 @@ Contents, each citing the paper passage it follows:
   fluid_step()    Gallouet-Merigot step of Sec. 5 (pressure spring, gravity,
                   symplectic update); with viscosity or surface tension the
                   semi-implicit velocity solve of Eq. 4 over the P1
-                  Laplacian of Eq. 3 (laplacian_weights, viscous_velocity).
+                  Laplacian of Eq. 3 (laplacian_weights, viscous_velocity),
+                  with the walls' terms of Sec. 5 (wall_weights,
+                  wall_tension).
   render_depth()  first point of each camera ray inside the fluid (the union
                   of the balls inside the box), with the free-surface culling
                   of Sec. 6's first-cell search; brute force over all balls.
@@ -301,8 +303,28 @@ def wall_weights(res, pos, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0)):
     return np.sum(np.where(a > 0, a / (2.0 * np.where(h > 0, h, np.inf)), 0.0), axis=1)
 
 
+def wall_tension(res, pos, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0)):
+    """Per cell, the walls' part of the surface-tension Laplacian of the
+    positions (Sec. 5, fluid-boundary interaction): each wall facet B_iw acts
+    as the facet to a neighbour placed cbrt(|V_i|) beyond the wall plane,
+    with the P1 weight |B_iw| / (2 h_iw) of the boundary term (h_iw the
+    site's distance to the wall), so it adds
+        |B_iw| / (2 h_iw) * (h_iw + cbrt(|V_i|)) * n_w
+    (n_w the wall's outward normal; walls -x, +x, -y, +y, -z, +z).  (n, 3)."""
+    pos = np.asarray(pos, np.float64)
+    lo = np.asarray(lo, np.float64)
+    hi = np.asarray(hi, np.float64)
+    h = np.stack([pos[:, 0] - lo[0], hi[0] - pos[:, 0], pos[:, 1] - lo[1], hi[1] - pos[:, 1],
+                  pos[:, 2] - lo[2], hi[2] - pos[:, 2]], axis=1)
+    normals = np.array([[-1, 0, 0], [1, 0, 0], [0, -1, 0], [0, 1, 0], [0, 0, -1], [0, 0, 1]], float)
+    a = res["wall_area"]
+    cv = np.cbrt(np.maximum(res["vol"], 0.0))
+    mag = np.where(a > 0, a / (2.0 * np.where(h > 0, h, np.inf)) * (h + cv[:, None]), 0.0)
+    return mag @ normals
+
+
 def viscous_velocity(x1, v, cen, w, dt, eps, g, mu, gamma, factors=None, wall_w=None,
-                     mu_wall=0.0):
+                     mu_wall=0.0, wall_t=None, gamma_wall=0.0):
     """Semi-implicit velocity update with viscosity and surface tension
     (Sec. 5, Eq. 4, unit mass):
     (I/dt + (D_mu - W_mu)) v^{k+1} = v^k/dt + F_p + F_g + F_t,
@@ -310,7 +332,9 @@ def viscous_velocity(x1, v, cen, w, dt, eps, g, mu, gamma, factors=None, wall_w=
     W_mu = mu_ij w_ij with mu_ij = mu (f_i + f_j) / 2 (per-site factors f for
     several fluids, the per-pair coefficients of Sec. 5; all 1 by default),
     D_mu = diag(sum_j mu_ij w_ij); walls at rest add mu_wall * wall_w to the
-    diagonal (no-slip); one dense solve for the three components."""
+    diagonal (no-slip); the walls' part of the surface tension adds
+    gamma_wall * wall_t (wall_tension) to F_t; one dense solve for the three
+    components."""
     x1 = np.asarray(x1, np.float64)
     n = x1.shape[0]
     f = np.ones(n) if factors is None else np.asarray(factors, np.float64)
@@ -319,13 +343,16 @@ def viscous_velocity(x1, v, cen, w, dt, eps, g, mu, gamma, factors=None, wall_w=
     lap_x = w @ x1 - d[:, None] * x1
     b = (np.asarray(v, np.float64) / dt + (np.asarray(cen, np.float64) - x1) / (eps * eps)
          + np.asarray(g, np.float64)[None, :] + gamma * lap_x)
+    if wall_t is not None and gamma_wall != 0.0:
+        b = b + gamma_wall * np.asarray(wall_t, np.float64)
     dw = np.zeros(n) if wall_w is None else mu_wall * np.asarray(wall_w, np.float64)
     a = np.diag(1.0 / dt + wm.sum(axis=1) + dw) - wm
     return np.linalg.solve(a, b)
 
 
 def fluid_step(pos, vel, psi, nu, dt, eps=0.01, g=(0.0, 0.0, -9.81), tol=1e-4,
-               max_newton=100, nthreads=0, mu=0.0, gamma=0.0, factors=None, mu_wall=0.0):
+               max_newton=100, nthreads=0, mu=0.0, gamma=0.0, factors=None, mu_wall=0.0,
+               gamma_wall=0.0):
     """One fluid step: advect + clamp, Newton at x^{k+1} warm-started from
     psi, centroids of the converged cells, velocity update -- explicit, or
     semi-implicit with viscosity mu and surface tension gamma (Eq. 4) when
@@ -333,12 +360,14 @@ def fluid_step(pos, vel, psi, nu, dt, eps=0.01, g=(0.0, 0.0, -9.81), tol=1e-4,
     x1, v = advect_and_clamp(pos, vel, dt)
     nr = newton(x1, nu, psi, tol=tol, max_newton=max_newton, nthreads=nthreads)
     cen = nr.res["cen"]
-    if mu == 0.0 and gamma == 0.0 and mu_wall == 0.0:
+    if mu == 0.0 and gamma == 0.0 and mu_wall == 0.0 and gamma_wall == 0.0:
         v1 = velocity_update(x1, v, cen, dt, eps=eps, g=g)
     else:
         w = laplacian_weights(nr.res, nr.psi)
         ww = wall_weights(nr.res, x1) if mu_wall > 0.0 else None
-        v1 = viscous_velocity(x1, v, cen, w, dt, eps, g, mu, gamma, factors, ww, mu_wall)
+        wt = wall_tension(nr.res, x1) if gamma_wall != 0.0 else None
+        v1 = viscous_velocity(x1, v, cen, w, dt, eps, g, mu, gamma, factors, ww, mu_wall, wt,
+                              gamma_wall)
     return x1, v1, nr
 
 

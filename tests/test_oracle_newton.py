@@ -227,6 +227,36 @@ def test_wall_weights_closed_form_and_no_slip():
     np.testing.assert_allclose(out[1], expl[1], rtol=1e-12, atol=1e-12)
 
 
+def test_wall_tension_closed_form():
+    """The walls' part of the surface tension (Sec. 5): a lone ball cut by
+    the floor at height h is pulled toward the floor by
+    pi (psi - h^2) / (2 h) * (h + cbrt(V)), V the ball minus its cap below
+    the floor, 4/3 pi r^3 - pi t^2 (3 r - t) / 3 with t = r - h; a ball in
+    the edge of the floor and the -x wall is pulled equally toward both; a
+    ball away from the walls not at all.  Its velocity update then gains
+    dt gamma_wall times that (explicit: no viscosity)."""
+    h, r = 0.05, 0.08
+    pos = np.array([[0.5, 0.5, h], [0.5, 0.5, 0.5], [h, 0.3, h]])
+    psi = np.array([r * r, 0.05 ** 2, r * r])
+    res = O.cells(pos, psi)
+    t = r - h
+    vol = 4.0 / 3.0 * math.pi * r ** 3 - math.pi * t * t * (3 * r - t) / 3.0
+    assert abs(res["vol"][0] - vol) < 1e-14
+    wt = O.wall_tension(res, pos)
+    mag = math.pi * (r * r - h * h) / (2 * h) * (h + vol ** (1.0 / 3.0))
+    np.testing.assert_allclose(wt[0], [0.0, 0.0, -mag], rtol=1e-12, atol=1e-15)
+    assert np.all(wt[1] == 0.0)
+    assert wt[2][0] < 0 and wt[2][2] < 0 and wt[2][1] == 0.0
+    assert abs(wt[2][0] - wt[2][2]) < 1e-12 * abs(wt[2][0])
+    w = O.laplacian_weights(res, psi)
+    v = np.zeros((3, 3))
+    dt, gw = 1e-3, 7.0
+    out = O.viscous_velocity(pos, v, res["cen"], w, dt, 0.01, np.zeros(3), 0.0, 0.0,
+                             wall_t=wt, gamma_wall=gw)
+    expl = O.velocity_update(pos, v, res["cen"], dt, eps=0.01, g=(0.0, 0.0, 0.0))
+    np.testing.assert_allclose(out, expl + dt * gw * wt, rtol=1e-12, atol=1e-15)
+
+
 def test_wall_weights_two_walls_clip_each_other():
     """A ball in the edge between the floor and the -x wall, both at distance
     h: each wall's disk (radius rho = sqrt(psi - h^2), centre at distance h
