@@ -112,6 +112,8 @@ typedef struct {
   double mu;            /* viscosity (Eq. 4; 0: none) */
   double gamma;         /* surface tension (Sec. 5; 0: none) */
   double mu_wall;       /* fluid-wall affinity of the viscosity (walls at rest; 0: none) */
+  double gamma_wall;    /* the walls' part of the surface tension: surface tension times
+                           the fluid's affinity to the walls (Sec. 5; 0: none) */
 } pot_params;
 
 /* Statistics of one Newton solve (and of the solve inside a fluid step). */
@@ -299,7 +301,11 @@ int pot_newton_solve_f64(pot_ctx* ctx, void* stream, int64_t n, const double* po
  * one Jacobi-PCG solve per component (relative residual 1e-6 in FP32,
  * 1e-11 in FP64); params->mu_wall > 0 adds walls at rest, mu_wall times the
  * cell's wall facets' weight |B_iw| / (2 h_iw) on the diagonal (Sec. 5's
- * fluid-boundary term); the free surface adds no Laplacian term.
+ * fluid-boundary term); params->gamma_wall != 0 adds the walls' part of the
+ * surface tension, each wall facet acting as the facet to a neighbour placed
+ * cbrt(|V_i|) beyond the wall (Sec. 5): gamma_wall times
+ * sum_w |B_iw| / (2 h_iw) (h_iw + cbrt(|V_i|)) n_w on the right-hand side
+ * (n_w the wall's outward normal); the free surface adds no Laplacian term.
  * With params->warm_start = 2, Newton starts from psi + (psi - psi_prev),
  * psi_prev the weights at the start of the previous pot_fluid_step on this
  * context with the same n (none after pot_create, pot_clear_history or a

@@ -57,6 +57,7 @@ int alloc_work(Work<T>& w, int64_t n, int64_t k, int64_t gcap, int sms) {
   POT_CHECK(alloc(&w.soff, 3 * n));
   POT_CHECK(alloc(&w.hint, 4 * n));
   POT_CHECK(alloc(&w.wallw, n));
+  POT_CHECK(alloc(&w.wallv, 6 * n));
   POT_CHECK(alloc(&w.psi_hist, n));
   POT_CHECK(alloc(&w.psi_fb, n));
   POT_CHECK(alloc(&w.rcell_acc, n));
@@ -82,7 +83,7 @@ void free_work(Work<T>& w) {
                   w.u,   w.x,        w.r,    w.z,     w.p0,   w.p1,  w.q,          w.vel_s,
                   w.psi_max, w.nu_max, w.srad, w.srad_lo, w.soff, w.hint, w.rcell_acc, w.rcell, w.gmax,
                   w.big_pl, w.big_d, w.big_j, w.psi_hist, w.psi_fb, w.wallw, w.vlist, w.vcount,
-                  w.vreach};
+                  w.vreach, w.wallv};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   w = Work<T>();
@@ -106,7 +107,7 @@ bool check_params(const pot_params* p) {
   return p && p->tol > 0.0 && p->max_newton >= 0 && p->max_halvings >= 0 && p->max_pcg > 0 &&
          p->pcg_chunk > 0 && isfinite(p->dt) && p->eps > 0.0 && p->substeps >= 0 &&
          p->mu >= 0.0 && p->gamma >= 0.0 && p->mu_wall >= 0.0 && isfinite(p->mu) &&
-         isfinite(p->gamma) && isfinite(p->mu_wall);
+         isfinite(p->gamma) && isfinite(p->mu_wall) && isfinite(p->gamma_wall);
 }
 
 template <typename T, typename CSR>

@@ -591,6 +591,9 @@ template <typename T>
 struct CellAcc {
   T hA, om, nx, ny, nz, hx, hy, hz, dg, rm2;
   T wg;      // sum over wall facets of |B| / (2 h): the walls' P1 Laplacian weight
+  // over wall facets, sum of |B| n / 2 and of |B| n / (2 h) (n the wall's
+  // outward normal): the walls' part of the surface tension
+  T wax, way, waz, wbx, wby, wbz;
   int nfac;  // facets of positive area
   int arc;   // facets with a circular edge
 };
@@ -609,7 +612,16 @@ __device__ __forceinline__ void acc_facet(CellAcc<T>& a, const V4<T>& pl, T pd, 
   if (pj >= 0)
     a.dg += fo.area / (T(2) * pd);
   else
-    a.wg += fo.area / (T(2) * pl.w);
+  {
+    const T wb = fo.area / (T(2) * pl.w);
+    a.wg += wb;
+    a.wax += T(0.5) * fo.area * pl.x;
+    a.way += T(0.5) * fo.area * pl.y;
+    a.waz += T(0.5) * fo.area * pl.z;
+    a.wbx += wb * pl.x;
+    a.wby += wb * pl.y;
+    a.wbz += wb * pl.z;
+  }
   a.rm2 = fmax(a.rm2, fo.rm2);
   a.nfac += fo.area > T(0) ? 1 : 0;
   a.arc += fo.arc;
@@ -638,6 +650,12 @@ __device__ __forceinline__ void seg_reduce(CellAcc<T>& a, int lane, int last) {
   a.hz = seg_sum(a.hz, lane, last);
   a.dg = seg_sum(a.dg, lane, last);
   a.wg = seg_sum(a.wg, lane, last);
+  a.wax = seg_sum(a.wax, lane, last);
+  a.way = seg_sum(a.way, lane, last);
+  a.waz = seg_sum(a.waz, lane, last);
+  a.wbx = seg_sum(a.wbx, lane, last);
+  a.wby = seg_sum(a.wby, lane, last);
+  a.wbz = seg_sum(a.wbz, lane, last);
 #pragma unroll
   for (int off = 1; off < 32; off <<= 1) {
     T t = __shfl_down_sync(kFull, a.rm2, off);
@@ -658,6 +676,7 @@ struct CellOut {
   double* grad;
   const double* snu;
   void* wallw;  // the walls' Laplacian weight per cell (optional)
+  void* wallv;  // the walls' surface-tension vectors per cell (6 values, optional)
   int32_t* fix_count;  // FP32 kernels: ill-conditioned cells for the FP64 pass (NULL: none)
   int32_t* fix_list;
 };
@@ -732,6 +751,15 @@ __device__ __forceinline__ bool write_cell(int64_t cell, const V4<T>& p, bool em
   o.row_cnt[cell] = cnt;
   if (o.grad) o.grad[cell] = o.snu[cell] - (double)(S)V;
   if (o.wallw) ((S*)o.wallw)[cell] = empty ? S(0) : (S)a.wg;
+  if (o.wallv) {
+    S* wv = (S*)o.wallv + 6 * cell;
+    wv[0] = empty ? S(0) : (S)a.wax;
+    wv[1] = empty ? S(0) : (S)a.way;
+    wv[2] = empty ? S(0) : (S)a.waz;
+    wv[3] = empty ? S(0) : (S)a.wbx;
+    wv[4] = empty ? S(0) : (S)a.wby;
+    wv[5] = empty ? S(0) : (S)a.wbz;
+  }
   if (sizeof(T) != 4 || empty || !(ps > T(0)) || (K == T(0) && inside)) return false;
   const T r = sqrt(ps);
   const T ball = T(4.0 * 3.14159265358979323846 / 3.0) * ps * r;
@@ -1328,6 +1356,12 @@ __global__ void __launch_bounds__(CellCfg<T>::warps * 32, sizeof(T) == 4 ? 6 : 2
         sa.hz += a.hz;
         sa.dg += a.dg;
         sa.wg += a.wg;
+        sa.wax += a.wax;
+        sa.way += a.way;
+        sa.waz += a.waz;
+        sa.wbx += a.wbx;
+        sa.wby += a.wby;
+        sa.wbz += a.wbz;
         sa.rm2 = fmax(sa.rm2, a.rm2);
         sa.nfac += a.nfac;
         sa.arc += a.arc;
@@ -1832,6 +1866,7 @@ int cells_eval(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* dom, 
   o.vol = w.vol;
   o.karea = w.karea;
   o.wallw = w.wallw;
+  o.wallv = w.wallv;
   o.diag = w.diag;
   o.cen = w.cen;
   o.row_cnt = ctx->row_cnt;

@@ -123,9 +123,11 @@ __global__ void k_extrapolate(int64_t n, const int32_t* __restrict__ perm, const
 // Eq. 4, unit mass) over the P1 Laplacian of Eq. 3, whose weights
 // w_ij = |B_ij| / (2 d_ij) are the converged cells' off-diagonal Hessian
 // entries with the sign flipped (vals = -w):
-//   (I/dt + mu (D - W) + mu_wall Dw) v^{k+1} = v^k/dt + (c - x)/eps^2 + g + gamma L x,
+//   (I/dt + mu (D - W) + mu_wall Dw) v^{k+1} = v^k/dt + (c - x)/eps^2 + g + gamma L x + T_w,
 //   D = diag(sum_j w_ij), (L x)_i = sum_j w_ij (x_j - x_i), Dw = diag of the
-//   wall facets' weights |B_iw| / (2 h_iw) (walls at rest: no-slip).
+//   wall facets' weights |B_iw| / (2 h_iw) (walls at rest: no-slip), T_w the
+//   walls' part of the surface tension, gamma_wall sum_w |B_iw| / (2 h_iw)
+//   (h_iw + cbrt |V_i|) n_w (a neighbour cbrt |V_i| beyond each wall).
 // This kernel forms the right-hand side per sorted site (into b, 3 per
 // site) and the system's diagonal (into diag).
 // With per-site factors f (several fluids), mu_ij = mu (f_i + f_j) / 2 (the
@@ -136,7 +138,8 @@ __global__ void k_visc_rhs(int64_t n, const int32_t* __restrict__ perm,
                            const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ cols,
                            T* vals, const V4<T>* __restrict__ sxp, const T* cen,
                            const T* __restrict__ vel, const float* __restrict__ factors,
-                           const T* __restrict__ wallw, T mu_wall, T dt, T inv_eps2, T gx, T gy,
+                           const T* __restrict__ wallw, T mu_wall, const T* __restrict__ wallv,
+                           const T* __restrict__ vol, T gamma_wall, T dt, T inv_eps2, T gx, T gy,
                            T gz, T mu, T gamma, T* b, T* diag) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -155,9 +158,20 @@ __global__ void k_visc_rhs(int64_t n, const int32_t* __restrict__ perm,
     lz += wij * (q.z - p.z);
   }
   const int64_t o = perm[i];
-  const T bx = vel[3 * o + 0] / dt + (cen[3 * i + 0] - p.x) * inv_eps2 + gx + gamma * lx;
-  const T by = vel[3 * o + 1] / dt + (cen[3 * i + 1] - p.y) * inv_eps2 + gy + gamma * ly;
-  const T bz = vel[3 * o + 2] / dt + (cen[3 * i + 2] - p.z) * inv_eps2 + gz + gamma * lz;
+  T tx = T(0), ty = T(0), tz = T(0);
+  if (gamma_wall != T(0)) {
+    // the walls' part of the surface tension: each wall facet is the facet
+    // to a neighbour cbrt(|V_i|) beyond the wall, weight |B| / (2 h):
+    // sum_w |B|/(2h) (h + cbrt V) n = sum |B| n / 2 + cbrt V sum |B| n / (2h)
+    const T* wv = wallv + 6 * i;
+    const T cv = cbrt(fmax(vol[i], T(0)));
+    tx = gamma_wall * (wv[0] + cv * wv[3]);
+    ty = gamma_wall * (wv[1] + cv * wv[4]);
+    tz = gamma_wall * (wv[2] + cv * wv[5]);
+  }
+  const T bx = vel[3 * o + 0] / dt + (cen[3 * i + 0] - p.x) * inv_eps2 + gx + gamma * lx + tx;
+  const T by = vel[3 * o + 1] / dt + (cen[3 * i + 1] - p.y) * inv_eps2 + gy + gamma * ly + ty;
+  const T bz = vel[3 * o + 2] / dt + (cen[3 * i + 2] - p.z) * inv_eps2 + gz + gamma * lz + tz;
   b[3 * i + 0] = bx;
   b[3 * i + 1] = by;
   b[3 * i + 2] = bz;
@@ -454,7 +468,8 @@ int fluid_substep(pot_ctx* ctx, cudaStream_t st, int64_t n, T* pos, T* vel, T* p
   }
   if (status == POT_OK || status == POT_ERR_NOT_CONVERGED || status == POT_ERR_LINESEARCH_FAILED) {
     Work<T>& w = ctx->work<T>();
-    const bool viscous = P->mu > 0.0 || P->gamma > 0.0 || P->mu_wall > 0.0;
+    const bool viscous =
+        P->mu > 0.0 || P->gamma > 0.0 || P->mu_wall > 0.0 || P->gamma_wall != 0.0;
     const bool solve = P->mu > 0.0 || P->mu_wall > 0.0;
     if (viscous) {
       // Eq. 4 over the converged cells: right-hand side from the old
@@ -466,7 +481,8 @@ int fluid_substep(pot_ctx* ctx, cudaStream_t st, int64_t n, T* pos, T* vel, T* p
       note_launch();
       k_visc_rhs<T><<<blocks_for(n, 256), 256, 0, st>>>(
           n, ctx->perm, ctx->row_ptr, ctx->csr_cols, w.csr_vals, w.sxp, w.cen, vel,
-          ctx->visc_factors_n == n ? ctx->visc_factors : nullptr, w.wallw, (T)P->mu_wall, (T)dt,
+          ctx->visc_factors_n == n ? ctx->visc_factors : nullptr, w.wallw, (T)P->mu_wall,
+          w.wallv, w.vol, (T)P->gamma_wall, (T)dt,
           (T)(1.0 / (P->eps * P->eps)), (T)P->gravity[0], (T)P->gravity[1], (T)P->gravity[2],
           (T)P->mu, (T)P->gamma, w.vel_s, w.diag);
       POT_CUDA(cudaGetLastError());

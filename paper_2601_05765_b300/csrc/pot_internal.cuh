@@ -167,6 +167,7 @@ struct Work {
   bool have_acc = false;    // rcell_acc belongs to the current grid order
   int64_t hint_n = -1;      // sites the hint was written for (-1: none)
   T* wallw = nullptr;       // walls' P1 Laplacian weight per cell (sorted)
+  T* wallv = nullptr;       // per cell (sorted): sum over wall facets of |B| n / 2 and of |B| n / (2h)
   T* psi_hist = nullptr;    // weights at the start of the last fluid step (caller order)
   T* psi_fb = nullptr;      // plain start kept while an extrapolated one is tried (sorted)
   int64_t hist_n = -1;      // sites psi_hist was written for (-1: none)

@@ -234,3 +234,38 @@ def test_wall_viscosity_matches_oracle(ctx, dtype, mu):
     scale = float(np.max(np.abs(v1)))
     atol = 1e-9 * scale if dtype == torch.float64 else 2e-3 * scale
     np.testing.assert_allclose(vel.cpu().numpy().astype(np.float64), v1, rtol=0, atol=atol)
+
+
+@pytest.mark.parametrize("dtype,mu,gamma", [(torch.float64, 0.0, 0.0), (torch.float32, 0.0, 0.0),
+                                            (torch.float32, 2000.0, 500.0)])
+def test_wall_tension_matches_oracle(ctx, dtype, mu, gamma):
+    """The walls' part of the surface tension (Sec. 5, fluid-boundary
+    interaction: each wall facet is the facet to a neighbour cbrt(|V_i|)
+    beyond the wall), alone (an explicit update) and with the bulk
+    viscosity and surface tension (a semi-implicit solve), against the
+    oracle's dense fluid step on a dam-break column standing in a box
+    corner."""
+    sc = scenes.dam_break(nx=10, ny=10, nz=20, width=0.16, seed=3)
+    dev = ctx.device
+    npdt = np.float64 if dtype == torch.float64 else np.float32
+    x0 = sc.pos.astype(npdt).astype(np.float64)
+    r0 = O.newton(x0, sc.nu, sc.psi.astype(np.float64), tol=1e-10)
+    psi0 = r0.psi.astype(npdt)
+    rng = np.random.default_rng(9)
+    vel0 = (rng.normal(size=sc.pos.shape) * 0.3).astype(npdt)
+    pos, vel, psi = tens(x0, dtype, dev), tens(vel0, dtype, dev), tens(psi0, dtype, dev)
+    gamma_wall = 3e4
+    tol = 1e-10 if dtype == torch.float64 else 1e-4
+    prm = pot.default_params(tol=tol, dt=2e-3, mu=mu, gamma=gamma, gamma_wall=gamma_wall)
+    st = pot.pot_fluid_step(ctx, pos, vel, psi, tens(sc.nu, torch.float64, dev), params=prm)
+    assert st["status"] == 0
+    args = (x0, vel0.astype(np.float64), psi0.astype(np.float64), sc.nu)
+    _, v1, _ = O.fluid_step(*args, dt=2e-3, tol=1e-11, mu=mu, gamma=gamma, gamma_wall=gamma_wall)
+    _, v_free, _ = O.fluid_step(*args, dt=2e-3, tol=1e-11, mu=mu, gamma=gamma)
+    assert np.max(np.abs(v1 - v_free)) > 1e-2  # the walls matter
+    scale = float(np.max(np.abs(v1)))
+    atol = 1e-9 * scale if dtype == torch.float64 else 2e-3 * scale
+    got = vel.cpu().numpy().astype(np.float64)
+    print("wall tension: max |dv| from the walls", float(np.max(np.abs(v1 - v_free))),
+          "GPU error", float(np.max(np.abs(got - v1))), "of scale", scale)
+    np.testing.assert_allclose(got, v1, rtol=0, atol=atol)
