@@ -591,9 +591,6 @@ template <typename T>
 struct CellAcc {
   T hA, om, nx, ny, nz, hx, hy, hz, dg, rm2;
   T wg;      // sum over wall facets of |B| / (2 h): the walls' P1 Laplacian weight
-  // over wall facets, sum of |B| n / 2 and of |B| n / (2 h) (n the wall's
-  // outward normal): the walls' part of the surface tension
-  T wax, way, waz, wbx, wby, wbz;
   int nfac;  // facets of positive area
   int arc;   // facets with a circular edge
 };
@@ -612,19 +609,24 @@ __device__ __forceinline__ void acc_facet(CellAcc<T>& a, const V4<T>& pl, T pd, 
   if (pj >= 0)
     a.dg += fo.area / (T(2) * pd);
   else
-  {
-    const T wb = fo.area / (T(2) * pl.w);
-    a.wg += wb;
-    a.wax += T(0.5) * fo.area * pl.x;
-    a.way += T(0.5) * fo.area * pl.y;
-    a.waz += T(0.5) * fo.area * pl.z;
-    a.wbx += wb * pl.x;
-    a.wby += wb * pl.y;
-    a.wbz += wb * pl.z;
-  }
+    a.wg += fo.area / (T(2) * pl.w);
   a.rm2 = fmax(a.rm2, fo.rm2);
   a.nfac += fo.area > T(0) ? 1 : 0;
   a.arc += fo.arc;
+}
+
+// The walls' part of the surface tension of a cell: over its wall facets
+// (area, plane: outward normal n and the site's distance h), the sums of
+// |B| n / 2 and of |B| n / (2 h), added into v[0..6).
+template <typename T>
+__device__ __forceinline__ void wall_vec(T area, const V4<T>& pl, T* v) {
+  const T wb = area / (T(2) * pl.w);
+  v[0] += T(0.5) * area * pl.x;
+  v[1] += T(0.5) * area * pl.y;
+  v[2] += T(0.5) * area * pl.z;
+  v[3] += wb * pl.x;
+  v[4] += wb * pl.y;
+  v[5] += wb * pl.z;
 }
 
 // sum over lanes [lane, last] into the first lane of the window (segment head)
@@ -650,12 +652,6 @@ __device__ __forceinline__ void seg_reduce(CellAcc<T>& a, int lane, int last) {
   a.hz = seg_sum(a.hz, lane, last);
   a.dg = seg_sum(a.dg, lane, last);
   a.wg = seg_sum(a.wg, lane, last);
-  a.wax = seg_sum(a.wax, lane, last);
-  a.way = seg_sum(a.way, lane, last);
-  a.waz = seg_sum(a.waz, lane, last);
-  a.wbx = seg_sum(a.wbx, lane, last);
-  a.wby = seg_sum(a.wby, lane, last);
-  a.wbz = seg_sum(a.wbz, lane, last);
 #pragma unroll
   for (int off = 1; off < 32; off <<= 1) {
     T t = __shfl_down_sync(kFull, a.rm2, off);
@@ -698,7 +694,7 @@ constexpr float kFixDiagOverR = 0.1f;
 template <typename T, typename S = T>
 __device__ __forceinline__ bool write_cell(int64_t cell, const V4<T>& p, bool empty, bool inside,
                                            bool qout, bool full, const CellAcc<T>& a, int cnt, T oa,
-                                           const CellOut& o) {
+                                           const CellOut& o, const T* wv) {
   const T ps = p.w;
   T V = T(0), K = T(0), dg = T(0);
   T cx = p.x, cy = p.y, cz = p.z;
@@ -752,13 +748,8 @@ __device__ __forceinline__ bool write_cell(int64_t cell, const V4<T>& p, bool em
   if (o.grad) o.grad[cell] = o.snu[cell] - (double)(S)V;
   if (o.wallw) ((S*)o.wallw)[cell] = empty ? S(0) : (S)a.wg;
   if (o.wallv) {
-    S* wv = (S*)o.wallv + 6 * cell;
-    wv[0] = empty ? S(0) : (S)a.wax;
-    wv[1] = empty ? S(0) : (S)a.way;
-    wv[2] = empty ? S(0) : (S)a.waz;
-    wv[3] = empty ? S(0) : (S)a.wbx;
-    wv[4] = empty ? S(0) : (S)a.wby;
-    wv[5] = empty ? S(0) : (S)a.wbz;
+    S* ov = (S*)o.wallv + 6 * cell;
+    for (int k = 0; k < 6; k++) ov[k] = empty ? S(0) : (S)wv[k];
   }
   if (sizeof(T) != 4 || empty || !(ps > T(0)) || (K == T(0) && inside)) return false;
   const T r = sqrt(ps);
@@ -1356,12 +1347,6 @@ __global__ void __launch_bounds__(CellCfg<T>::warps * 32, sizeof(T) == 4 ? 6 : 2
         sa.hz += a.hz;
         sa.dg += a.dg;
         sa.wg += a.wg;
-        sa.wax += a.wax;
-        sa.way += a.way;
-        sa.waz += a.waz;
-        sa.wbx += a.wbx;
-        sa.wby += a.wby;
-        sa.wbz += a.wbz;
         sa.rm2 = fmax(sa.rm2, a.rm2);
         sa.nfac += a.nfac;
         sa.arc += a.arc;
@@ -1374,13 +1359,16 @@ __global__ void __launch_bounds__(CellCfg<T>::warps * 32, sizeof(T) == 4 ? 6 : 2
 
     // (E) the window's cells
     if (take && mine) {
+      const int nw = __popc((mt >> kMetaWallShift) & 63);
+      T wv[6] = {};
+      if (o.wallv && !(mt & kMetaEmpty))  // the wall facets are the cell's first planes
+        for (int f = 0; f < nw && f < m; f++) wall_vec(S.fa[excl + f], S.pl[excl + f], wv);
       const bool fix =
           write_cell(cell, pw, (mt & kMetaEmpty) != 0, S.sc[lane].neg == 0,
                      S.sc[lane].qout != 0 && !fullw, fullw, S.sc[lane].a, S.sc[lane].emitted,
-                     sqrt(oxw * oxw + oyw * oyw + ozw * ozw), o);
+                     sqrt(oxw * oxw + oyw * oyw + ozw * ozw), o, wv);
       if (fix && o.fix_list)
-        flag_fix(cell, m, __popc((mt >> kMetaWallShift) & 63), S.pj + excl, kmax, cand,
-                 o.fix_count, o.fix_list);
+        flag_fix(cell, m, nw, S.pj + excl, kmax, cand, o.fix_count, o.fix_list);
     }
     __syncwarp();
     base += ncell;
@@ -1422,12 +1410,14 @@ __global__ void __launch_bounds__(128)
     CellAcc<T> a = {};
     bool neg = false, qout = false;
     int emitted = 0;
+    T warea = T(0);  // lanes 0..5 of the first round: the wall facets' areas
     for (int f0 = 0; f0 < m; f0 += 32) {
       const int f = f0 + lane;
       const bool has = f < m;
       Facet<T> fo = {};
       if (has) {
         fo = facet_eval<T, uint16_t>(pl, m, f, p.w, r, ox, oy, oz, oa, !full);
+        if (f0 == 0) warea = fo.area;
         if (fo.overflow) set_error(err, POT_ERR_POLYGON_OVERFLOW, cell);
         acc_facet(a, pl[f], pd[f], pj[f], fo);
         neg |= pl[f].w < T(0);
@@ -1445,12 +1435,17 @@ __global__ void __launch_bounds__(128)
     seg_reduce(a, lane, 31);
     const bool anyneg = __any_sync(kFull, neg);
     const bool anyq = __any_sync(kFull, qout);
+    const int nw = __popc((mt >> kMetaWallShift) & 63);
+    T wv[6] = {};
+    for (int k = 0; k < 6; k++) {
+      const T ak = __shfl_sync(kFull, warea, k);
+      if (k < nw) wall_vec(ak, pl[k], wv);
+    }
     if (lane == 0) {
       const bool fix = write_cell(cell, p, (mt & kMetaEmpty) != 0, !anyneg, anyq && !full, full, a,
-                                  emitted, oa, o);
+                                  emitted, oa, o, wv);
       if (fix && o.fix_list && m <= kPlaneCap)
-        flag_fix(cell, m, __popc((mt >> kMetaWallShift) & 63), pj, kmax, cand, o.fix_count,
-                 o.fix_list);
+        flag_fix(cell, m, nw, pj, kmax, cand, o.fix_count, o.fix_list);
     }
     __syncwarp();
   }
@@ -1499,12 +1494,14 @@ __global__ void __launch_bounds__(kFixWarps * 32)
     CellAcc<double> a = {};
     bool neg = false, qout = false;
     int emitted = 0;
+    double warea = 0.0;  // lanes 0..5 of the first round: the wall facets' areas
     for (int f0 = 0; f0 < m; f0 += 32) {
       const int f = f0 + lane;
       const bool has = f < m;
       Facet<double> fo = {};
       if (has) {
         fo = facet_eval<double, uint8_t>(pl, m, f, p.w, r, ox, oy, oz, oa, !full);
+        if (f0 == 0) warea = fo.area;
         if (fo.overflow) set_error(err, POT_ERR_POLYGON_OVERFLOW, cell);
         acc_facet(a, pl[f], pd[f], pj[f], fo);
         neg |= pl[f].w < 0.0;
@@ -1522,9 +1519,15 @@ __global__ void __launch_bounds__(kFixWarps * 32)
     seg_reduce(a, lane, 31);
     const bool anyneg = __any_sync(kFull, neg);
     const bool anyq = __any_sync(kFull, qout);
+    const int nw = __popc((mt >> kMetaWallShift) & 63);
+    double wv[6] = {};
+    for (int k = 0; k < 6; k++) {
+      const double ak = __shfl_sync(kFull, warea, k);
+      if (k < nw) wall_vec(ak, pl[k], wv);
+    }
     if (lane == 0)
       write_cell<double, float>(cell, p, (mt & kMetaEmpty) != 0, !anyneg, anyq && !full, full, a,
-                                emitted, oa, o);
+                                emitted, oa, o, wv);
     __syncwarp();
   }
 }
