@@ -23,6 +23,9 @@ Contents, each citing the paper passage it follows:
   render_depth()  first point of each camera ray inside the fluid (the union
                   of the balls inside the box), with the free-surface culling
                   of Sec. 6's first-cell search; brute force over all balls.
+  render_volume() the fluid along each camera ray (Sec. 6's volume
+                  traversal): first entry, length inside, last exit, from the
+                  union of the balls' intervals; brute force.
   mlp_*()         FP64 reference of the learned warm-start MLP (not in the
                   paper): forward, backward, Adam, on BF16-rounded operands.
 
@@ -437,3 +440,55 @@ def render_depth(pos, psi, origin, forward, up, fov_y, width, height, karea=None
     x = o[None, :] + best[h, None] * d[h]
     normal[h] = (x - p[arg[h]]) / np.sqrt(r2[arg[h]])[:, None]
     return depth.reshape(height, width), normal.reshape(height, width, 3)
+
+
+def render_volume(pos, psi, origin, forward, up, fov_y, width, height,
+                  lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0)):
+    """Traversal of the fluid volume along camera rays (Sec. 6, volume
+    traversal), from its plain definition: the fluid is the union of the
+    generalized Laguerre cells of Eq. 1, i.e. the union of the balls inside
+    the box, so the part of a ray in the fluid is the union of the ray's
+    intervals inside the balls, clipped to the box.  Brute force over all
+    balls: every ball's interval, then their union (sorted, merged).
+    Returns (first entry t, total length inside the fluid, last exit t),
+    each (height, width); -1 / 0 / -1 where the ray misses the fluid."""
+    pos = np.asarray(pos, np.float64)
+    psi = np.asarray(psi, np.float64)
+    o = np.asarray(origin, np.float64)
+    d = camera_rays(origin, forward, up, fov_y, width, height).reshape(-1, 3)
+    lo = np.asarray(lo, np.float64)
+    hi = np.asarray(hi, np.float64)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        ta = (lo[None, :] - o[None, :]) / d
+        tb = (hi[None, :] - o[None, :]) / d
+    t0 = np.max(np.minimum(ta, tb), axis=1).clip(min=0.0)
+    t1 = np.min(np.maximum(ta, tb), axis=1)
+    keep = psi > 0
+    p, r2 = pos[keep], psi[keep]
+    m = d.shape[0]
+    first = np.full(m, -1.0)
+    thick = np.zeros(m)
+    last = np.full(m, -1.0)
+    # each ball's interval along every ray
+    e = p[None, :, :] - o[None, None, :]
+    bb = np.einsum("rk,rbk->rb", d, np.broadcast_to(e, (m,) + e.shape[1:]))
+    c = np.sum(e * e, axis=2) - r2[None, :]
+    disc = bb * bb - c
+    for k in range(m):
+        ok = disc[k] > 0
+        sq = np.sqrt(disc[k, ok])
+        a = np.maximum(bb[k, ok] - sq, t0[k])
+        b = np.minimum(bb[k, ok] + sq, t1[k])
+        iv = sorted((x, y) for x, y in zip(a, b) if x < y)
+        if not iv:
+            continue
+        total, cur0, cur1 = 0.0, iv[0][0], iv[0][1]
+        for x, y in iv[1:]:
+            if x > cur1:
+                total += cur1 - cur0
+                cur0, cur1 = x, y
+            else:
+                cur1 = max(cur1, y)
+        total += cur1 - cur0
+        first[k], thick[k], last[k] = iv[0][0], total, cur1
+    return first.reshape(height, width), thick.reshape(height, width), last.reshape(height, width)

@@ -46,3 +46,40 @@ def test_occlusion_box_and_culling():
     a, _ = O.render_depth(p, psi, o, f, up, math.radians(20), 9, 9)
     b, _ = O.render_depth(p, psi, o, f, up, math.radians(20), 9, 9, karea=[1.0, 0.0])
     np.testing.assert_array_equal(a, b)
+
+
+def test_volume_closed_forms():
+    """The oracle's volume traversal: a lone ball along the axis is crossed
+    over its diameter, and off the axis over the chord 2 sqrt(r^2 - b^2)
+    (b the ray's distance from the centre); two disjoint balls add their
+    chords and the last exit is the far one's; two overlapping balls on the
+    axis give the length of their union, r1 + r2 + (their centres' distance);
+    a ball cut by the box face is crossed from the face; a ray missing
+    everything has no entry."""
+    o, f, up = (0.5, 0.5, -1.0), (0.0, 0.0, 1.0), (0.0, 1.0, 0.0)
+    r = 0.2
+    first, thick, last = O.render_volume(np.array([[0.5, 0.5, 0.5]]), [r * r], o, f, up,
+                                         math.radians(30), 41, 31)
+    assert abs(first[15, 20] - 1.3) < 1e-12 and abs(thick[15, 20] - 0.4) < 1e-12
+    assert abs(last[15, 20] - 1.7) < 1e-12
+    d = O.camera_rays(o, f, up, math.radians(30), 41, 31)
+    e = np.array([0.5, 0.5, 0.5]) - np.asarray(o)
+    bb = d @ e
+    b2 = np.sum(e * e) - bb * bb
+    hit = b2 < r * r - 1e-12
+    np.testing.assert_allclose(thick[hit], 2 * np.sqrt(r * r - b2[hit]), rtol=0, atol=1e-12)
+    assert np.all(thick[~hit & (b2 > r * r + 1e-12)] == 0.0)
+    assert np.all(first[thick == 0.0] == -1.0)
+    # two disjoint balls on the axis
+    p = np.array([[0.5, 0.5, 0.3], [0.5, 0.5, 0.75]])
+    first, thick, last = O.render_volume(p, [0.1 ** 2, 0.05 ** 2], o, f, up, math.radians(10), 5, 5)
+    assert abs(thick[2, 2] - 0.3) < 1e-12 and abs(first[2, 2] - 1.2) < 1e-12
+    assert abs(last[2, 2] - 1.8) < 1e-12
+    # overlapping balls on the axis: union = r1 + r2 + distance
+    p = np.array([[0.5, 0.5, 0.4], [0.5, 0.5, 0.55]])
+    _, thick, last = O.render_volume(p, [0.1 ** 2, 0.08 ** 2], o, f, up, math.radians(10), 5, 5)
+    assert abs(thick[2, 2] - (0.1 + 0.08 + 0.15)) < 1e-12 and abs(last[2, 2] - 1.63) < 1e-12
+    # a ball sticking out of the box face z = 0
+    first, thick, _ = O.render_volume(np.array([[0.5, 0.5, 0.05]]), [0.1 ** 2], o, f, up,
+                                      math.radians(10), 5, 5)
+    assert abs(first[2, 2] - 1.0) < 1e-12 and abs(thick[2, 2] - 0.15) < 1e-12
