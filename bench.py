@@ -814,7 +814,27 @@ def run_render(args):
         ms = times[len(times) // 2]
         out[name] = {"ms_per_frame": ms, "rays_per_s": 1920 * 1080 / (ms / 1e3),
                      "hit_fraction": float((depth >= 0).float().mean())}
-    print(json.dumps({"metric": "camera rays per second, first hit on the fluid (pot_render_depth)",
+    # the volume traversal (cell evaluation included)
+    for _ in range(args.warmup):
+        pot.render_volume(ctx, pos, psi, **cam)
+    times = []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        first, thick, _, visits = pot.render_volume(ctx, pos, psi, **cam)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    times.sort()
+    ms = times[len(times) // 2]
+    hit = first >= 0
+    out["volume"] = {"ms_per_frame": ms, "rays_per_s": 1920 * 1080 / (ms / 1e3),
+                     "hit_fraction": float(hit.float().mean()),
+                     "cells_per_ray_mean": float(visits[hit].float().mean()),
+                     "cells_per_ray_max": int(visits.max()),
+                     "note": "includes the cell evaluation at these weights"}
+    print(json.dumps({"metric": "camera rays per second, first hit on the fluid (pot_render_depth) "
+                                "and volume traversal (pot_render_volume)",
                       "workload": f"two-ball splash, {n} sites, step {args.advance}, 1920 x 1080, "
                                   f"grid build included",
                       "free_surface_cells": int((karea > 0).sum()), **out}))

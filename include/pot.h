@@ -438,6 +438,28 @@ int pot_render_depth(pot_ctx* ctx, void* stream, int64_t n, const float* pos, co
                      const float* karea, const pot_domain* dom, const pot_camera* cam,
                      float* depth, float* normal);
 
+/* ---- traversal of the fluid volume (Sec. 6, volume traversal) --------- */
+
+/* Walk each camera ray through the fluid cell by cell: the generalized
+ * Laguerre cells of Eq. 1 at (pos, psi) are evaluated first (as
+ * lgc_compute_cells does), then one thread per pixel goes from cell to cell
+ * across the restricted bisector facets, leaves the fluid through a free
+ * surface (a spherical patch) or the box, and finds the next entry through
+ * the air as the next ball along the ray (the fluid is the union of the
+ * balls inside the box).  Per pixel (height x width, row-major, device
+ * buffers written on `stream`): first: the ray parameter t of the first
+ * point in the fluid (-1: none); thickness: the length of the ray inside
+ * the fluid; last: t of the last exit (-1: none); visits (optional, int32):
+ * the cells visited.  pos (n,3), psi (n) device arrays in caller order.
+ * Camera as in pot_render_depth; no graphics API.  Uses ctx's FP32
+ * workspace (its cell data are overwritten).
+ * Errors: POT_ERR_INVALID_ARG (NULL pointers, n out of range, an FP64-only
+ * context, a bad camera or box), the geometry errors of lgc_compute_cells,
+ * POT_ERR_CUDA. */
+int pot_render_volume(pot_ctx* ctx, void* stream, int64_t n, const float* pos, const float* psi,
+                      const pot_domain* dom, const pot_camera* cam, float* first,
+                      float* thickness, float* last, int32_t* visits);
+
 #ifdef __cplusplus
 }
 #endif

@@ -32,42 +32,51 @@ __device__ __forceinline__ int rcell(float x, float lo, float inv, int dim) {
   return i >= dim ? dim - 1 : i;
 }
 
-__global__ void __launch_bounds__(256)
-    k_render(Ray cam, Box<float> box, const V4<float>* __restrict__ sxp,
-             const int32_t* __restrict__ perm, const float* __restrict__ karea,
-             const int32_t* __restrict__ cell_start, GridParams<float> g, int layers,
-             float* depth, float* normal) {
-  const int px = blockIdx.x * blockDim.x + threadIdx.x;
-  const int py = blockIdx.y * blockDim.y + threadIdx.y;
-  if (px >= cam.w || py >= cam.h) return;
-  const float sx = ((px + 0.5f) / cam.w * 2.f - 1.f) * cam.th;
-  const float sy = (1.f - (py + 0.5f) / cam.h * 2.f) * cam.tv;
-  float d[3];
-  for (int k = 0; k < 3; k++) d[k] = cam.f[k] + sx * cam.r[k] + sy * cam.u[k];
-  const float il = rsqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-  for (int k = 0; k < 3; k++) d[k] *= il;
-  // the box along the ray: [t0, t1]
-  float t0 = 0.f, t1 = INFINITY;
-  for (int k = 0; k < 3; k++) {
-    const float a = (box.lo[k] - cam.o[k]) / d[k], b = (box.hi[k] - cam.o[k]) / d[k];
-    t0 = fmaxf(t0, fminf(a, b));
-    t1 = fminf(t1, fmaxf(a, b));
-  }
+// The interval [a, b] of the ray o + t d (|d| = 1) inside ball p; false when
+// the ray misses it.  r^2 minus the squared distance from the centre to the
+// ray, without cancellation between |e|^2 and b^2.
+__device__ __forceinline__ bool ball_interval(const V4<float>& p, const float* o, const float* d,
+                                              float& a, float& b) {
+  const float ex = p.x - o[0], ey = p.y - o[1], ez = p.z - o[2];
+  const float bb = ex * d[0] + ey * d[1] + ez * d[2];
+  const float hx = ex - bb * d[0], hy = ey - bb * d[1], hz = ez - bb * d[2];
+  const float disc = p.w - (hx * hx + hy * hy + hz * hz);
+  if (!(disc >= 0.f)) return false;
+  const float sq = sqrtf(disc);
+  a = bb - sq;
+  b = bb + sq;
+  return true;
+}
+
+// The first point of the ray at or after t_from (and before t_end) inside a
+// ball: the smallest max(a, t_from) over the balls whose interval [a, b]
+// reaches past it.  One thread walks the sites' grid along the ray (3D DDA
+// from the point at t_from) and tests the balls of the sites within
+// `layers` cells of each cell it enters (layers = ceil(r_max / cell size)):
+// a ball entered at t has its centre within that many cells of the cell
+// holding the ray point at t, so once a cell is entered beyond the best
+// entry no later ball can be nearer and the walk stops.  Balls for which
+// skip(s) holds are left out.  Returns the entry t (INFINITY: none) and the
+// site in *hit (-1: none).
+template <typename Skip>
+__device__ float next_entry(const float* o, const float* d, float t_from, float t_end,
+                            const V4<float>* __restrict__ sxp, const int32_t* __restrict__ cell_start,
+                            const GridParams<float>& g, int layers, Skip skip, int* hit) {
   float best = INFINITY;
   int besti = -1;
-  if (t0 < t1) {
+  if (t_from < t_end) {
     int c[3], step[3];
     float tmax[3], tdel[3];
     for (int k = 0; k < 3; k++) {
-      const float x = cam.o[k] + t0 * d[k];
+      const float x = o[k] + t_from * d[k];
       c[k] = rcell(x, g.lo[k], g.inv_cs, g.dim[k]);
       step[k] = d[k] > 0.f ? 1 : -1;
       const float edge = g.lo[k] + (c[k] + (d[k] > 0.f ? 1 : 0)) * g.cs;
-      tmax[k] = d[k] != 0.f ? (edge - cam.o[k]) / d[k] : INFINITY;
+      tmax[k] = d[k] != 0.f ? (edge - o[k]) / d[k] : INFINITY;
       tdel[k] = d[k] != 0.f ? g.cs / fabsf(d[k]) : INFINITY;
     }
-    float tcell = t0;
-    while (tcell <= t1 && tcell <= best) {
+    float tcell = t_from;
+    while (tcell <= t_end && tcell <= best) {
       const int z0 = max(c[2] - layers, 0), z1 = min(c[2] + layers, g.dim[2] - 1);
       const int y0 = max(c[1] - layers, 0), y1 = min(c[1] + layers, g.dim[1] - 1);
       const int x0 = max(c[0] - layers, 0), x1 = min(c[0] + layers, g.dim[0] - 1);
@@ -77,18 +86,11 @@ __global__ void __launch_bounds__(256)
           const int a = cell_start[key0 + x0], b = cell_start[key0 + x1 + 1];
           for (int s = a; s < b; s++) {
             const V4<float> p = sxp[s];
-            if (!(p.w > 0.f)) continue;
-            if (karea && !(karea[perm[s]] > 0.f)) continue;
-            const float ex = p.x - cam.o[0], ey = p.y - cam.o[1], ez = p.z - cam.o[2];
-            const float bb = ex * d[0] + ey * d[1] + ez * d[2];
-            // r^2 minus the squared distance from the centre to the ray
-            // (no cancellation between |e|^2 and b^2)
-            const float hx = ex - bb * d[0], hy = ey - bb * d[1], hz = ez - bb * d[2];
-            const float disc = p.w - (hx * hx + hy * hy + hz * hz);
-            if (disc < 0.f) continue;
-            const float sq = sqrtf(disc);
-            const float t = fmaxf(bb - sq, t0);
-            if (t < fminf(bb + sq, t1) && t < best) {
+            if (!(p.w > 0.f) || skip(s)) continue;
+            float ta, tb;
+            if (!ball_interval(p, o, d, ta, tb)) continue;
+            const float t = fmaxf(ta, t_from);
+            if (t < fminf(tb, t_end) && t < best) {
               best = t;
               besti = s;
             }
@@ -102,6 +104,76 @@ __global__ void __launch_bounds__(256)
       tmax[k] += tdel[k];
     }
   }
+  *hit = besti;
+  return best;
+}
+
+// The site of least power distance |x - p|^2 - psi at x (the generalized
+// Laguerre cell holding x, Eq. 1), over the sites within `layers` grid
+// cells: a site whose ball holds x is that near.  -1 when no ball holds x.
+__device__ int locate(const float* x, const V4<float>* __restrict__ sxp,
+                      const int32_t* __restrict__ cell_start, const GridParams<float>& g,
+                      int layers) {
+  int c[3];
+  for (int k = 0; k < 3; k++) c[k] = rcell(x[k], g.lo[k], g.inv_cs, g.dim[k]);
+  float best = 0.f;
+  int besti = -1;
+  for (int z = max(c[2] - layers, 0); z <= min(c[2] + layers, g.dim[2] - 1); z++)
+    for (int y = max(c[1] - layers, 0); y <= min(c[1] + layers, g.dim[1] - 1); y++) {
+      const int key0 = (z * g.dim[1] + y) * g.dim[0];
+      const int a = cell_start[key0 + max(c[0] - layers, 0)];
+      const int b = cell_start[key0 + min(c[0] + layers, g.dim[0] - 1) + 1];
+      for (int s = a; s < b; s++) {
+        const V4<float> p = sxp[s];
+        if (!(p.w > 0.f)) continue;
+        const float dx = x[0] - p.x, dy = x[1] - p.y, dz = x[2] - p.z;
+        const float pw = dx * dx + dy * dy + dz * dz - p.w;
+        if (besti < 0 ? pw <= 0.f : pw < best) {
+          best = pw;
+          besti = s;
+        }
+      }
+    }
+  return besti;
+}
+
+// camera ray of pixel (px, py): unit direction into d
+__device__ __forceinline__ void pixel_ray(const Ray& cam, int px, int py, float* d) {
+  const float sx = ((px + 0.5f) / cam.w * 2.f - 1.f) * cam.th;
+  const float sy = (1.f - (py + 0.5f) / cam.h * 2.f) * cam.tv;
+  for (int k = 0; k < 3; k++) d[k] = cam.f[k] + sx * cam.r[k] + sy * cam.u[k];
+  const float il = rsqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+  for (int k = 0; k < 3; k++) d[k] *= il;
+}
+
+// the box along the ray: [t0, t1] (t0 >= 0)
+__device__ __forceinline__ void box_span(const Box<float>& box, const float* o, const float* d,
+                                         float& t0, float& t1) {
+  t0 = 0.f;
+  t1 = INFINITY;
+  for (int k = 0; k < 3; k++) {
+    const float a = (box.lo[k] - o[k]) / d[k], b = (box.hi[k] - o[k]) / d[k];
+    t0 = fmaxf(t0, fminf(a, b));
+    t1 = fminf(t1, fmaxf(a, b));
+  }
+}
+
+__global__ void __launch_bounds__(256)
+    k_render(Ray cam, Box<float> box, const V4<float>* __restrict__ sxp,
+             const int32_t* __restrict__ perm, const float* __restrict__ karea,
+             const int32_t* __restrict__ cell_start, GridParams<float> g, int layers,
+             float* depth, float* normal) {
+  const int px = blockIdx.x * blockDim.x + threadIdx.x;
+  const int py = blockIdx.y * blockDim.y + threadIdx.y;
+  if (px >= cam.w || py >= cam.h) return;
+  float d[3];
+  pixel_ray(cam, px, py, d);
+  float t0, t1;
+  box_span(box, cam.o, d, t0, t1);
+  int besti = -1;
+  const float best = next_entry(
+      cam.o, d, t0, t1, sxp, cell_start, g, layers,
+      [&](int s) { return karea && !(karea[perm[s]] > 0.f); }, &besti);
   const int pix = py * cam.w + px;
   depth[pix] = besti >= 0 ? best : -1.f;
   if (normal) {
@@ -119,16 +191,104 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// Volume traversal (Sec. 6): one thread per ray walks the fluid cell by
+// cell.  Inside cell c the ray leaves at the nearest of: the far point of
+// c's sphere (into air), the box, or the radical plane of a restricted-facet
+// neighbour j of c (the Hessian row's columns: the planes that bound the
+// cell inside its ball), crossed towards j (then the walk goes on in j).
+// The cell is the intersection of its ball, the box and those half-spaces,
+// convex, so the nearest crossing is its exit.  In air, the next entry into
+// the fluid is the next ball entry along the ray (the grid walk above, from
+// just past the exit), and the cell entered is located by power distance;
+// this replaces the walk through the unrestricted diagram.  A crossing the
+// cell-by-cell walk misses (a facet below the emission threshold, rounding
+// at an edge) only leaves the fluid early, and the air search re-enters it
+// at once.  Outputs per pixel: first entry t (-1: none), length inside the
+// fluid, last exit t (-1), cells visited.  kMaxVisits bounds the walk.
+constexpr int kMaxVisits = 1 << 15;
+
+__global__ void __launch_bounds__(128)
+    k_render_volume(Ray cam, Box<float> box, const V4<float>* __restrict__ sxp,
+                    const float* __restrict__ karea, const int32_t* __restrict__ cell_start,
+                    GridParams<float> g, int layers, const int32_t* __restrict__ row_ptr,
+                    const int32_t* __restrict__ cols, float* first, float* thick, float* last,
+                    int32_t* visits) {
+  const int px = blockIdx.x * blockDim.x + threadIdx.x;
+  const int py = blockIdx.y * blockDim.y + threadIdx.y;
+  if (px >= cam.w || py >= cam.h) return;
+  float d[3];
+  pixel_ray(cam, px, py, d);
+  float t0, t1;
+  box_span(box, cam.o, d, t0, t1);
+  // a step past an exit point into air, relative to the grid cell
+  const float step_off = 1e-6f * g.cs;
+  float tf = -1.f, tl = -1.f, len = 0.f;
+  int nv = 0;
+  float t = t0;
+  while (t < t1 && nv < kMaxVisits) {
+    // next entry into the fluid (balls of cells without free surface
+    // cannot be entered from air)
+    int s = -1;
+    const float te = next_entry(
+        cam.o, d, t, t1, sxp, cell_start, g, layers,
+        [&](int q) { return !(karea[q] > 0.f); }, &s);
+    if (s < 0) break;
+    t = te;
+    const float x[3] = {cam.o[0] + t * d[0], cam.o[1] + t * d[1], cam.o[2] + t * d[2]};
+    int c = locate(x, sxp, cell_start, g, layers);
+    if (c < 0) c = s;
+    if (tf < 0.f) tf = t;
+    // the walk through the fluid
+    while (nv < kMaxVisits) {
+      nv++;
+      const V4<float> p = sxp[c];
+      float ta, tb;
+      float tn = t1;
+      if (ball_interval(p, cam.o, d, ta, tb))
+        tn = fminf(tn, tb);
+      else
+        tn = t;  // grazing: leave at once
+      int next = -1;
+      const float ox = cam.o[0] - p.x, oy = cam.o[1] - p.y, oz = cam.o[2] - p.z;
+      for (int k = row_ptr[c]; k < row_ptr[c + 1]; k++) {
+        const int j = cols[k];
+        const V4<float> q = sxp[j];
+        // radical plane: (y - p) . m = (|m|^2 + psi_c - psi_j) / 2, m = p_j - p_c
+        const float mx = q.x - p.x, my = q.y - p.y, mz = q.z - p.z;
+        const float md = mx * d[0] + my * d[1] + mz * d[2];
+        if (!(md > 0.f)) continue;  // not towards j
+        const float hm = 0.5f * (mx * mx + my * my + mz * mz + p.w - q.w);
+        const float tj = (hm - (ox * mx + oy * my + oz * mz)) / md;
+        if (tj > t && tj < tn) {
+          tn = tj;
+          next = j;
+        }
+      }
+      if (tn > t) len += tn - t;
+      t = fmaxf(t, tn);
+      if (next < 0) break;
+      c = next;
+    }
+    tl = t;
+    if (t >= t1) break;
+    t += step_off;
+  }
+  const int pix = py * cam.w + px;
+  first[pix] = tf;
+  thick[pix] = len;
+  last[pix] = tl;
+  if (visits) visits[pix] = nv;
+}
+
 }  // namespace
 }  // namespace pot
 
 using namespace pot;
 
-extern "C" int pot_render_depth(pot_ctx* ctx, void* stream, int64_t n, const float* pos,
-                                const float* psi, const float* karea, const pot_domain* dom,
-                                const pot_camera* cam, float* depth, float* normal) {
-  if (!ctx || !pos || !psi || !dom || !cam || !depth || n <= 0 || n > ctx->n_max || !(ctx->mask & 1))
-    return POT_ERR_INVALID_ARG;
+namespace {
+
+// the camera's frame (right = forward x up, up' = right x forward)
+int make_ray(const pot_camera* cam, Ray& ray) {
   if (cam->width <= 0 || cam->height <= 0 || !(cam->fov_y > 0.0 && cam->fov_y < 3.14))
     return POT_ERR_INVALID_ARG;
   double f[3], up[3], r[3], u[3];
@@ -148,7 +308,6 @@ extern "C" int pot_render_depth(pot_ctx* ctx, void* stream, int64_t n, const flo
   u[0] = r[1] * f[2] - r[2] * f[1];
   u[1] = r[2] * f[0] - r[0] * f[2];
   u[2] = r[0] * f[1] - r[1] * f[0];
-  Ray ray;
   for (int k = 0; k < 3; k++) {
     ray.o[k] = (float)cam->origin[k];
     ray.f[k] = (float)f[k];
@@ -159,6 +318,18 @@ extern "C" int pot_render_depth(pot_ctx* ctx, void* stream, int64_t n, const flo
   ray.th = ray.tv * (float)cam->width / (float)cam->height;
   ray.w = cam->width;
   ray.h = cam->height;
+  return POT_OK;
+}
+
+}  // namespace
+
+extern "C" int pot_render_depth(pot_ctx* ctx, void* stream, int64_t n, const float* pos,
+                                const float* psi, const float* karea, const pot_domain* dom,
+                                const pot_camera* cam, float* depth, float* normal) {
+  if (!ctx || !pos || !psi || !dom || !cam || !depth || n <= 0 || n > ctx->n_max || !(ctx->mask & 1))
+    return POT_ERR_INVALID_ARG;
+  Ray ray;
+  POT_CHECK(make_ray(cam, ray));
   if (cudaSetDevice(ctx->device) != cudaSuccess) return POT_ERR_CUDA;
   cudaStream_t st = (cudaStream_t)stream;
   POT_CHECK(grid_build<float>(ctx, st, n, pos, psi, nullptr, dom));
@@ -175,6 +346,46 @@ extern "C" int pot_render_depth(pot_ctx* ctx, void* stream, int64_t n, const flo
   note_launch();
   k_render<<<grd, blk, 0, st>>>(ray, box, w.sxp, ctx->perm, karea, ctx->cell_start, w.grid, layers,
                                 depth, normal);
+  POT_CUDA(cudaGetLastError());
+  POT_CUDA(cudaStreamSynchronize(st));
+  return POT_OK;
+}
+
+extern "C" int pot_render_volume(pot_ctx* ctx, void* stream, int64_t n, const float* pos,
+                                 const float* psi, const pot_domain* dom, const pot_camera* cam,
+                                 float* first, float* thickness, float* last, int32_t* visits) {
+  if (!ctx || !pos || !psi || !dom || !cam || !first || !thickness || !last || n <= 0 ||
+      n > ctx->n_max || !(ctx->mask & 1))
+    return POT_ERR_INVALID_ARG;
+  for (int k = 0; k < 3; k++)
+    if (!(dom->hi[k] > dom->lo[k])) return POT_ERR_INVALID_ARG;
+  Ray ray;
+  POT_CHECK(make_ray(cam, ray));
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return POT_ERR_CUDA;
+  cudaStream_t st = (cudaStream_t)stream;
+  // the cells at these weights: their restricted facets (the Hessian rows'
+  // columns, sorted space) and free-surface areas
+  POT_CHECK(grid_build<float>(ctx, st, n, pos, psi, nullptr, dom));
+  // ceil(r_max / cell) layers of neighbour cells (grid_build read psi_max)
+  const double rmax = sqrt(fmax((double)*(float*)ctx->h_pinned, 0.0));
+  Work<float>& w = ctx->wf;
+  const int ce = cells_eval<float>(ctx, st, n, dom, false);
+  int64_t site = -1;
+  const int code = read_status(ctx, st, &site);
+  if (code != POT_OK) return code;
+  POT_CHECK(ce);
+  int64_t nnz_off = 0;
+  POT_CHECK(csr_compact<float>(ctx, st, n, &nnz_off));
+  const int layers = (int)fmax(1.0, ceil(rmax / (double)w.grid.cs));
+  Box<float> box;
+  for (int k = 0; k < 3; k++) {
+    box.lo[k] = (float)dom->lo[k];
+    box.hi[k] = (float)dom->hi[k];
+  }
+  dim3 blk(16, 8), grd((cam->width + 15) / 16, (cam->height + 7) / 8);
+  note_launch();
+  k_render_volume<<<grd, blk, 0, st>>>(ray, box, w.sxp, w.karea, ctx->cell_start, w.grid, layers,
+                                       ctx->row_ptr, ctx->csr_cols, first, thickness, last, visits);
   POT_CUDA(cudaGetLastError());
   POT_CUDA(cudaStreamSynchronize(st));
   return POT_OK;

@@ -139,6 +139,9 @@ def lib():
         L.pot_render_depth.argtypes = [P, P, I64, P, P, P, ctypes.POINTER(Domain),
                                        ctypes.POINTER(Camera), P, P]
         L.pot_render_depth.restype = ctypes.c_int
+        L.pot_render_volume.argtypes = [P, P, I64, P, P, ctypes.POINTER(Domain),
+                                        ctypes.POINTER(Camera), P, P, P, P]
+        L.pot_render_volume.restype = ctypes.c_int
         L.pot_measure_fp32_peak.argtypes = [P, P, ctypes.POINTER(ctypes.c_double),
                                             ctypes.POINTER(ctypes.c_double)]
         L.pot_measure_fp32_peak.restype = ctypes.c_int
@@ -389,6 +392,31 @@ def render_depth(ctx: Context, pos, psi, origin, forward, up, fov_y, width, heig
     if code != POT_OK:
         raise PotError(code, "pot_render_depth")
     return depth, normal
+
+
+def render_volume(ctx: Context, pos, psi, origin, forward, up, fov_y, width, height,
+                  domain=UNIT_BOX, stream=None, visits=True):
+    """Walk camera rays through the fluid cell by cell (pot_render_volume):
+    returns (first entry t, thickness, last exit t, cells visited or None),
+    each (height, width) on the device."""
+    dev = ctx.device
+    n = int(pos.shape[0])
+    pos = _dev(pos, torch.float32, (n, 3), "pos", dev)
+    psi = _dev(psi, torch.float32, (n,), "psi", dev)
+    first = torch.empty((height, width), dtype=torch.float32, device=dev)
+    thick = torch.empty((height, width), dtype=torch.float32, device=dev)
+    last = torch.empty((height, width), dtype=torch.float32, device=dev)
+    vis = torch.empty((height, width), dtype=torch.int32, device=dev) if visits else None
+    cam = Camera()
+    for k in range(3):
+        cam.origin[k], cam.forward[k], cam.up[k] = float(origin[k]), float(forward[k]), float(up[k])
+    cam.fov_y, cam.width, cam.height = float(fov_y), int(width), int(height)
+    code = lib().pot_render_volume(ctx.handle, _stream(stream), n, _ptr(pos), _ptr(psi),
+                                   ctypes.byref(_domain(domain)), ctypes.byref(cam), _ptr(first),
+                                   _ptr(thick), _ptr(last), _ptr(vis))
+    if code != POT_OK:
+        raise PotError(code, "pot_render_volume")
+    return first, thick, last, vis
 
 
 def set_viscosity_factors(ctx: Context, factors):
