@@ -220,12 +220,11 @@ __global__ void __launch_bounds__(128)
   pixel_ray(cam, px, py, d);
   float t0, t1;
   box_span(box, cam.o, d, t0, t1);
-  // a step past an exit point into air, relative to the grid cell
-  const float step_off = 1e-6f * g.cs;
   float tf = -1.f, tl = -1.f, len = 0.f;
   int nv = 0;
   float t = t0;
   while (t < t1 && nv < kMaxVisits) {
+    const float t_round = t;
     // next entry into the fluid (balls of cells without free surface
     // cannot be entered from air)
     int s = -1;
@@ -271,7 +270,11 @@ __global__ void __launch_bounds__(128)
     }
     tl = t;
     if (t >= t1) break;
-    t += step_off;
+    // a step past the exit point into air: a few ulp of t at least (a step
+    // below t's resolution would leave t where it is), and a round that
+    // made no progress steps on as well
+    const float step = fmaxf(1e-6f * g.cs, 4.8e-7f * fabsf(t));
+    t = fmaxf(t, t_round) + step;
   }
   const int pix = py * cam.w + px;
   first[pix] = tf;
