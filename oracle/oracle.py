@@ -443,7 +443,7 @@ def render_depth(pos, psi, origin, forward, up, fov_y, width, height, karea=None
 
 
 def render_volume(pos, psi, origin, forward, up, fov_y, width, height,
-                  lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0)):
+                  lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), pixels=None):
     """Traversal of the fluid volume along camera rays (Sec. 6, volume
     traversal), from its plain definition: the fluid is the union of the
     generalized Laguerre cells of Eq. 1, i.e. the union of the balls inside
@@ -451,11 +451,15 @@ def render_volume(pos, psi, origin, forward, up, fov_y, width, height,
     intervals inside the balls, clipped to the box.  Brute force over all
     balls: every ball's interval, then their union (sorted, merged).
     Returns (first entry t, total length inside the fluid, last exit t),
-    each (height, width); -1 / 0 / -1 where the ray misses the fluid."""
+    each (height, width); -1 / 0 / -1 where the ray misses the fluid.  With
+    `pixels` (flat pixel indices), only those rays, each result of their
+    length."""
     pos = np.asarray(pos, np.float64)
     psi = np.asarray(psi, np.float64)
     o = np.asarray(origin, np.float64)
     d = camera_rays(origin, forward, up, fov_y, width, height).reshape(-1, 3)
+    if pixels is not None:
+        d = d[np.asarray(pixels)]
     lo = np.asarray(lo, np.float64)
     hi = np.asarray(hi, np.float64)
     with np.errstate(divide="ignore", invalid="ignore"):
@@ -469,16 +473,16 @@ def render_volume(pos, psi, origin, forward, up, fov_y, width, height,
     first = np.full(m, -1.0)
     thick = np.zeros(m)
     last = np.full(m, -1.0)
-    # each ball's interval along every ray
-    e = p[None, :, :] - o[None, None, :]
-    bb = np.einsum("rk,rbk->rb", d, np.broadcast_to(e, (m,) + e.shape[1:]))
-    c = np.sum(e * e, axis=2) - r2[None, :]
-    disc = bb * bb - c
+    e = p - o[None, :]
+    ee = np.sum(e * e, axis=1) - r2
     for k in range(m):
-        ok = disc[k] > 0
-        sq = np.sqrt(disc[k, ok])
-        a = np.maximum(bb[k, ok] - sq, t0[k])
-        b = np.minimum(bb[k, ok] + sq, t1[k])
+        # every ball's interval along ray k
+        bb = e @ d[k]
+        disc = bb * bb - ee
+        ok = disc > 0
+        sq = np.sqrt(disc[ok])
+        a = np.maximum(bb[ok] - sq, t0[k])
+        b = np.minimum(bb[ok] + sq, t1[k])
         iv = sorted((x, y) for x, y in zip(a, b) if x < y)
         if not iv:
             continue
@@ -491,4 +495,6 @@ def render_volume(pos, psi, origin, forward, up, fov_y, width, height,
                 cur1 = max(cur1, y)
         total += cur1 - cur0
         first[k], thick[k], last[k] = iv[0][0], total, cur1
+    if pixels is not None:
+        return first, thick, last
     return first.reshape(height, width), thick.reshape(height, width), last.reshape(height, width)

@@ -93,3 +93,40 @@ def test_volume_traversal_matches_oracle():
         assert np.mean(et > 1e-3) < 5e-3
         assert int(to_np(visits).max()) < 1 << 15  # no walk ran out of visits
     ctx.close()
+
+
+def test_volume_traversal_full_size_sampled():
+    """The traversal on the 2.0M-site splash after 30 steps (the balls
+    pressed together), 320 x 180 rays from bench.py's render camera: no walk
+    runs out of visits, and on 200 sampled rays that reach the fluid the
+    length inside it, first entry and last exit agree with the oracle's
+    union of the balls' intervals over all 2M balls."""
+    sc = scenes.splash()
+    n = sc.n
+    dev = torch.device("cuda", 0)
+    ctx = pot.Context(n, 246, 0, fp64=False)
+    pos, vel, psi, nu = (torch.from_numpy(a).to(dev) for a in (sc.pos, sc.vel, sc.psi, sc.nu))
+    prm = pot.default_params(dt=sc.extra["dt"], eps=sc.extra["eps"])
+    pot.relax_to_centroids(ctx, pos, psi, nu, sc.extra["relax_rounds"], params=prm)
+    for _ in range(30):
+        pot.pot_fluid_step(ctx, pos, vel, psi, nu, params=prm)
+    cam = dict(origin=(0.5, -0.9, 0.8), forward=(0.0, 1.0, -0.55), up=(0.0, 0.0, 1.0),
+               fov_y=math.radians(40), width=320, height=180)
+    first, thick, last, visits = pot.render_volume(ctx, pos, psi, **cam)
+    gf, gt, gl = (to_np(a).astype(np.float64).ravel() for a in (first, thick, last))
+    vis = to_np(visits).ravel()
+    assert vis.max() < 1 << 15
+    hit = np.nonzero(gf >= 0)[0]
+    assert hit.size > 1000
+    pix = np.random.default_rng(7).choice(hit, 200, replace=False)
+    x, s = to_np(pos).astype(np.float64), to_np(psi).astype(np.float64)
+    rf, rt, rl = O.render_volume(x, s, pixels=pix, **cam)
+    assert np.all(rf >= 0)
+    et = np.abs(gt[pix] - rt) / float(rt.max())
+    ef = np.abs(gf[pix] - rf) / float(rl.max())
+    el = np.abs(gl[pix] - rl) / float(rl.max())
+    print("full-size traversal: thickness err / max p99 %.2e max %.2e; first p99 %.2e; last p99 %.2e;"
+          " cells per ray max %d" % (np.percentile(et, 99), et.max(), np.percentile(ef, 99),
+                                     np.percentile(el, 99), int(vis.max())))
+    assert np.percentile(et, 99) < 1e-4 and np.percentile(el, 99) < 1e-4 and np.percentile(ef, 99) < 1e-5
+    ctx.close()
