@@ -27,6 +27,8 @@
 //   signed solid angles, exact whether or not p_i lies in its cell.
 #include <math.h>
 
+#include <algorithm>
+
 #include "pot_internal.cuh"
 
 namespace pot {
@@ -1098,280 +1100,289 @@ template <typename T>
 __global__ void __launch_bounds__(CellCfg<T>::warps * 32, sizeof(T) == 4 ? 6 : 2)
     k_cells(int64_t n, const V4<T>* __restrict__ sxp, const int32_t* __restrict__ meta,
             int32_t* cand, int kmax, Box<T> box, T* stage_vals, const T* __restrict__ soff,
-            const T* __restrict__ srad, CellOut o, int32_t* err) {
+            const T* __restrict__ srad, CellOut o, int32_t* chunk_next, int32_t* err) {
   constexpr int W = CellCfg<T>::warps;
   __shared__ Window<T> s_win[W];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   Window<T>& S = s_win[wid];
   (void)err;
-  const int64_t c0 = ((int64_t)blockIdx.x * W + wid) * kCellsPerWarp;
-  if (c0 >= n) return;
-  const int64_t c1 = c0 + kCellsPerWarp < n ? c0 + kCellsPerWarp : n;
-  int64_t base = c0;
-  while (base < c1) {
-    // window: lane w stands for cell base + w
-    const int64_t cell = base + lane;
-    const bool valid = cell < c1;
-    const bool todo = valid && o.need[cell];  // cells finished in an earlier pass take no slot
-    const int mt = todo ? meta[cell] : 0;
-    const int m = mt & kMetaPlanes;
-    const bool mine = todo && m <= kSmallPlanes;  // larger cells are the big-cell kernel's
-    const int slots = mine ? m : 0;
-    const int incl = warp_incl(slots, lane);
-    const int excl = incl - slots;
-    // a prefix of the cells (m <= kSmallPlanes <= kWin, so the first always fits)
-    const bool take = valid && incl <= kWin;
-    const int ncell = __popc(__ballot_sync(kFull, take));
-    const int total = __shfl_sync(kFull, incl, ncell - 1);
-    const int np = take ? slots * (slots - 1) / 2 : 0;
-    const int pincl = warp_incl(np, lane);
-    V4<T> pw = {};
-    T rw = T(0), irw = T(0), oxw = T(0), oyw = T(0), ozw = T(0);
-    bool fullw = false;  // the security ball contains the site's ball: exact without an extent
-    if (take && mine) {
-      pw = sxp[cell];
-      rw = pw.w > T(0) ? sqrt(pw.w) : T(0);
-      irw = rw > T(0) ? T(1) / rw : T(0);
-      oxw = soff[3 * cell + 0];
-      oyw = soff[3 * cell + 1];
-      ozw = soff[3 * cell + 2];
-      fullw = srad[cell] >= rw + sqrt(oxw * oxw + oyw * oyw + ozw * ozw);
-      S.sc[lane].a = CellAcc<T>{};
-      S.sc[lane].neg = 0;
-      S.sc[lane].qout = 0;
-      S.sc[lane].emitted = 0;
-    }
-    if (lane < ncell) {
-      S.cex[lane] = excl;
-      S.cpp[lane] = pincl - np;
-    }
-    if (lane == ncell - 1) {
-      S.cex[ncell] = total;
-      S.cpp[ncell] = pincl;
-    }
-    __syncwarp();
-    const int ptot = S.cpp[ncell];
-
-    // (A) the window's planes, one slot per lane
-    for (int t0 = 0; t0 < total; t0 += 32) {
-      const int t = t0 + lane;
-      const int ow = t < total ? last_le(S.cex, ncell, t) : 0;
-      const int omt = __shfl_sync(kFull, mt, ow);
-      const V4<T> op = {__shfl_sync(kFull, pw.x, ow), __shfl_sync(kFull, pw.y, ow),
-                        __shfl_sync(kFull, pw.z, ow), __shfl_sync(kFull, pw.w, ow)};
-      const T orr = __shfl_sync(kFull, rw, ow);
-      if (t < total) {
-        plane_of(t - S.cex[ow], base + ow, op, omt, orr, sxp, cand, kmax, box, S.pl[t], S.pd[t],
-                 S.pj[t]);
-        S.owner[t] = (uint8_t)ow;
-        S.mask[t] = 0u;
-        S.dead[t] = 0;
-        S.fa[t] = T(0);
-        S.fo[t] = T(0);
-        S.fx[t] = T(0);
-        S.fy[t] = T(0);
-        S.fr[t] = T(0);
-        S.farc[t] = 0;
+  // each warp takes the next chunk of kCellsPerWarp cells until none is
+  // left: a warp that finishes early takes more, so no window waits idle
+  // for a slow warp of its block
+  const int64_t nchunk = (n + kCellsPerWarp - 1) / kCellsPerWarp;
+  for (;;) {
+    int chunk = 0;
+    if (lane == 0) chunk = atomicAdd(chunk_next, 1);
+    chunk = __shfl_sync(kFull, chunk, 0);
+    if (chunk >= nchunk) break;
+    const int64_t c0 = (int64_t)chunk * kCellsPerWarp;
+    const int64_t c1 = c0 + kCellsPerWarp < n ? c0 + kCellsPerWarp : n;
+    int64_t base = c0;
+    while (base < c1) {
+      // window: lane w stands for cell base + w
+      const int64_t cell = base + lane;
+      const bool valid = cell < c1;
+      const bool todo = valid && o.need[cell];  // cells finished in an earlier pass take no slot
+      const int mt = todo ? meta[cell] : 0;
+      const int m = mt & kMetaPlanes;
+      const bool mine = todo && m <= kSmallPlanes;  // larger cells are the big-cell kernel's
+      const int slots = mine ? m : 0;
+      const int incl = warp_incl(slots, lane);
+      const int excl = incl - slots;
+      // a prefix of the cells (m <= kSmallPlanes <= kWin, so the first always fits)
+      const bool take = valid && incl <= kWin;
+      const int ncell = __popc(__ballot_sync(kFull, take));
+      const int total = __shfl_sync(kFull, incl, ncell - 1);
+      const int np = take ? slots * (slots - 1) / 2 : 0;
+      const int pincl = warp_incl(np, lane);
+      V4<T> pw = {};
+      T rw = T(0), irw = T(0), oxw = T(0), oyw = T(0), ozw = T(0);
+      bool fullw = false;  // the security ball contains the site's ball: exact without an extent
+      if (take && mine) {
+        pw = sxp[cell];
+        rw = pw.w > T(0) ? sqrt(pw.w) : T(0);
+        irw = rw > T(0) ? T(1) / rw : T(0);
+        oxw = soff[3 * cell + 0];
+        oyw = soff[3 * cell + 1];
+        ozw = soff[3 * cell + 2];
+        fullw = srad[cell] >= rw + sqrt(oxw * oxw + oyw * oyw + ozw * ozw);
+        S.sc[lane].a = CellAcc<T>{};
+        S.sc[lane].neg = 0;
+        S.sc[lane].qout = 0;
+        S.sc[lane].emitted = 0;
       }
-    }
-    __syncwarp();
-
-    // (B) pairs of planes of each cell: k-th pair of a cell of mc planes is
-    // (f, f + s mod mc), s = k / mc + 1, f = k mod mc (each unordered pair once)
-    for (int p0 = 0; p0 < ptot; p0 += 32) {
-      const int p = p0 + lane;
-      const int c = p < ptot ? last_le(S.cpp, ncell, p) : 0;
-      const T psc = __shfl_sync(kFull, pw.w, c);
-      if (p < ptot) {
-        const int k = p - S.cpp[c];
-        const int sb = S.cex[c];
-        const int mc = S.cex[c + 1] - sb;
-        const int s = k / mc + 1;
-        const int f = k - (s - 1) * mc;
-        int g = f + s;
-        if (g >= mc) g -= mc;
-        const V4<T> F = S.pl[sb + f], G = S.pl[sb + g];
-        const T cxx = F.y * G.z - F.z * G.y, cyy = F.z * G.x - F.x * G.z, czz = F.x * G.y - F.y * G.x;
-        const T len2 = cxx * cxx + cyy * cyy + czz * czz;  // 1 - (n_f . n_g)^2
-        const T cs = F.x * G.x + F.y * G.y + F.z * G.z;
-        const T cf = G.w - F.w * cs;  // g's line offset in f's plane: > 0 keeps f's disk centre
-        const T cg = F.w - G.w * cs;
-        bool cross = false;
-        if (len2 > T(0)) {
-          // the line of f and g crosses the open ball iff
-          // h_f^2 - 2 cs h_f h_g + h_g^2 < psi (1 - cs^2)
-          const T lhs = cs >= T(0)
-                            ? (F.w - G.w) * (F.w - G.w) + T(2) * (len2 / (T(1) + cs)) * F.w * G.w
-                            : (F.w + G.w) * (F.w + G.w) - T(2) * (len2 / (T(1) - cs)) * F.w * G.w;
-          cross = lhs < psc * len2;
-        }
-        if (cross) {
-          atomicOr(&S.mask[sb + f], 1u << g);
-          atomicOr(&S.mask[sb + g], 1u << f);
-        } else {
-          const bool parallel = !(len2 > T(0));
-          if (parallel ? cf < T(0) : !(cf > T(0))) S.dead[sb + f] = 1;
-          if (parallel ? cg < T(0) : !(cg > T(0))) S.dead[sb + g] = 1;
-        }
+      if (lane < ncell) {
+        S.cex[lane] = excl;
+        S.cpp[lane] = pincl - np;
       }
-    }
-    __syncwarp();
-
-    // (C) tasks: a live facet has one per crossing line, or one for its
-    // whole disk; first the task prefix over the slots
-    int carry = 0;
-    for (int t0 = 0; t0 < total; t0 += 32) {
-      const int t = t0 + lane;
-      int nt = 0;
-      if (t < total && !S.dead[t]) {
-        const int pc = __popc(S.mask[t]);
-        nt = pc > 0 ? pc : 1;
+      if (lane == ncell - 1) {
+        S.cex[ncell] = total;
+        S.cpp[ncell] = pincl;
       }
-      const int inc = warp_incl(nt, lane);
-      if (t < total) S.tpre[t] = carry + inc - nt;
-      carry += __shfl_sync(kFull, inc, 31);
-    }
-    if (lane == 0) S.tpre[total] = carry;
-    __syncwarp();
-    const int ttot = carry;
-    // rounds of whole facets (a facet has at most kSmallPlanes - 1 tasks):
-    // each task stages its line for the other tasks of its facet
-    for (int R = 0; R < ttot;) {
-      const int Rend = S.tpre[last_le(S.tpre, total + 1, R + 32)];
-      const int q = R + lane;
-      const bool act = q < Rend;
-      const int slot = act ? last_le(S.tpre, total, q) : 0;
-      const int c = act ? S.owner[slot] : 0;
-      const T psc = __shfl_sync(kFull, pw.w, c);
-      const T oir = __shfl_sync(kFull, irw, c);
-      const T sox = __shfl_sync(kFull, oxw, c), soy = __shfl_sync(kFull, oyw, c),
-              soz = __shfl_sync(kFull, ozw, c);
-      const bool ofull = __shfl_sync(kFull, fullw, c);
-      const int head = act ? S.tpre[slot] - R : lane;
-      const int last = act ? S.tpre[slot + 1] - 1 - R : lane;
-      FacetFrame<T> fr = {};
-      unsigned M = 0u;
-      if (act) {
-        const int sb = S.cex[c];
-        const V4<T> P = S.pl[slot];
-        fr = facet_frame(P, psc, oir, sox, soy, soz);
-        M = S.mask[slot];
-        if (M) {
-          const int g = (int)__fns(M, 0, q - S.tpre[slot] + 1);
-          S.rec[lane] = line_rec(P, fr, S.pl[sb + g], g);
+      __syncwarp();
+      const int ptot = S.cpp[ncell];
+
+      // (A) the window's planes, one slot per lane
+      for (int t0 = 0; t0 < total; t0 += 32) {
+        const int t = t0 + lane;
+        const int ow = t < total ? last_le(S.cex, ncell, t) : 0;
+        const int omt = __shfl_sync(kFull, mt, ow);
+        const V4<T> op = {__shfl_sync(kFull, pw.x, ow), __shfl_sync(kFull, pw.y, ow),
+                          __shfl_sync(kFull, pw.z, ow), __shfl_sync(kFull, pw.w, ow)};
+        const T orr = __shfl_sync(kFull, rw, ow);
+        if (t < total) {
+          plane_of(t - S.cex[ow], base + ow, op, omt, orr, sxp, cand, kmax, box, S.pl[t], S.pd[t],
+                   S.pj[t]);
+          S.owner[t] = (uint8_t)ow;
+          S.mask[t] = 0u;
+          S.dead[t] = 0;
+          S.fa[t] = T(0);
+          S.fo[t] = T(0);
+          S.fx[t] = T(0);
+          S.fy[t] = T(0);
+          S.fr[t] = T(0);
+          S.farc[t] = 0;
         }
       }
       __syncwarp();
-      TaskOut<T> tk = {T(0), T(0), T(0), T(0), T(0), 0};
-      if (act)
-        tk = M ? facet_task(fr, S.rec, lane, head, last, __ffs(M) - 1, !ofull)
-               : facet_task(fr, S.rec, lane, 1, 0, 0, !ofull);
-      tk.area = seg_sum(tk.area, lane, last);
-      tk.om = seg_sum(tk.om, lane, last);
-      tk.mx = seg_sum(tk.mx, lane, last);
-      tk.my = seg_sum(tk.my, lane, last);
-      tk.rm2 = seg_max(tk.rm2, lane, last);
-      tk.arc = seg_sum(tk.arc, lane, last);
-      if (act && lane == head) {
-        S.fa[slot] = tk.area;
-        S.fo[slot] = tk.om;
-        S.fx[slot] = tk.mx;
-        S.fy[slot] = tk.my;
-        S.fr[slot] = tk.rm2;
-        S.farc[slot] = tk.arc > 0 ? 1 : 0;
-      }
-      __syncwarp();
-      R = Rend;
-    }
 
-    // (D) facets: pyramid, moment and Hessian terms per slot, emission, and
-    // a segmented sum per cell
-    for (int t0 = 0; t0 < total; t0 += 32) {
-      const int t = t0 + lane;
-      const bool inr = t < total;
-      const int ow = inr ? S.owner[t] : 0;
-      const T ops = __shfl_sync(kFull, pw.w, ow);
-      const T orr = __shfl_sync(kFull, rw, ow);
-      const T sox = __shfl_sync(kFull, oxw, ow), soy = __shfl_sync(kFull, oyw, ow),
-              soz = __shfl_sync(kFull, ozw, ow);
-      CellAcc<T> a = {};
-      bool neg = false, qo = false, emit = false;
-      T area = T(0);
-      if (inr) {
-        const V4<T> P = S.pl[t];
-        area = S.fa[t];
-        Facet<T> fo = {};
-        fo.area = area;
-        fo.omega = S.fo[t];
-        fo.rm2 = S.fr[t];
-        fo.arc = S.farc[t] && area > T(0);
-        T ux, uy, uz, vx, vy, vz;
-        onb(P.x, P.y, P.z, ux, uy, uz, vx, vy, vz);
-        const T mx = S.fx[t], my = S.fy[t];
-        fo.mx = P.w * P.x * area + ux * mx + vx * my;
-        fo.my = P.w * P.y * area + uy * mx + vy * my;
-        fo.mz = P.w * P.z * area + uz * mx + vz * my;
-        acc_facet(a, P, S.pd[t], S.pj[t], fo);
-        neg = P.w < T(0);
-        // the sphere point farthest from the security centre, q = p - r o/|o|,
-        // is cut off by this plane (clearly: n . (q - p) > h + 1e-6 r)
-        const T soa = sqrt(sox * sox + soy * soy + soz * soz);
-        qo = soa > T(0) && -orr * (P.x * sox + P.y * soy + P.z * soz) > (P.w + T(1e-6) * orr) * soa;
-        emit = S.pj[t] >= 0 && area > Real<T>::kEmitArea * ops;
-      }
-      const int cs0 = S.cex[ow];
-      const int lo = inr ? max(cs0 - t0, 0) : lane;
-      const int hi = inr ? min(S.cex[ow + 1] - 1 - t0, 31) : lane;
-      seg_reduce(a, lane, hi);
-      const unsigned segmask = inr ? ((0xffffffffu >> (31 - hi)) & ~((1u << lo) - 1u)) : 0u;
-      const unsigned negm = __ballot_sync(kFull, neg);
-      const unsigned qm = __ballot_sync(kFull, qo);
-      const unsigned emm = __ballot_sync(kFull, emit);
-      const int done = inr ? S.sc[ow].emitted : 0;
-      if (emit) {
-        const int rank = done + __popc(emm & segmask & ((1u << lane) - 1u));
-        const int64_t at = (base + ow) * kmax + rank;
-        cand[at] = S.pj[t];
-        stage_vals[at] = -area / (T(2) * S.pd[t]);
+      // (B) pairs of planes of each cell: k-th pair of a cell of mc planes is
+      // (f, f + s mod mc), s = k / mc + 1, f = k mod mc (each unordered pair once)
+      for (int p0 = 0; p0 < ptot; p0 += 32) {
+        const int p = p0 + lane;
+        const int c = p < ptot ? last_le(S.cpp, ncell, p) : 0;
+        const T psc = __shfl_sync(kFull, pw.w, c);
+        if (p < ptot) {
+          const int k = p - S.cpp[c];
+          const int sb = S.cex[c];
+          const int mc = S.cex[c + 1] - sb;
+          const int s = k / mc + 1;
+          const int f = k - (s - 1) * mc;
+          int g = f + s;
+          if (g >= mc) g -= mc;
+          const V4<T> F = S.pl[sb + f], G = S.pl[sb + g];
+          const T cxx = F.y * G.z - F.z * G.y, cyy = F.z * G.x - F.x * G.z, czz = F.x * G.y - F.y * G.x;
+          const T len2 = cxx * cxx + cyy * cyy + czz * czz;  // 1 - (n_f . n_g)^2
+          const T cs = F.x * G.x + F.y * G.y + F.z * G.z;
+          const T cf = G.w - F.w * cs;  // g's line offset in f's plane: > 0 keeps f's disk centre
+          const T cg = F.w - G.w * cs;
+          bool cross = false;
+          if (len2 > T(0)) {
+            // the line of f and g crosses the open ball iff
+            // h_f^2 - 2 cs h_f h_g + h_g^2 < psi (1 - cs^2)
+            const T lhs = cs >= T(0)
+                              ? (F.w - G.w) * (F.w - G.w) + T(2) * (len2 / (T(1) + cs)) * F.w * G.w
+                              : (F.w + G.w) * (F.w + G.w) - T(2) * (len2 / (T(1) - cs)) * F.w * G.w;
+            cross = lhs < psc * len2;
+          }
+          if (cross) {
+            atomicOr(&S.mask[sb + f], 1u << g);
+            atomicOr(&S.mask[sb + g], 1u << f);
+          } else {
+            const bool parallel = !(len2 > T(0));
+            if (parallel ? cf < T(0) : !(cf > T(0))) S.dead[sb + f] = 1;
+            if (parallel ? cg < T(0) : !(cg > T(0))) S.dead[sb + g] = 1;
+          }
+        }
       }
       __syncwarp();
-      if (inr && lane == lo) {
-        CellAcc<T>& sa = S.sc[ow].a;
-        sa.hA += a.hA;
-        sa.om += a.om;
-        sa.nx += a.nx;
-        sa.ny += a.ny;
-        sa.nz += a.nz;
-        sa.hx += a.hx;
-        sa.hy += a.hy;
-        sa.hz += a.hz;
-        sa.dg += a.dg;
-        sa.wg += a.wg;
-        sa.rm2 = fmax(sa.rm2, a.rm2);
-        sa.nfac += a.nfac;
-        sa.arc += a.arc;
-        S.sc[ow].neg |= (negm & segmask) != 0u;
-        S.sc[ow].qout |= (qm & segmask) != 0u;
-        S.sc[ow].emitted = done + __popc(emm & segmask);
-      }
-      __syncwarp();
-    }
 
-    // (E) the window's cells
-    if (take && mine) {
-      const int nw = __popc((mt >> kMetaWallShift) & 63);
-      T wv[6] = {};
-      if (o.wallv && !(mt & kMetaEmpty))  // the wall facets are the cell's first planes
-        for (int f = 0; f < nw && f < m; f++) wall_vec(S.fa[excl + f], S.pl[excl + f], wv);
-      const bool fix =
-          write_cell(cell, pw, (mt & kMetaEmpty) != 0, S.sc[lane].neg == 0,
-                     S.sc[lane].qout != 0 && !fullw, fullw, S.sc[lane].a, S.sc[lane].emitted,
-                     sqrt(oxw * oxw + oyw * oyw + ozw * ozw), o, wv);
-      if (fix && o.fix_list)
-        flag_fix(cell, m, nw, S.pj + excl, kmax, cand, o.fix_count, o.fix_list);
+      // (C) tasks: a live facet has one per crossing line, or one for its
+      // whole disk; first the task prefix over the slots
+      int carry = 0;
+      for (int t0 = 0; t0 < total; t0 += 32) {
+        const int t = t0 + lane;
+        int nt = 0;
+        if (t < total && !S.dead[t]) {
+          const int pc = __popc(S.mask[t]);
+          nt = pc > 0 ? pc : 1;
+        }
+        const int inc = warp_incl(nt, lane);
+        if (t < total) S.tpre[t] = carry + inc - nt;
+        carry += __shfl_sync(kFull, inc, 31);
+      }
+      if (lane == 0) S.tpre[total] = carry;
+      __syncwarp();
+      const int ttot = carry;
+      // rounds of whole facets (a facet has at most kSmallPlanes - 1 tasks):
+      // each task stages its line for the other tasks of its facet
+      for (int R = 0; R < ttot;) {
+        const int Rend = S.tpre[last_le(S.tpre, total + 1, R + 32)];
+        const int q = R + lane;
+        const bool act = q < Rend;
+        const int slot = act ? last_le(S.tpre, total, q) : 0;
+        const int c = act ? S.owner[slot] : 0;
+        const T psc = __shfl_sync(kFull, pw.w, c);
+        const T oir = __shfl_sync(kFull, irw, c);
+        const T sox = __shfl_sync(kFull, oxw, c), soy = __shfl_sync(kFull, oyw, c),
+                soz = __shfl_sync(kFull, ozw, c);
+        const bool ofull = __shfl_sync(kFull, fullw, c);
+        const int head = act ? S.tpre[slot] - R : lane;
+        const int last = act ? S.tpre[slot + 1] - 1 - R : lane;
+        FacetFrame<T> fr = {};
+        unsigned M = 0u;
+        if (act) {
+          const int sb = S.cex[c];
+          const V4<T> P = S.pl[slot];
+          fr = facet_frame(P, psc, oir, sox, soy, soz);
+          M = S.mask[slot];
+          if (M) {
+            const int g = (int)__fns(M, 0, q - S.tpre[slot] + 1);
+            S.rec[lane] = line_rec(P, fr, S.pl[sb + g], g);
+          }
+        }
+        __syncwarp();
+        TaskOut<T> tk = {T(0), T(0), T(0), T(0), T(0), 0};
+        if (act)
+          tk = M ? facet_task(fr, S.rec, lane, head, last, __ffs(M) - 1, !ofull)
+                 : facet_task(fr, S.rec, lane, 1, 0, 0, !ofull);
+        tk.area = seg_sum(tk.area, lane, last);
+        tk.om = seg_sum(tk.om, lane, last);
+        tk.mx = seg_sum(tk.mx, lane, last);
+        tk.my = seg_sum(tk.my, lane, last);
+        tk.rm2 = seg_max(tk.rm2, lane, last);
+        tk.arc = seg_sum(tk.arc, lane, last);
+        if (act && lane == head) {
+          S.fa[slot] = tk.area;
+          S.fo[slot] = tk.om;
+          S.fx[slot] = tk.mx;
+          S.fy[slot] = tk.my;
+          S.fr[slot] = tk.rm2;
+          S.farc[slot] = tk.arc > 0 ? 1 : 0;
+        }
+        __syncwarp();
+        R = Rend;
+      }
+
+      // (D) facets: pyramid, moment and Hessian terms per slot, emission, and
+      // a segmented sum per cell
+      for (int t0 = 0; t0 < total; t0 += 32) {
+        const int t = t0 + lane;
+        const bool inr = t < total;
+        const int ow = inr ? S.owner[t] : 0;
+        const T ops = __shfl_sync(kFull, pw.w, ow);
+        const T orr = __shfl_sync(kFull, rw, ow);
+        const T sox = __shfl_sync(kFull, oxw, ow), soy = __shfl_sync(kFull, oyw, ow),
+                soz = __shfl_sync(kFull, ozw, ow);
+        CellAcc<T> a = {};
+        bool neg = false, qo = false, emit = false;
+        T area = T(0);
+        if (inr) {
+          const V4<T> P = S.pl[t];
+          area = S.fa[t];
+          Facet<T> fo = {};
+          fo.area = area;
+          fo.omega = S.fo[t];
+          fo.rm2 = S.fr[t];
+          fo.arc = S.farc[t] && area > T(0);
+          T ux, uy, uz, vx, vy, vz;
+          onb(P.x, P.y, P.z, ux, uy, uz, vx, vy, vz);
+          const T mx = S.fx[t], my = S.fy[t];
+          fo.mx = P.w * P.x * area + ux * mx + vx * my;
+          fo.my = P.w * P.y * area + uy * mx + vy * my;
+          fo.mz = P.w * P.z * area + uz * mx + vz * my;
+          acc_facet(a, P, S.pd[t], S.pj[t], fo);
+          neg = P.w < T(0);
+          // the sphere point farthest from the security centre, q = p - r o/|o|,
+          // is cut off by this plane (clearly: n . (q - p) > h + 1e-6 r)
+          const T soa = sqrt(sox * sox + soy * soy + soz * soz);
+          qo = soa > T(0) && -orr * (P.x * sox + P.y * soy + P.z * soz) > (P.w + T(1e-6) * orr) * soa;
+          emit = S.pj[t] >= 0 && area > Real<T>::kEmitArea * ops;
+        }
+        const int cs0 = S.cex[ow];
+        const int lo = inr ? max(cs0 - t0, 0) : lane;
+        const int hi = inr ? min(S.cex[ow + 1] - 1 - t0, 31) : lane;
+        seg_reduce(a, lane, hi);
+        const unsigned segmask = inr ? ((0xffffffffu >> (31 - hi)) & ~((1u << lo) - 1u)) : 0u;
+        const unsigned negm = __ballot_sync(kFull, neg);
+        const unsigned qm = __ballot_sync(kFull, qo);
+        const unsigned emm = __ballot_sync(kFull, emit);
+        const int done = inr ? S.sc[ow].emitted : 0;
+        if (emit) {
+          const int rank = done + __popc(emm & segmask & ((1u << lane) - 1u));
+          const int64_t at = (base + ow) * kmax + rank;
+          cand[at] = S.pj[t];
+          stage_vals[at] = -area / (T(2) * S.pd[t]);
+        }
+        __syncwarp();
+        if (inr && lane == lo) {
+          CellAcc<T>& sa = S.sc[ow].a;
+          sa.hA += a.hA;
+          sa.om += a.om;
+          sa.nx += a.nx;
+          sa.ny += a.ny;
+          sa.nz += a.nz;
+          sa.hx += a.hx;
+          sa.hy += a.hy;
+          sa.hz += a.hz;
+          sa.dg += a.dg;
+          sa.wg += a.wg;
+          sa.rm2 = fmax(sa.rm2, a.rm2);
+          sa.nfac += a.nfac;
+          sa.arc += a.arc;
+          S.sc[ow].neg |= (negm & segmask) != 0u;
+          S.sc[ow].qout |= (qm & segmask) != 0u;
+          S.sc[ow].emitted = done + __popc(emm & segmask);
+        }
+        __syncwarp();
+      }
+
+      // (E) the window's cells
+      if (take && mine) {
+        const int nw = __popc((mt >> kMetaWallShift) & 63);
+        T wv[6] = {};
+        if (o.wallv && !(mt & kMetaEmpty))  // the wall facets are the cell's first planes
+          for (int f = 0; f < nw && f < m; f++) wall_vec(S.fa[excl + f], S.pl[excl + f], wv);
+        const bool fix =
+            write_cell(cell, pw, (mt & kMetaEmpty) != 0, S.sc[lane].neg == 0,
+                       S.sc[lane].qout != 0 && !fullw, fullw, S.sc[lane].a, S.sc[lane].emitted,
+                       sqrt(oxw * oxw + oyw * oyw + ozw * ozw), o, wv);
+        if (fix && o.fix_list)
+          flag_fix(cell, m, nw, S.pj + excl, kmax, cand, o.fix_count, o.fix_list);
+      }
+      __syncwarp();
+      base += ncell;
     }
-    __syncwarp();
-    base += ncell;
   }
 }
 
@@ -1888,14 +1899,25 @@ int cells_eval(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* dom, 
   // caller asked for them (a Newton solve), invalidated by the grid build
   VerletList<T> vl = {nullptr, nullptr, nullptr};
   if (w.verlet && w.vlist) vl = {w.vlist, w.vcount, w.vreach};
+  // resident blocks of the cell kernel (its warps loop over chunks)
   const int64_t warps = (n + kCellsPerWarp - 1) / kCellsPerWarp;
-  const int blocks = (int)((warps + CellCfg<T>::warps - 1) / CellCfg<T>::warps);
+  static const int per_sm = [] {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_cells<T>, CellCfg<T>::warps * 32, 0) !=
+        cudaSuccess)
+      b = 1;
+    return b;
+  }();
+  const int blocks = (int)std::min<int64_t>(
+      (warps + CellCfg<T>::warps - 1) / CellCfg<T>::warps,
+      (int64_t)std::max(per_sm, 1) * ctx->sm_count);
   int32_t* hcount = (int32_t*)(ctx->h_pinned + 24);
   ctx->last_passes = 0;
   int64_t todo = n;  // cells rebuilt in this pass
   for (int pass = 0; pass < kMaxPasses; pass++) {
     ctx->last_passes = pass + 1;
-    POT_CUDA(cudaMemsetAsync(ctx->need_count + 1, 0, (fix64 ? 2 : 1) * sizeof(int32_t), st));
+    // big cells, FP64 cells listed, the cell kernel's next chunk
+    POT_CUDA(cudaMemsetAsync(ctx->need_count + 1, 0, 3 * sizeof(int32_t), st));
     note_launch();
     k_candidates<T><<<blocks_for(n, 256), 256, 0, st>>>(
         n, w.sxp, ctx->cell_start, w.grid, box, w.psi_max, w.gmax, w.srad, w.srad_lo, w.soff,
@@ -1907,7 +1929,8 @@ int cells_eval(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* dom, 
     if (timed) POT_CUDA(cudaEventRecord(ctx->ev[6], st));
     k_cells<T><<<blocks, CellCfg<T>::warps * 32, 0, st>>>(n, w.sxp, ctx->meta, ctx->cand,
                                                            ctx->k_max, box, w.stage_vals, w.soff,
-                                                           w.srad, o, ctx->err);
+                                                           w.srad, o, ctx->need_count + 3,
+                                                           ctx->err);
     if (w.big_warps > 0) {
       note_launch();
       k_cells_big<T><<<w.big_warps / 4, 128, 0, st>>>(

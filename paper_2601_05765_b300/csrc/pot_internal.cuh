@@ -218,7 +218,7 @@ struct pot_ctx {
   int64_t pcg_graph_n[2] = {-1, -1};
   int32_t* err = nullptr;         // device status words
   uint8_t* need = nullptr;        // per cell: still to be (re)built in this evaluation
-  int32_t* need_count = nullptr;  // device counters: cells to rebuild, big cells, FP64 cells listed
+  int32_t* need_count = nullptr;  // device counters: cells to rebuild, big cells, FP64 cells listed, next chunk of the cell kernel
   int32_t* big_list = nullptr;    // cells with more planes than the shared window holds
   int32_t* fix_list = nullptr;    // FP32 cells re-evaluated in FP64 (ill-conditioned)
   int last_passes = 0;            // security-radius passes of the last cell evaluation
