@@ -631,36 +631,39 @@ __device__ __forceinline__ void wall_vec(T area, const V4<T>& pl, T* v) {
   v[5] += wb * pl.z;
 }
 
-// sum over lanes [lane, last] into the first lane of the window (segment head)
+// Segmented sum over lanes [lane, last] into the segment's first lane (max
+// for rm2), a fixed tree: after level off, a lane holds its lanes [lane,
+// min(lane + 2 off - 1, last)].  span (the same in every lane) bounds the
+// segments' lengths.  All fields go level by level: the shuffles of a level
+// are independent.
 template <typename T>
-__device__ __forceinline__ T seg_sum(T v, int lane, int last) {
+__device__ __forceinline__ void seg_reduce(CellAcc<T>& a, int lane, int last, int span = 32) {
 #pragma unroll
   for (int off = 1; off < 32; off <<= 1) {
-    T t = __shfl_down_sync(kFull, v, off);
-    if (lane + off <= last) v += t;
+    if (off >= span) break;
+    const T hA = __shfl_down_sync(kFull, a.hA, off), om = __shfl_down_sync(kFull, a.om, off);
+    const T nx = __shfl_down_sync(kFull, a.nx, off), ny = __shfl_down_sync(kFull, a.ny, off);
+    const T nz = __shfl_down_sync(kFull, a.nz, off), hx = __shfl_down_sync(kFull, a.hx, off);
+    const T hy = __shfl_down_sync(kFull, a.hy, off), hz = __shfl_down_sync(kFull, a.hz, off);
+    const T dg = __shfl_down_sync(kFull, a.dg, off), wg = __shfl_down_sync(kFull, a.wg, off);
+    const T rm2 = __shfl_down_sync(kFull, a.rm2, off);
+    const int nfac = __shfl_down_sync(kFull, a.nfac, off), arc = __shfl_down_sync(kFull, a.arc, off);
+    if (lane + off <= last) {
+      a.hA += hA;
+      a.om += om;
+      a.nx += nx;
+      a.ny += ny;
+      a.nz += nz;
+      a.hx += hx;
+      a.hy += hy;
+      a.hz += hz;
+      a.dg += dg;
+      a.wg += wg;
+      a.rm2 = fmax(a.rm2, rm2);
+      a.nfac += nfac;
+      a.arc += arc;
+    }
   }
-  return v;
-}
-
-template <typename T>
-__device__ __forceinline__ void seg_reduce(CellAcc<T>& a, int lane, int last) {
-  a.hA = seg_sum(a.hA, lane, last);
-  a.om = seg_sum(a.om, lane, last);
-  a.nx = seg_sum(a.nx, lane, last);
-  a.ny = seg_sum(a.ny, lane, last);
-  a.nz = seg_sum(a.nz, lane, last);
-  a.hx = seg_sum(a.hx, lane, last);
-  a.hy = seg_sum(a.hy, lane, last);
-  a.hz = seg_sum(a.hz, lane, last);
-  a.dg = seg_sum(a.dg, lane, last);
-  a.wg = seg_sum(a.wg, lane, last);
-#pragma unroll
-  for (int off = 1; off < 32; off <<= 1) {
-    T t = __shfl_down_sync(kFull, a.rm2, off);
-    if (lane + off <= last) a.rm2 = fmax(a.rm2, t);
-  }
-  a.nfac = seg_sum(a.nfac, lane, last);
-  a.arc = seg_sum(a.arc, lane, last);
 }
 
 struct CellOut {
@@ -1030,6 +1033,27 @@ __device__ __forceinline__ TaskOut<T> facet_task(const FacetFrame<T>& F, const L
   return out;
 }
 
+// the same segmented sums (max for rm2) over a facet's task results
+template <typename T>
+__device__ __forceinline__ void seg_task(TaskOut<T>& k, int lane, int last, int span) {
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    if (off >= span) break;
+    const T area = __shfl_down_sync(kFull, k.area, off), om = __shfl_down_sync(kFull, k.om, off);
+    const T mx = __shfl_down_sync(kFull, k.mx, off), my = __shfl_down_sync(kFull, k.my, off);
+    const T rm2 = __shfl_down_sync(kFull, k.rm2, off);
+    const int arc = __shfl_down_sync(kFull, k.arc, off);
+    if (lane + off <= last) {
+      k.area += area;
+      k.om += om;
+      k.mx += mx;
+      k.my += my;
+      k.rm2 = fmax(k.rm2, rm2);
+      k.arc += arc;
+    }
+  }
+}
+
 // A warp's window: the planes of consecutive cells, the crossing sets, the
 // task prefix and the per-facet sums of the tasks.
 template <typename T>
@@ -1049,15 +1073,6 @@ struct Window {
   CellSlot<T> sc[32];
 };
 
-template <typename T>
-__device__ __forceinline__ T seg_max(T v, int lane, int last) {
-#pragma unroll
-  for (int off = 1; off < 32; off <<= 1) {
-    T t = __shfl_down_sync(kFull, v, off);
-    if (lane + off <= last) v = fmax(v, t);
-  }
-  return v;
-}
 
 // inclusive warp prefix sum
 __device__ __forceinline__ int warp_incl(int v, int lane) {
@@ -1196,7 +1211,9 @@ __global__ void __launch_bounds__(CellCfg<T>::warps * 32, sizeof(T) == 4 ? 6 : 2
           const int k = p - S.cpp[c];
           const int sb = S.cex[c];
           const int mc = S.cex[c + 1] - sb;
-          const int s = k / mc + 1;
+          // k / mc: k < 496 and mc <= 32 put (k + 1/2) / mc at least 1/64
+          // from an integer, far beyond the error of the fast divide
+          const int s = __float2int_rz(__fdividef((float)k + 0.5f, (float)mc)) + 1;
           const int f = k - (s - 1) * mc;
           int g = f + s;
           if (g >= mc) g -= mc;
@@ -1209,11 +1226,13 @@ __global__ void __launch_bounds__(CellCfg<T>::warps * 32, sizeof(T) == 4 ? 6 : 2
           bool cross = false;
           if (len2 > T(0)) {
             // the line of f and g crosses the open ball iff
-            // h_f^2 - 2 cs h_f h_g + h_g^2 < psi (1 - cs^2)
-            const T lhs = cs >= T(0)
-                              ? (F.w - G.w) * (F.w - G.w) + T(2) * (len2 / (T(1) + cs)) * F.w * G.w
-                              : (F.w + G.w) * (F.w + G.w) - T(2) * (len2 / (T(1) - cs)) * F.w * G.w;
-            cross = lhs < psc * len2;
+            // h_f^2 - 2 cs h_f h_g + h_g^2 < psi (1 - cs^2), written as
+            // (h_f -+ h_g)^2 (1 + |cs|) +- 2 len2 h_f h_g < psi len2 (1 + |cs|)
+            // (upper signs for cs >= 0), without cancellation
+            const T a1 = T(1) + fabs(cs);
+            const T dd = cs >= T(0) ? F.w - G.w : F.w + G.w;
+            const T fg = (cs >= T(0) ? T(2) : T(-2)) * len2 * F.w * G.w;
+            cross = dd * dd * a1 + fg < psc * len2 * a1;
           }
           if (cross) {
             atomicOr(&S.mask[sb + f], 1u << g);
@@ -1276,12 +1295,7 @@ __global__ void __launch_bounds__(CellCfg<T>::warps * 32, sizeof(T) == 4 ? 6 : 2
         if (act)
           tk = M ? facet_task(fr, S.rec, lane, head, last, __ffs(M) - 1, !ofull)
                  : facet_task(fr, S.rec, lane, 1, 0, 0, !ofull);
-        tk.area = seg_sum(tk.area, lane, last);
-        tk.om = seg_sum(tk.om, lane, last);
-        tk.mx = seg_sum(tk.mx, lane, last);
-        tk.my = seg_sum(tk.my, lane, last);
-        tk.rm2 = seg_max(tk.rm2, lane, last);
-        tk.arc = seg_sum(tk.arc, lane, last);
+        seg_task(tk, lane, last, __reduce_max_sync(kFull, last - head + 1));
         if (act && lane == head) {
           S.fa[slot] = tk.area;
           S.fo[slot] = tk.om;
@@ -1332,7 +1346,7 @@ __global__ void __launch_bounds__(CellCfg<T>::warps * 32, sizeof(T) == 4 ? 6 : 2
         const int cs0 = S.cex[ow];
         const int lo = inr ? max(cs0 - t0, 0) : lane;
         const int hi = inr ? min(S.cex[ow + 1] - 1 - t0, 31) : lane;
-        seg_reduce(a, lane, hi);
+        seg_reduce(a, lane, hi, __reduce_max_sync(kFull, hi - lo + 1));
         const unsigned segmask = inr ? ((0xffffffffu >> (31 - hi)) & ~((1u << lo) - 1u)) : 0u;
         const unsigned negm = __ballot_sync(kFull, neg);
         const unsigned qm = __ballot_sync(kFull, qo);
