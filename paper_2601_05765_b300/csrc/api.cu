@@ -48,6 +48,7 @@ int alloc_work(Work<T>& w, int64_t n, int64_t k, int64_t gcap, int sms) {
   POT_CHECK(alloc(&w.z, n));
   POT_CHECK(alloc(&w.p0, n));
   POT_CHECK(alloc(&w.p1, n));
+  POT_CHECK(alloc(&w.zp, 2 * n));
   POT_CHECK(alloc(&w.q, n));
   POT_CHECK(alloc(&w.vel_s, 3 * n));
   POT_CHECK(alloc(&w.psi_max, 1));
@@ -83,7 +84,7 @@ void free_work(Work<T>& w) {
                   w.u,   w.x,        w.r,    w.z,     w.p0,   w.p1,  w.q,          w.vel_s,
                   w.psi_max, w.nu_max, w.srad, w.srad_lo, w.soff, w.hint, w.rcell_acc, w.rcell, w.gmax,
                   w.big_pl, w.big_d, w.big_j, w.psi_hist, w.psi_fb, w.wallw, w.vlist, w.vcount,
-                  w.vreach, w.wallv};
+                  w.vreach, w.wallv, w.zp};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   w = Work<T>();

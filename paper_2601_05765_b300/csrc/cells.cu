@@ -1721,22 +1721,58 @@ __global__ void __launch_bounds__(256)
 // ---------------------------------------------------------------------------
 // reductions, CSR, scatter
 
+// Per-thread terms of the residual: exact in FP64 for an FP64 evaluation;
+// for an FP32 one, g = nu - V as hi + lo floats (nu split into two floats,
+// the difference by an error-free two-difference) and sum g^2 in
+// double-float, so that no FP64 arithmetic runs per cell.
+template <typename T>
+struct ResidAcc {
+  double emax = 0.0, ss = 0.0, vmin = 1e300;
+  int64_t nemp = 0, npl = 0;
+  int mpl = 0;
+  __device__ __forceinline__ void add(T v, double nu) {
+    const double g = nu - (double)v;
+    if (nu > 0.0) emax = fmax(emax, fabs(g) / nu);
+    ss += g * g;
+    vmin = fmin(vmin, (double)v);
+    nemp += v <= T(0) ? 1 : 0;
+  }
+  __device__ __forceinline__ double sum_sq() const { return ss; }
+  __device__ __forceinline__ double vol_min() const { return vmin; }
+};
+template <>
+struct ResidAcc<float> {
+  float emax = 0.f, vmin = 3.0e38f;
+  DF ss;
+  int64_t nemp = 0, npl = 0;
+  int mpl = 0;
+  __device__ __forceinline__ void add(float v, double nu) {
+    const float hi = (float)nu, lo = (float)(nu - (double)hi);
+    const float s = hi - v, bb = s - hi;
+    const float gl = ((hi - (s - bb)) - (v + bb)) + lo;  // g = s + gl
+    if (hi > 0.f) emax = fmaxf(emax, fabsf(s + gl) / hi);
+    df_add_prod(ss, s, s);
+    ss.lo += 2.f * s * gl;
+    vmin = fminf(vmin, v);
+    nemp += v <= 0.f ? 1 : 0;
+  }
+  __device__ __forceinline__ double sum_sq() const { return df_value(ss); }
+  __device__ __forceinline__ double vol_min() const { return vmin < 3.0e38f ? vmin : 1e300; }
+};
+
 template <typename T>
 __global__ void k_resid(int64_t n, const T* __restrict__ vol, const double* __restrict__ snu,
                         const int32_t* __restrict__ meta, double* part) {
-  double emax = 0.0, ss = 0.0, vmin = 1e300, nemp = 0.0, npl = 0.0, mpl = 0.0;
+  ResidAcc<T> acc;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    double v = (double)vol[i], nu = snu[i];
-    double g = nu - v;
-    if (nu > 0.0) emax = fmax(emax, fabs(g) / nu);
-    ss += g * g;
-    vmin = fmin(vmin, v);
-    nemp += v <= 0.0 ? 1.0 : 0.0;
-    int m = meta[i] & kMetaPlanes;
-    npl += m;
-    mpl = fmax(mpl, (double)m);
+    acc.add(vol[i], snu[i]);
+    const int m = meta[i] & kMetaPlanes;
+    acc.npl += m;
+    acc.mpl = max(acc.mpl, m);
   }
+  double emax = acc.emax, ss = acc.sum_sq(), vmin = acc.vol_min();
+  double nemp = (double)acc.nemp, npl = (double)acc.npl, mpl = (double)acc.mpl;
   __shared__ double sh[6][8];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int off = 16; off > 0; off >>= 1) {
@@ -1766,10 +1802,12 @@ __global__ void k_resid(int64_t n, const T* __restrict__ vol, const double* __re
   }
 }
 
+// The block partials of k_resid over one warp: lane l takes blocks l, l + 32,
+// ... in order, then a fixed shuffle tree (deterministic).
 __global__ void k_resid_final(const double* __restrict__ part, int nb, double* out) {
-  if (threadIdx.x != 0) return;
+  const int lane = threadIdx.x;
   double r[6] = {0.0, 0.0, 1e300, 0.0, 0.0, 0.0};
-  for (int b = 0; b < nb; b++) {
+  for (int b = lane; b < nb; b += 32) {
     r[0] = fmax(r[0], part[6 * b + 0]);
     r[1] += part[6 * b + 1];
     r[2] = fmin(r[2], part[6 * b + 2]);
@@ -1777,7 +1815,16 @@ __global__ void k_resid_final(const double* __restrict__ part, int nb, double* o
     r[4] += part[6 * b + 4];
     r[5] = fmax(r[5], part[6 * b + 5]);
   }
-  for (int k = 0; k < 6; k++) out[k] = r[k];
+  for (int off = 16; off > 0; off >>= 1) {
+    r[0] = fmax(r[0], __shfl_down_sync(kFull, r[0], off));
+    r[1] += __shfl_down_sync(kFull, r[1], off);
+    r[2] = fmin(r[2], __shfl_down_sync(kFull, r[2], off));
+    r[3] += __shfl_down_sync(kFull, r[3], off);
+    r[4] += __shfl_down_sync(kFull, r[4], off);
+    r[5] = fmax(r[5], __shfl_down_sync(kFull, r[5], off));
+  }
+  if (lane == 0)
+    for (int k = 0; k < 6; k++) out[k] = r[k];
 }
 
 template <typename T>
@@ -1857,14 +1904,7 @@ __global__ void k_psi_update(int64_t n, const T* __restrict__ base, const T* __r
     v = base[s] + alpha * u[s];
     sxp[s].w = v;
   }
-  T m = v > T(0) ? v : T(0);
-  for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_down_sync(kFull, m, off));
-  if ((threadIdx.x & 31) == 0 && m > T(0)) {
-    if (sizeof(T) == 4)
-      atomicMax((int*)psi_max, __float_as_int((float)m));
-    else
-      atomicMax((unsigned long long*)psi_max, (unsigned long long)__double_as_longlong((double)m));
-  }
+  block_max_to(v > T(0) ? v : T(0), psi_max);
 }
 
 }  // namespace

@@ -26,13 +26,7 @@ __global__ void k_psi_max_in(const T* __restrict__ psi, int64_t n, T* out) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     m = fmax(m, psi[i]);
-  for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_down_sync(kFull, m, off));
-  if ((threadIdx.x & 31) == 0) {
-    if (sizeof(T) == 4)
-      atomicMax((int*)out, __float_as_int((float)m));
-    else
-      atomicMax((unsigned long long*)out, (unsigned long long)__double_as_longlong((double)m));
-  }
+  block_max_to(m, out);
 }
 
 __global__ void k_nu_max_in(const double* __restrict__ nu, int64_t n, double* out) {
@@ -40,9 +34,7 @@ __global__ void k_nu_max_in(const double* __restrict__ nu, int64_t n, double* ou
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     m = fmax(m, nu[i]);
-  for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_down_sync(kFull, m, off));
-  if ((threadIdx.x & 31) == 0)
-    atomicMax((unsigned long long*)out, (unsigned long long)__double_as_longlong(m));
+  block_max_to(m, out);
 }
 
 template <typename T>

@@ -596,9 +596,7 @@ __global__ void k_apply_warm(int64_t n, const float* __restrict__ out, const dou
     psi_base[s] = v;
   }
   // the candidate search radius follows the largest new weight
-  float m = fmaxf(v, 0.f);
-  for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_down_sync(kFull, m, off));
-  if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax((int*)psi_max, __float_as_int(m));
+  block_max_to(fmaxf(v, 0.f), psi_max);
 }
 
 // ---------------------------------------------------------------------------

@@ -45,10 +45,10 @@ __global__ void k_nu_min(int64_t n, const double* __restrict__ snu, double* part
 }
 
 __global__ void k_min_final(const double* __restrict__ part, int nb, double* out) {
-  if (threadIdx.x) return;
-  double m = 1e300;
-  for (int b = 0; b < nb; b++) m = fmin(m, part[b]);
-  *out = m;
+  double m = 1e300;  // one warp: strided, then a shuffle tree
+  for (int b = threadIdx.x; b < nb; b += 32) m = fmin(m, part[b]);
+  for (int off = 16; off > 0; off >>= 1) m = fmin(m, __shfl_down_sync(kFull, m, off));
+  if (threadIdx.x == 0) *out = m;
 }
 
 // x <- x + dt v, clamped into [lo+m, hi-m]; velocity through a wall -> 0
@@ -109,14 +109,7 @@ __global__ void k_extrapolate(int64_t n, const int32_t* __restrict__ perm, const
     sxp[s].w = v;
     psi_base[s] = v;
   }
-  T m = v > T(0) ? v : T(0);
-  for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_down_sync(kFull, m, off));
-  if ((threadIdx.x & 31) == 0 && m > T(0)) {
-    if (sizeof(T) == 4)
-      atomicMax((int*)psi_max, __float_as_int((float)m));
-    else
-      atomicMax((unsigned long long*)psi_max, (unsigned long long)__double_as_longlong((double)m));
-  }
+  block_max_to(v > T(0) ? v : T(0), psi_max);
 }
 
 // Semi-implicit velocity update with viscosity and surface tension (Sec. 5,
@@ -207,14 +200,7 @@ __global__ void k_set_psi(int64_t n, const T* __restrict__ src, V4<T>* sxp, T* b
     sxp[s].w = v;
     base[s] = v;
   }
-  T m = v > T(0) ? v : T(0);
-  for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_down_sync(kFull, m, off));
-  if ((threadIdx.x & 31) == 0 && m > T(0)) {
-    if (sizeof(T) == 4)
-      atomicMax((int*)psi_max, __float_as_int((float)m));
-    else
-      atomicMax((unsigned long long*)psi_max, (unsigned long long)__double_as_longlong((double)m));
-  }
+  block_max_to(v > T(0) ? v : T(0), psi_max);
 }
 
 template <typename T>

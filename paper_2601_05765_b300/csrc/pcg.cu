@@ -6,12 +6,18 @@
 // kernel (k_pcg_coop, below) when the device supports cooperative launches.
 // Larger ones take two kernels per iteration, no host round trip:
 //   k_spmv:   beta = rz / rz_prev; p_new = z + beta p_old fused into the
-//             gather of the SpMV (p double-buffered); q = M p_new; p_new . q
-//   k_update: alpha = rz / pq; x += alpha p; r -= alpha q; z = r / diag;
-//             r . z and r . r; convergence test
-// Dot products accumulate in FP64: per thread, then per block (fixed tree),
-// then over blocks by the last block to finish (an arrival counter after a
-// memory fence), which adds the block partials in index order and publishes
+//             gather of the SpMV; q = M p_new; p_new . q
+//   k_update: alpha = rz / pq; x += alpha p_new; r -= alpha q;
+//             z = r D^-1 (D^-1 formed once per solve); r . z and r . r;
+//             convergence test
+// z and p are stored interleaved, (z_j, p_j) per row: the SpMV gathers both
+// with one 8-byte (16-byte in FP64) load per entry, and k_update writes the
+// pair (z_new, p_new) of its row.
+// Dot products accumulate per thread exactly in FP64 (FP64 vectors) or in
+// double-float on the FP32 units (FP32 vectors), then in FP64 per block
+// (fixed tree), then over blocks by the last block to finish (an arrival
+// counter after a memory fence), which adds the block partials in index
+// order and publishes
 // the scalars and the decisions (converged, breakdown) for the next kernel.
 // The result is deterministic and no block re-reads all partials.
 //
@@ -31,6 +37,27 @@ namespace {
 
 constexpr int kPcgThreads = 256;
 constexpr int kTpr = 2;  // threads per CSR row (about 10 entries per row)
+
+// A thread's partial of a dot product: exact FP64 sums of the products of
+// FP64 vectors; double-float sums (FP32 units only) of FP32 vectors
+template <typename T>
+struct Dot {
+  double s = 0.0;
+  __device__ __forceinline__ void add(T a, T b) { s += a * b; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct Dot<float> {
+  DF s;
+  __device__ __forceinline__ void add(float a, float b) { df_add_prod(s, a, b); }
+  __device__ __forceinline__ double value() const { return df_value(s); }
+};
+
+// z and p of one row, stored together
+template <typename T>
+struct alignas(2 * sizeof(T)) ZP {
+  T z, p;
+};
 
 // partial-sum arrays (nb doubles each) and scalars at the end of pcg_red
 enum { kPartA = 0, kPartB = 1, kPartC = 2, kParts = 3 };
@@ -141,22 +168,24 @@ __device__ __forceinline__ bool grid_barrier(int32_t* counter, int32_t* timeout,
 
 template <typename T>
 __global__ void __launch_bounds__(kPcgThreads)
-    k_pcg_init(int64_t n, const double* __restrict__ b, const T* __restrict__ diag, T* x, T* r,
-               T* z, T* p0, double* part, double* scal, int nb, int32_t* ctl, double rtol2,
-               int max_iter) {
-  double rz = 0.0, rr = 0.0;
+    k_pcg_init(int64_t n, const double* __restrict__ b, const T* __restrict__ diag,
+               T* __restrict__ x, T* __restrict__ r, T* __restrict__ dinv, ZP<T>* __restrict__ zp,
+               double* part, double* scal, int nb, int32_t* ctl, double rtol2, int max_iter) {
+  Dot<T> rz, rr;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    T ri = (T)b[i];
-    T zi = diag[i] > T(0) ? ri / diag[i] : T(0);
+    const T d = diag[i];
+    const T di = d > T(0) ? T(1) / d : T(0);
+    const T ri = (T)b[i];
+    const T zi = ri * di;
     x[i] = T(0);
     r[i] = ri;
-    z[i] = zi;
-    p0[i] = T(0);
-    rz += (double)ri * (double)zi;
-    rr += (double)ri * (double)ri;
+    dinv[i] = di;
+    zp[i] = ZP<T>{zi, T(0)};
+    rz.add(ri, zi);
+    rr.add(ri, ri);
   }
-  if (arrive(part, nb, 2, rz, rr, 0.0, ctl)) {
+  if (arrive(part, nb, 2, rz.value(), rr.value(), 0.0, ctl)) {
     const double trz = sum_parts(part + kPartA * nb, nb);
     const double trr = sum_parts(part + kPartB * nb, nb);
     if (threadIdx.x == 0) {
@@ -179,15 +208,14 @@ __global__ void __launch_bounds__(kPcgThreads)
 template <typename T>
 __global__ void __launch_bounds__(kPcgThreads)
     k_spmv(int64_t n, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ cols,
-           const T* __restrict__ vals, const T* __restrict__ diag, const T* __restrict__ z,
-           T* pa, T* pb, T* q, double* part, double* scal, int nb, int32_t* ctl) {
+           const T* __restrict__ vals, const T* __restrict__ diag, const ZP<T>* __restrict__ zp,
+           T* __restrict__ pnew, T* __restrict__ q, double* part, double* scal, int nb,
+           int32_t* ctl) {
   if (ctl[kDone]) return;
   const int it = ctl[kIt];
   const T beta = it == 0 ? T(0) : (T)(scal[kRZ] / scal[kRZP]);
-  const T* __restrict__ pold = (it & 1) ? pb : pa;
-  T* pnew = (it & 1) ? pa : pb;
   const int sub = threadIdx.x & (kTpr - 1);
-  double pq = 0.0;
+  Dot<T> pq;
   const int64_t groups = (int64_t)gridDim.x * (blockDim.x / kTpr);
   // rows rounded up to a multiple of the group count: every lane of a warp
   // runs the same number of iterations (the shuffles use the full mask)
@@ -201,10 +229,11 @@ __global__ void __launch_bounds__(kPcgThreads)
       // unrolled so that the loads of several entries are in flight at once
 #pragma unroll 4
       for (int k = a + sub; k < e; k += kTpr) {
-        const int j = cols[k];
-        acc += vals[k] * (z[j] + beta * pold[j]);
+        const ZP<T> v = zp[cols[k]];
+        acc += vals[k] * (v.z + beta * v.p);
       }
-      pi = z[i] + beta * pold[i];
+      const ZP<T> v = zp[i];
+      pi = v.z + beta * v.p;
     }
 #pragma unroll
     for (int off = kTpr / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off);
@@ -212,10 +241,10 @@ __global__ void __launch_bounds__(kPcgThreads)
       const T qi = diag[i] * pi + acc;
       pnew[i] = pi;
       q[i] = qi;
-      pq += (double)pi * (double)qi;
+      pq.add(pi, qi);
     }
   }
-  if (arrive(part, nb, 1, pq, 0.0, 0.0, ctl)) {
+  if (arrive(part, nb, 1, pq.value(), 0.0, 0.0, ctl)) {
     const double tpq = sum_parts(part + kPartA * nb, nb);
     if (threadIdx.x == 0) {
       scal[kPQ] = tpq;
@@ -229,11 +258,17 @@ __global__ void __launch_bounds__(kPcgThreads)
   }
 }
 
+// rows of k_update in flight per thread (their loads issued together; two
+// in FP64 for registers), and its blocks per SM (one wave)
+template <typename T>
+constexpr int kUpdRows = sizeof(T) == 4 ? 4 : 2;
+constexpr int kUpdBlocksPerSm = 4;
+
 template <typename T, bool kGraph>
-__global__ void __launch_bounds__(kPcgThreads, kPcgMaxBlocksPerSm)
-    k_update(int64_t n, const T* __restrict__ diag, T* x, T* r, T* z, const T* __restrict__ pa,
-             const T* __restrict__ pb, const T* __restrict__ q, double* part, double* scal,
-             int nb, int32_t* ctl, cudaGraphConditionalHandle loop) {
+__global__ void __launch_bounds__(kPcgThreads, kUpdBlocksPerSm)
+    k_update(int64_t n, const T* __restrict__ dinv, T* __restrict__ x, T* __restrict__ r,
+             ZP<T>* __restrict__ zp, const T* __restrict__ pnew, const T* __restrict__ q,
+             double* part, double* scal, int nb, int32_t* ctl, cudaGraphConditionalHandle loop) {
   if (kGraph && blockIdx.x == 0 && threadIdx.x == 0) {
     // the only writer of the loop condition and of the trip counter
     const int trips = ctl[kTrips] + 1;
@@ -245,19 +280,37 @@ __global__ void __launch_bounds__(kPcgThreads, kPcgMaxBlocksPerSm)
   const int max_iter = ctl[kMaxIt];
   const int it = ctl[kIt];
   const T alpha = (T)(scal[kRZ] / scal[kPQ]);
-  const T* __restrict__ p = (it & 1) ? pa : pb;
-  double rzn = 0.0, rr = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    x[i] += alpha * p[i];
-    const T ri = r[i] - alpha * q[i];
-    const T zi = diag[i] > T(0) ? ri / diag[i] : T(0);
-    r[i] = ri;
-    z[i] = zi;
-    rzn += (double)ri * (double)zi;
-    rr += (double)ri * (double)ri;
+  Dot<T> rzn, rr;
+  const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n;
+       i0 += kUpdRows<T> * nthr) {
+    T pv[kUpdRows<T>], xv[kUpdRows<T>], rv[kUpdRows<T>], qv[kUpdRows<T>], dv[kUpdRows<T>];
+#pragma unroll
+    for (int u = 0; u < kUpdRows<T>; u++) {
+      const int64_t i = i0 + u * nthr;
+      if (i < n) {
+        pv[u] = pnew[i];
+        xv[u] = x[i];
+        rv[u] = r[i];
+        qv[u] = q[i];
+        dv[u] = dinv[i];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kUpdRows<T>; u++) {
+      const int64_t i = i0 + u * nthr;
+      if (i < n) {
+        const T ri = rv[u] - alpha * qv[u];
+        const T zi = ri * dv[u];
+        x[i] = xv[u] + alpha * pv[u];
+        r[i] = ri;
+        zp[i] = ZP<T>{zi, pv[u]};
+        rzn.add(ri, zi);
+        rr.add(ri, ri);
+      }
+    }
   }
-  if (arrive(part, nb, 2, rzn, rr, 0.0, ctl)) {
+  if (arrive(part, nb, 2, rzn.value(), rr.value(), 0.0, ctl)) {
     const double trz = sum_parts(part + kPartA * nb, nb);
     const double trr = sum_parts(part + kPartB * nb, nb);
     if (threadIdx.x == 0) {
@@ -297,7 +350,7 @@ __global__ void __launch_bounds__(kPcgThreads, 5)
   int32_t* counter = ctl + kBar;
   int32_t* timeout = ctl + kTimeout;
   int gen = 0;
-  double rz = 0.0, rr = 0.0;
+  Dot<T> rz0, rr0;
   for (int64_t i = tid; i < n; i += nthr) {
     const T d = diag[i];
     const T di = d > T(0) ? T(1) / d : T(0);
@@ -308,11 +361,11 @@ __global__ void __launch_bounds__(kPcgThreads, 5)
     r[i] = ri;
     z[i] = zi;
     pa[i] = T(0);
-    rz += (double)ri * (double)zi;
-    rr += (double)ri * (double)ri;
+    rz0.add(ri, zi);
+    rr0.add(ri, ri);
   }
-  rz = block_sum_all(rz);
-  rr = block_sum_all(rr);
+  const double rz = block_sum_all(rz0.value());
+  const double rr = block_sum_all(rr0.value());
   if (threadIdx.x == 0) {
     Prz[blockIdx.x] = rz;
     Prr[blockIdx.x] = rr;
@@ -333,7 +386,7 @@ __global__ void __launch_bounds__(kPcgThreads, 5)
     const T beta = it == 0 ? T(0) : (T)(trz / trz_prev);
     const T* pold = (it & 1) ? pb : pa;
     T* pnew = (it & 1) ? pa : pb;
-    double pq = 0.0;
+    Dot<T> pqt;
     for (int64_t i = tid / kTpr; i < n_round; i += groups) {
       T acc = T(0), pi = T(0);
       if (i < n) {
@@ -351,10 +404,10 @@ __global__ void __launch_bounds__(kPcgThreads, 5)
         const T qi = diag[i] * pi + acc;
         pnew[i] = pi;
         q[i] = qi;
-        pq += (double)pi * (double)qi;
+        pqt.add(pi, qi);
       }
     }
-    pq = block_sum_all(pq);
+    const double pq = block_sum_all(pqt.value());
     if (threadIdx.x == 0) Ppq[blockIdx.x] = pq;
     if (!grid_barrier(counter, timeout, ++gen * nb)) return;
     const double tpq = sum_parts_all(Ppq, nb);
@@ -363,18 +416,18 @@ __global__ void __launch_bounds__(kPcgThreads, 5)
       break;
     }
     const T alpha = (T)(trz / tpq);
-    double rzn = 0.0, rrn = 0.0;
+    Dot<T> rzt, rrt;
     for (int64_t i = tid; i < n; i += nthr) {
       x[i] += alpha * __ldcg(pnew + i);
       const T ri = r[i] - alpha * __ldcg(q + i);
       const T zi = ri * dinv[i];
       r[i] = ri;
       z[i] = zi;
-      rzn += (double)ri * (double)zi;
-      rrn += (double)ri * (double)ri;
+      rzt.add(ri, zi);
+      rrt.add(ri, ri);
     }
-    rzn = block_sum_all(rzn);
-    rrn = block_sum_all(rrn);
+    const double rzn = block_sum_all(rzt.value());
+    const double rrn = block_sum_all(rrt.value());
     if (threadIdx.x == 0) {
       Prz[blockIdx.x] = rzn;
       Prr[blockIdx.x] = rrn;
@@ -400,6 +453,13 @@ int pcg_blocks(int sm_count) { return sm_count * kPcgMaxBlocksPerSm; }
 size_t pcg_red_len(int sm_count) { return (size_t)kParts * pcg_blocks(sm_count) + kScalars; }
 
 namespace {
+
+// k_update's grid: one wave at kUpdBlocksPerSm blocks per SM, at most nb
+// (its partials use the same arrays)
+int upd_blocks(const pot_ctx* ctx, int nb) {
+  const int b = ctx->sm_count * kUpdBlocksPerSm;
+  return b < nb ? b : nb;
+}
 
 // The while-node graph of the PCG iterations for n rows (see the top).
 template <typename T>
@@ -430,12 +490,15 @@ int build_graph(pot_ctx* ctx, int64_t n, int nb, double* part, double* scal) {
   const int32_t* cols = ctx->csr_cols;
   const T* vals = w.csr_vals;
   const T* diag = w.diag;
-  const T* zc = w.z;
-  T *x = w.u, *r = w.r, *z = w.z, *pa = w.p0, *pb = w.p1, *q = w.q;
-  const T *pac = w.p0, *pbc = w.p1, *qc = w.q;
+  const T* dinv = w.x;
+  ZP<T>* zp = (ZP<T>*)w.zp;
+  const ZP<T>* zpc = zp;
+  T *x = w.u, *r = w.r, *pnew = w.p1, *q = w.q;
+  const T *pnewc = w.p1, *qc = w.q;
   int anb = nb;
+  int anbu = upd_blocks(ctx, nb);
   int32_t* ctl = ctx->pcg_ctl;
-  void* a1[] = {&an, &row_ptr, &cols, &vals, &diag, &zc, &pa, &pb, &q, &part, &scal, &anb, &ctl};
+  void* a1[] = {&an, &row_ptr, &cols, &vals, &diag, &zpc, &pnew, &q, &part, &scal, &anb, &ctl};
   cudaKernelNodeParams k1 = {};
   k1.func = (void*)k_spmv<T>;
   k1.gridDim = dim3(nb);
@@ -443,10 +506,10 @@ int build_graph(pot_ctx* ctx, int64_t n, int nb, double* part, double* scal) {
   k1.kernelParams = a1;
   cudaGraphNode_t n1, n2;
   POT_CUDA(cudaGraphAddKernelNode(&n1, body, nullptr, 0, &k1));
-  void* a2[] = {&an, &diag, &x, &r, &z, &pac, &pbc, &qc, &part, &scal, &anb, &ctl, &loop};
+  void* a2[] = {&an, &dinv, &x, &r, &zp, &pnewc, &qc, &part, &scal, &anbu, &ctl, &loop};
   cudaKernelNodeParams k2 = {};
   k2.func = (void*)k_update<T, true>;
-  k2.gridDim = dim3(nb);
+  k2.gridDim = dim3(anbu);
   k2.blockDim = dim3(kPcgThreads);
   k2.kernelParams = a2;
   POT_CUDA(cudaGraphAddKernelNode(&n2, body, &n1, 1, &k2));
@@ -518,8 +581,8 @@ int pcg_solve(pot_ctx* ctx, cudaStream_t st, int64_t n, int64_t nnz_off, double 
   // the arrival counter must start at zero
   POT_CUDA(cudaMemsetAsync(ctx->pcg_ctl + kArrive, 0, sizeof(int32_t), st));
   note_launch();
-  k_pcg_init<T><<<nb, kPcgThreads, 0, st>>>(n, ctx->grad, w.diag, w.u, w.r, w.z, w.p0, part, scal,
-                                            nb, ctx->pcg_ctl, rtol2, max_iter);
+  k_pcg_init<T><<<nb, kPcgThreads, 0, st>>>(n, ctx->grad, w.diag, w.u, w.r, w.x, (ZP<T>*)w.zp,
+                                            part, scal, nb, ctx->pcg_ctl, rtol2, max_iter);
   POT_CUDA(cudaGetLastError());
   const int gk = sizeof(T) == 4 ? 0 : 1;
   bool graph = ctx->pcg_exec[gk] && ctx->pcg_graph_n[gk] == n;
@@ -539,11 +602,12 @@ int pcg_solve(pot_ctx* ctx, cudaStream_t st, int64_t n, int64_t nnz_off, double 
       for (int k = 0; k < chunk; k++) {
         note_launch();
         k_spmv<T><<<nb, kPcgThreads, 0, st>>>(n, ctx->row_ptr, ctx->csr_cols, w.csr_vals, w.diag,
-                                              w.z, w.p0, w.p1, w.q, part, scal, nb, ctx->pcg_ctl);
+                                              (const ZP<T>*)w.zp, w.p1, w.q, part, scal, nb,
+                                              ctx->pcg_ctl);
         note_launch();
-        k_update<T, false><<<nb, kPcgThreads, 0, st>>>(n, w.diag, w.u, w.r, w.z, w.p0, w.p1, w.q,
-                                                       part, scal, nb, ctx->pcg_ctl,
-                                                       cudaGraphConditionalHandle{});
+        k_update<T, false><<<upd_blocks(ctx, nb), kPcgThreads, 0, st>>>(
+            n, w.x, w.u, w.r, (ZP<T>*)w.zp, w.p1, w.q, part, scal, upd_blocks(ctx, nb),
+            ctx->pcg_ctl, cudaGraphConditionalHandle{});
       }
       launched += chunk;
       POT_CUDA(cudaGetLastError());

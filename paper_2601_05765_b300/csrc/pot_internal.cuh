@@ -83,6 +83,46 @@ __device__ __forceinline__ double r_div(double a, double b) { return __ddiv_rn(a
 __device__ __forceinline__ float r_sqrt(float a) { return __fsqrt_rn(a); }
 __device__ __forceinline__ double r_sqrt(double a) { return __dsqrt_rn(a); }
 
+// Sums of FP32 products carried as an unevaluated pair hi + lo of floats
+// (double-float): each product a b is split exactly into p + e (one FMA)
+// and each addition is Knuth's error-free two-sum, so a thread's partial
+// over a few terms keeps about 44 bits while running on FP32 units alone
+// (the FP64 units of this GPU issue at a small fraction of the FP32 rate).
+// The partial becomes a double once, for the FP64 block and grid sums.
+struct DF {
+  float hi = 0.f, lo = 0.f;
+};
+__device__ __forceinline__ void df_add_prod(DF& s, float a, float b) {
+  const float p = a * b;
+  const float e = fmaf(a, b, -p);  // p + e = a b exactly
+  const float t = s.hi + p;
+  const float bp = t - s.hi;
+  const float err = (s.hi - (t - bp)) + (p - bp);  // s.hi + p = t + err exactly
+  s.hi = t;
+  s.lo += err + e;
+}
+__device__ __forceinline__ double df_value(const DF& s) { return (double)s.hi + (double)s.lo; }
+
+// Max of the non-negative values m of a block's threads into *out, one
+// atomic per block (non-negative IEEE values order like their bit patterns
+// read as signed integers).  Every thread of the block must call it.
+template <typename T>
+__device__ __forceinline__ void block_max_to(T m, T* out) {
+  __shared__ T sh[32];
+  for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_down_sync(kFull, m, off));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)((blockDim.x + 31) >> 5); w++) m = fmax(m, sh[w]);
+    if (m > T(0)) {
+      if (sizeof(T) == 4)
+        atomicMax((int*)out, __float_as_int((float)m));
+      else
+        atomicMax((unsigned long long*)out, (unsigned long long)__double_as_longlong((double)m));
+    }
+  }
+}
+
 // Bisector (radical) plane of sites i and j seen from i (Eq. 1):
 // points y - p_i with y.n <= h, n = (p_j - p_i)/d,
 // h = (d^2 + psi_i - psi_j) / (2 d).  Returns d2 (0 for coincident sites).
@@ -146,6 +186,7 @@ struct Work {
   T* z = nullptr;
   T* p0 = nullptr;
   T* p1 = nullptr;
+  T* zp = nullptr;          // PCG: (z, p) interleaved, 2 per site
   T* q = nullptr;
   T* vel_s = nullptr;       // sorted velocities, 3 per site
   T* psi_max = nullptr;     // device scalar: max psi of the current evaluation
