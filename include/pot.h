@@ -151,8 +151,10 @@ typedef struct {
  * planes, in strongly compressed fluid (sites much closer than nu^(1/3))
  * cells reach past several neighbours and need more.  A cell that needs
  * more than k_max gives POT_ERR_NEIGHBOUR_OVERFLOW.  Workspace: about
- * 16 k_max + 280 bytes per site and precision.  Newton solves and fluid
- * steps on the same sites reuse the previous solve's cell centres.
+ * 16 k_max + 1000 bytes per site for each precision in precision_mask
+ * (about 9.9 GB for the FP32 entry points at 2M sites and k_max 246).
+ * Newton solves and fluid steps on the same sites reuse the previous
+ * solve's cell centres.
  * precision_mask: bit 0 = FP32 geometry (mixed-precision entry points),
  * bit 1 = FP64 entry points (*_f64).
  * Returns POT_ERR_INVALID_ARG / POT_ERR_CUDA on failure (*ctx = NULL). */

@@ -276,7 +276,7 @@ int pot_create(pot_ctx** out, int device, int64_t n_max, int32_t k_max, int32_t 
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   ctx->sm_count = sms > 0 ? sms : 148;
-  ctx->grid_cap = n_max * 2 > (1 << 16) ? n_max * 2 : (1 << 16);
+  ctx->grid_cap = n_max * 8 > (1 << 16) ? n_max * 8 : (1 << 16);
   const int64_t n = n_max, k = k_max;
   int s = POT_OK;
 #define A(ptr, cnt) \

@@ -120,13 +120,15 @@ int grid_build(pot_ctx* ctx, cudaStream_t st, int64_t n, const T* pos, const T* 
     ext[k] = dom->hi[k] - dom->lo[k];
     emax = fmax(emax, ext[k]);
   }
-  // cell ~ a few site spacings: the diameter of the largest ball, but no more
-  // than 3 nu_max^(1/3) (weights grow like a pressure inside deep fluid, so
-  // the largest ball says little about the spacing); the search of a cell
-  // covers as many grid cells as its radius needs.  Never more cells than
-  // the grid capacity.
-  double cs = 2.0 * sqrt(pmax);
-  if (numax > 0.0) cs = fmin(cs, 3.0 * cbrt(numax));
+  // cell ~ a couple of site spacings: 0.7 times the diameter of the largest
+  // ball, but no more than 2.1 nu_max^(1/3) (weights grow like a pressure
+  // inside deep fluid, so the largest ball says little about the spacing);
+  // the search of a cell covers as many grid cells as its radius needs.
+  // (Measured on the 2M splash: the cell kernel runs 6 % faster on the order
+  // of this grid than on one of cells 1/0.7 as wide, the candidate pass a
+  // little slower.)  Never more cells than the grid capacity.
+  double cs = 1.4 * sqrt(pmax);
+  if (numax > 0.0) cs = fmin(cs, 2.1 * cbrt(numax));
   cs = fmax(cs, emax / 1024.0);
   int dim[3];
   for (;;) {
