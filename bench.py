@@ -49,14 +49,14 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 SMALL_SPACING = 0.032  # ~2000 sites with the splash recipe
-# FP32 FLOP of the cell work (fadd + fmul + 2 ffma executed by the version
-# that runs only the edge pieces that occur; the current kernel executes
-# 12,988 per cell, adding exact zeros for the absent pieces) and DRAM bytes
-# per cell processed by k_cells, from ncu captures of the splash recipe at
-# 536k sites, step 30 (the bench's run in miniature);
-# profiles/k_cells_splash_536k_step30.md
-K_CELLS_FLOP_PER_CELL = 10049.0
-K_CELLS_DRAM_BYTES_PER_CELL = 385.0
+# Per cell processed by k_cells, from an ncu capture of one launch on the
+# splash recipe at 536k sites, step 30 (the bench's run in miniature;
+# profiles/k_cells_splash_536k_step30.md): FP32 FLOP executed (fadd + fmul +
+# 2 ffma of the instruction mix), warp instructions issued, and DRAM bytes
+# (cold caches: ncu flushes them before the launch).
+K_CELLS_FLOP_PER_CELL = 5479.0
+K_CELLS_WARP_INST_PER_CELL = 871.2
+K_CELLS_DRAM_BYTES_PER_CELL = 377.6
 
 
 def parse():
@@ -88,6 +88,9 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the other workloads' numbers (FP32 peak, 2^20 cloud, 1000-site solve)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--pcg-host-loop", action="store_true",
+                    help="step mode: host-driven PCG launches instead of the device-side loop "
+                         "(slower; lets a profiler see every PCG kernel)")
     return ap.parse_args()
 
 
@@ -252,8 +255,11 @@ def k_cells_roofline(kc, clocks, sm_count, fp32_peak=None):
     2 ffma) counted by ncu on the splash at converged weights; peak = the
     FP32 FMA throughput measured on this GPU by the library's FMA-chain
     kernel (else SMs x 128 FP32 lanes x 2 FLOP x the median SM clock sampled
-    during the timed region).  Traffic per launch = DRAM bytes per processed
-    cell from the same capture x cells per launch."""
+    during the timed region).  The kernel is mostly control, shuffles and
+    shared-memory traffic around its FP32 math, so the instruction issue
+    rate is given too: warp instructions per cell from the same capture
+    against 4 issue slots per SM per clock.  Traffic per launch = DRAM bytes
+    per processed cell from the same capture x cells per launch."""
     if not kc["launches"] or kc["ms"] <= 0:
         return None
     mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2032.0
@@ -274,6 +280,11 @@ def k_cells_roofline(kc, clocks, sm_count, fp32_peak=None):
         out["frac"] = out["achieved"] / peak
     if K_CELLS_DRAM_BYTES_PER_CELL:
         out["traffic"] = K_CELLS_DRAM_BYTES_PER_CELL * cells_per_launch
+    issue_peak = sm_count * 4 * mhz * 1e6 / 1e9
+    issue = K_CELLS_WARP_INST_PER_CELL * cells_per_launch / (launch_ms / 1e3) / 1e9
+    out["issue"] = {"achieved": issue, "peak": issue_peak, "unit": "G warp instructions/s",
+                    "frac": issue / issue_peak,
+                    "peak_kind": f"{sm_count} SMs x 4 issue slots x {mhz:.0f} MHz"}
     return out
 
 
@@ -365,7 +376,8 @@ def run_ours(args):
     vel = torch.from_numpy(sc.vel).to(dev)
     psi = torch.from_numpy(sc.psi).to(dev)
     nu = torch.from_numpy(sc.nu).to(dev)
-    prm = pot.default_params(dt=sc.extra["dt"], eps=sc.extra["eps"])
+    prm = pot.default_params(dt=sc.extra["dt"], eps=sc.extra["eps"],
+                             pcg_host_loop=1 if args.pcg_host_loop else 0)
     stream = torch.cuda.current_stream()
 
     # the recipe's start state (untimed): sites at their cell centroids
@@ -463,6 +475,8 @@ def run_ours(args):
                              f"+/-3 m/s along x, lattice spacing s = {args.spacing:g} jittered by 0.3 s "
                              f"(seed {3 + rank}), nu = 0.9 s^3, spring eps = s/16, dt = eps/2",
                    "parallelism": f"replicas x{world}",
+                   "pcg": ("host-driven launches (profiling run)" if args.pcg_host_loop
+                           else "device-side loop"),
                    "l2": "working set > 126 MB L2, no flush"},
         "newton_solve_ms": {"median": solve_ms[len(solve_ms) // 2],
                             "p90": solve_ms[min(len(solve_ms) - 1, int(0.9 * len(solve_ms)))]},

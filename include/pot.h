@@ -98,7 +98,8 @@ typedef struct {
   int32_t max_newton;   /* Newton iteration cap (100, Sec. 7) */
   int32_t max_halvings; /* KMT step halvings per iteration (30) */
   int32_t max_pcg;      /* PCG iteration cap per Newton step (2000) */
-  int32_t pcg_chunk;    /* PCG iterations per CUDA-graph launch (16) */
+  int32_t pcg_chunk;    /* PCG iterations per host-driven batch of launches (16;
+                           see pcg_host_loop) */
   double pcg_rtol;      /* PCG relative residual; <= 0 selects the adaptive
                            forcing term (default) */
   double dt;            /* fluid step (2e-3) */
@@ -114,6 +115,14 @@ typedef struct {
   double mu_wall;       /* fluid-wall affinity of the viscosity (walls at rest; 0: none) */
   double gamma_wall;    /* the walls' part of the surface tension: surface tension times
                            the fluid's affinity to the walls (Sec. 5; 0: none) */
+  int32_t pcg_host_loop; /* 0: each PCG solve runs on the device alone (one
+                           persistent cooperative kernel for up to 2^17 rows,
+                           else a CUDA graph whose while node repeats the two
+                           iteration kernels); 1: the host launches the two
+                           kernels pcg_chunk iterations at a time and checks
+                           for convergence between batches (slower; every
+                           launch visible to a profiler) */
+  int32_t reserved_params; /* 0 */
 } pot_params;
 
 /* Statistics of one Newton solve (and of the solve inside a fluid step). */

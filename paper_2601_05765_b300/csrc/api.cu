@@ -108,7 +108,8 @@ bool check_params(const pot_params* p) {
   return p && p->tol > 0.0 && p->max_newton >= 0 && p->max_halvings >= 0 && p->max_pcg > 0 &&
          p->pcg_chunk > 0 && isfinite(p->dt) && p->eps > 0.0 && p->substeps >= 0 &&
          p->mu >= 0.0 && p->gamma >= 0.0 && p->mu_wall >= 0.0 && isfinite(p->mu) &&
-         isfinite(p->gamma) && isfinite(p->mu_wall) && isfinite(p->gamma_wall);
+         isfinite(p->gamma) && isfinite(p->mu_wall) && isfinite(p->gamma_wall) &&
+         (p->pcg_host_loop == 0 || p->pcg_host_loop == 1);
 }
 
 template <typename T, typename CSR>

@@ -336,7 +336,8 @@ int newton_sorted_impl(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domai
     int iters = 0;
     {
       EvTimer tm(ctx, 1, st);
-      int ps = pcg_solve<T>(ctx, st, n, nnz_off, rtol, P->max_pcg, P->pcg_chunk, &iters, nullptr);
+      int ps = pcg_solve<T>(ctx, st, n, nnz_off, rtol, P->max_pcg, P->pcg_chunk,
+                            P->pcg_host_loop != 0, &iters, nullptr);
       S->ms_pcg += tm.stop();
       S->pcg_iters += iters;
       if (ps != POT_OK) return ps;
@@ -481,8 +482,8 @@ int fluid_substep(pot_ctx* ctx, cudaStream_t st, int64_t n, T* pos, T* vel, T* p
           k_visc_b<T><<<blocks_for(n, 256), 256, 0, st>>>(n, w.vel_s, c, ctx->grad);
           int iters = 0;
           const double rtol = sizeof(T) == 4 ? 1e-6 : 1e-11;
-          POT_CHECK(pcg_solve<T>(ctx, st, n, nnz_off, rtol, P->max_pcg, P->pcg_chunk, &iters,
-                                 nullptr));
+          POT_CHECK(pcg_solve<T>(ctx, st, n, nnz_off, rtol, P->max_pcg, P->pcg_chunk,
+                                 P->pcg_host_loop != 0, &iters, nullptr));
           S->visc_iters += iters;
         }
         note_launch();

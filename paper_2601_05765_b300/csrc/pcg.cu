@@ -27,7 +27,8 @@
 // k_update's block 0 alone ends the loop (cudaGraphSetConditional): when an
 // earlier kernel has set the done flag, or when its own trip counter passes
 // the cap + 1, so the loop ends even if the done flag were never set.  The
-// host waits once per solve.  Without the graph (its construction failed)
+// host waits once per solve.  Without the graph (its construction failed,
+// or the caller asked for host-driven launches, pot_params.pcg_host_loop)
 // the same kernels run in chunks from the host, which checks the done flag
 // once per chunk.
 #include "pot_internal.cuh"
@@ -522,7 +523,7 @@ int build_graph(pot_ctx* ctx, int64_t n, int nb, double* part, double* scal) {
 
 template <typename T>
 int pcg_solve(pot_ctx* ctx, cudaStream_t st, int64_t n, int64_t nnz_off, double rtol, int max_iter,
-              int chunk, int* iters, double* rel_res) {
+              int chunk, bool host_loop, int* iters, double* rel_res) {
   (void)nnz_off;
   Work<T>& w = ctx->work<T>();
   // one full wave of the SpMV kernel: as many blocks as fit on the SMs
@@ -546,7 +547,7 @@ int pcg_solve(pot_ctx* ctx, cudaStream_t st, int64_t n, int64_t nnz_off, double 
   // 12.6 -> 9.3 ms per FP64 solve with the persistent kernel)
   int coop = 0, per_coop = 0;
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device);
-  if (coop && n <= kPcgCoopMaxRows &&
+  if (coop && !host_loop && n <= kPcgCoopMaxRows &&
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_coop, k_pcg_coop<T>, kPcgThreads,
                                                             0) == cudaSuccess &&
       per_coop >= 1) {
@@ -585,8 +586,8 @@ int pcg_solve(pot_ctx* ctx, cudaStream_t st, int64_t n, int64_t nnz_off, double 
                                             part, scal, nb, ctx->pcg_ctl, rtol2, max_iter);
   POT_CUDA(cudaGetLastError());
   const int gk = sizeof(T) == 4 ? 0 : 1;
-  bool graph = ctx->pcg_exec[gk] && ctx->pcg_graph_n[gk] == n;
-  if (!graph) {
+  bool graph = !host_loop && ctx->pcg_exec[gk] && ctx->pcg_graph_n[gk] == n;
+  if (!graph && !host_loop) {
     graph = build_graph<T>(ctx, n, nb, part, scal) == POT_OK;
     if (!graph) cudaGetLastError();  // clear it: the chunked loop below runs instead
   }
@@ -622,9 +623,9 @@ int pcg_solve(pot_ctx* ctx, cudaStream_t st, int64_t n, int64_t nnz_off, double 
   return POT_OK;
 }
 
-template int pcg_solve<float>(pot_ctx*, cudaStream_t, int64_t, int64_t, double, int, int, int*,
-                              double*);
-template int pcg_solve<double>(pot_ctx*, cudaStream_t, int64_t, int64_t, double, int, int, int*,
-                               double*);
+template int pcg_solve<float>(pot_ctx*, cudaStream_t, int64_t, int64_t, double, int, int, bool,
+                              int*, double*);
+template int pcg_solve<double>(pot_ctx*, cudaStream_t, int64_t, int64_t, double, int, int, bool,
+                               int*, double*);
 
 }  // namespace pot

@@ -366,6 +366,6 @@ int pcg_blocks(int sm_count);       // largest grid of the PCG kernels
 size_t pcg_red_len(int sm_count);   // doubles of ctx->pcg_red
 template <typename T>
 int pcg_solve(pot_ctx* ctx, cudaStream_t st, int64_t n, int64_t nnz_off, double rtol, int max_iter,
-              int chunk, int* iters, double* rel_res);
+              int chunk, bool host_loop, int* iters, double* rel_res);
 
 }  // namespace pot

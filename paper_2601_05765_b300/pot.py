@@ -56,7 +56,8 @@ class Params(ctypes.Structure):
                 ("dt", ctypes.c_double), ("eps", ctypes.c_double), ("gravity", ctypes.c_double * 3),
                 ("wall_margin", ctypes.c_double), ("warm_start", ctypes.c_int32),
                 ("substeps", ctypes.c_int32), ("mu", ctypes.c_double), ("gamma", ctypes.c_double),
-                ("mu_wall", ctypes.c_double), ("gamma_wall", ctypes.c_double)]
+                ("mu_wall", ctypes.c_double), ("gamma_wall", ctypes.c_double),
+                ("pcg_host_loop", ctypes.c_int32), ("reserved_params", ctypes.c_int32)]
 
 
 class SolveStats(ctypes.Structure):
