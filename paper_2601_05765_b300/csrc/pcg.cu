@@ -13,13 +13,14 @@
 // z and p are stored interleaved, (z_j, p_j) per row: the SpMV gathers both
 // with one 8-byte (16-byte in FP64) load per entry, and k_update writes the
 // pair (z_new, p_new) of its row.
-// Dot products accumulate per thread exactly in FP64 (FP64 vectors) or in
-// double-float on the FP32 units (FP32 vectors), then in FP64 per block
-// (fixed tree), then over blocks by the last block to finish (an arrival
-// counter after a memory fence), which adds the block partials in index
-// order and publishes
-// the scalars and the decisions (converged, breakdown) for the next kernel.
-// The result is deterministic and no block re-reads all partials.
+// Dot products accumulate per thread, then per block (fixed tree), then
+// over blocks by the last block to finish (an arrival counter after a
+// memory fence), which adds the block partials in index order and publishes
+// the scalars, the next step length and the decisions (converged,
+// breakdown) for the next kernel: exactly in FP64 for FP64 vectors, in
+// double-float on the FP32 units for FP32 vectors (this GPU's FP64 units
+// issue at a small fraction of the FP32 rate).  The result is deterministic
+// and no block re-reads all partials.
 //
 // The iterations run as a CUDA graph: a while node whose body is the two
 // kernels, built once per context, precision and row count (the tolerance
@@ -39,18 +40,49 @@ namespace {
 constexpr int kPcgThreads = 256;
 constexpr int kTpr = 2;  // threads per CSR row (about 10 entries per row)
 
-// A thread's partial of a dot product: exact FP64 sums of the products of
-// FP64 vectors; double-float sums (FP32 units only) of FP32 vectors
+// Partial sums of dot products: exact FP64 sums of the products of FP64
+// vectors; double-float sums (FP32 units only) of FP32 vectors, kept in
+// double-float through the block and grid sums and converted to FP64 once,
+// for the scalars.  A partial travels between blocks in one 8-byte word (a
+// double, or the two floats of a double-float).
 template <typename T>
 struct Dot {
   double s = 0.0;
   __device__ __forceinline__ void add(T a, T b) { s += a * b; }
+  __device__ __forceinline__ void merge(const Dot& o) { s += o.s; }
+  __device__ __forceinline__ Dot down(int off) const {
+    Dot d;
+    d.s = __shfl_down_sync(kFull, s, off);
+    return d;
+  }
+  __device__ __forceinline__ double pack() const { return s; }
+  __device__ __forceinline__ static Dot unpack(double w) {
+    Dot d;
+    d.s = w;
+    return d;
+  }
   __device__ __forceinline__ double value() const { return s; }
 };
 template <>
 struct Dot<float> {
   DF s;
   __device__ __forceinline__ void add(float a, float b) { df_add_prod(s, a, b); }
+  __device__ __forceinline__ void merge(const Dot& o) { df_add(s, o.s); }
+  __device__ __forceinline__ Dot down(int off) const {
+    Dot d;
+    d.s.hi = __shfl_down_sync(kFull, s.hi, off);
+    d.s.lo = __shfl_down_sync(kFull, s.lo, off);
+    return d;
+  }
+  __device__ __forceinline__ double pack() const {
+    return __hiloint2double(__float_as_int(s.hi), __float_as_int(s.lo));
+  }
+  __device__ __forceinline__ static Dot unpack(double w) {
+    Dot d;
+    d.s.hi = __int_as_float(__double2hiint(w));
+    d.s.lo = __int_as_float(__double2loint(w));
+    return d;
+  }
   __device__ __forceinline__ double value() const { return df_value(s); }
 };
 
@@ -60,9 +92,16 @@ struct alignas(2 * sizeof(T)) ZP {
   T z, p;
 };
 
-// partial-sum arrays (nb doubles each) and scalars at the end of pcg_red
+// partial-sum arrays (nb packed partials each) and scalars at the end of
+// pcg_red; the step lengths alpha and beta, formed once per iteration by
+// the last block of the kernel before, sit in the scalars' last two
+// doubles as T values
 enum { kPartA = 0, kPartB = 1, kPartC = 2, kParts = 3 };
-enum { kRZ = 0, kRZP = 1, kPQ = 2, kRR = 3, kRR0 = 4, kRtol2 = 5, kScalars = 8 };
+enum { kRZ = 0, kRZP = 1, kPQ = 2, kRR = 3, kRR0 = 4, kRtol2 = 5, kSteps = 6, kScalars = 8 };
+template <typename T>
+__device__ __forceinline__ T* steps(double* scal) {  // [0] alpha, [1] beta
+  return reinterpret_cast<T*>(scal + kSteps);
+}
 // control words (ctx->pcg_ctl holds 8)
 enum { kDone = 0, kIt = 1, kBreak = 2, kIters = 3, kArrive = 4, kTrips = 5, kMaxIt = 6,
        kBar = 8, kTimeout = 9 };
@@ -73,31 +112,33 @@ constexpr int kBarrierSpins = 1 << 24;
 // largest system solved by the persistent kernel
 constexpr int64_t kPcgCoopMaxRows = 1 << 17;
 
-// Block sum of v (fixed shape) into thread 0's return value.
-__device__ __forceinline__ double block_sum(double v) {
+// Block sum of v (fixed tree) into thread 0's return value.
+template <typename T>
+__device__ __forceinline__ Dot<T> block_sum(Dot<T> v) {
   __shared__ double sh[kPcgThreads / 32];
-  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(kFull, v, off);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  for (int off = 16; off > 0; off >>= 1) v.merge(v.down(off));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v.pack();
   __syncthreads();
-  double s = 0.0;
+  Dot<T> s;
   if (threadIdx.x == 0)
-    for (int w = 0; w < kPcgThreads / 32; w++) s += sh[w];
+    for (int w = 0; w < kPcgThreads / 32; w++) s.merge(Dot<T>::unpack(sh[w]));
   __syncthreads();
   return s;
 }
 
 // Publish up to three block partials; returns true in every thread of the
 // block that arrived last (which then sees every block's partials).
-__device__ __forceinline__ bool arrive(double* part, int nb, int count, double a, double b,
-                                       double c, int32_t* ctl) {
+template <typename T>
+__device__ __forceinline__ bool arrive(double* part, int nb, int count, const Dot<T>& a,
+                                       const Dot<T>& b, const Dot<T>& c, int32_t* ctl) {
   __shared__ bool last;
-  a = block_sum(a);
-  if (count > 1) b = block_sum(b);
-  if (count > 2) c = block_sum(c);
+  const Dot<T> sa = block_sum(a);
+  const Dot<T> sb = count > 1 ? block_sum(b) : Dot<T>();
+  const Dot<T> sc = count > 2 ? block_sum(c) : Dot<T>();
   if (threadIdx.x == 0) {
-    part[kPartA * nb + blockIdx.x] = a;
-    if (count > 1) part[kPartB * nb + blockIdx.x] = b;
-    if (count > 2) part[kPartC * nb + blockIdx.x] = c;
+    part[kPartA * nb + blockIdx.x] = sa.pack();
+    if (count > 1) part[kPartB * nb + blockIdx.x] = sb.pack();
+    if (count > 2) part[kPartC * nb + blockIdx.x] = sc.pack();
     __threadfence();
     last = atomicAdd(&ctl[kArrive], 1) == nb - 1;
   }
@@ -108,34 +149,11 @@ __device__ __forceinline__ bool arrive(double* part, int nb, int count, double a
 
 // Sum of nb partials in index order (strided per thread, fixed tree), in
 // thread 0; called by the last block only.
-__device__ __forceinline__ double sum_parts(const double* part, int nb) {
-  double s = 0.0;
-  for (int b = threadIdx.x; b < nb; b += kPcgThreads) s += __ldcg(part + b);
+template <typename T>
+__device__ __forceinline__ Dot<T> sum_parts(const double* part, int nb) {
+  Dot<T> s;
+  for (int b = threadIdx.x; b < nb; b += kPcgThreads) s.merge(Dot<T>::unpack(__ldcg(part + b)));
   return block_sum(s);
-}
-
-// Block sum of v (fixed tree), returned to every thread of the block.
-__device__ __forceinline__ double block_sum_all(double v) {
-  __shared__ double sh[kPcgThreads / 32];
-  __shared__ double res;
-  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(kFull, v, off);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < kPcgThreads / 32; w++) s += sh[w];
-    res = s;
-  }
-  __syncthreads();
-  return res;
-}
-
-// Sum of the nb block partials in index order (the same fixed tree in every
-// block, so every block gets the same bits), returned to every thread.
-__device__ __forceinline__ double sum_parts_all(const double* part, int nb) {
-  double s = 0.0;
-  for (int b = threadIdx.x; b < nb; b += kPcgThreads) s += __ldcg(part + b);
-  return block_sum_all(s);
 }
 
 // Grid-wide barrier of the persistent solve (a cooperative launch, every
@@ -186,10 +204,12 @@ __global__ void __launch_bounds__(kPcgThreads)
     rz.add(ri, zi);
     rr.add(ri, ri);
   }
-  if (arrive(part, nb, 2, rz.value(), rr.value(), 0.0, ctl)) {
-    const double trz = sum_parts(part + kPartA * nb, nb);
-    const double trr = sum_parts(part + kPartB * nb, nb);
+  if (arrive(part, nb, 2, rz, rr, Dot<T>(), ctl)) {
+    const Dot<T> rzs = sum_parts<T>(part + kPartA * nb, nb);
+    const Dot<T> rrs = sum_parts<T>(part + kPartB * nb, nb);
     if (threadIdx.x == 0) {
+      const double trz = rzs.value(), trr = rrs.value();
+      steps<T>(scal)[1] = T(0);  // beta of the first iteration
       scal[kRZ] = trz;
       scal[kRZP] = 1.0;
       scal[kRR] = trr;
@@ -214,7 +234,7 @@ __global__ void __launch_bounds__(kPcgThreads)
            int32_t* ctl) {
   if (ctl[kDone]) return;
   const int it = ctl[kIt];
-  const T beta = it == 0 ? T(0) : (T)(scal[kRZ] / scal[kRZP]);
+  const T beta = steps<T>(scal)[1];
   const int sub = threadIdx.x & (kTpr - 1);
   Dot<T> pq;
   const int64_t groups = (int64_t)gridDim.x * (blockDim.x / kTpr);
@@ -245,10 +265,12 @@ __global__ void __launch_bounds__(kPcgThreads)
       pq.add(pi, qi);
     }
   }
-  if (arrive(part, nb, 1, pq.value(), 0.0, 0.0, ctl)) {
-    const double tpq = sum_parts(part + kPartA * nb, nb);
+  if (arrive(part, nb, 1, pq, Dot<T>(), Dot<T>(), ctl)) {
+    const Dot<T> pqs = sum_parts<T>(part + kPartA * nb, nb);
     if (threadIdx.x == 0) {
+      const double tpq = pqs.value();
       scal[kPQ] = tpq;
+      steps<T>(scal)[0] = (T)(scal[kRZ] / tpq);  // alpha
       if (!(tpq > 0.0)) {  // M not positive definite along p: breakdown
         ctl[kBreak] = 1;
         ctl[kIters] = it;
@@ -277,10 +299,9 @@ __global__ void __launch_bounds__(kPcgThreads, kUpdBlocksPerSm)
     if (ctl[kDone] || trips > ctl[kMaxIt] + 1) cudaGraphSetConditional(loop, 0u);
   }
   if (ctl[kDone]) return;
-  const double rtol2 = scal[kRtol2];
   const int max_iter = ctl[kMaxIt];
   const int it = ctl[kIt];
-  const T alpha = (T)(scal[kRZ] / scal[kPQ]);
+  const T alpha = steps<T>(scal)[0];
   Dot<T> rzn, rr;
   const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n;
@@ -311,15 +332,17 @@ __global__ void __launch_bounds__(kPcgThreads, kUpdBlocksPerSm)
       }
     }
   }
-  if (arrive(part, nb, 2, rzn.value(), rr.value(), 0.0, ctl)) {
-    const double trz = sum_parts(part + kPartA * nb, nb);
-    const double trr = sum_parts(part + kPartB * nb, nb);
+  if (arrive(part, nb, 2, rzn, rr, Dot<T>(), ctl)) {
+    const Dot<T> rzs = sum_parts<T>(part + kPartA * nb, nb);
+    const Dot<T> rrs = sum_parts<T>(part + kPartB * nb, nb);
     if (threadIdx.x == 0) {
+      const double trz = rzs.value(), trr = rrs.value();
+      steps<T>(scal)[1] = (T)(trz / scal[kRZ]);  // beta of the next iteration
       scal[kRZP] = scal[kRZ];
       scal[kRZ] = trz;
       scal[kRR] = trr;
       ctl[kIt] = it + 1;
-      if (trr <= rtol2 * scal[kRR0] || it + 1 >= max_iter) {
+      if (trr <= scal[kRtol2] * scal[kRR0] || it + 1 >= max_iter) {
         ctl[kIters] = it + 1;
         ctl[kDone] = 1;
       }
@@ -337,8 +360,10 @@ __global__ void __launch_bounds__(kPcgThreads, kUpdBlocksPerSm)
 // barrier; beta and the convergence test, again from the ordered sums, so
 // every block takes the same decisions.  Data other blocks wrote within the
 // launch is read through L2 (ld.cg): an SM's L1 is not kept coherent.
+// Thread 0 of each block forms the scalars; the block gets the step length
+// and the decision through shared memory.
 template <typename T>
-__global__ void __launch_bounds__(kPcgThreads, 5)
+__global__ void __launch_bounds__(kPcgThreads, 4)
     k_pcg_coop(int64_t n, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ cols,
                const T* __restrict__ vals, const T* __restrict__ diag,
                const double* __restrict__ b, T* x, T* r, T* z, T* pa, T* pb, T* q, T* dinv,
@@ -351,6 +376,12 @@ __global__ void __launch_bounds__(kPcgThreads, 5)
   int32_t* counter = ctl + kBar;
   int32_t* timeout = ctl + kTimeout;
   int gen = 0;
+  // thread 0 of every block forms the scalars from the ordered partial sums
+  // (the same bits in every block) and hands the block the step length and
+  // the decision
+  __shared__ T s_step;
+  __shared__ int s_state;  // 0: go on, 1: converged or at the cap, 2: breakdown
+  double trz = 0.0, trr0 = 0.0;
   Dot<T> rz0, rr0;
   for (int64_t i = tid; i < n; i += nthr) {
     const T d = diag[i];
@@ -365,26 +396,34 @@ __global__ void __launch_bounds__(kPcgThreads, 5)
     rz0.add(ri, zi);
     rr0.add(ri, ri);
   }
-  const double rz = block_sum_all(rz0.value());
-  const double rr = block_sum_all(rr0.value());
-  if (threadIdx.x == 0) {
-    Prz[blockIdx.x] = rz;
-    Prr[blockIdx.x] = rr;
+  {
+    const Dot<T> rzb = block_sum(rz0), rrb = block_sum(rr0);
+    if (threadIdx.x == 0) {
+      Prz[blockIdx.x] = rzb.pack();
+      Prr[blockIdx.x] = rrb.pack();
+    }
   }
   if (!grid_barrier(counter, timeout, ++gen * nb)) return;
-  double trz = sum_parts_all(Prz, nb);
-  const double trr0 = sum_parts_all(Prr, nb);
-  double trz_prev = 1.0;
+  {
+    const Dot<T> rzs = sum_parts<T>(Prz, nb), rrs = sum_parts<T>(Prr, nb);
+    if (threadIdx.x == 0) {
+      trz = rzs.value();
+      trr0 = rrs.value();
+      s_step = T(0);  // beta of the first iteration
+      s_state = !(trr0 > 0.0) || max_iter <= 0 ? 1 : 0;
+    }
+    __syncthreads();
+  }
   int it = 0;
   bool brk = false;
-  bool done = !(trr0 > 0.0) || max_iter <= 0;
+  bool done = s_state != 0;
   const int sub = threadIdx.x & (kTpr - 1);
   const int64_t groups = nthr / kTpr;
   // rows rounded up to a multiple of the group count: every lane of a warp
   // runs the same number of row iterations (full-mask shuffles)
   const int64_t n_round = ((n + groups - 1) / groups) * groups;
   while (!done) {
-    const T beta = it == 0 ? T(0) : (T)(trz / trz_prev);
+    const T beta = s_step;
     const T* pold = (it & 1) ? pb : pa;
     T* pnew = (it & 1) ? pa : pb;
     Dot<T> pqt;
@@ -408,15 +447,27 @@ __global__ void __launch_bounds__(kPcgThreads, 5)
         pqt.add(pi, qi);
       }
     }
-    const double pq = block_sum_all(pqt.value());
-    if (threadIdx.x == 0) Ppq[blockIdx.x] = pq;
+    {
+      const Dot<T> pqb = block_sum(pqt);
+      if (threadIdx.x == 0) Ppq[blockIdx.x] = pqb.pack();
+    }
     if (!grid_barrier(counter, timeout, ++gen * nb)) return;
-    const double tpq = sum_parts_all(Ppq, nb);
-    if (!(tpq > 0.0)) {  // M not positive definite along p: breakdown
+    {
+      const Dot<T> pqs = sum_parts<T>(Ppq, nb);
+      if (threadIdx.x == 0) {
+        const double tpq = pqs.value();
+        if (tpq > 0.0)
+          s_step = (T)(trz / tpq);  // alpha
+        else
+          s_state = 2;  // M not positive definite along p: breakdown
+      }
+      __syncthreads();
+    }
+    if (s_state == 2) {
       brk = true;
       break;
     }
-    const T alpha = (T)(trz / tpq);
+    const T alpha = s_step;
     Dot<T> rzt, rrt;
     for (int64_t i = tid; i < n; i += nthr) {
       x[i] += alpha * __ldcg(pnew + i);
@@ -427,18 +478,26 @@ __global__ void __launch_bounds__(kPcgThreads, 5)
       rzt.add(ri, zi);
       rrt.add(ri, ri);
     }
-    const double rzn = block_sum_all(rzt.value());
-    const double rrn = block_sum_all(rrt.value());
-    if (threadIdx.x == 0) {
-      Prz[blockIdx.x] = rzn;
-      Prr[blockIdx.x] = rrn;
+    {
+      const Dot<T> rzb = block_sum(rzt), rrb = block_sum(rrt);
+      if (threadIdx.x == 0) {
+        Prz[blockIdx.x] = rzb.pack();
+        Prr[blockIdx.x] = rrb.pack();
+      }
     }
     if (!grid_barrier(counter, timeout, ++gen * nb)) return;
-    trz_prev = trz;
-    trz = sum_parts_all(Prz, nb);
-    const double trr = sum_parts_all(Prr, nb);
     it++;
-    done = trr <= rtol2 * trr0 || it >= max_iter;
+    {
+      const Dot<T> rzs = sum_parts<T>(Prz, nb), rrs = sum_parts<T>(Prr, nb);
+      if (threadIdx.x == 0) {
+        const double trz_new = rzs.value(), trr = rrs.value();
+        s_step = (T)(trz_new / trz);  // beta of the next iteration
+        trz = trz_new;
+        s_state = trr <= rtol2 * trr0 || it >= max_iter ? 1 : 0;
+      }
+      __syncthreads();
+    }
+    done = s_state != 0;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     ctl[kIters] = it;

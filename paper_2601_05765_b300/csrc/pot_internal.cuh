@@ -101,6 +101,13 @@ __device__ __forceinline__ void df_add_prod(DF& s, float a, float b) {
   s.hi = t;
   s.lo += err + e;
 }
+__device__ __forceinline__ void df_add(DF& s, const DF& o) {
+  const float t = s.hi + o.hi;
+  const float bp = t - s.hi;
+  const float err = (s.hi - (t - bp)) + (o.hi - bp);  // s.hi + o.hi = t + err exactly
+  s.hi = t;
+  s.lo += err + o.lo;
+}
 __device__ __forceinline__ double df_value(const DF& s) { return (double)s.hi + (double)s.lo; }
 
 // Max of the non-negative values m of a block's threads into *out, one
