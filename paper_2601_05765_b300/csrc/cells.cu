@@ -1921,9 +1921,14 @@ int cells_eval(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* dom, 
     box.lo[k] = (T)dom->lo[k];
     box.hi[k] = (T)dom->hi[k];
   }
-  const int64_t ncell = (int64_t)w.grid.dim[0] * w.grid.dim[1] * w.grid.dim[2];
-  note_launch();
-  k_gmax<T><<<blocks_for(ncell, 256), 256, 0, st>>>(ncell, ctx->cell_start, w.sxp, w.gmax);
+  // the largest weight of each grid cell bounds h for the walk of a pass
+  // without neighbour lists; a walk that builds lists takes every site
+  // within its reach and does not need it
+  if (!(w.verlet && w.vlist)) {
+    const int64_t ncell = (int64_t)w.grid.dim[0] * w.grid.dim[1] * w.grid.dim[2];
+    note_launch();
+    k_gmax<T><<<blocks_for(ncell, 256), 256, 0, st>>>(ncell, ctx->cell_start, w.sxp, w.gmax);
+  }
   note_launch();
   k_srad_init<T><<<blocks_for(n, 256), 256, 0, st>>>(
       n, w.sxp, ctx->snu, w.rcell, w.have_rcell ? 1 : 0, w.rcell_acc, w.have_acc ? 1 : 0, ctx->perm,
@@ -2025,6 +2030,11 @@ int cells_eval(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* dom, 
 template <typename T>
 int repair_empty(pot_ctx* ctx, cudaStream_t st, int64_t n, int* repaired) {
   Work<T>& w = ctx->work<T>();
+  // the largest weight of each grid cell (an evaluation with neighbour
+  // lists does not form it)
+  const int64_t ncell = (int64_t)w.grid.dim[0] * w.grid.dim[1] * w.grid.dim[2];
+  note_launch();
+  k_gmax<T><<<blocks_for(ncell, 256), 256, 0, st>>>(ncell, ctx->cell_start, w.sxp, w.gmax);
   POT_CUDA(cudaMemsetAsync(ctx->need_count, 0, sizeof(int32_t), st));
   note_launch();
   k_repair<T><<<blocks_for(n, 256), 256, 0, st>>>(n, w.sxp, w.psi_base, w.vol, ctx->cell_start, w.grid,
