@@ -279,13 +279,15 @@ int lgc_compute_cells_noalloc(void* stream, int64_t n, const float* pos, const f
  * eps0 = 1/2 min(min nu, min V(psi_start)).  Stops when
  * max_i |V_i - nu_i| / nu_i <= params->tol.
  * psi_inout: start (must give non-empty cells) in, solution out.
- * Mixed precision: FP32 geometry and matrix, FP64 residuals, PCG dot
- * products and KMT test.  This entry point stops at 0.9 params->tol on its
- * FP32-evaluated error, a margin for the FP32 rounding of the volumes (about
- * 1e-6 of the target), so the weights meet params->tol in exact arithmetic;
- * its KMT test also accepts the same decrease of the max relative error (the
- * l2 norm of an FP32 evaluation stalls at its rounding floor).  Errors: POT_ERR_EMPTY_CELL_AT_START (if the repair
- * fails),
+ * Mixed precision: FP32 geometry and matrix; the residual sums and PCG dot
+ * products accumulate the FP32 terms in double-float (about 44 bits) and
+ * give FP64 scalars, and the KMT test and step lengths run in FP64.  This
+ * entry point stops at 0.9 params->tol on its FP32-evaluated error, a
+ * margin for the FP32 rounding of the volumes (about 1e-6 of the target),
+ * so the weights meet params->tol in exact arithmetic; its KMT test also
+ * accepts the same decrease of the max relative error (the l2 norm of an
+ * FP32 evaluation stalls at its rounding floor).  Errors:
+ * POT_ERR_EMPTY_CELL_AT_START (if the repair fails),
  * POT_ERR_NOT_CONVERGED, POT_ERR_LINESEARCH_FAILED, geometry errors.
  * psi_inout holds the last accepted iterate on NOT_CONVERGED. */
 int pot_newton_solve(pot_ctx* ctx, void* stream, int64_t n, const float* pos, const double* targets,
