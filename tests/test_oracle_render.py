@@ -83,3 +83,63 @@ def test_volume_closed_forms():
     first, thick, _ = O.render_volume(np.array([[0.5, 0.5, 0.05]]), [0.1 ** 2], o, f, up,
                                       math.radians(10), 5, 5)
     assert abs(first[2, 2] - 1.0) < 1e-12 and abs(thick[2, 2] - 0.15) < 1e-12
+
+
+def test_smooth_single_ball_is_the_ball():
+    """One ball has no neighbours: its smoothed surface is its sphere, so
+    sphere tracing stops within the hit tolerance of the exact entry, with
+    the sphere's normal; rays outside the silhouette miss."""
+    o, f, up = (0.5, 0.5, -1.0), (0.0, 0.0, 1.0), (0.0, 1.0, 0.0)
+    p = np.array([[0.5, 0.5, 0.5]])
+    r, k = 0.2, 0.02
+    depth, normal, steps = O.render_smooth(p, [r * r], o, f, up, math.radians(30), 21, 15, k)
+    ref, refn = O.render_depth(p, [r * r], o, f, up, math.radians(30), 21, 15)
+    hit = ref >= 0
+    assert np.array_equal(depth >= 0, hit)
+    d = O.camera_rays(o, f, up, math.radians(30), 21, 15)
+    cos = -np.sum(d * refn, axis=2)  # ray against the outward normal
+    # the march stops where f <= 1e-3 k: before the sphere by at most that / cos
+    gap = ref[hit] - depth[hit]
+    assert np.all(gap >= -1e-12) and np.all(gap <= O.SMOOTH_HIT * k / cos[hit] + 1e-12)
+    np.testing.assert_allclose(normal[hit], refn[hit], atol=2e-3)
+    assert steps.max() < O.SMOOTH_MAX_STEPS
+
+
+def test_smooth_bridge_between_two_balls():
+    """Two equal overlapping balls (centres at x = 0.5 -/+ a) are Laguerre
+    neighbours.  On their mid plane both distances are D - r (D from either
+    centre), so the cubic smooth union is D - r - k/6: a ray in that plane
+    meets the surface where D = r + k/6 -- the bridge the smoothing adds
+    above the crease of the two spheres (a closed form)."""
+    a, r, k = 0.06, 0.1, 0.03
+    p = np.array([[0.5 - a, 0.5, 0.5], [0.5 + a, 0.5, 0.5]])
+    psi = np.array([r * r, r * r])
+    for y0 in (0.0, 0.02, 0.04):
+        o = (0.5, 0.5 + y0, 1.5)  # straight down, in the plane x = 0.5
+        depth, normal, _ = O.render_smooth(p, psi, o, (0.0, 0.0, -1.0), (0.0, 1.0, 0.0),
+                                           math.radians(10), 1, 1, k)
+        zc = math.sqrt((r + k / 6) ** 2 - a * a - y0 * y0)
+        t_exact = 1.0 - zc
+        cos = zc / (r + k / 6)
+        assert -1e-12 <= t_exact - depth[0, 0] <= O.SMOOTH_HIT * k / cos + 1e-12
+        # the normal is the bisector of the two spheres' normals: no x part
+        n_exact = np.array([0.0, y0, zc]) / math.hypot(y0, zc)
+        np.testing.assert_allclose(normal[0, 0], n_exact, atol=1e-2)
+        # the union of the balls alone (the crease, D = r) lies below
+        assert 1.0 - math.sqrt(r * r - a * a - y0 * y0) > t_exact + 0.1 * k
+
+
+def test_smooth_small_k_is_the_union():
+    """As k goes to 0 the smooth union tends to the union of the balls: on
+    a random cloud the hits agree with the first-hit oracle."""
+    rng = np.random.default_rng(5)
+    n = 60
+    pos = rng.uniform(0.3, 0.7, (n, 3))
+    psi = rng.uniform(0.04, 0.08, n) ** 2
+    o, f, up = (0.5, 0.5, -0.5), (0.0, 0.0, 1.0), (0.0, 1.0, 0.0)
+    k = 1e-5
+    depth, _, steps = O.render_smooth(pos, psi, o, f, up, math.radians(30), 24, 18, k)
+    ref, _ = O.render_depth(pos, psi, o, f, up, math.radians(30), 24, 18)
+    both = (depth >= 0) & (ref >= 0)
+    assert np.mean((depth >= 0) == (ref >= 0)) > 0.99
+    assert np.max(np.abs(depth[both] - ref[both])) < 1e-4
