@@ -794,7 +794,9 @@ def run_render(args):
     """First hit of camera rays (pot_render_depth) on the 2M splash after
     `advance` fluid steps from the recipe's start state: a 1920 x 1080 depth
     and normal image, median of `steps` frames after `warmup`, with the
-    balls of cells without free surface skipped and without."""
+    balls of cells without free surface skipped and without; then the
+    volume traversal and the sphere tracing of the smoothed surface over
+    the same frame."""
     import math
 
     import torch
@@ -847,8 +849,29 @@ def run_render(args):
                      "cells_per_ray_mean": float(visits[hit].float().mean()),
                      "cells_per_ray_max": int(visits.max()),
                      "note": "includes the cell evaluation at these weights"}
-    print(json.dumps({"metric": "camera rays per second, first hit on the fluid (pot_render_depth) "
-                                "and volume traversal (pot_render_volume)",
+    # sphere tracing of the smoothed surface, smoothing radius half a spacing
+    ks = 0.5 * args.spacing
+    for _ in range(args.warmup):
+        pot.render_smooth(ctx, pos, psi, k=ks, **cam)
+    times = []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        sd, _, sst = pot.render_smooth(ctx, pos, psi, k=ks, **cam)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    times.sort()
+    ms = times[len(times) // 2]
+    hit = sd >= 0
+    out["smooth"] = {"ms_per_frame": ms, "rays_per_s": 1920 * 1080 / (ms / 1e3),
+                     "k": ks, "hit_fraction": float(hit.float().mean()),
+                     "steps_per_ray_mean": float(sst.float().mean()),
+                     "steps_per_ray_max": int(sst.max()),
+                     "note": "includes the cell evaluation at these weights"}
+    print(json.dumps({"metric": "camera rays per second, first hit on the fluid (pot_render_depth), "
+                                "volume traversal (pot_render_volume) and sphere tracing of the "
+                                "smoothed surface (pot_render_smooth)",
                       "workload": f"two-ball splash, {n} sites, step {args.advance}, 1920 x 1080, "
                                   f"grid build included",
                       "free_surface_cells": int((karea > 0).sum()), **out}))

@@ -473,6 +473,31 @@ int pot_render_volume(pot_ctx* ctx, void* stream, int64_t n, const float* pos, c
                       const pot_domain* dom, const pot_camera* cam, float* first,
                       float* thickness, float* last, int32_t* visits);
 
+/* ---- smoothed free surface (Sec. 6, surface smoothing) ----------------- */
+
+/* Sphere-trace each camera ray to the smoothed free surface: the cells at
+ * (pos, psi) are evaluated first (as lgc_compute_cells does); at a ray
+ * point x the closest site i (least |x - p_i| - r_i) and its Laguerre
+ * neighbourhood (the sites sharing a restricted facet with it) give the
+ * signed distance f = smin_k(d_(1), d_(2)), the cubic polynomial smooth
+ * union of the two nearest spheres of that set with smoothing radius
+ * k_smooth (smin_k(a, b) = min(a, b) - k h^3 / 6, h = max(k - |a - b|, 0)
+ * / k).  A ray point farther than k/6 from every ball jumps to the next
+ * entry into the balls grown by k/6; otherwise the march steps by f (at
+ * least 1e-4 k) and stops at f <= 1e-3 k, after at most 1024 evaluations.
+ * Per pixel (height x width, row-major, device buffers written on
+ * `stream`): depth: t of the hit (-1: none); normal (3 per pixel,
+ * optional): the unit gradient of f there (0: none); steps (optional,
+ * int32): evaluations of f taken.  pos (n,3), psi (n) device arrays in
+ * caller order.  Camera as in pot_render_depth; no graphics API.  Uses
+ * ctx's FP32 workspace (its cell data are overwritten).
+ * Errors: POT_ERR_INVALID_ARG (NULL pointers, n out of range, an FP64-only
+ * context, k_smooth not positive and finite, a bad camera or box), the
+ * geometry errors of lgc_compute_cells, POT_ERR_CUDA. */
+int pot_render_smooth(pot_ctx* ctx, void* stream, int64_t n, const float* pos, const float* psi,
+                      const pot_domain* dom, const pot_camera* cam, float k_smooth, float* depth,
+                      float* normal, int32_t* steps);
+
 #ifdef __cplusplus
 }
 #endif

@@ -546,31 +546,8 @@ def laguerre_neighbours(pos, psi, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0)):
     return nb
 
 
-def render_smooth(pos, psi, origin, forward, up, fov_y, width, height, k,
-                  lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), pixels=None, neighbours=None):
-    """First hit of each camera ray on the smoothed fluid surface by sphere
-    tracing (Sec. 6, surface smoothing; readings above).  All rays march
-    together; every step is brute force over all balls.  Returns depth (t
-    of the hit, -1 when none), the unit normal there (gradient of f; 0 when
-    none) and the evaluations of f taken per ray, each (height, width[, 3]),
-    or per pixel of `pixels`.  Parity unpinned beyond the closed forms of
-    tests/test_oracle_render.py (one ball; the bridge of two balls)."""
-    pos = np.asarray(pos, np.float64)
-    psi = np.asarray(psi, np.float64)
-    o = np.asarray(origin, np.float64)
-    d = camera_rays(origin, forward, up, fov_y, width, height).reshape(-1, 3)
-    if pixels is not None:
-        d = d[np.asarray(pixels)]
-    nb = laguerre_neighbours(pos, psi, lo, hi) if neighbours is None else neighbours
-    lo = np.asarray(lo, np.float64)
-    hi = np.asarray(hi, np.float64)
-    with np.errstate(divide="ignore", invalid="ignore"):
-        ta = (lo[None, :] - o[None, :]) / d
-        tb = (hi[None, :] - o[None, :]) / d
-    t0 = np.max(np.minimum(ta, tb), axis=1).clip(min=0.0)
-    t1 = np.min(np.maximum(ta, tb), axis=1)
-    r = np.sqrt(np.maximum(psi, 0.0))
-    live = psi > 0
+def _smooth_march(o, d, t0, t1, pos, r, live, nb, k):
+    """The sphere-tracing march of render_smooth for a block of rays."""
     grow = k / 6.0
     m = d.shape[0]
     t = t0.copy()
@@ -641,6 +618,42 @@ def render_smooth(pos, psi, origin, forward, up, fov_y, width, height, k,
         t[rest] += np.maximum(f[~done], SMOOTH_MIN_STEP * k)
         act[rest] &= (t[rest] <= t1[rest]) & (steps[rest] < SMOOTH_MAX_STEPS)
         act[idx[far]] &= steps[idx[far]] < SMOOTH_MAX_STEPS
+    return depth, normal, steps
+
+
+def render_smooth(pos, psi, origin, forward, up, fov_y, width, height, k,
+                  lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), pixels=None, neighbours=None):
+    """First hit of each camera ray on the smoothed fluid surface by sphere
+    tracing (Sec. 6, surface smoothing; readings above).  Rays march in
+    blocks of 256; every step is brute force over all balls.  Returns depth (t
+    of the hit, -1 when none), the unit normal there (gradient of f; 0 when
+    none) and the evaluations of f taken per ray, each (height, width[, 3]),
+    or per pixel of `pixels`.  Parity unpinned beyond the closed forms of
+    tests/test_oracle_render.py (one ball; the bridge of two balls)."""
+    pos = np.asarray(pos, np.float64)
+    psi = np.asarray(psi, np.float64)
+    o = np.asarray(origin, np.float64)
+    d = camera_rays(origin, forward, up, fov_y, width, height).reshape(-1, 3)
+    if pixels is not None:
+        d = d[np.asarray(pixels)]
+    nb = laguerre_neighbours(pos, psi, lo, hi) if neighbours is None else neighbours
+    lo = np.asarray(lo, np.float64)
+    hi = np.asarray(hi, np.float64)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        ta = (lo[None, :] - o[None, :]) / d
+        tb = (hi[None, :] - o[None, :]) / d
+    t0 = np.max(np.minimum(ta, tb), axis=1).clip(min=0.0)
+    t1 = np.min(np.maximum(ta, tb), axis=1)
+    r = np.sqrt(np.maximum(psi, 0.0))
+    live = psi > 0
+    m = d.shape[0]
+    depth = np.full(m, -1.0)
+    normal = np.zeros((m, 3))
+    steps = np.zeros(m, np.int64)
+    for b0 in range(0, m, 256):  # blocks of rays march together
+        sl = slice(b0, min(m, b0 + 256))
+        depth[sl], normal[sl], steps[sl] = _smooth_march(o, d[sl], t0[sl], t1[sl], pos, r, live,
+                                                         nb, k)
     if pixels is not None:
         return depth, normal, steps
     return depth.reshape(height, width), normal.reshape(height, width, 3), steps.reshape(height, width)

@@ -56,12 +56,14 @@ __device__ __forceinline__ bool ball_interval(const V4<float>& p, const float* o
 // a ball entered at t has its centre within that many cells of the cell
 // holding the ray point at t, so once a cell is entered beyond the best
 // entry no later ball can be nearer and the walk stops.  Balls for which
-// skip(s) holds are left out.  Returns the entry t (INFINITY: none) and the
-// site in *hit (-1: none).
+// skip(s) holds are left out.  With grow > 0 the balls' radii are grown by
+// it (layers must then cover r_max + grow).  Returns the entry t (INFINITY:
+// none) and the site in *hit (-1: none).
 template <typename Skip>
 __device__ float next_entry(const float* o, const float* d, float t_from, float t_end,
                             const V4<float>* __restrict__ sxp, const int32_t* __restrict__ cell_start,
-                            const GridParams<float>& g, int layers, Skip skip, int* hit) {
+                            const GridParams<float>& g, int layers, Skip skip, int* hit,
+                            float grow = 0.f) {
   float best = INFINITY;
   int besti = -1;
   if (t_from < t_end) {
@@ -85,8 +87,12 @@ __device__ float next_entry(const float* o, const float* d, float t_from, float 
           const int key0 = (z * g.dim[1] + y) * g.dim[0];
           const int a = cell_start[key0 + x0], b = cell_start[key0 + x1 + 1];
           for (int s = a; s < b; s++) {
-            const V4<float> p = sxp[s];
+            V4<float> p = sxp[s];
             if (!(p.w > 0.f) || skip(s)) continue;
+            if (grow > 0.f) {
+              const float rg = sqrtf(p.w) + grow;
+              p.w = rg * rg;
+            }
             float ta, tb;
             if (!ball_interval(p, o, d, ta, tb)) continue;
             const float t = fmaxf(ta, t_from);
@@ -283,6 +289,134 @@ __global__ void __launch_bounds__(128)
   if (visits) visits[pix] = nv;
 }
 
+// The site whose ball surface is nearest x, argmin |x - p| - r over the
+// sites within `layers` grid cells (every site whose grown ball, radius
+// r + grow, holds x is that near when layers covers r_max + grow); -1 and
+// INFINITY when there is none.
+__device__ int nearest_surface(const float* x, const V4<float>* __restrict__ sxp,
+                               const int32_t* __restrict__ cell_start, const GridParams<float>& g,
+                               int layers, float& dmin) {
+  int c[3];
+  for (int k = 0; k < 3; k++) c[k] = rcell(x[k], g.lo[k], g.inv_cs, g.dim[k]);
+  float best = INFINITY;
+  int besti = -1;
+  for (int z = max(c[2] - layers, 0); z <= min(c[2] + layers, g.dim[2] - 1); z++)
+    for (int y = max(c[1] - layers, 0); y <= min(c[1] + layers, g.dim[1] - 1); y++) {
+      const int key0 = (z * g.dim[1] + y) * g.dim[0];
+      const int a = cell_start[key0 + max(c[0] - layers, 0)];
+      const int b = cell_start[key0 + min(c[0] + layers, g.dim[0] - 1) + 1];
+      for (int s = a; s < b; s++) {
+        const V4<float> p = sxp[s];
+        if (!(p.w > 0.f)) continue;
+        const float dx = x[0] - p.x, dy = x[1] - p.y, dz = x[2] - p.z;
+        const float dist = sqrtf(dx * dx + dy * dy + dz * dz) - sqrtf(p.w);
+        if (dist < best) {
+          best = dist;
+          besti = s;
+        }
+      }
+    }
+  dmin = best;
+  return besti;
+}
+
+// Sphere tracing of the smoothed free surface (Sec. 6, surface smoothing).
+// The signed distance of ball i is d_i(x) = |x - p_i| - r_i; at x the
+// closest site i (nearest ball surface) and its Laguerre neighbourhood (the
+// sites of its Hessian row: restricted facets above the emission
+// threshold) give f = smin_k(d_(1), d_(2)), the cubic polynomial smooth
+// union of the two nearest spheres of that set, smin_k(a, b) = min(a, b) -
+// k h^3 / 6 with h = max(k - |a - b|, 0) / k.  f is 1-Lipschitz within one
+// neighbourhood and f >= d_(1) - k/6, so the surface {f = 0} lies within
+// k/6 of the balls: a ray point farther than that from every ball jumps to
+// the next entry into the balls grown by k/6 (the grid walk), otherwise the
+// march steps by f (at least kSmoothMinStep k) and stops at f <= kSmoothHit
+// k.  Outputs per pixel: t of the hit (-1: none), the unit normal there
+// (the smooth minimum's blend of the two spheres' normals; 0: none), and
+// the evaluations taken (at most kSmoothMaxSteps).
+constexpr float kSmoothHit = 1e-3f;
+constexpr float kSmoothMinStep = 1e-4f;
+constexpr int kSmoothMaxSteps = 1024;
+
+__global__ void __launch_bounds__(128)
+    k_render_smooth(Ray cam, Box<float> box, const V4<float>* __restrict__ sxp,
+                    const int32_t* __restrict__ cell_start, GridParams<float> g, int layers,
+                    const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ cols,
+                    float k, float* depth, float* normal, int32_t* steps) {
+  const int px = blockIdx.x * blockDim.x + threadIdx.x;
+  const int py = blockIdx.y * blockDim.y + threadIdx.y;
+  if (px >= cam.w || py >= cam.h) return;
+  float d[3];
+  pixel_ray(cam, px, py, d);
+  float t0, t1;
+  box_span(box, cam.o, d, t0, t1);
+  const float grow = k / 6.f;
+  float t = t0, hit_t = -1.f;
+  float nrm[3] = {0.f, 0.f, 0.f};
+  int ns = 0;
+  while (t <= t1 && ns < kSmoothMaxSteps) {
+    ns++;
+    const float x[3] = {cam.o[0] + t * d[0], cam.o[1] + t * d[1], cam.o[2] + t * d[2]};
+    float d1;
+    const int i = nearest_surface(x, sxp, cell_start, g, layers, d1);
+    if (!(d1 <= grow)) {
+      // farther than k/6 from every ball: the next entry into the grown balls
+      int s = -1;
+      const float te = next_entry(cam.o, d, t, t1, sxp, cell_start, g, layers,
+                                  [](int) { return false; }, &s, grow);
+      if (s < 0 || te > t1) break;
+      if (te > t || i < 0) {
+        t = fmaxf(te, t + kSmoothMinStep * k * (te > t ? 0.f : 1.f));
+        continue;
+      }
+      // at the grown surface within rounding: a step of the march
+    }
+    const V4<float> p = sxp[i];
+    float d2 = INFINITY;
+    int j2 = -1;
+    for (int e = row_ptr[i]; e < row_ptr[i + 1]; e++) {
+      const int j = cols[e];
+      const V4<float> q = sxp[j];
+      if (!(q.w > 0.f)) continue;
+      const float dx = x[0] - q.x, dy = x[1] - q.y, dz = x[2] - q.z;
+      const float dj = sqrtf(dx * dx + dy * dy + dz * dz) - sqrtf(q.w);
+      if (dj < d2) {
+        d2 = dj;
+        j2 = j;
+      }
+    }
+    float f = d1, h = 0.f;
+    if (j2 >= 0) {
+      h = fmaxf(k - fabsf(d1 - d2), 0.f) / k;
+      f = fminf(d1, d2) - k * h * h * h / 6.f;
+    }
+    if (f <= kSmoothHit * k) {
+      hit_t = t;
+      // d(smin)/da = 1 - h^2/2 for the smaller distance a, h^2/2 for the other
+      const float wlo = 1.f - 0.5f * h * h;
+      const float w1 = d1 <= d2 ? wlo : 1.f - wlo;
+      float g1[3] = {x[0] - p.x, x[1] - p.y, x[2] - p.z};
+      const float l1 = rsqrtf(g1[0] * g1[0] + g1[1] * g1[1] + g1[2] * g1[2]);
+      for (int c = 0; c < 3; c++) nrm[c] = w1 * g1[c] * l1;
+      if (j2 >= 0) {
+        const V4<float> q = sxp[j2];
+        float g2[3] = {x[0] - q.x, x[1] - q.y, x[2] - q.z};
+        const float l2 = rsqrtf(g2[0] * g2[0] + g2[1] * g2[1] + g2[2] * g2[2]);
+        for (int c = 0; c < 3; c++) nrm[c] += (1.f - w1) * g2[c] * l2;
+      }
+      const float ln = rsqrtf(nrm[0] * nrm[0] + nrm[1] * nrm[1] + nrm[2] * nrm[2]);
+      for (int c = 0; c < 3; c++) nrm[c] *= ln;
+      break;
+    }
+    t += fmaxf(f, kSmoothMinStep * k);
+  }
+  const int pix = py * cam.w + px;
+  depth[pix] = hit_t;
+  if (normal)
+    for (int c = 0; c < 3; c++) normal[3 * pix + c] = nrm[c];
+  if (steps) steps[pix] = ns;
+}
+
 }  // namespace
 }  // namespace pot
 
@@ -389,6 +523,48 @@ extern "C" int pot_render_volume(pot_ctx* ctx, void* stream, int64_t n, const fl
   note_launch();
   k_render_volume<<<grd, blk, 0, st>>>(ray, box, w.sxp, w.karea, ctx->cell_start, w.grid, layers,
                                        ctx->row_ptr, ctx->csr_cols, first, thickness, last, visits);
+  POT_CUDA(cudaGetLastError());
+  POT_CUDA(cudaStreamSynchronize(st));
+  return POT_OK;
+}
+
+extern "C" int pot_render_smooth(pot_ctx* ctx, void* stream, int64_t n, const float* pos,
+                                 const float* psi, const pot_domain* dom, const pot_camera* cam,
+                                 float k_smooth, float* depth, float* normal, int32_t* steps) {
+  if (!ctx || !pos || !psi || !dom || !cam || !depth || n <= 0 || n > ctx->n_max ||
+      !(ctx->mask & 1) || !(k_smooth > 0.f) || !isfinite(k_smooth))
+    return POT_ERR_INVALID_ARG;
+  for (int k = 0; k < 3; k++)
+    if (!(dom->hi[k] > dom->lo[k])) return POT_ERR_INVALID_ARG;
+  Ray ray;
+  POT_CHECK(make_ray(cam, ray));
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return POT_ERR_CUDA;
+  cudaStream_t st = (cudaStream_t)stream;
+  // the cells at these weights: the Laguerre neighbourhoods are the Hessian
+  // rows' columns (sorted space)
+  POT_CHECK(grid_build<float>(ctx, st, n, pos, psi, nullptr, dom));
+  const double rmax = sqrt(fmax((double)*(float*)ctx->h_pinned, 0.0));
+  Work<float>& w = ctx->wf;
+  const int ce = cells_eval<float>(ctx, st, n, dom, false);
+  int64_t site = -1;
+  const int code = read_status(ctx, st, &site);
+  if (code != POT_OK) return code;
+  POT_CHECK(ce);
+  int64_t nnz_off = 0;
+  POT_CHECK(csr_compact<float>(ctx, st, n, &nnz_off));
+  // grid layers covering the grown balls, r_max + k/6
+  const int layers =
+      (int)fmax(1.0, ceil((rmax + (double)k_smooth / 6.0) / (double)w.grid.cs));
+  Box<float> box;
+  for (int k = 0; k < 3; k++) {
+    box.lo[k] = (float)dom->lo[k];
+    box.hi[k] = (float)dom->hi[k];
+  }
+  dim3 blk(16, 8), grd((cam->width + 15) / 16, (cam->height + 7) / 8);
+  note_launch();
+  k_render_smooth<<<grd, blk, 0, st>>>(ray, box, w.sxp, ctx->cell_start, w.grid, layers,
+                                       ctx->row_ptr, ctx->csr_cols, k_smooth, depth, normal,
+                                       steps);
   POT_CUDA(cudaGetLastError());
   POT_CUDA(cudaStreamSynchronize(st));
   return POT_OK;

@@ -143,6 +143,9 @@ def lib():
         L.pot_render_volume.argtypes = [P, P, I64, P, P, ctypes.POINTER(Domain),
                                         ctypes.POINTER(Camera), P, P, P, P]
         L.pot_render_volume.restype = ctypes.c_int
+        L.pot_render_smooth.argtypes = [P, P, I64, P, P, ctypes.POINTER(Domain),
+                                        ctypes.POINTER(Camera), ctypes.c_float, P, P, P]
+        L.pot_render_smooth.restype = ctypes.c_int
         L.pot_measure_fp32_peak.argtypes = [P, P, ctypes.POINTER(ctypes.c_double),
                                             ctypes.POINTER(ctypes.c_double)]
         L.pot_measure_fp32_peak.restype = ctypes.c_int
@@ -418,6 +421,30 @@ def render_volume(ctx: Context, pos, psi, origin, forward, up, fov_y, width, hei
     if code != POT_OK:
         raise PotError(code, "pot_render_volume")
     return first, thick, last, vis
+
+
+def render_smooth(ctx: Context, pos, psi, origin, forward, up, fov_y, width, height, k,
+                  domain=UNIT_BOX, stream=None, normals=True, steps=True):
+    """Sphere-trace camera rays to the smoothed free surface with smoothing
+    radius k (pot_render_smooth): returns (depth, normal or None, steps or
+    None), (height, width[, 3]) on the device."""
+    dev = ctx.device
+    n = int(pos.shape[0])
+    pos = _dev(pos, torch.float32, (n, 3), "pos", dev)
+    psi = _dev(psi, torch.float32, (n,), "psi", dev)
+    depth = torch.empty((height, width), dtype=torch.float32, device=dev)
+    nrm = torch.empty((height, width, 3), dtype=torch.float32, device=dev) if normals else None
+    st = torch.empty((height, width), dtype=torch.int32, device=dev) if steps else None
+    cam = Camera()
+    for c in range(3):
+        cam.origin[c], cam.forward[c], cam.up[c] = float(origin[c]), float(forward[c]), float(up[c])
+    cam.fov_y, cam.width, cam.height = float(fov_y), int(width), int(height)
+    code = lib().pot_render_smooth(ctx.handle, _stream(stream), n, _ptr(pos), _ptr(psi),
+                                   ctypes.byref(_domain(domain)), ctypes.byref(cam), float(k),
+                                   _ptr(depth), _ptr(nrm), _ptr(st))
+    if code != POT_OK:
+        raise PotError(code, "pot_render_smooth")
+    return depth, nrm, st
 
 
 def set_viscosity_factors(ctx: Context, factors):

@@ -130,3 +130,54 @@ def test_volume_traversal_full_size_sampled():
                                      np.percentile(el, 99), int(vis.max())))
     assert np.percentile(et, 99) < 1e-4 and np.percentile(el, 99) < 1e-4 and np.percentile(ef, 99) < 1e-5
     ctx.close()
+
+
+def test_smooth_surface_matches_oracle():
+    """Sphere tracing of the smoothed free surface (pot_render_smooth, Sec.
+    6) on the small splash during its impact, smoothing radius half a
+    spacing, against the oracle's march over all balls with its own FP64
+    cells: hit or miss agree except on rays that graze the surface or cross
+    where the closest site changes (f jumps there), depths agree to the
+    march's stopping tolerance, normals to FP32 precision."""
+    sc = scenes.splash(spacing=0.02, seed=3)
+    n = sc.n
+    dev = torch.device("cuda", 0)
+    ctx = pot.Context(n, 246, 0, fp64=False)
+    pos, vel, psi, nu = (torch.from_numpy(a).to(dev) for a in (sc.pos, sc.vel, sc.psi, sc.nu))
+    prm = pot.default_params(dt=sc.extra["dt"], eps=sc.extra["eps"])
+    pot.relax_to_centroids(ctx, pos, psi, nu, sc.extra["relax_rounds"], params=prm)
+    for _ in range(20):
+        pot.pot_fluid_step(ctx, pos, vel, psi, nu, params=prm)
+    k = 0.5 * 0.02
+    cam = dict(origin=(0.5, -0.9, 0.8), forward=(0.0, 1.0, -0.55), up=(0.0, 0.0, 1.0),
+               fov_y=math.radians(40), width=64, height=48)
+    depth, normal, steps = pot.render_smooth(ctx, pos, psi, k=k, **cam)
+    x, s = to_np(pos).astype(np.float64), to_np(psi).astype(np.float64)
+    rd, rn, rs = O.render_smooth(x, s, k=k, **cam)
+    gd, gn, gs = (to_np(a).astype(np.float64) for a in (depth, normal, steps))
+    hit, ref_hit = gd >= 0, rd >= 0
+    assert ref_hit.mean() > 0.1 and (~ref_hit).mean() > 0.1
+    disagree = np.mean(hit != ref_hit)
+    both = hit & ref_hit
+    scale = float(rd.max())
+    err = np.abs(gd - rd)[both] / scale
+    dots = np.sum(gn[both] * rn[both], axis=1)
+    print("smooth surface: hit disagreement %.2e; depth err / max p50 %.2e p99 %.2e max %.2e;"
+          " normal dot p1 %.5f; steps max %d mean %.1f (oracle %d %.1f)"
+          % (disagree, np.median(err), np.percentile(err, 99), err.max(), np.percentile(dots, 1),
+             gs.max(), gs.mean(), rs.max(), rs.mean()))
+    assert disagree < 1e-2
+    # the march stops within 1e-3 k of f = 0 on both sides
+    assert np.percentile(err, 99) < 1e-3 * k / scale * 20
+    assert np.mean(err > 1e-2) < 1e-2  # a jump of the closest site may move a few hits
+    assert np.all(np.abs(np.linalg.norm(gn[both], axis=1) - 1) < 1e-3)
+    assert np.mean(dots > 0.99) > 0.98
+    assert np.mean(gs >= 1024) < 1e-2
+    # the smoothing only adds fluid: every ray that meets the balls meets
+    # the smoothed surface no later
+    d0, _ = pot.render_depth(ctx, pos, psi, **cam)
+    g0 = to_np(d0).astype(np.float64)
+    ok = (g0 >= 0) & hit
+    assert np.mean(g0 >= 0) <= np.mean(hit) + 1e-3
+    assert np.mean(gd[ok] > g0[ok] + 1e-4 * scale) < 1e-2
+    ctx.close()
