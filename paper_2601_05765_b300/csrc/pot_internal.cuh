@@ -29,7 +29,7 @@ constexpr int kMaxK = 1024;        // candidate bisectors per cell (k_max <= 102
 constexpr int kPlaneCap = 252;     // planes of a cell kept without bisecting its security radius
 constexpr int kSmallPlanes = 32;   // planes of a cell in the cell kernel (32-bit crossing sets)
 constexpr int kVerletCap = 160;    // sites of a neighbour list of the candidate pass
-constexpr float kVerletReach = 1.2f;  // a list's reach over the reach it was built for
+constexpr float kVerletReach = 1.05f;  // a list's reach over the reach it was built for
 constexpr int kBigPlanes = kMaxK + 6;  // planes of a cell in the big-cell kernel
 constexpr int kBigWarpsPerSm = 8;  // warps of the big-cell kernel per SM
 constexpr int kMaxLines = 24;      // edges of one facet polygon
