@@ -1068,6 +1068,7 @@ struct Window {
   T fa[kWin], fo[kWin], fx[kWin], fy[kWin], fr[kWin];  // facet area, solid angle, moment, extent
   uint8_t farc[kWin];
   LineRec<T> rec[32];  // the lines of the current round's tasks
+  uint8_t rstart[32];  // the round's slot (from its first) starting at each task offset
   int cex[33];      // first slot of each window cell
   int cpp[33];      // first plane pair of each window cell
   CellSlot<T> sc[32];
@@ -1264,20 +1265,38 @@ __global__ void __launch_bounds__(CellCfg<T>::warps * 32, sizeof(T) == 4 ? 6 : 2
       __syncwarp();
       const int ttot = carry;
       // rounds of whole facets (a facet has at most kSmallPlanes - 1 tasks):
-      // each task stages its line for the other tasks of its facet
-      for (int R = 0; R < ttot;) {
-        const int Rend = S.tpre[last_le(S.tpre, total + 1, R + 32)];
-        const int q = R + lane;
-        const bool act = q < Rend;
-        const int slot = act ? last_le(S.tpre, total, q) : 0;
+      // each task stages its line for the other tasks of its facet.  A
+      // round looks at the 32 slots from sR: lane l's slot starts its tasks
+      // at st (relative to R) and has nt of them; the slots whose tasks end
+      // by 32 form a prefix (st + nt is the next slot's st) and make the
+      // round; their facet starts, as bits, give each task lane its facet's
+      // first and last lane, and the slot is read back by its start.
+      for (int R = 0, sR = 0; R < ttot;) {
+        const int sl = sR + lane;
+        const bool sv = sl < total;
+        const int st = sv ? S.tpre[sl] - R : 64;
+        const int nt = sv ? S.tpre[sl + 1] - R - st : 0;
+        const bool fits = sv && st + nt <= 32;
+        const int span = __reduce_max_sync(kFull, fits ? st + nt : 0);
+        const unsigned starts = __reduce_or_sync(kFull, fits && nt > 0 ? 1u << st : 0u);
+        if (fits && nt > 0) S.rstart[st] = (uint8_t)lane;
+        const int sR0 = sR;
+        sR += __popc(__ballot_sync(kFull, fits));
+        __syncwarp();
+        const int Rend = R + span;
+        const bool act = lane < span;
+        const unsigned upto = 0xffffffffu >> (31 - lane);  // bits 0..lane
+        const int fs = act ? 31 - __clz(starts & upto) : lane;
+        const unsigned above = starts & ~upto;
+        const int slot = act ? sR0 + S.rstart[fs] : 0;
         const int c = act ? S.owner[slot] : 0;
         const T psc = __shfl_sync(kFull, pw.w, c);
         const T oir = __shfl_sync(kFull, irw, c);
         const T sox = __shfl_sync(kFull, oxw, c), soy = __shfl_sync(kFull, oyw, c),
                 soz = __shfl_sync(kFull, ozw, c);
         const bool ofull = __shfl_sync(kFull, fullw, c);
-        const int head = act ? S.tpre[slot] - R : lane;
-        const int last = act ? S.tpre[slot + 1] - 1 - R : lane;
+        const int head = fs;
+        const int last = !act ? lane : above ? __ffs(above) - 2 : span - 1;
         FacetFrame<T> fr = {};
         unsigned M = 0u;
         if (act) {
@@ -1286,7 +1305,7 @@ __global__ void __launch_bounds__(CellCfg<T>::warps * 32, sizeof(T) == 4 ? 6 : 2
           fr = facet_frame(P, psc, oir, sox, soy, soz);
           M = S.mask[slot];
           if (M) {
-            const int g = (int)__fns(M, 0, q - S.tpre[slot] + 1);
+            const int g = (int)__fns(M, 0, lane - head + 1);
             S.rec[lane] = line_rec(P, fr, S.pl[sb + g], g);
           }
         }
