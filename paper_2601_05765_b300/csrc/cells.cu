@@ -765,8 +765,9 @@ __device__ __forceinline__ bool write_cell(int64_t cell, const V4<T>& p, bool em
 // Append an ill-conditioned FP32 cell to the FP64 list and put its full
 // plane list back into its candidate row (the cell kernel rewrote the row in
 // place into its Hessian columns): j of its bisector planes, in plane order
-// after the walls.
-__device__ __forceinline__ void flag_fix(int64_t cell, int m, int nw, const int* pj, int kmax,
+// after the walls.  Rare (no fluid cell is listed), so kept out of line: the
+// cell kernel's code stays smaller.
+__device__ __noinline__ void flag_fix(int64_t cell, int m, int nw, const int* pj, int kmax,
                                          int32_t* cand, int32_t* fix_count, int32_t* fix_list) {
   fix_list[atomicAdd(fix_count, 1)] = (int32_t)cell;
   for (int f = nw; f < m; f++) cand[cell * kmax + (f - nw)] = pj[f];
