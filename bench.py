@@ -614,12 +614,22 @@ def run_warmstart(args):
         e = scene.extra
         return e["dt"] / e["substeps"], e["eps"], e["substeps"], e["relax_rounds"]
 
+    # the 76-input model of the configuration (no weight-change input; it
+    # corrects the previous weights), trained on the same runs
+    mlp76 = pot.Mlp(max(sc.n, 65536), 0)
+    mlp76.set_inputs(76)
+    mlp76.set_params(W.init_params(0, device=dev, n_inputs=76))
+    xs76, ys76 = [], []
     for k, col in enumerate(cols):
         dts, eps, nsub, relax = sub(col)
         x, y = W.collect(ctx_t, mlp, col, steps=40 * nsub, every=2, per_sample=4096, seed=10 + k,
                          dt=dts, eps=eps, relax=relax)
         xs.append(x)
         ys.append(y)
+        x, y = W.collect(ctx_t, mlp76, col, steps=40 * nsub, every=2, per_sample=4096, seed=10 + k,
+                         dt=dts, eps=eps, relax=relax, history=False)
+        xs76.append(x)
+        ys76.append(y)
     ctx_t.close()
     extra = "none"
     if args.train_splash:
@@ -639,12 +649,15 @@ def run_warmstart(args):
     hist = W.train(mlp, x, y, epochs=60, batch=8192, lr=1e-3)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
+    hist76 = W.train(mlp76, torch.cat(xs76), torch.cat(ys76), epochs=60, batch=8192, lr=1e-3)
 
     def both(ctx, scene, dt, warm, eps=0.01, relax=0):
         res = W.compare(ctx, mlp, scene, steps=args.steps, dt=dt, warm_steps=warm, eps=eps,
                         relax=relax)
+        res["mlp76"] = W.compare(ctx, mlp76, scene, steps=args.steps, dt=dt, warm_steps=warm,
+                                 eps=eps, relax=relax, modes=((1, "mlp"),))["mlp"]
         out = {}
-        for k in ("plain", "extrapolated", "mlp"):
+        for k in ("plain", "extrapolated", "mlp", "mlp76"):
             out[k] = W.summarize(res[k])
             ms = sorted(st["ms_total"] for st in res[k])
             out[k]["ms_total_median"] = ms[len(ms) // 2]
@@ -670,19 +683,23 @@ def run_warmstart(args):
                      "scenes": "dam-break columns 24x24x48, seeds 10-19, the substeps of their "
                                "first 40 steps of 2e-3",
                      "extra_scenes": extra},
-        "plain": plain, "extrapolated": spl["extrapolated"], "mlp": learned,
+        "training_76": {"loss_first": hist76[0], "loss_last": hist76[-1],
+                        "inputs": "24 neighbour offsets, previous weight, velocity (76); the "
+                                  "prediction corrects the previous weights"},
+        "plain": plain, "extrapolated": spl["extrapolated"], "mlp": learned, "mlp76": spl["mlp76"],
         "newton_iters_saved": plain["newton_iters"] - learned["newton_iters"],
         "ms_saved_per_solve": plain["ms_total"] - learned["ms_total"],
         "holdout_dam_break": {"workload": f"dam-break column 36x36x72 ({dam.n} sites), seed 20, "
                                           f"substeps {12 * nsub_d}..{12 * nsub_d + args.steps - 1} "
                                           f"of {dts:.3g}, eps {eps_d:.3g}",
                               "plain": held["plain"], "extrapolated": held["extrapolated"],
-                              "mlp": held["mlp"],
+                              "mlp": held["mlp"], "mlp76": held["mlp76"],
                               "newton_iters_saved": held["plain"]["newton_iters"] - held["mlp"]["newton_iters"],
                               "ms_saved_per_solve": held["plain"]["ms_total"] - held["mlp"]["ms_total"]}}))
     pot.set_warm_start(ctx, None)
     ctx.close()
     mlp.close()
+    mlp76.close()
 
 
 def _pcts(v):

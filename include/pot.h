@@ -404,6 +404,15 @@ int pot_mlp_features(pot_ctx* ctx, pot_mlp* mlp, void* stream, int64_t n, const 
                      const double* targets, const pot_domain* dom, const pot_params* params,
                      uint16_t* feat);
 
+/* Inputs of the model: 77 (default: the 24 neighbour offsets, the previous
+ * weight, the velocity and the previous weight change; the prediction
+ * corrects the extrapolation psi + (psi - psi_old)) or 76 (the inputs the
+ * warm-start configuration names, without the weight change: input 77 is
+ * 0 and the prediction corrects the previous weights, psi + h^2 y).  The
+ * features (pot_mlp_features) and the fluid step's warm start follow the
+ * choice.  Errors: POT_ERR_INVALID_ARG (mlp NULL, n_inputs not 76 or 77). */
+int pot_mlp_set_inputs(pot_mlp* mlp, int32_t n_inputs);
+
 /* Weight history of the warm start.  Each warm-started pot_fluid_step keeps
  * its starting weights (caller order) as the next step's psi_old, valid while
  * the site count stays n.  This call seeds the history with psi_old (device,

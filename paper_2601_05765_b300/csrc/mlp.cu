@@ -739,6 +739,7 @@ struct pot_mlp {
   float* dpsi_s = nullptr;    // features: previous weight change (sorted)
   float* psi_hist = nullptr;  // warm start: weights of the previous step (caller order)
   int64_t hist_n = -1;        // sites of psi_hist (-1: no history)
+  bool use_hist = true;       // 77 inputs (the previous weight change) or 76
 };
 
 namespace pot {
@@ -897,7 +898,7 @@ int mlp_features_sorted(pot_ctx* ctx, pot_mlp* mm, cudaStream_t st, int64_t n, c
 int mlp_warm_start(pot_ctx* ctx, pot_mlp* mm, cudaStream_t st, int64_t n, const float* vel,
                    const float* psi, float dt, float** psi_prev) {
   if (!mm || n > mm->max_rows) return POT_ERR_INVALID_ARG;
-  const bool hist = mm->hist_n == n;
+  const bool hist = mm->use_hist && mm->hist_n == n;
   POT_CHECK(mlp_features_sorted(ctx, mm, st, n, vel, psi, hist ? mm->psi_hist : nullptr, dt, nullptr,
                                 mm->x));
   // this step's weights are the next step's history
@@ -1080,7 +1081,8 @@ int pot_mlp_features(pot_ctx* ctx, pot_mlp* mm, void* stream, int64_t n, const f
                                                      (float)prm->wall_margin);
   POT_CUDA(cudaGetLastError());
   POT_CHECK(grid_build<float>(ctx, st, n, mm->pos_tmp, psi, targets, dom));
-  POT_CHECK(mlp_features_sorted(ctx, mm, st, n, mm->vel_adv, psi, psi_old, dt, ctx->perm, feat));
+  POT_CHECK(mlp_features_sorted(ctx, mm, st, n, mm->vel_adv, psi, mm->use_hist ? psi_old : nullptr,
+                                dt, ctx->perm, feat));
   POT_CUDA(cudaStreamSynchronize(st));
   return POT_OK;
 }
@@ -1096,6 +1098,12 @@ int pot_mlp_set_history(pot_mlp* mm, void* stream, int64_t n, const float* psi_o
   POT_CUDA(cudaMemcpyAsync(mm->psi_hist, psi_old, n * sizeof(float), cudaMemcpyDeviceToDevice, st));
   POT_CUDA(cudaStreamSynchronize(st));
   mm->hist_n = n;
+  return POT_OK;
+}
+
+int pot_mlp_set_inputs(pot_mlp* mm, int32_t n_inputs) {
+  if (!mm || (n_inputs != 76 && n_inputs != 77)) return POT_ERR_INVALID_ARG;
+  mm->use_hist = n_inputs == 77;
   return POT_OK;
 }
 

@@ -146,6 +146,8 @@ def lib():
         L.pot_render_smooth.argtypes = [P, P, I64, P, P, ctypes.POINTER(Domain),
                                         ctypes.POINTER(Camera), ctypes.c_float, P, P, P]
         L.pot_render_smooth.restype = ctypes.c_int
+        L.pot_mlp_set_inputs.argtypes = [P, ctypes.c_int32]
+        L.pot_mlp_set_inputs.restype = ctypes.c_int
         L.pot_measure_fp32_peak.argtypes = [P, P, ctypes.POINTER(ctypes.c_double),
                                             ctypes.POINTER(ctypes.c_double)]
         L.pot_measure_fp32_peak.restype = ctypes.c_int
@@ -578,6 +580,11 @@ class Mlp:
         psi_old = _dev(psi_old, torch.float32, (n,), "psi_old", self.device)
         self._check(lib().pot_mlp_set_history(self._h, _stream(stream), n, _ptr(psi_old)),
                     "pot_mlp_set_history")
+
+    def set_inputs(self, n_inputs):
+        """77 inputs (with the previous weight change; the default) or 76
+        (without it: the prediction corrects the previous weights)."""
+        self._check(lib().pot_mlp_set_inputs(self._h, int(n_inputs)), "pot_mlp_set_inputs")
 
 
 def pot_mlp_features(ctx: Context, mlp: Mlp, pos, vel, psi, targets, domain=UNIT_BOX, params=None,

@@ -5,8 +5,8 @@ steps, the features at the state the step solves at (positions advanced by
 dt v and clamped, previous weights psi^k, velocities, the change
 psi^k - psi^{k-1}) and the converged weights psi^{k+1} of `per_sample` random
 sites give samples (x, y = (psi^{k+1} - psi^k - (psi^k - psi^{k-1})) / h^2,
-the departure from the linear extrapolation; without psi^{k-1} the plain
-change), h = nu^(1/3).
+the departure from the linear extrapolation; without psi^{k-1}, and for the
+76-input model, the plain change), h = nu^(1/3).
 
 Training: Adam on the mean squared error, shuffled batches, all kernels in
 libpot.so (tensor-core forward and back-propagation).  Evaluation: the same
@@ -32,10 +32,11 @@ _SHAPES = ((80, 128), (128,), (128, 128), (128,), (128, 128), (128,), (128,), (1
 _N_FEAT = 77
 
 
-def init_params(seed: int = 0, device="cuda") -> torch.Tensor:
+def init_params(seed: int = 0, device="cuda", n_inputs: int = _N_FEAT) -> torch.Tensor:
     """Fresh parameters: He-uniform weights (limit sqrt(6 / fan_in)), zero
     biases, the head scaled by 0.1 so that the first predictions are small,
-    zero weights for the padding inputs.  FP32 vector on `device`."""
+    zero weights for the padding inputs (from n_inputs on).  FP32 vector on
+    `device`."""
     gen = torch.Generator(device="cpu").manual_seed(seed)
     parts = []
     for k, shp in enumerate(_SHAPES):
@@ -43,7 +44,7 @@ def init_params(seed: int = 0, device="cuda") -> torch.Tensor:
             lim = math.sqrt(6.0 / shp[0])
             w = (torch.rand(shp, generator=gen, dtype=torch.float64) * 2.0 - 1.0) * lim
             if k == 0:
-                w[_N_FEAT:, :] = 0.0
+                w[n_inputs:, :] = 0.0
             if k == 6:
                 w *= 0.1
         else:
@@ -67,8 +68,11 @@ def settle(ctx, pos, vel, psi, nu, prm, relax=0):
     return pot.pot_newton_solve(ctx, pos, nu, psi, params=prm, check=False)
 
 
-def collect(ctx, mlp, scene, steps, every, per_sample, seed, dt, tol=1e-4, eps=0.01, relax=0):
-    """Samples from `steps` plain-Newton fluid steps of `scene`."""
+def collect(ctx, mlp, scene, steps, every, per_sample, seed, dt, tol=1e-4, eps=0.01, relax=0,
+            history=True):
+    """Samples from `steps` plain-Newton fluid steps of `scene`; without
+    `history` (the 76-input model) no weight change enters the features or
+    the target."""
     dev = ctx.device
     pos, vel, psi, nu = _state(scene, dev)
     prm = pot.default_params(dt=dt, tol=tol, eps=eps)
@@ -80,9 +84,9 @@ def collect(ctx, mlp, scene, steps, every, per_sample, seed, dt, tol=1e-4, eps=0
     for k in range(steps):
         take = k % every == 0
         psi_prev = psi.clone()
-        hist = psi_old
+        hist = psi_old if history else None
         if take:
-            feat = pot.pot_mlp_features(ctx, mlp, pos, vel, psi, nu, params=prm, psi_old=psi_old)
+            feat = pot.pot_mlp_features(ctx, mlp, pos, vel, psi, nu, params=prm, psi_old=hist)
         psi_old = psi_prev
         st = pot.pot_fluid_step(ctx, pos, vel, psi, nu, params=prm, check=False)
         if st["status"] != 0:
@@ -117,7 +121,8 @@ def train(mlp, x, y, epochs, batch=8192, lr=1e-3, seed=0):
     return hist
 
 
-def compare(ctx, mlp, scene, steps, dt, warm_steps=0, tol=1e-4, eps=0.01, relax=0):
+def compare(ctx, mlp, scene, steps, dt, warm_steps=0, tol=1e-4, eps=0.01, relax=0,
+            modes=((0, "plain"), (2, "extrapolated"), (1, "mlp"))):
     """Run the same fluid steps from the same state with the plain start
     (previous weights), the extrapolated start (warm_start 2) and the MLP
     start; returns per-step stats of each.  The warm-up steps run with the
@@ -135,7 +140,7 @@ def compare(ctx, mlp, scene, steps, dt, warm_steps=0, tol=1e-4, eps=0.01, relax=
         pot.pot_fluid_step(ctx, pos, vel, psi, nu, params=prm)
     state = (pos.clone(), vel.clone(), psi.clone())
     out = {}
-    for mode, name in ((0, "plain"), (2, "extrapolated"), (1, "mlp")):
+    for mode, name in modes:
         pos, vel, psi = (t.clone() for t in state)
         p = pot.default_params(dt=dt, tol=tol, eps=eps, warm_start=mode)
         pot.set_warm_start(ctx, mlp if mode == 1 else None)

@@ -107,3 +107,58 @@ def test_extrapolated_start(setup):
     assert used[0] == 0 and all(u == 1 for u in used[1:]), used
     assert sum(s["newton_iters"] for s in res[2][1]) <= sum(s["newton_iters"] for s in res[0][1])
     np.testing.assert_allclose(res[2][0], res[0][0], rtol=0, atol=1e-8 * float(np.max(res[0][0])))
+
+
+def test_76_input_model(setup):
+    """The configuration's 76-input model (no weight-change input; the
+    prediction corrects the previous weights): its features leave input 77
+    at 0 whatever the history, a zero model is the plain start exactly, and
+    a model trained on a few dam-break steps starts no worse than the plain
+    start on unseen steps of another seed, every step converged."""
+    ctx, _ = setup
+    dev = ctx.device
+    mlp76 = pot.Mlp(65536, 0)
+    try:
+        mlp76.set_inputs(76)
+        with pytest.raises(pot.PotError):
+            mlp76.set_inputs(75)
+        sc = column(19)
+        pos, vel, psi, nu = (torch.from_numpy(a).to(dev) for a in (sc.pos, sc.vel, sc.psi, sc.nu))
+        prm = pot.default_params(dt=DT)
+        W.settle(ctx, pos, vel, psi, nu, prm)
+        old = psi * 0.9  # a history that would give a nonzero change feature
+        f76 = pot.pot_mlp_features(ctx, mlp76, pos, vel, psi, nu, params=prm, psi_old=old)
+        assert bool(torch.all(f76[:, 76] == 0))
+        mlp77 = pot.Mlp(65536, 0)
+        f77 = pot.pot_mlp_features(ctx, mlp77, pos, vel, psi, nu, params=prm, psi_old=old)
+        mlp77.close()
+        assert bool(torch.any(f77[:, 76] != 0))
+        assert torch.equal(f76[:, :76], f77[:, :76])
+        # zero model: the plain start
+        mlp76.set_params(torch.zeros(pot.Mlp.num_params(), dtype=torch.float32, device=dev))
+        res = W.compare(ctx, mlp76, column(19), steps=3, dt=DT, warm_steps=2,
+                        modes=((0, "plain"), (1, "mlp")))
+        for a, b in zip(res["plain"], res["mlp"]):
+            assert a["status"] == 0 and b["status"] == 0 and b["mlp_used"] == 1
+            assert b["err_start"] == a["err_start"] and b["newton_iters"] == a["newton_iters"]
+        # trained
+        mlp76.set_params(W.init_params(0, device=dev, n_inputs=76))
+        xs, ys = [], []
+        for seed in (10, 11, 12):
+            x, y = W.collect(ctx, mlp76, column(seed), steps=30, every=2, per_sample=2048,
+                             seed=seed, dt=DT, history=False)
+            assert bool(torch.all(x[:, 76] == 0))
+            xs.append(x)
+            ys.append(y)
+        hist = W.train(mlp76, torch.cat(xs), torch.cat(ys), epochs=120, batch=4096, lr=1e-3)
+        assert hist[-1] < 0.1 * hist[0]
+        res = W.compare(ctx, mlp76, column(19), steps=8, dt=DT, warm_steps=12,
+                        modes=((0, "plain"), (1, "mlp")))
+        plain, learned = W.summarize(res["plain"]), W.summarize(res["mlp"])
+        print("76 inputs, Newton / PCG iterations per step: plain", plain["newton_iters"],
+              plain["pcg_iters"], "learned", learned["newton_iters"], learned["pcg_iters"])
+        assert learned["all_converged"] and learned["fallback_rate"] == 0.0
+        assert learned["newton_iters"] <= plain["newton_iters"], (learned, plain)
+    finally:
+        pot.set_warm_start(ctx, None)
+        mlp76.close()
