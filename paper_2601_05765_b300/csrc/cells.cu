@@ -2075,6 +2075,7 @@ int residuals(pot_ctx* ctx, cudaStream_t st, int64_t n, double out[6]) {
   k_resid_final<<<1, 32, 0, st>>>(ctx->red, kRedBlocks, ctx->red_out);
   POT_CUDA(cudaMemcpyAsync(ctx->h_pinned, ctx->red_out, 6 * sizeof(double),
                            cudaMemcpyDeviceToHost, st));
+  if (!out) return POT_OK;  // the caller's next wait on the stream completes the copy
   POT_CUDA(cudaStreamSynchronize(st));
   for (int k = 0; k < 6; k++) out[k] = ctx->h_pinned[k];
   return POT_OK;
@@ -2106,12 +2107,15 @@ int csr_compact(pot_ctx* ctx, cudaStream_t st, int64_t n, int64_t* nnz_off) {
   note_launch();
   k_csr_copy<T><<<blocks_for(n * 8, 256), 256, 0, st>>>(n, ctx->row_ptr, ctx->cand, w.stage_vals,
                                                          ctx->k_max, ctx->csr_cols, w.csr_vals);
-  int32_t* h = (int32_t*)(ctx->h_pinned + 8);
+  int32_t* h = (int32_t*)(ctx->h_pinned + 28);
   POT_CUDA(cudaMemcpyAsync(h, ctx->row_ptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  if (!nnz_off) return POT_OK;  // read later with csr_nnz, after a wait on the stream
   POT_CUDA(cudaStreamSynchronize(st));
   *nnz_off = h[0];
   return POT_OK;
 }
+
+int64_t csr_nnz(const pot_ctx* ctx) { return *(const int32_t*)(ctx->h_pinned + 28); }
 
 template <typename T>
 int csr_user(pot_ctx* ctx, cudaStream_t st, int64_t n, int32_t* row_ptr, int32_t* cols, T* vals,

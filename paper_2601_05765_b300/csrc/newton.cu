@@ -237,12 +237,15 @@ int eval_and_reduce(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* 
                     double res[6], pot_solve_stats* S) {
   EvTimer tm(ctx, 0, st);
   const int ce = cells_eval<T>(ctx, st, n, dom, true);
-  if (ce == POT_OK) POT_CHECK(residuals<T>(ctx, st, n, res));
+  // the residual summary is copied back with the status word: one wait
+  if (ce == POT_OK) POT_CHECK(residuals<T>(ctx, st, n, nullptr));
+  int64_t site;
+  const int code = read_status(ctx, st, &site);  // also clears the device status
+  if (ce == POT_OK)
+    for (int k = 0; k < 6; k++) res[k] = ctx->h_pinned[k];
   S->ms_cells += tm.stop();
   S->cell_evals++;
   S->passes += ctx->last_passes;
-  int64_t site;
-  const int code = read_status(ctx, st, &site);  // also clears the device status
   if (code != POT_OK) S->error_site = site;
   return code != POT_OK ? code : ce;
 }
@@ -326,8 +329,7 @@ int newton_sorted_impl(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domai
     if (err <= tol_stop) return POT_OK;
     if (it >= P->max_newton) return POT_ERR_NOT_CONVERGED;
     int64_t nnz_off = 0;
-    POT_CHECK(csr_compact<T>(ctx, st, n, &nnz_off));
-    S->nnz = nnz_off + n;
+    POT_CHECK(csr_compact<T>(ctx, st, n, nullptr));  // its size is read after the PCG's wait
     // inexact Newton: the linear residual only needs to be small against
     // the distance still to go to the tolerance, and far from it no smaller
     // than the error the next Newton step leaves anyway (about err^2)
@@ -340,6 +342,7 @@ int newton_sorted_impl(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domai
                             P->pcg_host_loop != 0, &iters, nullptr);
       S->ms_pcg += tm.stop();
       S->pcg_iters += iters;
+      S->nnz = csr_nnz(ctx) + n;
       if (ps != POT_OK) return ps;
     }
     double alpha = 1.0;

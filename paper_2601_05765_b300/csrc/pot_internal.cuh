@@ -329,7 +329,9 @@ int cell_diagnostics(pot_ctx* ctx, cudaStream_t st, int64_t n, float* off, float
                      int32_t* planes);
 
 // FP64 reductions over sorted cells:
-// out = {max |V-nu|/nu, sum (nu-V)^2, min V, #empty, #planes, max planes}.  Host sync.
+// out = {max |V-nu|/nu, sum (nu-V)^2, min V, #empty, #planes, max planes}.  Host
+// sync; with out NULL only enqueued (the values are at ctx->h_pinned[0..5]
+// after the caller's next wait on the stream).
 template <typename T>
 int residuals(pot_ctx* ctx, cudaStream_t st, int64_t n, double out[6]);
 
@@ -343,8 +345,10 @@ int repair_empty(pot_ctx* ctx, cudaStream_t st, int64_t n, int* repaired);
 int read_status(pot_ctx* ctx, cudaStream_t st, int64_t* site);
 
 // internal CSR (off-diagonal, sorted space) from the staged rows; nnz on host
+// (nnz_off NULL: not waited for; csr_nnz reads it after the next wait)
 template <typename T>
 int csr_compact(pot_ctx* ctx, cudaStream_t st, int64_t n, int64_t* nnz_off);
+int64_t csr_nnz(const pot_ctx* ctx);
 
 // caller-order CSR with the diagonal
 template <typename T>
