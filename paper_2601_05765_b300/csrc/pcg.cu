@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(kPcgThreads)
     if (i < n) {
       const int a = row_ptr[i], e = row_ptr[i + 1];
       // unrolled so that the loads of several entries are in flight at once
-#pragma unroll 4
+#pragma unroll 2
       for (int k = a + sub; k < e; k += kTpr) {
         const ZP<T> v = zp[cols[k]];
         acc += vals[k] * (v.z + beta * v.p);
