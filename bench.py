@@ -55,8 +55,8 @@ SMALL_SPACING = 0.032  # ~2000 sites with the splash recipe
 # 2 ffma of the instruction mix), warp instructions issued, and DRAM bytes
 # (cold caches: ncu flushes them before the launch).
 K_CELLS_FLOP_PER_CELL = 5479.5
-K_CELLS_WARP_INST_PER_CELL = 812.0
-K_CELLS_DRAM_BYTES_PER_CELL = 376.8
+K_CELLS_WARP_INST_PER_CELL = 801.6
+K_CELLS_DRAM_BYTES_PER_CELL = 381.3
 
 
 def parse():
