@@ -1944,7 +1944,9 @@ __global__ void k_psi_update(int64_t n, const T* __restrict__ base, const T* __r
 // host side
 
 template <typename T>
-int cells_eval(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* dom, bool want_grad) {
+int cells_eval(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* dom, bool want_grad,
+               bool tail_resid) {
+  ctx->tail_ready = false;
   Work<T>& w = ctx->work<T>();
   if (!w.grid_valid) return POT_ERR_INVALID_ARG;
   Box<T> box;
@@ -2040,6 +2042,12 @@ int cells_eval(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* dom, 
     k_need_update<T><<<blocks_for(n, 256), 256, 0, st>>>(n, w.sxp, w.rcell, ctx->meta, w.soff,
                                                           w.srad, w.srad_lo, ctx->need,
                                                           ctx->need_count);
+    if (tail_resid) {
+      // needed only if this is the last pass; a later pass enqueues them again
+      POT_CHECK(residuals<T>(ctx, st, n, nullptr));
+      POT_CUDA(cudaMemcpyAsync(ctx->h_pinned + 8, ctx->err, 2 * sizeof(int32_t),
+                               cudaMemcpyDeviceToHost, st));
+    }
     POT_CUDA(cudaMemcpyAsync(hcount, ctx->need_count, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     POT_CUDA(cudaStreamSynchronize(st));
     float ms = 0.f;
@@ -2053,6 +2061,7 @@ int cells_eval(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* dom, 
   }
   POT_CUDA(cudaGetLastError());
   w.have_rcell = true;
+  ctx->tail_ready = tail_resid;
   // cells still unresolved after the last pass are not exact
   if (*hcount != 0) return POT_ERR_NEIGHBOUR_OVERFLOW;
   return POT_OK;
@@ -2096,6 +2105,11 @@ int read_status(pot_ctx* ctx, cudaStream_t st, int64_t* site) {
   int32_t* h = (int32_t*)(ctx->h_pinned + 8);
   POT_CUDA(cudaMemcpyAsync(h, ctx->err, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   POT_CUDA(cudaStreamSynchronize(st));
+  return status_on_host(ctx, site);
+}
+
+int status_on_host(pot_ctx* ctx, int64_t* site) {
+  const int32_t* h = (const int32_t*)(ctx->h_pinned + 8);
   int code = h[0];
   int32_t s = h[1];
   if (site) *site = -1;
@@ -2230,7 +2244,7 @@ int cell_diagnostics(pot_ctx* ctx, cudaStream_t st, int64_t n, float* off, float
 }
 
 #define POT_INST(T)                                                                              \
-  template int cells_eval<T>(pot_ctx*, cudaStream_t, int64_t, const pot_domain*, bool);          \
+  template int cells_eval<T>(pot_ctx*, cudaStream_t, int64_t, const pot_domain*, bool, bool);    \
   template int residuals<T>(pot_ctx*, cudaStream_t, int64_t, double*);                          \
   template int repair_empty<T>(pot_ctx*, cudaStream_t, int64_t, int*);                          \
   template int csr_compact<T>(pot_ctx*, cudaStream_t, int64_t, int64_t*);                       \

@@ -236,11 +236,17 @@ template <typename T>
 int eval_and_reduce(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* dom,
                     double res[6], pot_solve_stats* S) {
   EvTimer tm(ctx, 0, st);
-  const int ce = cells_eval<T>(ctx, st, n, dom, true);
-  // the residual summary is copied back with the status word: one wait
-  if (ce == POT_OK) POT_CHECK(residuals<T>(ctx, st, n, nullptr));
+  // the residual summary and the status word come back with the last
+  // pass's wait
+  const int ce = cells_eval<T>(ctx, st, n, dom, true, true);
   int64_t site;
-  const int code = read_status(ctx, st, &site);  // also clears the device status
+  int code;
+  if (ctx->tail_ready) {
+    code = status_on_host(ctx, &site);  // also clears the device status
+  } else {
+    if (ce == POT_OK) POT_CHECK(residuals<T>(ctx, st, n, nullptr));
+    code = read_status(ctx, st, &site);
+  }
   if (ce == POT_OK)
     for (int k = 0; k < 6; k++) res[k] = ctx->h_pinned[k];
   S->ms_cells += tm.stop();

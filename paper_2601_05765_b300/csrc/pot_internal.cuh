@@ -270,6 +270,7 @@ struct pot_ctx {
   int32_t* big_list = nullptr;    // cells with more planes than the shared window holds
   int32_t* fix_list = nullptr;    // FP32 cells re-evaluated in FP64 (ill-conditioned)
   int last_passes = 0;            // security-radius passes of the last cell evaluation
+  bool tail_ready = false;        // residuals and status of the last evaluation are on the host
   int64_t kc_launches = 0;        // cell-kernel timer: launches, cells processed, device ms
   int64_t kc_cells = 0;
   double kc_ms = 0.0;
@@ -318,9 +319,13 @@ template <typename T>
 int grid_build(pot_ctx* ctx, cudaStream_t st, int64_t n, const T* pos, const T* psi,
                const double* targets, const pot_domain* dom);
 
-// Cell evaluation in sorted space (cells.cu): candidates + geometry.
+// Cell evaluation in sorted space (cells.cu): candidates + geometry.  With
+// tail_resid, every pass also enqueues the residual summary and a copy of
+// the status word before its wait, so that after the last pass both are on
+// the host (ctx->tail_ready) without a further wait.
 template <typename T>
-int cells_eval(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* dom, bool want_grad);
+int cells_eval(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* dom, bool want_grad,
+               bool tail_resid = false);
 // keep the last evaluation's cell centres and extents (caller order) as the
 // security-ball hint of the next Newton solve on the same sites
 template <typename T>
@@ -343,6 +348,9 @@ int repair_empty(pot_ctx* ctx, cudaStream_t st, int64_t n, int* repaired);
 
 // read and clear the device status word; returns a POT status
 int read_status(pot_ctx* ctx, cudaStream_t st, int64_t* site);
+// the same from the copy already on the host (ctx->h_pinned + 8, written
+// by a wait that followed the copy); clears the device word if set
+int status_on_host(pot_ctx* ctx, int64_t* site);
 
 // internal CSR (off-diagonal, sorted space) from the staged rows; nnz on host
 // (nnz_off NULL: not waited for; csr_nnz reads it after the next wait)
