@@ -1795,8 +1795,29 @@ template <typename T>
 __global__ void k_resid(int64_t n, const T* __restrict__ vol, const double* __restrict__ snu,
                         const int32_t* __restrict__ meta, double* part) {
   ResidAcc<T> acc;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // four cells per step with their loads issued together, added in the
+  // same order as one at a time
+#pragma unroll 1
+  for (; i + 3 * stride < n; i += 4 * stride) {
+    T v[4];
+    double nu[4];
+    int m[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      v[u] = vol[i + u * stride];
+      nu[u] = snu[i + u * stride];
+      m[u] = meta[i + u * stride] & kMetaPlanes;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      acc.add(v[u], nu[u]);
+      acc.npl += m[u];
+      acc.mpl = max(acc.mpl, m[u]);
+    }
+  }
+  for (; i < n; i += stride) {
     acc.add(vol[i], snu[i]);
     const int m = meta[i] & kMetaPlanes;
     acc.npl += m;
@@ -1862,15 +1883,32 @@ template <typename T>
 __global__ void k_csr_copy(int64_t n, const int32_t* __restrict__ row_ptr,
                            const int32_t* __restrict__ cand, const T* __restrict__ stage, int kmax,
                            int32_t* cols, T* vals) {
-  // 8 threads per row
+  // 4 threads per row, each with up to three entries' loads in flight
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  int64_t s = t >> 3;
-  int sub = (int)(t & 7);
+  int64_t s = t >> 2;
+  int sub = (int)(t & 3);
   if (s >= n) return;
-  int a = row_ptr[s], cnt = row_ptr[s + 1] - a;
-  for (int k = sub; k < cnt; k += 8) {
-    cols[a + k] = cand[s * kmax + k];
-    vals[a + k] = stage[s * kmax + k];
+  const int a = row_ptr[s], cnt = row_ptr[s + 1] - a;
+  const int32_t* cr = cand + s * kmax;
+  const T* vr = stage + s * kmax;
+#pragma unroll 1
+  for (int k = sub; k < cnt; k += 12) {
+    int c[3];
+    T v[3];
+#pragma unroll
+    for (int u = 0; u < 3; u++) {
+      if (k + 4 * u < cnt) {
+        c[u] = cr[k + 4 * u];
+        v[u] = vr[k + 4 * u];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 3; u++) {
+      if (k + 4 * u < cnt) {
+        cols[a + k + 4 * u] = c[u];
+        vals[a + k + 4 * u] = v[u];
+      }
+    }
   }
 }
 
@@ -2130,7 +2168,7 @@ int csr_compact(pot_ctx* ctx, cudaStream_t st, int64_t n, int64_t* nnz_off) {
   Work<T>& w = ctx->work<T>();
   POT_CHECK(scan_exclusive(ctx, st, ctx->row_cnt, ctx->row_ptr, n));
   note_launch();
-  k_csr_copy<T><<<blocks_for(n * 8, 256), 256, 0, st>>>(n, ctx->row_ptr, ctx->cand, w.stage_vals,
+  k_csr_copy<T><<<blocks_for(n * 4, 256), 256, 0, st>>>(n, ctx->row_ptr, ctx->cand, w.stage_vals,
                                                          ctx->k_max, ctx->csr_cols, w.csr_vals);
   int32_t* h = (int32_t*)(ctx->h_pinned + 28);
   POT_CUDA(cudaMemcpyAsync(h, ctx->row_ptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
