@@ -409,10 +409,15 @@ int oracle_cells(int64_t n, const double* pos, const double* psi, const double* 
   memset(&g, 0, sizeof(g));
   if (!brute) grid_build(&g, n, pos, psi);
   int nbad = 0;
+  /* the thread count applies to this call only (a num_threads clause, not
+     the process-wide setting, so a later call with 0 gets every core again) */
 #ifdef _OPENMP
-  if (nthreads > 0) omp_set_num_threads(nthreads);
+  int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#else
+  int nt = 1;
 #endif
-#pragma omp parallel reduction(+ : nbad)
+  (void)nt;
+#pragma omp parallel num_threads(nt) reduction(+ : nbad)
   {
     int64_t cap = brute ? (n > 0 ? n : 1) : 4096;
     int64_t* cand = (int64_t*)malloc(sizeof(int64_t) * cap);
