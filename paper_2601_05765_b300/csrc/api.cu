@@ -67,6 +67,9 @@ int alloc_work(Work<T>& w, int64_t n, int64_t k, int64_t gcap, int sms) {
   POT_CHECK(alloc(&w.vcount, n));
   POT_CHECK(alloc(&w.vreach, n));
   POT_CHECK(alloc(&w.gmax, gcap + 1));
+  w.ccap = gcap / 8 + 4096;
+  POT_CHECK(alloc(&w.cmax, w.ccap));
+  POT_CHECK(alloc(&w.cnb, w.ccap));
   // cells with more planes than the cell kernel takes (kSmallPlanes) exist
   // only when the lists may hold that many
   if (k + 6 > kSmallPlanes) {
@@ -84,7 +87,7 @@ void free_work(Work<T>& w) {
                   w.u,   w.x,        w.r,    w.z,     w.p0,   w.p1,  w.q,          w.vel_s,
                   w.psi_max, w.nu_max, w.srad, w.srad_lo, w.soff, w.hint, w.rcell_acc, w.rcell, w.gmax,
                   w.big_pl, w.big_d, w.big_j, w.psi_hist, w.psi_fb, w.wallw, w.vlist, w.vcount,
-                  w.vreach, w.wallv, w.zp};
+                  w.vreach, w.wallv, w.zp, w.cmax, w.cnb};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   w = Work<T>();

@@ -102,6 +102,30 @@ struct VerletList {
   T* reach;
 };
 
+// Largest weight near a site: the grid's cells grouped f x f x f into coarse
+// cells, and per coarse cell the largest weight over its 3 x 3 x 3 coarse
+// neighbourhood (nb == nullptr: not formed; the global largest weight
+// serves).  A site j outside the neighbourhood of p_i's coarse cell differs
+// from it by more than f fine cells along some axis, so it lies farther
+// than (f - 1/2) cs from p_i (the half cell covers the rounding of the cell
+// coordinates).
+template <typename T>
+struct Coarse {
+  const T* nb;
+  int f;
+  int dim[3];
+};
+
+template <typename T>
+__device__ __forceinline__ int64_t coarse_key(const V4<T>& p, const GridParams<T>& g,
+                                              const Coarse<T>& co) {
+  // (clamped: a coordinate that is not a number stays inside the grid)
+  const int cx = min(max(cell_coord(p.x, g.lo[0], g.inv_cs, g.dim[0]) / co.f, 0), co.dim[0] - 1);
+  const int cy = min(max(cell_coord(p.y, g.lo[1], g.inv_cs, g.dim[1]) / co.f, 0), co.dim[1] - 1);
+  const int cz = min(max(cell_coord(p.z, g.lo[2], g.inv_cs, g.dim[2]) / co.f, 0), co.dim[2] - 1);
+  return ((int64_t)cz * co.dim[1] + cy) * co.dim[0] + cx;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256)
     k_candidates(int64_t n, const V4<T>* __restrict__ sxp, const int32_t* __restrict__ cell_start,
@@ -109,7 +133,7 @@ __global__ void __launch_bounds__(256)
                  const T* __restrict__ gmax, T* __restrict__ srad, const T* __restrict__ srad_lo,
                  const T* __restrict__ soff, uint8_t* __restrict__ need, int kmax,
                  int32_t* __restrict__ cand, int32_t* __restrict__ meta, int32_t* big_count,
-                 int32_t* big_list, int32_t* err, VerletList<T> vl) {
+                 int32_t* big_list, int32_t* err, VerletList<T> vl, Coarse<T> co) {
   int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n || !need[s]) return;
   const V4<T> p = sxp[s];
@@ -138,7 +162,16 @@ __global__ void __launch_bounds__(256)
   // within r + r_j
   const T Re = R + sqrt(ox * ox + oy * oy + oz * oz);
   const T pmx = *psi_max;
-  const T D = fmin(Re + sqrt(fmax(Re * Re - ps + pmx, T(0))), r + sqrt(pmx));
+  T D = fmin(Re + sqrt(fmax(Re * Re - ps + pmx, T(0))), r + sqrt(pmx));
+  // With the global largest weight, no site beyond D is a candidate.  When
+  // D stays within the coarse neighbourhood's reach, the sites beyond that
+  // reach are excluded by the same bound, and those inside it carry at most
+  // the neighbourhood's largest weight, which gives the same bound with a
+  // smaller weight.
+  if (co.nb != nullptr && D <= (T(co.f) - T(0.5)) * g.cs) {
+    const T pl = co.nb[coarse_key(p, g, co)];
+    D = fmin(D, fmin(Re + sqrt(fmax(Re * Re - ps + pl, T(0))), r + sqrt(pl)));
+  }
   const T D2 = D * D;
   int nc = 0;
   bool empty = false;
@@ -1602,6 +1635,47 @@ __global__ void k_gmax(int64_t ncell, const int32_t* __restrict__ cell_start,
   gmax[c] = m;
 }
 
+// Largest weight (clamped at 0) of the sites of each coarse cell: sites of
+// one warp that share a coarse cell (consecutive in grid order, so most do)
+// combine before one atomic.  Non-negative floating-point values order like
+// their bit patterns as unsigned integers.
+template <typename T>
+__global__ void k_cmax(int64_t n, const V4<T>* __restrict__ sxp, GridParams<T> g, Coarse<T> co,
+                       T* cmax) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool ok = s < n;
+  int64_t key = -1;
+  T v = T(0);
+  if (ok) {
+    const V4<T> p = sxp[s];
+    key = coarse_key(p, g, co);
+    v = p.w > T(0) ? p.w : T(0);
+  }
+  if constexpr (sizeof(T) == 4) {
+    const unsigned grp = __match_any_sync(kFull, (unsigned long long)key);
+    const unsigned m = __reduce_max_sync(grp, __float_as_uint(v));
+    if (ok && (int)(threadIdx.x & 31) == __ffs(grp) - 1) atomicMax((unsigned*)cmax + key, m);
+  } else {
+    if (ok)
+      atomicMax((unsigned long long*)cmax + key, (unsigned long long)__double_as_longlong(v));
+  }
+}
+
+// Largest of cmax over each coarse cell's 3 x 3 x 3 neighbourhood.
+template <typename T>
+__global__ void k_cnb(Coarse<T> co, const T* __restrict__ cmax, T* nb) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nxy = (int64_t)co.dim[0] * co.dim[1];
+  if (c >= nxy * co.dim[2]) return;
+  const int cx = (int)(c % co.dim[0]), cy = (int)((c / co.dim[0]) % co.dim[1]), cz = (int)(c / nxy);
+  T m = T(0);
+  for (int z = max(cz - 1, 0); z <= min(cz + 1, co.dim[2] - 1); z++)
+    for (int y = max(cy - 1, 0); y <= min(cy + 1, co.dim[1] - 1); y++)
+      for (int x = max(cx - 1, 0); x <= min(cx + 1, co.dim[0] - 1); x++)
+        m = fmax(m, cmax[z * nxy + (int64_t)y * co.dim[0] + x]);
+  nb[c] = m;
+}
+
 // First security ball of an evaluation.  Centre: kept from the previous
 // evaluation in the same grid order (the Newton solve keeps it fixed), else
 // the hint of the previous solve on these sites (centroid - site, caller
@@ -2025,6 +2099,32 @@ int cells_eval(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* dom, 
     box64.lo[k] = dom->lo[k];
     box64.hi[k] = dom->hi[k];
   }
+  // largest weights near each site (coarse cells of f x f x f grid cells;
+  // f such that the neighbourhood reaches past 2 sqrt(psi_max) at the grid
+  // build's weights, the largest reach of a candidate) -- only where the
+  // workspace holds them
+  Coarse<T> co = {nullptr, 1, {1, 1, 1}};
+  if (w.cmax && w.cnb) {
+    int f = std::max(2, (int)ceil(2.0 * sqrt(fmax(w.grid_pmax, 0.0)) / (double)w.grid.cs + 0.5));
+    int64_t ncc = 0;
+    int cdim[3];
+    for (;; f++) {
+      ncc = 1;
+      for (int k = 0; k < 3; k++) {
+        cdim[k] = (w.grid.dim[k] + f - 1) / f;
+        ncc *= cdim[k];
+      }
+      if (ncc <= w.ccap) break;
+    }
+    co.f = f;
+    for (int k = 0; k < 3; k++) co.dim[k] = cdim[k];
+    POT_CUDA(cudaMemsetAsync(w.cmax, 0, sizeof(T) * ncc, st));
+    note_launch();
+    k_cmax<T><<<blocks_for(n, 256), 256, 0, st>>>(n, w.sxp, w.grid, co, w.cmax);
+    note_launch();
+    k_cnb<T><<<blocks_for(ncc, 256), 256, 0, st>>>(co, w.cmax, w.cnb);
+    co.nb = w.cnb;
+  }
   // neighbour lists: kept across the evaluations of one grid order when the
   // caller asked for them (a Newton solve), invalidated by the grid build
   VerletList<T> vl = {nullptr, nullptr, nullptr};
@@ -2052,7 +2152,7 @@ int cells_eval(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* dom, 
     k_candidates<T><<<blocks_for(n, 256), 256, 0, st>>>(
         n, w.sxp, ctx->cell_start, w.grid, box, w.psi_max, w.gmax, w.srad, w.srad_lo, w.soff,
         ctx->need, ctx->k_max, ctx->cand, ctx->meta, ctx->need_count + 1, ctx->big_list, ctx->err,
-        vl);
+        vl, co);
     note_launch();
     // the no-alloc entry point's context has no events: no timing there
     const bool timed = ctx->ev[6] && ctx->ev[7];

@@ -165,6 +165,7 @@ int grid_build(pot_ctx* ctx, cudaStream_t st, int64_t n, const T* pos, const T* 
   // the candidate pass's neighbour lists belong to the previous order
   if (w.vreach) POT_CUDA(cudaMemsetAsync(w.vreach, 0, sizeof(T) * n, st));
   w.grid = g;
+  w.grid_pmax = pmax;
   w.grid_valid = true;
   w.have_rcell = false;
   w.have_acc = false;

@@ -209,6 +209,10 @@ struct Work {
   int* big_j = nullptr;
   int big_warps = 0;        // warps of the big-cell kernel (0: no big cells possible)
   T* gmax = nullptr;        // per grid cell: largest psi of its sites
+  T* cmax = nullptr;        // per coarse cell (f x f x f grid cells): largest psi of its sites
+  T* cnb = nullptr;         // per coarse cell: largest psi over its 3 x 3 x 3 coarse neighbourhood
+  int64_t ccap = 0;         // coarse cells cmax and cnb hold
+  double grid_pmax = 0.0;   // largest psi at the grid build
   GridParams<T> grid{};
   bool grid_valid = false;
   bool have_rcell = false;  // rcell belongs to the current grid order
