@@ -172,6 +172,11 @@ __global__ void __launch_bounds__(256)
     const T pl = co.nb[coarse_key(p, g, co)];
     D = fmin(D, fmin(Re + sqrt(fmax(Re * Re - ps + pl, T(0))), r + sqrt(pl)));
   }
+  // The bound holds in exact arithmetic; a site right at it (a plane that
+  // only touches the ball, or lies on the security ball) is left to the
+  // tests on h below, which decide it in their own rounding: the reach
+  // carries a relative margin far above the rounding of D and of d.
+  D *= T(1.0001);
   const T D2 = D * D;
   int nc = 0;
   bool empty = false;
@@ -1635,22 +1640,16 @@ __global__ void k_gmax(int64_t ncell, const int32_t* __restrict__ cell_start,
   gmax[c] = m;
 }
 
-// Largest weight (clamped at 0) of the sites of each coarse cell: sites of
-// one warp that share a coarse cell (consecutive in grid order, so most do)
-// combine before one atomic.  Non-negative floating-point values order like
-// their bit patterns as unsigned integers.
+// Largest weight (clamped at 0) of the sites of each coarse cell, added by
+// every lane of a warp (ok: the lane has a site): lanes that share a coarse
+// cell (consecutive in grid order, so most do) combine before one atomic.
+// Non-negative floating-point values order like their bit patterns as
+// unsigned integers.
 template <typename T>
-__global__ void k_cmax(int64_t n, const V4<T>* __restrict__ sxp, GridParams<T> g, Coarse<T> co,
-                       T* cmax) {
-  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool ok = s < n;
-  int64_t key = -1;
-  T v = T(0);
-  if (ok) {
-    const V4<T> p = sxp[s];
-    key = coarse_key(p, g, co);
-    v = p.w > T(0) ? p.w : T(0);
-  }
+__device__ __forceinline__ void coarse_max_add(bool ok, const V4<T>& p, const GridParams<T>& g,
+                                               const Coarse<T>& co, T* cmax) {
+  const int64_t key = ok ? coarse_key(p, g, co) : -1;
+  const T v = ok && p.w > T(0) ? p.w : T(0);
   if constexpr (sizeof(T) == 4) {
     const unsigned grp = __match_any_sync(kFull, (unsigned long long)key);
     const unsigned m = __reduce_max_sync(grp, __float_as_uint(v));
@@ -1689,10 +1688,14 @@ __global__ void k_srad_init(int64_t n, const V4<T>* __restrict__ sxp, const doub
                             const T* __restrict__ rcell, int have_prev,
                             const T* __restrict__ rcell_acc, int have_acc,
                             const int32_t* __restrict__ perm, const T* __restrict__ hint,
-                            int use_hint, T* srad, T* srad_lo, T* soff, uint8_t* need) {
-  int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+                            int use_hint, T* srad, T* srad_lo, T* soff, uint8_t* need,
+                            GridParams<T> g, Coarse<T> co, T* cmax) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const V4<T> p = s < n ? sxp[s] : V4<T>{T(0), T(0), T(0), T(0)};
+  // the coarse cells' largest weights (every lane of the warp takes part)
+  if (cmax) coarse_max_add(s < n, p, g, co, cmax);
   if (s >= n) return;
-  const T ps = sxp[s].w;
+  const T ps = p.w;
   const T r = ps > T(0) ? sqrt(ps) : T(0);
   T ox = T(0), oy = T(0), oz = T(0);
   T prev = T(0);
@@ -2074,10 +2077,35 @@ int cells_eval(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* dom, 
     note_launch();
     k_gmax<T><<<blocks_for(ncell, 256), 256, 0, st>>>(ncell, ctx->cell_start, w.sxp, w.gmax);
   }
+  // largest weights near each site: coarse cells of f x f x f grid cells,
+  // f at least 4 and such that the neighbourhood reaches past
+  // 2 sqrt(psi_max) at the grid build's weights (the largest reach of a
+  // candidate); only where the workspace holds them
+  Coarse<T> co = {nullptr, 1, {1, 1, 1}};
+  int64_t ncc = 0;
+  if (w.cmax && w.cnb) {
+    int f = std::max(4, (int)ceil(2.0 * sqrt(fmax(w.grid_pmax, 0.0)) / (double)w.grid.cs + 0.5));
+    for (;; f++) {
+      ncc = 1;
+      for (int k = 0; k < 3; k++) {
+        co.dim[k] = (w.grid.dim[k] + f - 1) / f;
+        ncc *= co.dim[k];
+      }
+      if (ncc <= w.ccap) break;
+    }
+    co.f = f;
+    POT_CUDA(cudaMemsetAsync(w.cmax, 0, sizeof(T) * ncc, st));
+  }
   note_launch();
   k_srad_init<T><<<blocks_for(n, 256), 256, 0, st>>>(
       n, w.sxp, ctx->snu, w.rcell, w.have_rcell ? 1 : 0, w.rcell_acc, w.have_acc ? 1 : 0, ctx->perm,
-      w.hint, (w.use_hint && w.hint && w.hint_n == n) ? 1 : 0, w.srad, w.srad_lo, w.soff, ctx->need);
+      w.hint, (w.use_hint && w.hint && w.hint_n == n) ? 1 : 0, w.srad, w.srad_lo, w.soff, ctx->need,
+      w.grid, co, ncc > 0 ? w.cmax : nullptr);
+  if (ncc > 0) {
+    note_launch();
+    k_cnb<T><<<blocks_for(ncc, 256), 256, 0, st>>>(co, w.cmax, w.cnb);
+    co.nb = w.cnb;
+  }
   CellOut o;
   o.rcell = w.rcell;
   o.need = ctx->need;
@@ -2098,32 +2126,6 @@ int cells_eval(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* dom, 
   for (int k = 0; k < 3; k++) {
     box64.lo[k] = dom->lo[k];
     box64.hi[k] = dom->hi[k];
-  }
-  // largest weights near each site (coarse cells of f x f x f grid cells;
-  // f such that the neighbourhood reaches past 2 sqrt(psi_max) at the grid
-  // build's weights, the largest reach of a candidate) -- only where the
-  // workspace holds them
-  Coarse<T> co = {nullptr, 1, {1, 1, 1}};
-  if (w.cmax && w.cnb) {
-    int f = std::max(2, (int)ceil(2.0 * sqrt(fmax(w.grid_pmax, 0.0)) / (double)w.grid.cs + 0.5));
-    int64_t ncc = 0;
-    int cdim[3];
-    for (;; f++) {
-      ncc = 1;
-      for (int k = 0; k < 3; k++) {
-        cdim[k] = (w.grid.dim[k] + f - 1) / f;
-        ncc *= cdim[k];
-      }
-      if (ncc <= w.ccap) break;
-    }
-    co.f = f;
-    for (int k = 0; k < 3; k++) co.dim[k] = cdim[k];
-    POT_CUDA(cudaMemsetAsync(w.cmax, 0, sizeof(T) * ncc, st));
-    note_launch();
-    k_cmax<T><<<blocks_for(n, 256), 256, 0, st>>>(n, w.sxp, w.grid, co, w.cmax);
-    note_launch();
-    k_cnb<T><<<blocks_for(ncc, 256), 256, 0, st>>>(co, w.cmax, w.cnb);
-    co.nb = w.cnb;
   }
   // neighbour lists: kept across the evaluations of one grid order when the
   // caller asked for them (a Newton solve), invalidated by the grid build
