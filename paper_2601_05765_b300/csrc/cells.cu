@@ -230,7 +230,10 @@ __global__ void __launch_bounds__(256)
   // and their sites: each pass tests one site or opens the next cell, so
   // the lanes of a warp stay on the same short path instead of diverging on
   // nested loop bounds.  Candidates come out in ascending sorted index.
-  const int nxr = c1[0] - c0[0] + 1, nyr = c1[1] - c0[1] + 1, nzr = c1[2] - c0[2] + 1;
+  // A walk that builds a list opens whole rows instead (fixed y and z):
+  // the cells of a row that meet the ball of radius Dw are one run of x,
+  // and their sites one range of grid order, opened at once.
+  const int nxr = build ? 1 : c1[0] - c0[0] + 1, nyr = c1[1] - c0[1] + 1, nzr = c1[2] - c0[2] + 1;
   int ix = 0, iy = 0, iz = use_list ? nzr : 0;  // the next cell to open (none with a list)
   int t = 0, b = 0;            // the open cell's sites [t, b)
   while (!empty) {
@@ -267,6 +270,20 @@ __global__ void __launch_bounds__(256)
     T ey = fmax(T(0), fmax(ylo - p.y, p.y - (ylo + g.cs)));
     if (cy == 0 && p.y < ylo) ey = T(0);
     if (cy == g.dim[1] - 1 && p.y > ylo) ey = T(0);
+    if (build) {
+      // the row's cells within Dw of p: x within hw of p.x (widened by
+      // 1e-3 so that rounding never drops a cell the ball meets; the sites
+      // are tested against Dw one by one).  A list takes every site within
+      // its reach, with no bound on h: the weights change between
+      // evaluations.
+      const T e2 = ey * ey + ez * ez;
+      if (e2 >= Dw2) continue;
+      const T hw = sqrt(Dw2 - e2) * T(1.001);
+      const int row = (cz * g.dim[1] + cy) * g.dim[0];
+      t = cell_start[row + cell_coord(p.x - hw, g.lo[0], g.inv_cs, g.dim[0])];
+      b = cell_start[row + cell_coord(p.x + hw, g.lo[0], g.inv_cs, g.dim[0]) + 1];
+      continue;
+    }
     const T xlo = g.lo[0] + cx * g.cs;
     T ex = fmax(T(0), fmax(xlo - p.x, p.x - (xlo + g.cs)));
     if (cx == 0 && p.x < xlo) ex = T(0);
@@ -274,9 +291,7 @@ __global__ void __launch_bounds__(256)
     const T dl2 = ex * ex + ey * ey + ez * ez;
     if (dl2 >= Dw2) continue;
     const int key = (cz * g.dim[1] + cy) * g.dim[0] + cx;
-    // (a list takes every site within its reach: no bound on h there, the
-    // weights change between evaluations)
-    if (dl2 > T(0) && !build) {
+    if (dl2 > T(0)) {
       const T dl = sqrt(dl2);
       const T c = gmax[key] - ps;
       const T hmin = c >= T(0) ? T(0.5) * dl - c / (T(2) * dl) : T(0.5) * dl;
