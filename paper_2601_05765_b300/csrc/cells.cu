@@ -90,9 +90,6 @@ __device__ __forceinline__ void set_error(int32_t* err, int code, int64_t site) 
 // without that limit.  Cells of more than kSmallPlanes planes go to the
 // big-cell kernel.
 //
-// Grid cells are skipped with a lower bound of h over their sites: for
-// |p_i - p_j| >= delta and psi_j <= gmax,  h_ij >= delta/2 - (gmax - psi_i)/(2 delta)
-// (increasing in the distance when gmax >= psi_i), and h_ij >= delta/2 otherwise.
 // Per-site neighbour lists of the candidate pass (kVerletCap sorted indices
 // per site, their count and the reach they were built with; reach 0: none).
 template <typename T>
@@ -130,7 +127,7 @@ template <typename T>
 __global__ void __launch_bounds__(256)
     k_candidates(int64_t n, const V4<T>* __restrict__ sxp, const int32_t* __restrict__ cell_start,
                  GridParams<T> g, Box<T> box, const T* __restrict__ psi_max,
-                 const T* __restrict__ gmax, T* __restrict__ srad, const T* __restrict__ srad_lo,
+                 T* __restrict__ srad, const T* __restrict__ srad_lo,
                  const T* __restrict__ soff, uint8_t* __restrict__ need, int kmax,
                  int32_t* __restrict__ cand, int32_t* __restrict__ meta, int32_t* big_count,
                  int32_t* big_list, int32_t* err, VerletList<T> vl, Coarse<T> co) {
@@ -218,24 +215,20 @@ __global__ void __launch_bounds__(256)
   }
   const T Dw = build ? T(kVerletReach) * D : D;  // reach of the grid walk
   const T Dw2 = Dw * Dw;
-  int c0[3], c1[3];
-  const T pc[3] = {p.x, p.y, p.z};
-#pragma unroll
-  for (int k = 0; k < 3; k++) {
-    c0[k] = cell_coord(pc[k] - Dw, g.lo[k], g.inv_cs, g.dim[k]);
-    c1[k] = cell_coord(pc[k] + Dw, g.lo[k], g.inv_cs, g.dim[k]);
-  }
+  // the rows of grid cells (fixed y and z) the walk visits
+  const int cy0 = cell_coord(p.y - Dw, g.lo[1], g.inv_cs, g.dim[1]);
+  const int cz0 = cell_coord(p.z - Dw, g.lo[2], g.inv_cs, g.dim[2]);
+  const int nyr = cell_coord(p.y + Dw, g.lo[1], g.inv_cs, g.dim[1]) - cy0 + 1;
+  const int nzr = cell_coord(p.z + Dw, g.lo[2], g.inv_cs, g.dim[2]) - cz0 + 1;
   int nv = 0;
-  // One flat loop over the box of grid cells (x fastest, then y, then z)
-  // and their sites: each pass tests one site or opens the next cell, so
-  // the lanes of a warp stay on the same short path instead of diverging on
-  // nested loop bounds.  Candidates come out in ascending sorted index.
-  // A walk that builds a list opens whole rows instead (fixed y and z):
-  // the cells of a row that meet the ball of radius Dw are one run of x,
-  // and their sites one range of grid order, opened at once.
-  const int nxr = build ? 1 : c1[0] - c0[0] + 1, nyr = c1[1] - c0[1] + 1, nzr = c1[2] - c0[2] + 1;
-  int ix = 0, iy = 0, iz = use_list ? nzr : 0;  // the next cell to open (none with a list)
-  int t = 0, b = 0;            // the open cell's sites [t, b)
+  // One flat loop over the rows of grid cells within the reach (y, then z)
+  // and their sites: the cells of a row that meet the ball of radius Dw
+  // around p are one run of x, and their sites one range of grid order.
+  // Each pass tests one site or opens the next row, so the lanes of a warp
+  // stay on the same short path instead of diverging on nested loop
+  // bounds.  Candidates come out in ascending sorted index.
+  int iy = 0, iz = use_list ? nzr : 0;  // the next row to open (none with a list)
+  int t = 0, b = 0;                     // the open row's sites [t, b)
   while (!empty) {
     if (t < b) {
       if (t != s) {
@@ -254,14 +247,13 @@ __global__ void __launch_bounds__(256)
       continue;
     }
     if (iz >= nzr) break;
-    const int cx = c0[0] + ix, cy = c0[1] + iy, cz = c0[2] + iz;
-    if (++ix == nxr) {
-      ix = 0;
-      if (++iy == nyr) {
-        iy = 0;
-        iz++;
-      }
+    const int cy = cy0 + iy, cz = cz0 + iz;
+    if (++iy == nyr) {
+      iy = 0;
+      iz++;
     }
+    // distance from p to the row's cells in y and z (a cell on the grid's
+    // edge extends past it: sites outside the box are in the edge cells)
     const T zlo = g.lo[2] + cz * g.cs;
     T ez = fmax(T(0), fmax(zlo - p.z, p.z - (zlo + g.cs)));
     if (cz == 0 && p.z < zlo) ez = T(0);
@@ -270,35 +262,15 @@ __global__ void __launch_bounds__(256)
     T ey = fmax(T(0), fmax(ylo - p.y, p.y - (ylo + g.cs)));
     if (cy == 0 && p.y < ylo) ey = T(0);
     if (cy == g.dim[1] - 1 && p.y > ylo) ey = T(0);
-    if (build) {
-      // the row's cells within Dw of p: x within hw of p.x (widened by
-      // 1e-3 so that rounding never drops a cell the ball meets; the sites
-      // are tested against Dw one by one).  A list takes every site within
-      // its reach, with no bound on h: the weights change between
-      // evaluations.
-      const T e2 = ey * ey + ez * ez;
-      if (e2 >= Dw2) continue;
-      const T hw = sqrt(Dw2 - e2) * T(1.001);
-      const int row = (cz * g.dim[1] + cy) * g.dim[0];
-      t = cell_start[row + cell_coord(p.x - hw, g.lo[0], g.inv_cs, g.dim[0])];
-      b = cell_start[row + cell_coord(p.x + hw, g.lo[0], g.inv_cs, g.dim[0]) + 1];
-      continue;
-    }
-    const T xlo = g.lo[0] + cx * g.cs;
-    T ex = fmax(T(0), fmax(xlo - p.x, p.x - (xlo + g.cs)));
-    if (cx == 0 && p.x < xlo) ex = T(0);
-    if (cx == g.dim[0] - 1 && p.x > xlo) ex = T(0);
-    const T dl2 = ex * ex + ey * ey + ez * ez;
-    if (dl2 >= Dw2) continue;
-    const int key = (cz * g.dim[1] + cy) * g.dim[0] + cx;
-    if (dl2 > T(0)) {
-      const T dl = sqrt(dl2);
-      const T c = gmax[key] - ps;
-      const T hmin = c >= T(0) ? T(0.5) * dl - c / (T(2) * dl) : T(0.5) * dl;
-      if (hmin >= Re) continue;
-    }
-    t = cell_start[key];
-    b = cell_start[key + 1];
+    const T e2 = ey * ey + ez * ez;
+    if (e2 >= Dw2) continue;
+    // the row's cells within Dw of p: x within hw of p.x (widened by 1e-3
+    // so that rounding never drops a cell the ball meets; the sites are
+    // tested against Dw one by one)
+    const T hw = sqrt(Dw2 - e2) * T(1.001);
+    const int row = (cz * g.dim[1] + cy) * g.dim[0];
+    t = cell_start[row + cell_coord(p.x - hw, g.lo[0], g.inv_cs, g.dim[0])];
+    b = cell_start[row + cell_coord(p.x + hw, g.lo[0], g.inv_cs, g.dim[0]) + 1];
   }
   if (build) {
     // a walk cut short (empty cell) or a list over capacity is no list
@@ -2084,14 +2056,6 @@ int cells_eval(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* dom, 
     box.lo[k] = (T)dom->lo[k];
     box.hi[k] = (T)dom->hi[k];
   }
-  // the largest weight of each grid cell bounds h for the walk of a pass
-  // without neighbour lists; a walk that builds lists takes every site
-  // within its reach and does not need it
-  if (!(w.verlet && w.vlist)) {
-    const int64_t ncell = (int64_t)w.grid.dim[0] * w.grid.dim[1] * w.grid.dim[2];
-    note_launch();
-    k_gmax<T><<<blocks_for(ncell, 256), 256, 0, st>>>(ncell, ctx->cell_start, w.sxp, w.gmax);
-  }
   // largest weights near each site: coarse cells of f x f x f grid cells,
   // f at least 4 and such that the neighbourhood reaches past
   // 2 sqrt(psi_max) at the grid build's weights (the largest reach of a
@@ -2167,7 +2131,7 @@ int cells_eval(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* dom, 
     POT_CUDA(cudaMemsetAsync(ctx->need_count + 1, 0, 3 * sizeof(int32_t), st));
     note_launch();
     k_candidates<T><<<blocks_for(n, 256), 256, 0, st>>>(
-        n, w.sxp, ctx->cell_start, w.grid, box, w.psi_max, w.gmax, w.srad, w.srad_lo, w.soff,
+        n, w.sxp, ctx->cell_start, w.grid, box, w.psi_max, w.srad, w.srad_lo, w.soff,
         ctx->need, ctx->k_max, ctx->cand, ctx->meta, ctx->need_count + 1, ctx->big_list, ctx->err,
         vl, co);
     note_launch();
@@ -2225,8 +2189,7 @@ int cells_eval(pot_ctx* ctx, cudaStream_t st, int64_t n, const pot_domain* dom, 
 template <typename T>
 int repair_empty(pot_ctx* ctx, cudaStream_t st, int64_t n, int* repaired) {
   Work<T>& w = ctx->work<T>();
-  // the largest weight of each grid cell (an evaluation with neighbour
-  // lists does not form it)
+  // the largest weight of each grid cell (only the repair uses it)
   const int64_t ncell = (int64_t)w.grid.dim[0] * w.grid.dim[1] * w.grid.dim[2];
   note_launch();
   k_gmax<T><<<blocks_for(ncell, 256), 256, 0, st>>>(ncell, ctx->cell_start, w.sxp, w.gmax);
