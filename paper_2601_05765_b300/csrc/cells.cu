@@ -716,9 +716,18 @@ struct CellOut {
 // 1/20 of its ball could miss 1e-5 relative.  The Hessian diagonal carries
 // r times the solid-angle rounding, about 2e-6 r: a diagonal below 0.1 r
 // could miss 1e-5 relative.  Cells without a spherical part and with the
-// site inside are sums of positive pyramids: well conditioned.
+// site inside are sums of positive pyramids: well conditioned.  Where two
+// lines of a facet cross inside its disk at an angle whose sine is below
+// kIllSine, their vertex, computed by each of the two tasks from its own
+// line, moves by the FP32 rounding over that sine, and the facets' solid
+// angles no longer close up: measured against the FP64 oracle on 30k
+// random balls whose radii double across the box, such cells reach 2.8e-6
+// of their ball (sines near 4e-3; cells whose smallest sine is above 1.5e-2
+// stay below 9e-7, 7e-6 relative where they are not recomputed), so a cell
+// with such a vertex is also recomputed below a third of its ball.
 constexpr float kFixBallOverVol = 20.0f;
 constexpr float kFixDiagOverR = 0.1f;
+constexpr float kFixIllBallOverVol = 3.0f;
 
 // T: arithmetic of the cell, S: storage type of the outputs.  Returns true
 // when an FP32 cell is ill-conditioned (see above).
@@ -736,7 +745,7 @@ __device__ __forceinline__ bool write_cell(int64_t cell, const V4<T>& p, bool em
     // ball (or its ball misses the polytope), |K| = 0 exactly.  The formula
     // would leave a few ulp of 4 pi psi there, a volume error that grows
     // like psi^(3/2) in deep fluid.
-    if (a.nfac > 0 && a.arc == 0) {
+    if (a.nfac > 0 && (a.arc & kArcMask) == 0) {
       K = T(0);
     } else {
       K = ps * (T(4.0 * 3.14159265358979323846) * (inside ? T(1) : T(0)) - a.om);
@@ -762,7 +771,7 @@ __device__ __forceinline__ bool write_cell(int64_t cell, const V4<T>& p, bool em
     const T rq = sqrt(ps) + oa;
     if (full || a.nfac == 0)  // the whole ball (any cell inside it is within rq)
       rc = V > T(0) ? rq : T(0);
-    else if (a.arc > 0 && !qout && oa > T(0))
+    else if ((a.arc & kArcMask) > 0 && !qout && oa > T(0))
       rc = fmax(sqrt(a.rm2), rq);
     else
       rc = sqrt(a.rm2);
@@ -785,7 +794,8 @@ __device__ __forceinline__ bool write_cell(int64_t cell, const V4<T>& p, bool em
   if (sizeof(T) != 4 || empty || !(ps > T(0)) || (K == T(0) && inside)) return false;
   const T r = sqrt(ps);
   const T ball = T(4.0 * 3.14159265358979323846 / 3.0) * ps * r;
-  return V * T(kFixBallOverVol) < ball || dg < T(kFixDiagOverR) * r;
+  return V * T(kFixBallOverVol) < ball || dg < T(kFixDiagOverR) * r ||
+         (a.arc >= kIllFlag && V * T(kFixIllBallOverVol) < ball);
 }
 
 // Append an ill-conditioned FP32 cell to the FP64 list and put its full
@@ -972,6 +982,10 @@ __device__ __forceinline__ TaskOut<T> facet_task(const FacetFrame<T>& F, const L
   const T w = own_live ? sqrt(w2) : T(0);
   T t0 = -w, t1 = w;
   bool none = !own_live, dead = false, other_live = false;
+  // a line crossing g's chord inside the disk at a small angle: the vertex
+  // they make moves by the rounding of e over s (FP32 cells with one are
+  // recomputed in FP64 when small against their ball, see write_cell)
+  bool ill = false;
   // the chord end B = Q, where an arc starts if it survives; the nearest
   // chord start ahead of it: first g's own
   const T Bx = G.qx, By = G.qy;
@@ -996,12 +1010,16 @@ __device__ __forceinline__ TaskOut<T> facet_task(const FacetFrame<T>& F, const L
       if (K.a * G.a + K.b * G.b < T(0) || (K.gl & 255) < g) none = true;
       continue;
     }
-    if (s > T(0))
-      t1 = fmin(t1, fast_div(e, s));
-    else if (s < T(0))
-      t0 = fmax(t0, fast_div(e, s));
-    else if (e < T(0))
+    if (s != T(0)) {
+      const T te = fast_div(e, s);
+      if (s > T(0))
+        t1 = fmin(t1, te);
+      else
+        t0 = fmax(t0, te);
+      ill = ill || (fabs(s) < T(kIllSine) && fabs(te) < w);
+    } else if (e < T(0)) {
       none = true;
+    }
     const T scr = Bx * K.sy - By * K.sx, sdt = Bx * K.sx + By * K.sy;
     T ps_ = pangle(scr, sdt);
     // the arc start inside k's cut-off arc (from its start to its end):
@@ -1062,6 +1080,7 @@ __device__ __forceinline__ TaskOut<T> facet_task(const FacetFrame<T>& F, const L
       if (pangle(Bx * gy - By * gx, Bx * gx + By * gy) <= best) out.rm2 = fmax(out.rm2, F.far2);
     }
   }
+  if (ill) out.arc += kIllFlag;
   return out;
 }
 
@@ -1357,7 +1376,7 @@ __global__ void __launch_bounds__(CellCfg<T>::warps * 32, sizeof(T) == 4 ? 6 : 2
           S.fx[slot] = tk.mx;
           S.fy[slot] = tk.my;
           S.fr[slot] = tk.rm2;
-          S.farc[slot] = tk.arc > 0 ? 1 : 0;
+          S.farc[slot] = (uint8_t)(((tk.arc & kArcMask) > 0 ? 1 : 0) | (tk.arc >= kIllFlag ? 2 : 0));
         }
         __syncwarp();
         R = Rend;
@@ -1384,7 +1403,7 @@ __global__ void __launch_bounds__(CellCfg<T>::warps * 32, sizeof(T) == 4 ? 6 : 2
           fo.area = area;
           fo.omega = S.fo[t];
           fo.rm2 = S.fr[t];
-          fo.arc = S.farc[t] && area > T(0);
+          fo.arc = ((S.farc[t] & 1) && area > T(0) ? 1 : 0) + ((S.farc[t] & 2) ? kIllFlag : 0);
           T ux, uy, uz, vx, vy, vz;
           onb(P.x, P.y, P.z, ux, uy, uz, vx, vy, vz);
           const T mx = S.fx[t], my = S.fy[t];

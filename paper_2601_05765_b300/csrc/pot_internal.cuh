@@ -35,6 +35,11 @@ constexpr int kBigWarpsPerSm = 8;  // warps of the big-cell kernel per SM
 constexpr int kMaxLines = 24;      // edges of one facet polygon
 constexpr int kCellWarps = 4;      // warps per block of the cell kernel
 constexpr int kCellsPerWarp = 32;  // cells per warp task
+// facet arc counts carry, from bit 16 up, the count of ill-conditioned
+// vertices (two lines crossing inside a disk with sine below kIllSine)
+constexpr int kIllFlag = 1 << 16;
+constexpr int kArcMask = kIllFlag - 1;
+constexpr float kIllSine = 1.5e-2f;
 
 // meta word written by the candidate kernel
 constexpr int kMetaPlanes = 0x7ff;  // planes (walls + candidates) <= kMaxK + 6

@@ -71,6 +71,35 @@ def test_uniform_cloud(ctx, n):
     assert v.sum() <= 1.0 and np.all(v <= 4 / 3 * math.pi * r ** 3 * (1 + 1e-6))
 
 
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_graded_weights_cloud(ctx, dtype):
+    """Ball radii doubling across the box (r = U(0.7,1.0) R0 (1 + x)):
+    the largest weight near most sites is below the global one, so the
+    candidate search reaches only as far as the nearby weights allow.  Every
+    cell against the oracle: exact topology, volumes, gradient, Hessian."""
+    n = 30011
+    rng = np.random.default_rng(17)
+    pos = rng.uniform(0.0, 1.0, (n, 3))
+    r0 = (3.0 / (4.0 * math.pi * n)) ** (1.0 / 3.0)
+    r = rng.uniform(0.7, 1.0, n) * r0 * (1.0 + pos[:, 0])
+    ft = np.float32 if dtype == torch.float32 else np.float64
+    pos, psi = pos.astype(ft), (r * r).astype(ft)
+    nu = np.full(n, 0.5 / n)
+    out = run(ctx, pos, psi, nu, dtype)
+    ref = oracle_of(pos, psi)
+    rep = compare_cells(out, ref, psi, nu, **(TOL32 if dtype == torch.float32 else TOL64))
+    # cells emptied by a plane at h = -r within rounding are decided either
+    # way: every cell of zero GPU volume has an oracle volume within the
+    # volume floor (1e-9 of its ball in FP32, 1e-14 in FP64; the converse is
+    # part of compare_cells)
+    n_empty_ref = int(np.sum(ref["vol"] <= 0))
+    v = to_np(out["volumes"]).astype(np.float64)
+    ball = 4.0 / 3.0 * math.pi * psi.astype(np.float64) ** 1.5
+    floor = 1e-9 if dtype == torch.float32 else 1e-14
+    assert np.all(ref["vol"][v <= 0] <= floor * ball[v <= 0])
+    print(rep, out["stats"], "oracle empty", n_empty_ref)
+
+
 def test_uniform_cloud_fp64(ctx):
     sc = scenes.uniform_cloud(n=20000, seed=5)
     pos, psi = sc.pos.astype(np.float64), sc.psi.astype(np.float64)
