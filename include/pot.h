@@ -222,7 +222,10 @@ int pot_cell_diagnostics(pot_ctx* ctx, void* stream, int64_t n, float* center_of
  *   centroids  = (n,3) cell centroids c_i (pressure force, Sec. 5), optional,
  *   karea      = |K_i| free-surface area (Sec. 3.3), optional.
  * Inputs: pos (n,3) float, psi (n) float, targets (n) double or NULL.
- * FP32 geometry; grad in FP64.
+ * FP32 geometry; grad in FP64.  Cells whose FP32 rounding could exceed
+ * 1e-5 of their volume or of their Hessian diagonal (small against their
+ * ball, a small diagonal, or two facet lines crossing inside a disk at a
+ * sine below 1.5e-2) are recomputed from the same inputs in FP64.
  * Errors: POT_ERR_NEIGHBOUR_OVERFLOW, POT_ERR_COINCIDENT_SITES,
  *         POT_ERR_POLYGON_OVERFLOW (stats->error_site names a site),
  *         POT_ERR_CAPACITY (hess->nnz > hess->cap). */
