@@ -100,6 +100,25 @@ def test_graded_weights_cloud(ctx, dtype):
     print(rep, out["stats"], "oracle empty", n_empty_ref)
 
 
+def test_graded_weights_cloud_large_sampled():
+    """The same construction at 300,007 sites with radii growing 2.5-fold
+    across the box (r = U(0.7,1.0) R0 (1 + 1.5x)), FP32, 10k sampled cells
+    against the oracle (cells of up to about 100 cutting bisectors: a
+    context with k_max 246)."""
+    n = 300007
+    rng = np.random.default_rng(29)
+    pos = rng.uniform(0.0, 1.0, (n, 3))
+    r0 = (3.0 / (4.0 * math.pi * n)) ** (1.0 / 3.0)
+    r = rng.uniform(0.7, 1.0, n) * r0 * (1.0 + 1.5 * pos[:, 0])
+    pos, psi = pos.astype(np.float32), (r * r).astype(np.float32)
+    nu = np.full(n, 0.5 / n)
+    with pot.Context(n, 246, 0) as big:
+        out = run(big, pos, psi, nu)
+        q = np.random.default_rng(30).choice(n, 10000, replace=False)
+        rep = compare_cells(out, oracle_of(pos, psi, query=q), psi, nu, **TOL32)
+    print(rep, out["stats"])
+
+
 def test_uniform_cloud_fp64(ctx):
     sc = scenes.uniform_cloud(n=20000, seed=5)
     pos, psi = sc.pos.astype(np.float64), sc.psi.astype(np.float64)
