@@ -39,6 +39,13 @@
  * caps, box corner, cubic lattices (two regimes), Monte Carlo volume / free
  * surface / facet areas / centroid, finite differences of V in psi, symmetry
  * of the Hessian, sum of volumes <= box volume, brute force vs grid search.
+ *
+ * Domain: each polygon vertex is the intersection of two lines, so inputs
+ * whose bisector traces are parallel to within about 1e-8 without being
+ * identical (a cubic lattice whose float32 positions are off the exact
+ * lattice by rounding, or jittered by less than about 1e-4 of the spacing,
+ * with balls reaching the cube edges) are outside it: there it can return
+ * volumes above the lattice cube that contains the cell.
  */
 #include <math.h>
 #include <stdint.h>
