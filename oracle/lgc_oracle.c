@@ -43,7 +43,7 @@
  * Domain: each polygon vertex is the intersection of two lines, so inputs
  * whose bisector traces are parallel to within about 1e-8 without being
  * identical (a cubic lattice whose float32 positions are off the exact
- * lattice by rounding, or jittered by less than about 1e-4 of the spacing,
+ * lattice by rounding, or jittered by 1e-5 of the spacing or less,
  * with balls reaching the cube edges) are outside it: there it can return
  * volumes above the lattice cube that contains the cell.
  */
