@@ -953,6 +953,16 @@ __device__ __forceinline__ LineRec<T> line_rec(const V4<T>& P, const FacetFrame<
   return L;
 }
 
+// The crossing point of two crossing lines of a facet (the lower plane
+// index first: every task that needs it computes the same bits).
+template <typename T>
+__device__ __forceinline__ void meet(const LineRec<T>& L1, const LineRec<T>& L2, T& x, T& y) {
+  const T det = L1.a * L2.b - L2.a * L1.b;
+  const T id = T(1) / det;
+  x = (L1.c * L2.b - L2.c * L1.b) * id;
+  y = (L1.a * L2.c - L2.a * L1.c) * id;
+}
+
 // One task of facet f: its line `own` (rec[me]) among the facet's lines
 // rec[lo..hi], or the facet's whole disk when no line crosses it (own.gl <
 // 0).  Moments are in the facet frame about the disk centre; rm2 is the
@@ -981,6 +991,7 @@ __device__ __forceinline__ TaskOut<T> facet_task(const FacetFrame<T>& F, const L
   const T w2 = F.rho2 - G.c * G.c;
   const T w = own_live ? sqrt(w2) : T(0);
   T t0 = -w, t1 = w;
+  int k0 = -1, k1 = -1;  // the lines that cut the chord's start and end
   bool none = !own_live, dead = false, other_live = false;
   // a line crossing g's chord inside the disk at a small angle: the vertex
   // they make moves by the rounding of e over s (FP32 cells with one are
@@ -1012,10 +1023,15 @@ __device__ __forceinline__ TaskOut<T> facet_task(const FacetFrame<T>& F, const L
     }
     if (s != T(0)) {
       const T te = fast_div(e, s);
-      if (s > T(0))
-        t1 = fmin(t1, te);
-      else
-        t0 = fmax(t0, te);
+      if (s > T(0)) {
+        if (te < t1) {
+          t1 = te;
+          k1 = j;
+        }
+      } else if (te > t0) {
+        t0 = te;
+        k0 = j;
+      }
       ill = ill || (fabs(s) < T(kIllSine) && fabs(te) < w);
     } else if (e < T(0)) {
       none = true;
@@ -1045,9 +1061,17 @@ __device__ __forceinline__ TaskOut<T> facet_task(const FacetFrame<T>& F, const L
     return out;
   }
   if (none || !(t0 < t1)) return out;
-  // the segment of g on the boundary: triangle piece from the disk centre
-  const T Ax = Fx + t0 * dx, Ay = Fy + t0 * dy;
-  const T Cx = Fx + t1 * dx, Cy = Fy + t1 * dy;
+  // the segment of g on the boundary: triangle piece from the disk centre.
+  // A clipped end is the crossing of g with the line that cuts it, computed
+  // from the two lines in plane order, so that the task of that line gets
+  // the same vertex to the last bit (where two lines are nearly parallel,
+  // e / s moves the vertex far along them, and two tasks computing it
+  // each from its own line would leave a gap or an overlap between their
+  // pieces)
+  T Ax = Fx + t0 * dx, Ay = Fy + t0 * dy;
+  T Cx = Fx + t1 * dx, Cy = Fy + t1 * dy;
+  if (k0 >= 0) meet(rec[min(me, k0)], rec[max(me, k0)], Ax, Ay);
+  if (k1 >= 0) meet(rec[min(me, k1)], rec[max(me, k1)], Cx, Cy);
   {
     const T ah = fabs(F.h), h2 = F.h * F.h;
     const T cr = Ax * Cy - Ay * Cx;
