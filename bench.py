@@ -54,9 +54,9 @@ SMALL_SPACING = 0.032  # ~2000 sites with the splash recipe
 # profiles/k_cells_splash_536k_step30.md): FP32 FLOP executed (fadd + fmul +
 # 2 ffma of the instruction mix), warp instructions issued, and DRAM bytes
 # (cold caches: ncu flushes them before the launch).
-K_CELLS_FLOP_PER_CELL = 5480.4
-K_CELLS_WARP_INST_PER_CELL = 807.5
-K_CELLS_DRAM_BYTES_PER_CELL = 382.0
+K_CELLS_FLOP_PER_CELL = 5505.7
+K_CELLS_WARP_INST_PER_CELL = 823.8
+K_CELLS_DRAM_BYTES_PER_CELL = 383.1
 
 
 def parse():

@@ -119,6 +119,27 @@ def test_graded_weights_cloud_large_sampled():
     print(rep, out["stats"])
 
 
+@pytest.mark.parametrize("jitter", [1e-2, 3e-2])
+def test_nearly_regular_lattice(ctx, jitter):
+    """Sites of a 30^3 cubic lattice of spacing s jittered by U(-j, j) s and
+    balls of radius 0.9 s that contain the cube corners: every face facet
+    is bounded by nearly coincident lines (its side neighbour's trace and
+    its edge neighbours'), whose vertices the facet tasks must share.  Every
+    cell against the oracle in FP32."""
+    m = 30
+    s = 1.0 / m
+    rng = np.random.default_rng(7)
+    g = (np.stack(np.meshgrid(np.arange(m), np.arange(m), np.arange(m), indexing="ij"), -1)
+         .reshape(-1, 3) + 0.5) * s
+    pos = (g + rng.uniform(-jitter, jitter, g.shape) * s).astype(np.float32)
+    n = pos.shape[0]
+    psi = np.full(n, (0.9 * s) ** 2, np.float32)
+    nu = np.full(n, 0.9 * s ** 3)
+    out = run(ctx, pos, psi, nu)
+    rep = compare_cells(out, oracle_of(pos, psi), psi, nu, **TOL32)
+    print(rep)
+
+
 def test_uniform_cloud_fp64(ctx):
     sc = scenes.uniform_cloud(n=20000, seed=5)
     pos, psi = sc.pos.astype(np.float64), sc.psi.astype(np.float64)
